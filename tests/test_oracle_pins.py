@@ -1,0 +1,389 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each case states its derivation.  Notation: Algorithm 1 (lpa, lpaMove), Algorithm 2
+(hashtableAccumulate), Eq. 1 (modularity), Eq. 3 (update rule), Section 4 items
+(1)-(5) (asynchronous update, 20 iterations, tolerance, pruning, strict tie-break).
+"""
+import os
+import random
+from collections import defaultdict
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_11468_gb300 import graphgen as gg
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_form_traces.txt")
+
+
+def G(csr):
+    return oracle.Graph.of(csr)
+
+
+# --------------------------------------------------------------------------------------
+# closed-form traces (tests/golden/closed_form_traces.txt)
+
+def _load_traces():
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            case, mode, params, tol, mi, pl, dn, rule = [x.strip() for x in line.split("|")]
+            p = dict(kv.split("=") for kv in params.split(","))
+            p = {k: int(v) for k, v in p.items()}
+            if "x" in dn:
+                val, rep = dn.split("x")
+                dns = [int(val)] * int(rep)
+            else:
+                dns = [int(x) for x in dn.split(",")]
+            rows.append((case, mode, p, float(tol), int(mi), int(pl), dns, rule))
+    return rows
+
+
+def _graph_for(case, p):
+    if case.startswith("cliques"):
+        return gg.cliques(p["k"], p["s"])
+    if case.startswith("bridge"):
+        return gg.two_cliques_bridge(p["s"])
+    if case.startswith("knn"):
+        return gg.complete_bipartite(p["n"])
+    if case.startswith("star"):
+        return gg.star(p["n"])
+    raise KeyError(case)
+
+
+def _expected_labels(case, p, rule, n):
+    if rule == "clique-min":
+        return [(v // p["s"]) * p["s"] for v in range(n)]
+    if rule == "A=0,B=s":
+        s = p["s"]
+        return [0] * s + [s] * s
+    if rule == "all=0":
+        return [0] * n
+    return None
+
+
+@pytest.mark.parametrize("row", _load_traces(), ids=lambda r: f"{r[0]}-{r[1]}")
+def test_closed_form_trace(row):
+    """Derivations (unit weights, ties -> smallest label):
+
+    cliques (k disjoint K_s, ids contiguous): l=0 is a PL iteration; every vertex but
+      the clique minimum c0 sees s-1 labels of weight 1 and takes c0 (< own id); c0's
+      best is c0+1 > c0, so PL blocks it.  dN = k(s-1).  l=1: all neighbours hold c0,
+      nobody moves, dN/N = 0 < tau -> stop after 2 iterations.  Async (order 0..n-1)
+      reaches the same labels: vertex c0+t sees c0 with weight t >= 1.
+    bridge (K_s on [0,s), K_s on [s,2s), edge (s-1,s)), sync: l=0 (PL): A\\{0} -> 0,
+      vertex s sees {s-1, s+1..2s-1} tied -> s-1 (< s), B\\{s} -> s; dN = 2s-1.
+      l=1: vertex s sees label s with weight s-1 > 1 -> back to s; nobody else moves
+      (for s >= 4 a vertex of B sees s with weight s-2 > 1); dN = 1.  If 1/(2s) < tau
+      (s=12) the run stops here, else l=2 has dN = 0.
+    bridge, async: l=0: vertex s already sees s-1 relabelled 0 and ties to 0; B then
+      cascades to 0 (vertex s+t sees 0 with weight t+1); dN = (s-1) + 1 + (s-1)
+      = 2s-1; l=1 dN = 0.
+    K_{n,n}, no PL: A takes n, B takes 0, then they swap forever: dN = 2n each
+      iteration up to the cap (the community swap of Section 4.1).
+    K_{n,n}, PL every 4: l=0 blocks A (best n > a) and moves B to 0; l=1 moves A\\{0}
+      to 0 (n-1 moves; B sees min label 0 = own); l=2 dN = 0.
+    star K_{1,n}: l=0 blocks the centre, leaves move to 0; l=1 only the centre is
+      active and keeps 0.
+    """
+    case, mode, p, tol, mi, pl, dns, rule = row
+    g = G(_graph_for(case, p))
+    run = oracle.lpa_sync if mode == "sync" else oracle.lpa_async
+    r = run(g, tol, mi, pl)
+    assert r.dN == dns
+    assert r.iterations == len(dns)
+    assert r.converged == (len(dns) < mi)
+    exp = _expected_labels(case, p, rule, g.n)
+    if exp is not None:
+        assert r.labels.tolist() == exp
+    if rule == "oscillating":
+        n = p["n"]
+        # after an even number of sweeps the labels are back to the first-sweep state of
+        # the previous pair: A holds 0 and B holds n after 20 (even) sweeps
+        assert r.labels.tolist() == [0] * n + [n] * n
+
+
+def test_cliques_modularity_closed_form():
+    """k equal cliques as communities: sigma_c = Sigma_c = s(s-1), 2m = k s(s-1), so
+    Q = k (1/k - 1/k^2) = 1 - 1/k (Eq. 1)."""
+    k, s = 5, 6
+    g = G(gg.cliques(k, s))
+    r = oracle.lpa_sync(g)
+    assert oracle.modularity_exact(g, r.labels) == 1 - Fraction(1, k)
+    assert abs(oracle.modularity(g, r.labels) - (1 - 1 / k)) < 1e-15
+
+
+def test_bridge_modularity_closed_form():
+    """Two K_s plus a bridge split into the two cliques: sigma = s(s-1) per side,
+    Sigma = s(s-1)+1, 2m = 2s(s-1)+2: Q = 2[s(s-1)/(2m) - 1/4]."""
+    s = 6
+    g = G(gg.two_cliques_bridge(s))
+    r = oracle.lpa_sync(g)
+    two_m = 2 * s * (s - 1) + 2
+    assert oracle.modularity_exact(g, r.labels) == 2 * (Fraction(s * (s - 1), two_m) - Fraction(1, 4))
+    # the asynchronous run merges everything: single community, Q = 0
+    ra = oracle.lpa_async(g)
+    assert oracle.modularity_exact(g, ra.labels) == 0
+
+
+# --------------------------------------------------------------------------------------
+# hashtable (Section 4.2, Algorithm 2)
+
+def test_capacity_reading():
+    """p1 = nextPow2(D) - 1 with nextPow2 = smallest power of two strictly above D:
+    the smallest 2^k - 1 that is >= D."""
+    for d in range(1, 5000):
+        p1 = oracle.ht_capacity(d)
+        assert p1 == (1 << d.bit_length()) - 1
+        assert p1 >= d and (p1 + 1) & p1 == 0
+        assert p1 <= 2 * d - 1          # fits the 2*D_i reservation of Section 4.2
+
+
+def test_probe_sequence_matches_unreduced_recurrence():
+    """The oracle keeps i and delta reduced mod p1; Algorithm 2 lets them grow
+    (i <- i + delta, delta <- 2 delta + (k mod p2)).  Slots s_t = i_t mod p1 agree."""
+    rnd = random.Random(1)
+    for p1 in [1, 3, 7, 15, 31, 255, 4095, (1 << 20) - 1]:
+        p2 = 2 * p1 + 1
+        for _ in range(20):
+            k = rnd.randrange(0, 1 << 31)
+            i, d = k, 1
+            for t in range(40):
+                assert oracle.ht_probe_slot(p1, k, t) == i % p1
+                i = i + d
+                d = 2 * d + (k % p2)
+
+
+@pytest.mark.parametrize("k", range(1, 12))
+def test_hashtable_equals_sort_and_count(k):
+    """Per-vertex (key, sum) sets of the Algorithm 2 table equal a plain count, at
+    D = 2^k - 1, 2^k, 2^k + 1, for few and for all-distinct keys; the failed path is
+    never taken."""
+    rnd = random.Random(k)
+    for D in (2 ** k - 1, 2 ** k, 2 ** k + 1):
+        for universe in (3, max(1, D // 4), 1 << 30):
+            keys = [rnd.randrange(universe) for _ in range(D)]
+            vals = [float(rnd.randint(1, 8)) for _ in range(D)]
+            p1 = oracle.ht_capacity(D)
+            Hk, Hv, fb = oracle.ht_build(keys, vals, p1)
+            ref = defaultdict(float)
+            for kk, vv in zip(keys, vals):
+                ref[kk] += vv
+            got = {int(a): float(b) for a, b in zip(Hk, Hv) if a != -1}
+            assert got == dict(ref)
+            assert len([a for a in Hk if a != -1]) == len(ref)   # each key in one slot
+            assert fb <= D
+
+
+def test_hashtable_full_table_uses_fallback():
+    """A table filled to capacity (D = p1 distinct keys) still accepts every key: the
+    linear fallback after MAX_RETRIES probes finds the remaining empty slots."""
+    p1 = 15
+    keys = list(range(0, 15 * 17, 17))          # 15 distinct keys, all = 2 (mod 15)
+    Hk, Hv, fb = oracle.ht_build(keys, [1.0] * 15, p1)
+    assert sorted(int(a) for a in Hk) == sorted(keys)
+    assert fb >= 0
+
+
+# --------------------------------------------------------------------------------------
+# modularity (Eq. 1)
+
+def _dense(g):
+    n = g.n
+    W = np.zeros((n, n))
+    for i in range(n):
+        for e in range(g.off[i], g.off[i + 1]):
+            W[i, g.idx[e]] += 1.0 if g.w is None else g.w[e]
+    return W
+
+
+def _newman_pairwise(W, C):
+    """(1/2m) sum_{i,j} [A_ij - K_i K_j / 2m] delta(C_i, C_j) over all ordered pairs."""
+    K = W.sum(1)
+    two_m = W.sum()
+    q = Fraction(0)
+    for i in range(len(C)):
+        for j in range(len(C)):
+            if C[i] == C[j]:
+                q += Fraction(int(W[i, j])) - Fraction(int(K[i]) * int(K[j]), int(two_m))
+    return q / int(two_m)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_modularity_pairwise_bruteforce(seed):
+    """Community form of Eq. 1 (oracle) = Newman's pairwise sum, exactly, N <= 10."""
+    rnd = random.Random(seed)
+    n = rnd.randint(2, 10)
+    g = G(gg.random_small(n, 0.5, seed, self_loops=(seed % 3 == 0)))
+    if g.m == 0:
+        return
+    W = _dense(g)
+    for _ in range(5):
+        C = [rnd.randrange(n) for _ in range(n)]
+        q = _newman_pairwise(W, C)
+        assert oracle.modularity_exact(g, C) == q
+        assert abs(oracle.modularity(g, C) - float(q)) < 1e-14
+        assert -0.5 <= float(q) <= 1.0
+
+
+def test_modularity_special_partitions():
+    """Single community: Q = 0.  Singletons (no self-loops): Q = -sum_i (K_i/2m)^2."""
+    g = G(gg.random_small(40, 0.2, 7))
+    K = _dense(g).sum(1)
+    two_m = K.sum()
+    assert oracle.modularity_exact(g, [0] * g.n) == 0
+    sing = oracle.modularity_exact(g, list(range(g.n)))
+    assert sing == -sum(Fraction(int(k), int(two_m)) ** 2 for k in K)
+
+
+# --------------------------------------------------------------------------------------
+# dense-matrix restatement of the synchronous and asynchronous sweeps (N <= 64)
+
+def _best_dense(W, C, i):
+    """Eq. 3 on a dense weight matrix: argmax over labels of non-self neighbours."""
+    cand = {}
+    for j in np.nonzero(W[i])[0]:
+        if j == i:
+            continue
+        cand[C[j]] = cand.get(C[j], 0.0) + W[i, j]
+    if not cand:
+        return None
+    mx = max(cand.values())
+    return min(c for c, v in cand.items() if v == mx)
+
+
+def _dense_sync(W, tol, max_iters, pl_period):
+    n = W.shape[0]
+    C = list(range(n))
+    act = [True] * n
+    dns, labels_per_iter = [], []
+    for l in range(max_iters):
+        pl = pl_period > 0 and l % pl_period == 0
+        Cn = list(C)
+        an = [False] * n
+        ch = 0
+        for i in range(n):
+            if not act[i]:
+                continue
+            c = _best_dense(W, C, i)
+            if c is not None and c != C[i] and (not pl or c < C[i]):
+                Cn[i] = c
+                ch += 1
+                for j in np.nonzero(W[i])[0]:
+                    an[j] = True
+        C, act = Cn, an
+        dns.append(ch)
+        labels_per_iter.append(list(C))
+        if not pl and ch / n < tol:
+            break
+    return dns, labels_per_iter
+
+
+def _dense_async(W, tol, max_iters, pl_period):
+    n = W.shape[0]
+    C = list(range(n))
+    act = [True] * n
+    dns = []
+    for l in range(max_iters):
+        pl = pl_period > 0 and l % pl_period == 0
+        ch = 0
+        for i in range(n):
+            if not act[i]:
+                continue
+            act[i] = False
+            c = _best_dense(W, C, i)
+            if c is not None and c != C[i] and (not pl or c < C[i]):
+                C[i] = c
+                ch += 1
+                for j in np.nonzero(W[i])[0]:
+                    act[j] = True
+        dns.append(ch)
+        if not pl and ch / n < tol:
+            break
+    return dns, C
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_sync_matches_dense_restatement_every_iteration(seed):
+    rnd = random.Random(100 + seed)
+    n = rnd.randint(5, 64)
+    p = rnd.choice([0.05, 0.1, 0.2, 0.4])
+    g = G(gg.random_small(n, p, seed, wmax=rnd.choice([1, 3, 8]), self_loops=(seed % 4 == 0)))
+    W = _dense(g)
+    tol, mi, pl = rnd.choice([0.0, 0.05, 0.2]), rnd.choice([5, 20]), rnd.choice([0, 2, 4])
+    dns, per_iter = _dense_sync(W, tol, mi, pl)
+    r = oracle.lpa_sync(g, tol, mi, pl)
+    assert r.dN == dns
+    assert r.labels.tolist() == per_iter[-1]
+    for t in range(1, len(per_iter) + 1):       # labels after every iteration
+        rt = oracle.lpa_sync(g, tol, t, pl)
+        assert rt.labels.tolist() == per_iter[t - 1]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_async_matches_dense_restatement(seed):
+    rnd = random.Random(200 + seed)
+    n = rnd.randint(5, 64)
+    g = G(gg.random_small(n, rnd.choice([0.05, 0.15, 0.3]), 50 + seed, wmax=rnd.choice([1, 8])))
+    W = _dense(g)
+    dns, C = _dense_async(W, 0.05, 20, 4)
+    r = oracle.lpa_async(g, 0.05, 20, 4)
+    assert r.dN == dns
+    assert r.labels.tolist() == C
+
+
+def test_resume_equals_single_run():
+    """State after k iterations (labels, active set, next iteration) resumes to the same
+    result as an uninterrupted run (the whole state of Algorithm 1's loop)."""
+    g = G(gg.sbm(600, 30, 8, 2, seed=3, weights="int8"))
+    full = oracle.lpa_sync(g, 0.0, 12, 4)
+    part = oracle.lpa_sync(g, 0.0, 5, 4)
+    rest = oracle.lpa_sync(g, 0.0, 12, 4, labels=part.labels, active=part.active, start_iter=part.iterations)
+    assert rest.labels.tolist() == full.labels.tolist()
+    assert part.dN + rest.dN == full.dN
+
+
+def test_violations_bruteforce():
+    rnd = random.Random(5)
+    for seed in range(6):
+        g = G(gg.random_small(30, 0.2, seed))
+        W = _dense(g)
+        C = [rnd.randrange(5) for _ in range(g.n)]
+        bad = 0
+        for i in range(g.n):
+            cand = defaultdict(float)
+            for j in np.nonzero(W[i])[0]:
+                if j != i:
+                    cand[C[j]] += W[i, j]
+            if cand and cand.get(C[i], 0.0) < max(cand.values()):
+                bad += 1
+        assert oracle.violations(g, C) == bad
+
+
+def test_label_weights_definition():
+    g = G(gg.random_small(20, 0.5, 9, self_loops=True))
+    C = [v % 4 for v in range(g.n)]
+    W = _dense(g)
+    for i in range(g.n):
+        ref = defaultdict(float)
+        for j in np.nonzero(W[i])[0]:
+            if j != i:
+                ref[C[j]] += W[i, j]
+        assert oracle.label_weights(g, C, i) == dict(ref)
+
+
+def test_empty_and_isolated():
+    """n = 0 runs no iteration; isolated and self-loop-only vertices keep their label
+    and never count as moved."""
+    g0 = oracle.Graph(np.zeros(1, np.int64), np.zeros(0, np.int32), None)
+    r0 = oracle.lpa_sync(g0)
+    assert r0.iterations == 0 and r0.dN == []
+    g = G(gg.from_edges(4, [(0, 0), (1, 2)]))      # 0: self-loop only, 3: isolated
+    r = oracle.lpa_sync(g, 0.05, 20, 4)
+    assert r.labels.tolist() == [0, 1, 1, 3]
+    assert r.dN == [1, 0]
