@@ -180,6 +180,47 @@ def test_hashtable_equals_sort_and_count(k):
             assert fb <= D
 
 
+def _alg2_unreduced(keys, vals, p1, max_retries=oracle.MAX_RETRIES):
+    """Algorithm 2, single-threaded, with Python's unbounded integers: i <- k, delta <- 1;
+    s = i mod p1; take s if empty or holding k; else i <- i + delta,
+    delta <- 2 delta + (k mod p2).  After max_retries probes: linear scan from s."""
+    p2 = 2 * p1 + 1
+    Hk = [-1] * p1
+    Hv = [0.0] * p1
+    for k, v in zip(keys, vals):
+        i, d = k, 1
+        s = None
+        for _ in range(max_retries):
+            s = i % p1
+            if Hk[s] in (k, -1):
+                break
+            i, d = i + d, 2 * d + (k % p2)
+        else:
+            for u in range(1, p1 + 1):
+                q = (s + u) % p1
+                if Hk[q] in (k, -1):
+                    s = q
+                    break
+        Hk[s] = k
+        Hv[s] += v
+    return Hk, Hv
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_hashtable_layout_matches_unreduced_algorithm2(seed):
+    """Same insertion order -> the same slot for every key (pins the probe recurrence
+    and the fallback of the oracle's table, not only its contents)."""
+    rnd = random.Random(300 + seed)
+    for D in (1, 2, 3, 7, 8, 31, 32, 33, 255, 1000):
+        keys = [rnd.randrange(1 << 31) if seed % 2 else rnd.randrange(max(1, D)) for _ in range(D)]
+        vals = [float(rnd.randint(1, 8)) for _ in range(D)]
+        p1 = oracle.ht_capacity(D)
+        Hk, Hv, _ = oracle.ht_build(keys, vals, p1)
+        rk, rv = _alg2_unreduced(keys, vals, p1)
+        assert Hk.tolist() == rk
+        assert Hv.tolist() == rv
+
+
 def test_hashtable_full_table_uses_fallback():
     """A table filled to capacity (D = p1 distinct keys) still accepts every key: the
     linear fallback after MAX_RETRIES probes finds the remaining empty slots."""
