@@ -1,0 +1,199 @@
+/*
+ * lpa.h -- C ABI of the GB300 (sm_103a) label-propagation library liblpa.so.
+ *
+ * The library implements the community-detection method of "nu-LPA: Fast GPU-based
+ * Label Propagation Algorithm (LPA) for Community Detection" (Sahu, arXiv 2411.11468):
+ * every unprocessed vertex i takes the label with the largest total edge weight among
+ * its neighbours' labels (Eq. 3), ties going to the smallest label (Section 4,
+ * item 5); Pick-Less (Section 4.1) restricts moves to smaller labels every
+ * pl_period-th iteration; a vertex that changes label marks its neighbours for the
+ * next sweep (Section 4, item 4); the loop stops when the changed fraction falls
+ * below the tolerance on a non-Pick-Less iteration or after max_iters sweeps
+ * (Algorithm 1).  Neighbour-label weights are accumulated in per-vertex open-addressing
+ * hashtables with the hybrid quadratic-double probe of Algorithm 2 (Section 4.2).
+ *
+ * Input graphs are undirected CSR graphs as in the paper's Preliminaries: every
+ * edge {i, j} is stored in row i and in row j with the same weight w_ij >= 0.
+ * Vertex ids and labels are int32; weights and label sums are float32 (the
+ * paper's Configuration paragraph).  Modularity (Eq. 1) is accumulated in float64.
+ *
+ * Conventions for every call:
+ *  - Status: every call returns LPA_OK (0) or a negative LPA_E* code; lpa_strerror()
+ *    names the code and lpa_last_error() returns a message for the calling thread's
+ *    last failure.  No call traps or asserts on the device.
+ *  - Ownership: the library copies its inputs into device memory it owns; callers
+ *    keep their arrays.  Handles are freed with the matching *_destroy call.
+ *  - Streams: `cuda_stream` is a cudaStream_t (NULL = the legacy default stream).
+ *    All device work of a handle is ordered on that stream.  Calls that return
+ *    host-visible results synchronise that stream before returning.
+ *  - Threads: one handle must not be used by two threads at once; distinct handles
+ *    are independent.
+ *  - Pointers marked "host or device" are host pointers unless the call's flags say
+ *    LPA_DEVICE_PTRS (or its on_device argument is non-zero), in which case they are
+ *    device pointers valid on the current CUDA device.
+ */
+#ifndef LPA_H
+#define LPA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define LPA_OK        0
+#define LPA_EINVAL   (-1)   /* invalid argument or invalid graph                      */
+#define LPA_ENOMEM   (-2)   /* device or pinned host allocation failed                */
+#define LPA_ECUDA    (-3)   /* a CUDA runtime call or kernel launch failed            */
+#define LPA_ETIMEOUT (-4)   /* a bounded device wait gave up (status word set)        */
+#define LPA_ESTATE   (-5)   /* call not valid in the handle's current state           */
+
+/* ---- lpa_run modes (Section 4 item 1 is the asynchronous mode) -------------------- */
+#define LPA_SYNC    0       /* deterministic: every sweep reads the previous sweep's labels */
+#define LPA_ASYNC   1       /* the paper's mode: labels updated in place while others read */
+#define LPA_RESUME  16      /* or-ed into mode: continue from the handle's current state    */
+
+/* ---- lpa_create / lpa_batch_create flags ------------------------------------------ */
+#define LPA_OFFSETS_I32      0   /* offsets are int32_t[n+1]                           */
+#define LPA_OFFSETS_I64      1   /* offsets are int64_t[n+1]                           */
+#define LPA_HOST_PTRS        0   /* input arrays are host pointers                     */
+#define LPA_DEVICE_PTRS      2   /* input arrays are device pointers                   */
+#define LPA_CHECK_SYMMETRIC  4   /* also verify that the graph is undirected           */
+
+/* ---- statistics ------------------------------------------------------------------- */
+#define LPA_STATS_MAX_ITERS 64   /* per-iteration arrays hold the first 64 iterations  */
+#define LPA_NUM_KERNELS     12   /* kernel slots of the per-kernel arrays              */
+
+/* Kernel slots, in launch order within one sweep. */
+#define LPA_K_THREAD      0   /* thread per vertex, private table (lowest degrees)     */
+#define LPA_K_GROUP       1   /* small lane group per vertex, shared table in smem     */
+#define LPA_K_WARP        2   /* warp per vertex, table in smem                        */
+#define LPA_K_CTA         3   /* thread block per vertex, table in smem                */
+#define LPA_K_CTA_LARGE   4   /* thread block per vertex, large smem table             */
+#define LPA_K_HUB_BEGIN   5   /* hubs: take the processed flags                        */
+#define LPA_K_HUB_ACC     6   /* hubs: several blocks accumulate into an HBM table     */
+#define LPA_K_HUB_ARGMAX  7   /* hubs: max-reduce and clear the HBM table              */
+#define LPA_K_HUB_MOVE    8   /* hubs: move and mark neighbours                        */
+#define LPA_K_APPLY       9   /* synchronous mode: publish the sweep's new labels      */
+#define LPA_K_OTHER      10   /* initialisation and bookkeeping                        */
+
+typedef struct lpa_stats {
+    /* input */
+    int32_t time_kernels;     /* non-zero: time every kernel with CUDA events          */
+    /* output */
+    int32_t iterations;       /* sweeps run (absolute index of the next sweep)         */
+    int32_t converged;        /* 1 when the tolerance test ended the run               */
+    int32_t first_iter;       /* absolute index of the first sweep of this call        */
+    int64_t changed[LPA_STATS_MAX_ITERS];   /* dN: vertices that changed label        */
+    int64_t active[LPA_STATS_MAX_ITERS];    /* vertices processed (unprocessed at start) */
+    int64_t edges[LPA_STATS_MAX_ITERS];     /* CSR entries scanned                    */
+    int64_t marks[LPA_STATS_MAX_ITERS];     /* CSR entries of moved vertices (marks)  */
+    float   iter_ms[LPA_STATS_MAX_ITERS];   /* device time of each sweep              */
+    float   total_ms;                       /* device time of the whole call          */
+    int32_t launches;                       /* kernels launched by this call          */
+    int64_t probe_fallbacks;                /* linear-probe fallbacks (Algorithm 2 budget spent) */
+    /* per kernel slot (filled when time_kernels != 0), indexed [iteration][slot]
+       for the first LPA_STATS_MAX_ITERS iterations of this call                    */
+    float   kernel_ms[LPA_STATS_MAX_ITERS][LPA_NUM_KERNELS];
+    int64_t kernel_edges[LPA_STATS_MAX_ITERS][LPA_NUM_KERNELS];
+    int64_t kernel_active[LPA_STATS_MAX_ITERS][LPA_NUM_KERNELS];
+} lpa_stats;
+
+/* Degree-bucket configuration.  A vertex of degree D is handled by the first bucket
+ * whose limit is >= D; vertices above cta_large_max are hubs.  Limits must increase
+ * and each smem table must fit: group_max <= 255, warp_max <= 2047,
+ * cta_max <= 8191, cta_large_max <= 16383. */
+typedef struct lpa_tuning {
+    int32_t thread_max;       /* thread per vertex for 1 <= D <= thread_max (<= 15)      */
+    int32_t group_max;        /* group of group_lanes lanes per vertex                   */
+    int32_t group_lanes;      /* 2, 4, 8 or 16                                           */
+    int32_t warp_max;         /* warp per vertex                                         */
+    int32_t cta_max;          /* block of cta_threads per vertex, smem table             */
+    int32_t cta_threads;      /* 128, 256, 512 or 1024                                   */
+    int32_t cta_large_max;    /* block of cta_large_threads per vertex, large smem table */
+    int32_t cta_large_threads;
+    int32_t hub_chunk;        /* CSR entries per block in the hub accumulate kernel     */
+    int32_t hub_table_shift;  /* hub table capacity = nextPow2(D << shift) - 1 (0 = paper) */
+    int32_t reserved[6];
+} lpa_tuning;
+
+typedef struct lpa_graph lpa_graph;
+
+/* Copies an undirected CSR graph to the device and prepares the degree buckets.
+ *  offsets   host or device; int32_t or int64_t [n_vertices + 1] (flags), offsets[0] = 0,
+ *            non-decreasing, offsets[n_vertices] = n_entries.
+ *  indices   host or device; int32_t [n_entries], each in [0, n_vertices).  Self-loops are
+ *            allowed and skipped by the sweep (Algorithm 1 skips j = i).
+ *  weights   host or device; float [n_entries], finite and >= 0; NULL = unit weights.
+ *  n_vertices in [0, 2^31 - 1); n_entries >= 0.
+ *  flags     LPA_OFFSETS_I32 / LPA_OFFSETS_I64, LPA_HOST_PTRS / LPA_DEVICE_PTRS,
+ *            optionally LPA_CHECK_SYMMETRIC.
+ *  cuda_stream the stream all work of the handle is ordered on.
+ *  out       receives the handle; NULL on failure.
+ * Errors: LPA_EINVAL for a violated precondition (checked on the device), LPA_ENOMEM,
+ * LPA_ECUDA.  Labels start as vertex ids (Algorithm 1). */
+int lpa_create(const void *offsets, const int32_t *indices, const float *weights,
+               int64_t n_vertices, int64_t n_entries, int flags, void *cuda_stream,
+               lpa_graph **out);
+
+/* Runs label propagation (Algorithm 1).
+ *  tolerance  stop after a non-Pick-Less sweep l with dN / n < tolerance (double compare).
+ *  max_iters  absolute cap on the sweep index (the paper uses 20); sweeps run while l < max_iters.
+ *  pl_period  Pick-Less on sweeps with l % pl_period == 0 (the paper: 4); 0 disables it.
+ *  mode       LPA_SYNC or LPA_ASYNC, optionally | LPA_RESUME.  Without LPA_RESUME the
+ *             labels restart at vertex ids, every vertex is unprocessed and l starts at 0;
+ *             with it the run continues from the handle's labels, flags and next l.
+ *  stats      optional (NULL allowed); see lpa_stats.
+ * LPA_SYNC is deterministic: with integer-valued weights and weighted degrees below 2^24
+ * every label sum is exact and the labels equal the synchronous definition bit for bit.
+ * LPA_ASYNC lets sweeps read labels written in the same sweep (nondeterministic). */
+int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mode,
+            lpa_stats *stats);
+
+/* Copies the n = n_vertices labels to `out` (host or device per out_on_device). */
+int lpa_labels(const lpa_graph *g, int32_t *out, int64_t n, int out_on_device);
+
+/* Modularity of the current labels, Eq. 1 in its community form
+ * Q = sum_c [sigma_c / 2m - (Sigma_c / 2m)^2], accumulated in float64 on the device.
+ * A graph with no edge weight (2m = 0) has Q = 0. */
+int lpa_modularity(const lpa_graph *g, double *q);
+
+/* Sets the labels (each in [0, n)), marks every vertex unprocessed and resets the
+ * next sweep index to 0 (host or device per on_device). */
+int lpa_set_labels(lpa_graph *g, const int32_t *labels, int64_t n, int on_device);
+
+/* Checkpoint of the loop state of Algorithm 1: labels [n], unprocessed flags [n]
+ * (0/1) and the next sweep index.  Either array may be NULL. */
+int lpa_get_state(const lpa_graph *g, int32_t *labels, uint8_t *unprocessed, int32_t *next_iter,
+                  int64_t n, int on_device);
+int lpa_set_state(lpa_graph *g, const int32_t *labels, const uint8_t *unprocessed, int32_t next_iter,
+                  int64_t n, int on_device);
+
+/* Replaces the stream of the handle (the caller orders any pending work). */
+int lpa_set_stream(lpa_graph *g, void *cuda_stream);
+
+/* Degree-bucket configuration of a handle (defaults set by lpa_create). */
+int lpa_get_tuning(const lpa_graph *g, lpa_tuning *t);
+int lpa_set_tuning(lpa_graph *g, const lpa_tuning *t);
+
+/* Sizes of a handle. */
+int64_t lpa_num_vertices(const lpa_graph *g);
+int64_t lpa_num_entries(const lpa_graph *g);
+/* Device bytes held by a handle. */
+int64_t lpa_device_bytes(const lpa_graph *g);
+
+void lpa_destroy(lpa_graph *g);
+
+const char *lpa_strerror(int status);
+const char *lpa_last_error(void);
+const char *lpa_kernel_name(int slot);
+
+/* sizeof(lpa_stats) for which = 0, sizeof(lpa_tuning) for which = 1 (binding checks). */
+size_t lpa_struct_size(int which);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPA_H */

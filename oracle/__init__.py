@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import ctypes as ct
 import os
+import platform
 import subprocess
 from dataclasses import dataclass
 from fractions import Fraction
@@ -25,7 +26,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lpa_oracle.c")
-_LIB = os.path.join(_HERE, "liblpa_oracle.so")
+_LIB = os.path.join(_HERE, f"liblpa_oracle.{platform.machine()}.so")   # per host architecture
 
 MAX_RETRIES = 32      # hashtable probe budget before the linear fallback (reading of Algorithm 2)
 
@@ -55,6 +56,8 @@ def lib():
         L.orc_lpa_async.restype = ct.c_int
         L.orc_sweep_range.argtypes = [i64, P, P, P, ct.c_int, i64, i64, P, P]
         L.orc_sweep_range.restype = i64
+        L.orc_sweep_window.argtypes = [i64, i64, P, P, P, P, ct.c_int, P]
+        L.orc_sweep_window.restype = i64
         L.orc_label_weights.argtypes = [i64, P, P, P, P, P, P, P]
         L.orc_label_weights.restype = i64
         L.orc_ht_capacity.argtypes = [i64]
@@ -143,6 +146,20 @@ def sweep_range(g: Graph, labels, v0: int, v1: int, pl: bool = False):
     C = _np(labels, np.int32)
     out = np.empty(v1 - v0, dtype=np.int32)
     e = lib().orc_sweep_range(g.n, _p(g.off), _p(g.idx), _p(g.w), int(pl), int(v0), int(v1), _p(C), _p(out))
+    if e < 0:
+        raise MemoryError("oracle allocation failed")
+    return out, int(e)
+
+
+def sweep_window(v0: int, v1: int, off_w, idx_w, w_w, labels, pl: bool = False):
+    """sweep_range on a window of rows: off_w = offsets[v0:v1+1] (absolute), idx_w / w_w =
+    the entries offsets[v0]:offsets[v1]; labels = all n labels.  Returns (new labels, entries)."""
+    ow = _np(off_w, np.int64)
+    iw = _np(idx_w, np.int32)
+    ww = _np(w_w, np.float32)
+    C = _np(labels, np.int32)
+    out = np.empty(v1 - v0, dtype=np.int32)
+    e = lib().orc_sweep_window(int(v0), int(v1), _p(ow), _p(iw), _p(ww), _p(C), int(pl), _p(out))
     if e < 0:
         raise MemoryError("oracle allocation failed")
     return out, int(e)

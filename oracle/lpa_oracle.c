@@ -220,25 +220,57 @@ int orc_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, const float
 }
 
 /* One synchronous sweep over vertices [v0, v1) only, with all of them active and the
- * given frozen labels: the per-vertex step of Algorithm 1 (lpaMove) on a bounded
- * sample.  Writes the new labels of [v0, v1) to out (length v1 - v0) and returns the
- * number of CSR entries scanned (for rate measurements), or -1 on allocation failure. */
+ * given frozen labels C (all n labels): the per-vertex step of Algorithm 1 (lpaMove) on a
+ * bounded sample.  The rows come as a window: off_w[k] - off_w[0] is where row v0+k starts
+ * in idx_w / w_w (length v1 - v0 + 1).  Writes the new labels of [v0, v1) to out and
+ * returns the number of CSR entries scanned, or -1 on allocation failure. */
+int64_t orc_sweep_window(int64_t v0, int64_t v1, const int64_t *off_w, const int32_t *idx_w,
+                         const float *w_w, const int32_t *C, int pl, int32_t *out)
+{
+    const int64_t nv = v1 - v0, base = off_w[0];
+    int64_t dmax = 0;
+    for (int64_t k = 0; k < nv; ++k)
+        if (off_w[k + 1] - off_w[k] > dmax) dmax = off_w[k + 1] - off_w[k];
+    /* a one-row CSR per vertex: offsets {0, D}, rows taken from the window */
+    orc_work wk;
+    if (orc_work_alloc(&wk, dmax) != 0) return -1;
+    for (int64_t k = 0; k < nv; ++k) {
+        const int64_t i = v0 + k;
+        const int64_t b = off_w[k] - base, d = off_w[k + 1] - off_w[k];
+        int64_t cnt = 0;
+        for (int64_t e = 0; e < d; ++e) {
+            const int32_t j = idx_w[b + e];
+            if (j == i) continue;
+            wk.scratch[cnt].label = C[j];
+            wk.scratch[cnt].pos = e;
+            wk.scratch[cnt].w = w_w ? w_w[b + e] : 1.0f;
+            ++cnt;
+        }
+        qsort(wk.scratch, (size_t)cnt, sizeof(orc_item), orc_item_cmp);
+        int32_t best = -1;
+        float bw = 0.0f;
+        for (int64_t q = 0; q < cnt;) {             /* sort-and-count, labels ascending */
+            int32_t lab = wk.scratch[q].label;
+            float sum = 0.0f;
+            for (; q < cnt && wk.scratch[q].label == lab; ++q) sum += wk.scratch[q].w;
+            if (best < 0 || sum > bw) {
+                best = lab;
+                bw = sum;
+            }
+        }
+        const int32_t cur = C[i];
+        out[k] = (best >= 0 && best != cur && (!pl || best < cur)) ? best : cur;
+    }
+    orc_work_free(&wk);
+    return off_w[nv] - base;
+}
+
+/* Same on a whole CSR (offsets absolute). */
 int64_t orc_sweep_range(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                         int pl, int64_t v0, int64_t v1, const int32_t *C, int32_t *out)
 {
     (void)n;
-    int64_t dmax = 0;
-    for (int64_t i = v0; i < v1; ++i)
-        if (off[i + 1] - off[i] > dmax) dmax = off[i + 1] - off[i];
-    orc_work wk;
-    if (orc_work_alloc(&wk, dmax) != 0) return -1;
-    for (int64_t i = v0; i < v1; ++i) {
-        int32_t c = orc_best_label(i, off, idx, w, C, wk.lab, wk.sum, wk.scratch);
-        int32_t cur = C[i];
-        out[i - v0] = (c >= 0 && c != cur && (!pl || c < cur)) ? c : cur;
-    }
-    orc_work_free(&wk);
-    return off[v1] - off[v0];
+    return orc_sweep_window(v0, v1, off + v0, idx + off[v0], w ? w + off[v0] : NULL, C, pl, out);
 }
 
 /* ---------------------------------------------------------------------------

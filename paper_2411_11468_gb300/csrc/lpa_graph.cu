@@ -1,0 +1,1110 @@
+// Host side of liblpa.so: graph handles, validation, degree buckets, the iteration loop of
+// Algorithm 1 (lpa), label/state access and the float64 modularity reduction (Eq. 1).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "lpa_internal.h"
+
+namespace lpa {
+
+static thread_local std::string t_error;
+void set_error(const std::string &msg) { t_error = msg; }
+
+}  // namespace lpa
+
+using namespace lpa;
+
+#define LPA_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t _e = (call);                                                             \
+        if (_e != cudaSuccess) {                                                             \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(_e));                   \
+            return _e == cudaErrorMemoryAllocation ? LPA_ENOMEM : LPA_ECUDA;                 \
+        }                                                                                    \
+    } while (0)
+
+#define LPA_CHECK(st)                                                                        \
+    do {                                                                                     \
+        int _s = (st);                                                                       \
+        if (_s != LPA_OK) return _s;                                                         \
+    } while (0)
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ------------------------------------------------------------------------------------
+// kernels used at creation, initialisation and for modularity
+
+__global__ void k_off32to64(const int32_t *in, int64_t *out, int64_t n1)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i];
+}
+
+// error bits: 1 offsets decrease, 2 offsets[0] != 0, 4 offsets[n] != m, 8 index out of
+// range, 16 weight negative / NaN / Inf
+__global__ void k_validate(const int64_t *off, const int32_t *idx, const float *w, int64_t n, int64_t m,
+                           unsigned *err)
+{
+    unsigned bad = 0;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (tid == 0) {
+        if (off[0] != 0) bad |= 2u;
+        if (off[n] != m) bad |= 4u;
+    }
+    for (int64_t i = tid; i < n; i += stride)
+        if (off[i] > off[i + 1]) bad |= 1u;
+    for (int64_t e = tid; e < m; e += stride) {
+        const int32_t j = idx[e];
+        if (j < 0 || (int64_t)j >= n) bad |= 8u;
+        if (w) {
+            const float x = w[e];
+            if (!(isfinite(x) && x >= 0.0f)) bad |= 16u;
+        }
+    }
+    if (bad) atomicOr(err, bad);
+}
+
+__device__ __forceinline__ unsigned long long mix_sym(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Undirectedness check: multiset of (min, max, weight) over entries with i < j must equal
+// the one over entries with i > j; compared through wrapping sums of a 64-bit hash.
+__global__ void k_symmetric(const int64_t *off, const int32_t *idx, const float *w, int64_t n,
+                            unsigned long long *acc)
+{
+    unsigned long long lo = 0, hi = 0, clo = 0, chi = 0;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        for (int64_t e = off[i] + lane; e < off[i + 1]; e += 32) {
+            const int64_t j = idx[e];
+            if (j == i) continue;
+            const unsigned long long a = (unsigned long long)(i < j ? i : j), b = (unsigned long long)(i < j ? j : i);
+            const unsigned wb = w ? __float_as_uint(w[e]) : 0x3F800000u;
+            const unsigned long long h = mix_sym((a << 32 | b) + 0x9E3779B97F4A7C15ull) ^ mix_sym(wb + 0x632BE59BD9B4E019ull);
+            if (i < j) { lo += h; ++clo; } else { hi += h; ++chi; }
+        }
+    }
+    atomicAdd(acc + 0, lo);
+    atomicAdd(acc + 1, hi);
+    atomicAdd(acc + 2, clo);
+    atomicAdd(acc + 3, chi);
+}
+
+__device__ __forceinline__ int bucket_of(int64_t D, const lpa_tuning &t)
+{
+    if (D <= 0) return -1;
+    if (D <= t.thread_max) return B_THREAD;
+    if (D <= t.group_max) return B_GROUP;
+    if (D <= t.warp_max) return B_WARP;
+    if (D <= t.cta_max) return B_CTA;
+    if (D <= t.cta_large_max) return B_CTA_LARGE;
+    return B_HUB;
+}
+
+// per tile of 1024 vertices: how many fall in each bucket
+__global__ void __launch_bounds__(1024) k_bucket_count(const int64_t *off, int64_t n, lpa_tuning t, int32_t *cnt)
+{
+    __shared__ int32_t s[B_COUNT];
+    if (threadIdx.x < B_COUNT) s[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+    if (i < n) {
+        const int b = bucket_of(off[i + 1] - off[i], t);
+        if (b >= 0) atomicAdd(&s[b], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < B_COUNT) cnt[blockIdx.x * B_COUNT + threadIdx.x] = s[threadIdx.x];
+}
+
+// stable fill: vertices of a tile keep ascending order inside each bucket list
+__global__ void __launch_bounds__(1024) k_bucket_fill(const int64_t *off, int64_t n, lpa_tuning t,
+                                                      const int64_t *base, int32_t *lists)
+{
+    __shared__ int32_t wcnt[B_COUNT][32];
+    const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+    const int b = (i < n) ? bucket_of(off[i + 1] - off[i], t) : -1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned my_rank = 0;
+    for (int q = 0; q < B_COUNT; ++q) {
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, b == q);
+        if (b == q) my_rank = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) wcnt[q][warp] = __popc(bal);
+    }
+    __syncthreads();
+    if (b >= 0) {
+        int64_t pos = base[blockIdx.x * B_COUNT + b];
+        for (int w2 = 0; w2 < warp; ++w2) pos += wcnt[b][w2];
+        lists[pos + my_rank] = (int32_t)i;
+    }
+}
+
+__global__ void k_gather_rows(const int32_t *vs, int64_t k, const int64_t *off, int64_t *o0, int64_t *o1)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < k) {
+        o0[t] = off[vs[t]];
+        o1[t] = off[vs[t] + 1];
+    }
+}
+
+__global__ void k_init_labels(const int64_t *off, int64_t n, int32_t *C, uint8_t *flag)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        C[i] = (int32_t)i;
+        flag[i] = off[i + 1] > off[i] ? 1 : 0;
+    }
+}
+
+// set_state: check labels, sanitise flags (vertices without edges are never processed)
+__global__ void k_check_state(const int64_t *off, int64_t n, const int32_t *C, uint8_t *flag, unsigned *err)
+{
+    unsigned bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (C[i] < 0 || (int64_t)C[i] >= n) bad = 1;
+        if (flag) flag[i] = (flag[i] != 0 && off[i + 1] > off[i]) ? 1 : 0;
+    }
+    if (bad) atomicOr(err, bad);
+}
+
+__device__ __forceinline__ double warp_sum_d(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+
+// Eq. 1 numerators: per row i, K_i = sum_j w_ij and the weight of entries with C_j = C_i;
+// Sigma_{C_i} += K_i.  float64 accumulation.
+__global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int32_t *idx, const float *w,
+                                                  const int32_t *C, int64_t n, double *Sig, double *acc)
+{
+    __shared__ double s_in[8], s_k[8];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double tin = 0.0, tk = 0.0;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int64_t o0 = off[i], o1 = off[i + 1];
+        if (o0 == o1) continue;
+        const int32_t ci = C[i];
+        double k = 0.0, in = 0.0;
+        for (int64_t e = o0 + lane; e < o1; e += 32) {
+            const double we = w ? (double)w[e] : 1.0;
+            k += we;
+            if (C[idx[e]] == ci) in += we;
+        }
+        k = warp_sum_d(k);
+        in = warp_sum_d(in);
+        if (lane == 0) {
+            atomicAdd(Sig + ci, k);
+            tin += in;
+            tk += k;
+        }
+    }
+    if (lane == 0) {
+        s_in[threadIdx.x >> 5] = tin;
+        s_k[threadIdx.x >> 5] = tk;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < 8; ++q) {
+            a += s_in[q];
+            b += s_k[q];
+        }
+        atomicAdd(acc + 0, a);
+        atomicAdd(acc + 1, b);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mod_sq(double *Sig, int64_t n, double *acc)
+{
+    __shared__ double s[8];
+    double t = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const double x = Sig[c];
+        if (x != 0.0) {
+            t += x * x;
+            Sig[c] = 0.0;
+        }
+    }
+    t = warp_sum_d(t);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int q = 0; q < 8; ++q) a += s[q];
+        atomicAdd(acc + 2, a);
+    }
+}
+
+int grid_for(int64_t work, int threads, int max_per_sm = 8)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int64_t b = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)sms * max_per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+uint32_t capacity_bits(int64_t x)
+{
+    uint32_t b = 1;
+    while (b < 31 && ((int64_t)1 << b) - 1 < x) ++b;
+    return b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+struct lpa_graph {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0, m = 0;
+    int64_t *off = nullptr;
+    int32_t *idx = nullptr;
+    float *w = nullptr;
+    int32_t *C = nullptr;
+    uint8_t *flagA = nullptr, *flagB = nullptr;   // flagA: unprocessed flags for the next sweep
+    int32_t *mover_v = nullptr, *mover_c = nullptr;
+    unsigned long long *mover_count = nullptr;
+    unsigned long long *fallbacks = nullptr;
+    unsigned long long *ctr = nullptr;            // [ctr_iters][LPA_NUM_KERNELS][kCtrFields]
+    int ctr_iters = 0;
+    unsigned long long *h_ctr = nullptr;          // pinned mirror
+    unsigned *d_err = nullptr;
+    double *Sig = nullptr, *macc = nullptr;
+    // buckets
+    lpa_tuning tuning{};
+    int32_t *lists = nullptr;
+    int64_t bucket_start[B_COUNT + 1] = {};
+    // hubs
+    HubArgs hub{};
+    void *hub_mem = nullptr;
+    int64_t n_chunks = 0, n_slices = 0, table_slots = 0;
+    int32_t *tab_k = nullptr;
+    float *tab_v = nullptr;
+    int next_iter = 0;
+    int64_t bytes = 0, bucket_bytes = 0;
+    std::vector<cudaEvent_t> events;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(lpa_graph *g, T **p, size_t count, int64_t *counter = nullptr)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        return LPA_ENOMEM;
+    }
+    *(counter ? counter : &g->bytes) += (int64_t)(count * sizeof(T));
+    return LPA_OK;
+}
+
+void dfree(void *p)
+{
+    if (p) cudaFree(p);
+}
+
+lpa_tuning default_tuning()
+{
+    lpa_tuning t{};
+    t.thread_max = 7;
+    t.group_max = 31;
+    t.group_lanes = 8;
+    t.warp_max = 255;
+    t.cta_max = 4095;
+    t.cta_threads = 512;
+    t.cta_large_max = 16383;
+    t.cta_large_threads = 1024;
+    t.hub_chunk = 8192;
+    t.hub_table_shift = 1;
+    return t;
+}
+
+int check_tuning(const lpa_tuning &t)
+{
+    auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
+    if (t.thread_max < 0 || t.thread_max > 15) return LPA_EINVAL;
+    if (t.group_max < t.thread_max || t.group_max > 255) return LPA_EINVAL;
+    if (!(t.group_lanes == 2 || t.group_lanes == 4 || t.group_lanes == 8 || t.group_lanes == 16)) return LPA_EINVAL;
+    if (t.warp_max < t.group_max || t.warp_max > 2047) return LPA_EINVAL;
+    if (t.cta_max < t.warp_max || t.cta_max > 8191) return LPA_EINVAL;
+    if (t.cta_large_max < t.cta_max || t.cta_large_max > 16383) return LPA_EINVAL;
+    if (!pow2(t.cta_threads) || t.cta_threads < 128 || t.cta_threads > 1024) return LPA_EINVAL;
+    if (!pow2(t.cta_large_threads) || t.cta_large_threads < 128 || t.cta_large_threads > 1024) return LPA_EINVAL;
+    if (t.hub_chunk < 256 || t.hub_chunk > (1 << 24)) return LPA_EINVAL;
+    if (t.hub_table_shift < 0 || t.hub_table_shift > 3) return LPA_EINVAL;
+    return LPA_OK;
+}
+
+// smem slots for a bucket whose largest degree is dmax: capacity + 1 (a power of two)
+int slots_for(int dmax) { return (int)((1u << capacity_bits(dmax < 1 ? 1 : dmax))); }
+
+void free_buckets(lpa_graph *g)
+{
+    dfree(g->lists);
+    g->lists = nullptr;
+    dfree(g->hub_mem);
+    g->hub_mem = nullptr;
+    dfree(g->tab_k);
+    g->tab_k = nullptr;
+    dfree(g->tab_v);
+    g->tab_v = nullptr;
+    g->hub = HubArgs{};
+    g->n_chunks = g->n_slices = g->table_slots = 0;
+    g->bucket_bytes = 0;
+}
+
+int build_buckets(lpa_graph *g)
+{
+    free_buckets(g);
+    const int64_t n = g->n;
+    const int64_t tiles = (n + 1023) / 1024;
+    std::vector<int32_t> cnt((size_t)std::max<int64_t>(tiles, 1) * B_COUNT, 0);
+    std::vector<int64_t> base(cnt.size(), 0);
+    int32_t *d_cnt = nullptr;
+    int64_t *d_base = nullptr;
+    if (cudaMalloc((void **)&d_cnt, cnt.size() * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc((void **)&d_base, base.size() * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        dfree(d_cnt);
+        dfree(d_base);
+        set_error("build_buckets: cudaMalloc failed");
+        return LPA_ENOMEM;
+    }
+    auto cleanup = [&]() {
+        dfree(d_cnt);
+        dfree(d_base);
+    };
+    if (tiles > 0) {
+        k_bucket_count<<<(unsigned)tiles, 1024, 0, g->stream>>>(g->off, n, g->tuning, d_cnt);
+        cudaMemcpyAsync(cnt.data(), d_cnt, cnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream);
+        cudaError_t e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            set_error(std::string("bucket count: ") + cudaGetErrorString(e));
+            return LPA_ECUDA;
+        }
+    }
+    int64_t total[B_COUNT] = {};
+    for (int64_t t = 0; t < tiles; ++t)
+        for (int b = 0; b < B_COUNT; ++b) total[b] += cnt[t * B_COUNT + b];
+    g->bucket_start[0] = 0;
+    for (int b = 0; b < B_COUNT; ++b) g->bucket_start[b + 1] = g->bucket_start[b] + total[b];
+    int64_t run[B_COUNT];
+    for (int b = 0; b < B_COUNT; ++b) run[b] = g->bucket_start[b];
+    for (int64_t t = 0; t < tiles; ++t)
+        for (int b = 0; b < B_COUNT; ++b) {
+            base[t * B_COUNT + b] = run[b];
+            run[b] += cnt[t * B_COUNT + b];
+        }
+    int st = dalloc(g, &g->lists, (size_t)g->bucket_start[B_COUNT], &g->bucket_bytes);
+    if (st != LPA_OK) {
+        cleanup();
+        return st;
+    }
+    if (tiles > 0) {
+        cudaMemcpyAsync(d_base, base.data(), base.size() * sizeof(int64_t), cudaMemcpyHostToDevice, g->stream);
+        k_bucket_fill<<<(unsigned)tiles, 1024, 0, g->stream>>>(g->off, n, g->tuning, d_base, g->lists);
+    }
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    cleanup();
+    if (e != cudaSuccess) {
+        set_error(std::string("bucket fill: ") + cudaGetErrorString(e));
+        return LPA_ECUDA;
+    }
+
+    // hubs: tables in HBM, accumulate chunks and argmax slices
+    const int64_t H = total[B_HUB];
+    if (H == 0) return LPA_OK;
+    const int32_t *hub_list = g->lists + g->bucket_start[B_HUB];
+    std::vector<int32_t> hv((size_t)H);
+    std::vector<int64_t> o0((size_t)H), o1((size_t)H);
+    int64_t *d_o = nullptr;
+    LPA_CUDA(cudaMalloc((void **)&d_o, (size_t)(2 * H) * sizeof(int64_t)));
+    k_gather_rows<<<(unsigned)((H + 255) / 256), 256, 0, g->stream>>>(hub_list, H, g->off, d_o, d_o + H);
+    cudaMemcpyAsync(hv.data(), hub_list, H * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream);
+    cudaMemcpyAsync(o0.data(), d_o, H * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
+    cudaMemcpyAsync(o1.data(), d_o + H, H * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
+    e = cudaStreamSynchronize(g->stream);
+    dfree(d_o);
+    if (e != cudaSuccess) {
+        set_error(std::string("hub rows: ") + cudaGetErrorString(e));
+        return LPA_ECUDA;
+    }
+    const int64_t chunk = g->tuning.hub_chunk;
+    const int64_t slice = 8192;
+    std::vector<uint32_t> p1((size_t)H), bb((size_t)H);
+    std::vector<int64_t> tab((size_t)H);
+    std::vector<int32_t> ch, sh;
+    std::vector<int64_t> ce0, ce1, ss0, ss1;
+    int64_t slots = 0;
+    for (int64_t h = 0; h < H; ++h) {
+        const int64_t D = o1[h] - o0[h];
+        const int64_t want = std::min<int64_t>(D << g->tuning.hub_table_shift, (int64_t)1 << 31);
+        bb[h] = capacity_bits(want);
+        p1[h] = (uint32_t)(((int64_t)1 << bb[h]) - 1);
+        tab[h] = slots;
+        for (int64_t e0 = o0[h]; e0 < o1[h]; e0 += chunk) {
+            ch.push_back((int32_t)h);
+            ce0.push_back(e0);
+            ce1.push_back(std::min(o1[h], e0 + chunk));
+        }
+        for (int64_t s0 = 0; s0 < (int64_t)p1[h]; s0 += slice) {
+            sh.push_back((int32_t)h);
+            ss0.push_back(slots + s0);
+            ss1.push_back(slots + std::min<int64_t>(p1[h], s0 + slice));
+        }
+        slots += p1[h];
+    }
+    g->n_chunks = (int64_t)ch.size();
+    g->n_slices = (int64_t)sh.size();
+    g->table_slots = slots;
+    // one allocation for the hub arrays (8-byte fields first)
+    const size_t n8 = (size_t)(H /*tab*/ + H /*best*/ + 2 * g->n_chunks + 2 * g->n_slices);
+    const size_t n4 = (size_t)(H /*v*/ + H /*p1*/ + H /*b*/ + g->n_chunks + g->n_slices);
+    const size_t bytes = n8 * 8 + n4 * 4 + (size_t)H;
+    unsigned char *mem = nullptr;
+    LPA_CHECK(dalloc(g, &mem, bytes, &g->bucket_bytes));
+    g->hub_mem = mem;
+    unsigned char *p = mem;
+    auto take = [&](size_t b) {
+        unsigned char *r = p;
+        p += b;
+        return r;
+    };
+    int64_t *d_tab = (int64_t *)take(H * 8);
+    unsigned long long *d_best = (unsigned long long *)take(H * 8);
+    int64_t *d_ce0 = (int64_t *)take(g->n_chunks * 8);
+    int64_t *d_ce1 = (int64_t *)take(g->n_chunks * 8);
+    int64_t *d_ss0 = (int64_t *)take(g->n_slices * 8);
+    int64_t *d_ss1 = (int64_t *)take(g->n_slices * 8);
+    int32_t *d_hv = (int32_t *)take(H * 4);
+    uint32_t *d_p1 = (uint32_t *)take(H * 4);
+    uint32_t *d_b = (uint32_t *)take(H * 4);
+    int32_t *d_ch = (int32_t *)take(g->n_chunks * 4);
+    int32_t *d_sh = (int32_t *)take(g->n_slices * 4);
+    uint8_t *d_act = (uint8_t *)take(H);
+    LPA_CUDA(cudaMemcpyAsync(d_tab, tab.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_ce0, ce0.data(), g->n_chunks * 8, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_ce1, ce1.data(), g->n_chunks * 8, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_ss0, ss0.data(), g->n_slices * 8, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_ss1, ss1.data(), g->n_slices * 8, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_hv, hv.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_p1, p1.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_b, bb.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_ch, ch.data(), g->n_chunks * 4, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_sh, sh.data(), g->n_slices * 4, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemsetAsync(d_act, 0, H, g->stream));
+    LPA_CUDA(cudaMemsetAsync(d_best, 0, H * 8, g->stream));
+    LPA_CHECK(dalloc(g, &g->tab_k, (size_t)slots, &g->bucket_bytes));
+    LPA_CHECK(dalloc(g, &g->tab_v, (size_t)slots, &g->bucket_bytes));
+    LPA_CUDA(launch_hub_table_clear(g->tab_k, g->tab_v, slots, g->stream));
+    HubArgs &ha = g->hub;
+    ha.hub_v = d_hv;
+    ha.hub_p1 = d_p1;
+    ha.hub_b = d_b;
+    ha.hub_tab = d_tab;
+    ha.hub_act = d_act;
+    ha.hub_best = d_best;
+    ha.chunk_h = d_ch;
+    ha.chunk_e0 = d_ce0;
+    ha.chunk_e1 = d_ce1;
+    ha.slice_h = d_sh;
+    ha.slice_s0 = d_ss0;
+    ha.slice_s1 = d_ss1;
+    ha.tab_k = g->tab_k;
+    ha.tab_v = g->tab_v;
+    ha.n_hubs = (int32_t)H;
+    LPA_CUDA(cudaStreamSynchronize(g->stream));
+    return LPA_OK;
+}
+
+int ensure_ctr(lpa_graph *g, int iters)
+{
+    if (iters <= g->ctr_iters) return LPA_OK;
+    dfree(g->ctr);
+    if (g->h_ctr) cudaFreeHost(g->h_ctr);
+    g->ctr = nullptr;
+    g->h_ctr = nullptr;
+    const size_t per = (size_t)LPA_NUM_KERNELS * kCtrFields;
+    LPA_CHECK(dalloc(g, &g->ctr, per * iters));
+    cudaError_t e = cudaMallocHost((void **)&g->h_ctr, per * iters * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+        g->h_ctr = nullptr;
+        return LPA_ENOMEM;
+    }
+    g->ctr_iters = iters;
+    return LPA_OK;
+}
+
+cudaEvent_t event_at(lpa_graph *g, size_t k)
+{
+    while (g->events.size() <= k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        g->events.push_back(e);
+    }
+    return g->events[k];
+}
+
+void destroy_graph(lpa_graph *g)
+{
+    if (!g) return;
+    DeviceGuard dg(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    free_buckets(g);
+    dfree(g->off);
+    dfree(g->idx);
+    dfree(g->w);
+    dfree(g->C);
+    dfree(g->flagA);
+    dfree(g->flagB);
+    dfree(g->mover_v);
+    dfree(g->mover_c);
+    dfree(g->mover_count);
+    dfree(g->fallbacks);
+    dfree(g->ctr);
+    dfree(g->d_err);
+    dfree(g->Sig);
+    dfree(g->macc);
+    if (g->h_ctr) cudaFreeHost(g->h_ctr);
+    for (cudaEvent_t e : g->events) cudaEventDestroy(e);
+    delete g;
+}
+
+int init_state(lpa_graph *g)
+{
+    k_init_labels<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->off, g->n, g->C, g->flagA);
+    LPA_CUDA(cudaGetLastError());
+    g->next_iter = 0;
+    return LPA_OK;
+}
+
+}  // namespace
+
+// =======================================================================================
+extern "C" {
+
+const char *lpa_strerror(int status)
+{
+    switch (status) {
+    case LPA_OK: return "success";
+    case LPA_EINVAL: return "invalid argument";
+    case LPA_ENOMEM: return "out of memory";
+    case LPA_ECUDA: return "CUDA error";
+    case LPA_ETIMEOUT: return "device wait timed out";
+    case LPA_ESTATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+const char *lpa_last_error(void) { return t_error.c_str(); }
+
+const char *lpa_kernel_name(int slot)
+{
+    static const char *names[LPA_NUM_KERNELS] = {"thread", "group", "warp", "cta", "cta_large", "hub_begin",
+                                                 "hub_acc", "hub_argmax", "hub_move", "apply", "other", "unused"};
+    if (slot < 0 || slot >= LPA_NUM_KERNELS) return "";
+    return names[slot];
+}
+
+int lpa_create(const void *offsets, const int32_t *indices, const float *weights, int64_t n_vertices,
+               int64_t n_entries, int flags, void *cuda_stream, lpa_graph **out)
+{
+    if (!out) {
+        set_error("lpa_create: out is NULL");
+        return LPA_EINVAL;
+    }
+    *out = nullptr;
+    if (n_vertices < 0 || n_vertices >= ((int64_t)1 << 31) - 1 || n_entries < 0 || !offsets ||
+        (n_entries > 0 && !indices)) {
+        set_error("lpa_create: bad sizes or NULL arrays");
+        return LPA_EINVAL;
+    }
+    if ((flags & LPA_OFFSETS_I64) == 0 && n_entries > INT32_MAX) {
+        set_error("lpa_create: int32 offsets cannot address more than 2^31-1 entries");
+        return LPA_EINVAL;
+    }
+    lpa_graph *g = new lpa_graph();
+    cudaGetDevice(&g->device);
+    g->stream = (cudaStream_t)cuda_stream;
+    g->n = n_vertices;
+    g->m = n_entries;
+    g->tuning = default_tuning();
+    const bool dev_ptrs = (flags & LPA_DEVICE_PTRS) != 0;
+    const cudaMemcpyKind kind = dev_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int st = LPA_OK;
+    auto fail = [&](int s) {
+        destroy_graph(g);
+        return s;
+    };
+    cudaError_t ce = sweep_init_constants();
+    if (ce != cudaSuccess) {
+        set_error(std::string("constants: ") + cudaGetErrorString(ce));
+        return fail(LPA_ECUDA);
+    }
+    const int64_t n = g->n, m = g->m;
+    if ((st = dalloc(g, &g->off, (size_t)(n + 1))) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->idx, (size_t)m)) != LPA_OK) return fail(st);
+    if (weights && (st = dalloc(g, &g->w, (size_t)m)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->C, (size_t)n)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->flagA, (size_t)n)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->flagB, (size_t)n)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->mover_v, (size_t)n)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->mover_c, (size_t)n)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->mover_count, 1)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->fallbacks, 1)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->d_err, 4)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->macc, 4)) != LPA_OK) return fail(st);
+    if ((st = ensure_ctr(g, 32)) != LPA_OK) return fail(st);
+
+    cudaStream_t s = g->stream;
+    auto cuda_fail = [&](cudaError_t e, const char *what) {
+        set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        return fail(e == cudaErrorMemoryAllocation ? LPA_ENOMEM : LPA_ECUDA);
+    };
+    cudaError_t e;
+    if (flags & LPA_OFFSETS_I64) {
+        e = cudaMemcpyAsync(g->off, offsets, (size_t)(n + 1) * sizeof(int64_t), kind, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy offsets");
+    } else {
+        int32_t *tmp = nullptr;
+        e = cudaMalloc((void **)&tmp, (size_t)(n + 1) * sizeof(int32_t));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        e = cudaMemcpyAsync(tmp, offsets, (size_t)(n + 1) * sizeof(int32_t), kind, s);
+        if (e == cudaSuccess) {
+            k_off32to64<<<grid_for(n + 1, 256, 16), 256, 0, s>>>(tmp, g->off, n + 1);
+            e = cudaStreamSynchronize(s);
+        }
+        cudaFree(tmp);
+        if (e != cudaSuccess) return cuda_fail(e, "copy offsets");
+    }
+    if (m > 0) {
+        e = cudaMemcpyAsync(g->idx, indices, (size_t)m * sizeof(int32_t), kind, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy indices");
+        if (weights) {
+            e = cudaMemcpyAsync(g->w, weights, (size_t)m * sizeof(float), kind, s);
+            if (e != cudaSuccess) return cuda_fail(e, "copy weights");
+        }
+    }
+    // validation on the device
+    cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s);
+    k_validate<<<grid_for(std::max<int64_t>(n, m), 256, 16), 256, 0, s>>>(g->off, g->idx, g->w, n, m, g->d_err);
+    unsigned err = 0;
+    cudaMemcpyAsync(&err, g->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "validate");
+    if (err) {
+        std::string msg = "lpa_create: invalid graph:";
+        if (err & 1) msg += " offsets decrease;";
+        if (err & 2) msg += " offsets[0] != 0;";
+        if (err & 4) msg += " offsets[n] != n_entries;";
+        if (err & 8) msg += " index out of range;";
+        if (err & 16) msg += " weight negative, NaN or Inf;";
+        set_error(msg);
+        return fail(LPA_EINVAL);
+    }
+    if (flags & LPA_CHECK_SYMMETRIC) {
+        unsigned long long *acc = nullptr;
+        if ((st = dalloc(g, &acc, 4)) != LPA_OK) return fail(st);
+        cudaMemsetAsync(acc, 0, 4 * sizeof(unsigned long long), s);
+        k_symmetric<<<grid_for(n * 32, 256, 16), 256, 0, s>>>(g->off, g->idx, g->w, n, acc);
+        unsigned long long h[4];
+        cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s);
+        e = cudaStreamSynchronize(s);
+        cudaFree(acc);
+        g->bytes -= 4 * (int64_t)sizeof(unsigned long long);
+        if (e != cudaSuccess) return cuda_fail(e, "symmetry check");
+        if (h[0] != h[1] || h[2] != h[3]) {
+            set_error("lpa_create: graph is not undirected (entry (i,j,w) without (j,i,w))");
+            return fail(LPA_EINVAL);
+        }
+    }
+    if ((st = build_buckets(g)) != LPA_OK) return fail(st);
+    if ((st = init_state(g)) != LPA_OK) return fail(st);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "init");
+    *out = g;
+    return LPA_OK;
+}
+
+void lpa_destroy(lpa_graph *g) { destroy_graph(g); }
+
+int64_t lpa_num_vertices(const lpa_graph *g) { return g ? g->n : -1; }
+int64_t lpa_num_entries(const lpa_graph *g) { return g ? g->m : -1; }
+int64_t lpa_device_bytes(const lpa_graph *g) { return g ? g->bytes + g->bucket_bytes : -1; }
+
+int lpa_set_stream(lpa_graph *g, void *cuda_stream)
+{
+    if (!g) return LPA_EINVAL;
+    g->stream = (cudaStream_t)cuda_stream;
+    return LPA_OK;
+}
+
+int lpa_get_tuning(const lpa_graph *g, lpa_tuning *t)
+{
+    if (!g || !t) return LPA_EINVAL;
+    *t = g->tuning;
+    return LPA_OK;
+}
+
+int lpa_set_tuning(lpa_graph *g, const lpa_tuning *t)
+{
+    if (!g || !t) return LPA_EINVAL;
+    if (check_tuning(*t) != LPA_OK) {
+        set_error("lpa_set_tuning: thresholds out of range or not increasing");
+        return LPA_EINVAL;
+    }
+    DeviceGuard dg(g->device);
+    if (t->cta_large_max > 8191 && max_dynamic_smem() < (size_t)16384 * 8) {
+        set_error("lpa_set_tuning: cta_large table does not fit in shared memory");
+        return LPA_EINVAL;
+    }
+    g->tuning = *t;
+    return build_buckets(g);
+}
+
+int lpa_labels(const lpa_graph *g, int32_t *out, int64_t n, int out_on_device)
+{
+    if (!g || (!out && n > 0) || n != g->n) {
+        set_error("lpa_labels: bad arguments");
+        return LPA_EINVAL;
+    }
+    DeviceGuard dg(g->device);
+    if (n == 0) return LPA_OK;
+    LPA_CUDA(cudaMemcpyAsync(out, g->C, (size_t)n * sizeof(int32_t),
+                             out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+    LPA_CUDA(cudaStreamSynchronize(g->stream));
+    return LPA_OK;
+}
+
+int lpa_get_state(const lpa_graph *g, int32_t *labels, uint8_t *unprocessed, int32_t *next_iter, int64_t n,
+                  int on_device)
+{
+    if (!g || n != g->n) return LPA_EINVAL;
+    DeviceGuard dg(g->device);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (labels && n) LPA_CUDA(cudaMemcpyAsync(labels, g->C, (size_t)n * 4, k, g->stream));
+    if (unprocessed && n) LPA_CUDA(cudaMemcpyAsync(unprocessed, g->flagA, (size_t)n, k, g->stream));
+    LPA_CUDA(cudaStreamSynchronize(g->stream));
+    if (next_iter) *next_iter = g->next_iter;
+    return LPA_OK;
+}
+
+int lpa_set_state(lpa_graph *g, const int32_t *labels, const uint8_t *unprocessed, int32_t next_iter, int64_t n,
+                  int on_device)
+{
+    if (!g || n != g->n || next_iter < 0) {
+        set_error("lpa_set_state: bad arguments");
+        return LPA_EINVAL;
+    }
+    DeviceGuard dg(g->device);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (n == 0) {
+        g->next_iter = next_iter;
+        return LPA_OK;
+    }
+    // stage into the mover buffers so a rejected state leaves the handle unchanged
+    if (labels) LPA_CUDA(cudaMemcpyAsync(g->mover_v, labels, (size_t)n * 4, k, g->stream));
+    else LPA_CUDA(cudaMemcpyAsync(g->mover_v, g->C, (size_t)n * 4, cudaMemcpyDeviceToDevice, g->stream));
+    if (unprocessed) LPA_CUDA(cudaMemcpyAsync(g->flagB, unprocessed, (size_t)n, k, g->stream));
+    else LPA_CUDA(cudaMemcpyAsync(g->flagB, g->flagA, (size_t)n, cudaMemcpyDeviceToDevice, g->stream));
+    LPA_CUDA(cudaMemsetAsync(g->d_err, 0, 4, g->stream));
+    k_check_state<<<grid_for(n, 256, 16), 256, 0, g->stream>>>(g->off, n, g->mover_v, g->flagB, g->d_err);
+    unsigned err = 0;
+    LPA_CUDA(cudaMemcpyAsync(&err, g->d_err, 4, cudaMemcpyDeviceToHost, g->stream));
+    LPA_CUDA(cudaStreamSynchronize(g->stream));
+    if (err) {
+        set_error("lpa_set_state: label outside [0, n)");
+        return LPA_EINVAL;
+    }
+    LPA_CUDA(cudaMemcpyAsync(g->C, g->mover_v, (size_t)n * 4, cudaMemcpyDeviceToDevice, g->stream));
+    std::swap(g->flagA, g->flagB);
+    LPA_CUDA(cudaStreamSynchronize(g->stream));
+    g->next_iter = next_iter;
+    return LPA_OK;
+}
+
+int lpa_set_labels(lpa_graph *g, const int32_t *labels, int64_t n, int on_device)
+{
+    if (!g || !labels || n != g->n) {
+        set_error("lpa_set_labels: bad arguments");
+        return LPA_EINVAL;
+    }
+    DeviceGuard dg(g->device);
+    if (n == 0) {
+        g->next_iter = 0;
+        return LPA_OK;
+    }
+    // every vertex with an edge becomes unprocessed; flags staged in flagB
+    k_init_labels<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->off, g->n, g->mover_c, g->flagB);
+    LPA_CUDA(cudaGetLastError());
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LPA_CUDA(cudaMemcpyAsync(g->mover_v, labels, (size_t)n * 4, k, g->stream));
+    LPA_CUDA(cudaMemsetAsync(g->d_err, 0, 4, g->stream));
+    k_check_state<<<grid_for(n, 256, 16), 256, 0, g->stream>>>(g->off, n, g->mover_v, nullptr, g->d_err);
+    unsigned err = 0;
+    LPA_CUDA(cudaMemcpyAsync(&err, g->d_err, 4, cudaMemcpyDeviceToHost, g->stream));
+    LPA_CUDA(cudaStreamSynchronize(g->stream));
+    if (err) {
+        set_error("lpa_set_labels: label outside [0, n)");
+        return LPA_EINVAL;
+    }
+    LPA_CUDA(cudaMemcpyAsync(g->C, g->mover_v, (size_t)n * 4, cudaMemcpyDeviceToDevice, g->stream));
+    std::swap(g->flagA, g->flagB);
+    LPA_CUDA(cudaStreamSynchronize(g->stream));
+    g->next_iter = 0;
+    return LPA_OK;
+}
+
+int lpa_modularity(const lpa_graph *gc, double *q)
+{
+    lpa_graph *g = const_cast<lpa_graph *>(gc);
+    if (!g || !q) return LPA_EINVAL;
+    DeviceGuard dg(g->device);
+    *q = 0.0;
+    if (g->n == 0) return LPA_OK;
+    if (!g->Sig) {
+        LPA_CHECK(dalloc(g, &g->Sig, (size_t)g->n));
+        LPA_CUDA(cudaMemsetAsync(g->Sig, 0, (size_t)g->n * sizeof(double), g->stream));
+    }
+    LPA_CUDA(cudaMemsetAsync(g->macc, 0, 3 * sizeof(double), g->stream));
+    k_mod_rows<<<grid_for(g->n * 32, 256, 16), 256, 0, g->stream>>>(g->off, g->idx, g->w, g->C, g->n, g->Sig, g->macc);
+    k_mod_sq<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->Sig, g->n, g->macc);
+    double h[3];
+    LPA_CUDA(cudaMemcpyAsync(h, g->macc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    LPA_CUDA(cudaStreamSynchronize(g->stream));
+    const double in = h[0], two_m = h[1], sq = h[2];
+    *q = (two_m == 0.0) ? 0.0 : in / two_m - sq / (two_m * two_m);
+    return LPA_OK;
+}
+
+int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mode, lpa_stats *stats)
+{
+    if (!g || max_iters < 0 || pl_period < 0 || !std::isfinite(tolerance) ||
+        ((mode & ~LPA_RESUME) != LPA_SYNC && (mode & ~LPA_RESUME) != LPA_ASYNC)) {
+        set_error("lpa_run: bad arguments");
+        return LPA_EINVAL;
+    }
+    DeviceGuard dg(g->device);
+    const bool async_mode = (mode & ~LPA_RESUME) == LPA_ASYNC;
+    cudaStream_t s = g->stream;
+    const bool timing = stats && stats->time_kernels;
+    if (stats) {
+        const int32_t tk = stats->time_kernels;
+        memset(stats, 0, sizeof(*stats));
+        stats->time_kernels = tk;
+    }
+    if (!(mode & LPA_RESUME)) LPA_CHECK(init_state(g));
+    const int start = g->next_iter;
+    if (stats) {
+        stats->first_iter = start;
+        stats->iterations = start;
+    }
+    if (g->n == 0 || start >= max_iters) {
+        LPA_CUDA(cudaStreamSynchronize(s));
+        return LPA_OK;
+    }
+    const int span = max_iters - start;
+    LPA_CHECK(ensure_ctr(g, span));
+    const size_t per = (size_t)LPA_NUM_KERNELS * kCtrFields;
+    LPA_CUDA(cudaMemsetAsync(g->ctr, 0, per * span * sizeof(unsigned long long), s));
+    LPA_CUDA(cudaMemsetAsync(g->fallbacks, 0, sizeof(unsigned long long), s));
+    LPA_CUDA(cudaMemsetAsync(g->mover_count, 0, sizeof(unsigned long long), s));
+    if (!async_mode) LPA_CUDA(cudaMemsetAsync(g->flagB, 0, (size_t)g->n, s));
+
+    struct Rec {
+        int iter, slot;
+        size_t ev0, ev1;
+    };
+    std::vector<Rec> recs;
+    size_t evn = 0;
+    cudaEvent_t run0 = event_at(g, evn++), run1 = event_at(g, evn++);
+    if (!run0 || !run1) {
+        set_error("cudaEventCreate failed");
+        return LPA_ECUDA;
+    }
+    std::vector<std::pair<size_t, size_t>> iter_ev;
+    LPA_CUDA(cudaEventRecord(run0, s));
+
+    const lpa_tuning &t = g->tuning;
+    const int64_t *bs = g->bucket_start;
+    int launches = 0;
+    int l = start;
+    bool converged = false;
+    for (; l < max_iters; ++l) {
+        const int rel = l - start;
+        const bool pl = pl_period > 0 && (l % pl_period) == 0;
+        SweepArgs a{};
+        a.off = g->off;
+        a.idx = g->idx;
+        a.w = g->w;
+        a.C = g->C;
+        a.flag_cur = g->flagA;
+        a.flag_next = async_mode ? g->flagA : g->flagB;
+        a.mover_v = g->mover_v;
+        a.mover_c = g->mover_c;
+        a.mover_count = g->mover_count;
+        a.ctr = g->ctr + per * rel;
+        a.fallbacks = g->fallbacks;
+        a.pl = pl ? 1 : 0;
+        a.async_mode = async_mode ? 1 : 0;
+
+        size_t ie0 = evn++, ie1 = evn++;
+        if (!event_at(g, ie1)) return LPA_ECUDA;
+        LPA_CUDA(cudaEventRecord(g->events[ie0], s));
+        auto timed = [&](int slot, auto &&launch) -> cudaError_t {
+            ++launches;
+            size_t e0 = 0, e1 = 0;
+            if (timing && rel < LPA_STATS_MAX_ITERS) {
+                e0 = evn++;
+                e1 = evn++;
+                if (!event_at(g, e1)) return cudaErrorUnknown;
+                cudaEventRecord(g->events[e0], s);
+            }
+            cudaError_t e = launch();
+            if (timing && rel < LPA_STATS_MAX_ITERS) {
+                cudaEventRecord(g->events[e1], s);
+                recs.push_back({rel, slot, e0, e1});
+            }
+            return e;
+        };
+        const int32_t *L = g->lists;
+        if (bs[B_THREAD + 1] > bs[B_THREAD])
+            LPA_CUDA(timed(LPA_K_THREAD, [&] {
+                return launch_thread_bucket(L + bs[B_THREAD], bs[B_THREAD + 1] - bs[B_THREAD], a, 16, s);
+            }));
+        if (bs[B_GROUP + 1] > bs[B_GROUP])
+            LPA_CUDA(timed(LPA_K_GROUP, [&] {
+                return launch_group_bucket(L + bs[B_GROUP], bs[B_GROUP + 1] - bs[B_GROUP], a, t.group_lanes,
+                                           slots_for(t.group_max), s);
+            }));
+        if (bs[B_WARP + 1] > bs[B_WARP])
+            LPA_CUDA(timed(LPA_K_WARP, [&] {
+                return launch_warp_bucket(L + bs[B_WARP], bs[B_WARP + 1] - bs[B_WARP], a, slots_for(t.warp_max), s);
+            }));
+        if (bs[B_CTA + 1] > bs[B_CTA])
+            LPA_CUDA(timed(LPA_K_CTA, [&] {
+                return launch_cta_bucket(L + bs[B_CTA], bs[B_CTA + 1] - bs[B_CTA], a, t.cta_threads,
+                                         slots_for(t.cta_max), LPA_K_CTA, s);
+            }));
+        if (bs[B_CTA_LARGE + 1] > bs[B_CTA_LARGE])
+            LPA_CUDA(timed(LPA_K_CTA_LARGE, [&] {
+                return launch_cta_bucket(L + bs[B_CTA_LARGE], bs[B_CTA_LARGE + 1] - bs[B_CTA_LARGE], a,
+                                         t.cta_large_threads, slots_for(t.cta_large_max), LPA_K_CTA_LARGE, s);
+            }));
+        if (g->hub.n_hubs > 0) {
+            LPA_CUDA(timed(LPA_K_HUB_BEGIN, [&] { return launch_hub_begin(g->hub, a, s); }));
+            LPA_CUDA(timed(LPA_K_HUB_ACC, [&] { return launch_hub_acc(g->hub, a, g->n_chunks, 1024, s); }));
+            LPA_CUDA(timed(LPA_K_HUB_ARGMAX, [&] { return launch_hub_argmax(g->hub, a, g->n_slices, s); }));
+            LPA_CUDA(timed(LPA_K_HUB_MOVE, [&] { return launch_hub_move(g->hub, a, s); }));
+        }
+        if (!async_mode) {
+            LPA_CUDA(timed(LPA_K_APPLY, [&] { return launch_apply(a, g->n, s); }));
+            LPA_CUDA(cudaMemsetAsync(g->mover_count, 0, sizeof(unsigned long long), s));
+            std::swap(g->flagA, g->flagB);        // next sweep reads the marks; old flags are all clear
+        }
+        LPA_CUDA(cudaEventRecord(g->events[ie1], s));
+        iter_ev.push_back({ie0, ie1});
+        unsigned long long *hc = g->h_ctr + per * rel;
+        LPA_CUDA(cudaMemcpyAsync(hc, a.ctr, per * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        LPA_CUDA(cudaStreamSynchronize(s));
+        int64_t dn = 0;
+        for (int k = 0; k < LPA_NUM_KERNELS; ++k) dn += (int64_t)hc[k * kCtrFields + CTR_MOVED];
+        if (!pl && (double)dn / (double)g->n < tolerance) {
+            converged = true;
+            ++l;
+            break;
+        }
+    }
+    LPA_CUDA(cudaEventRecord(run1, s));
+    unsigned long long fb = 0;
+    LPA_CUDA(cudaMemcpyAsync(&fb, g->fallbacks, sizeof(fb), cudaMemcpyDeviceToHost, s));
+    LPA_CUDA(cudaStreamSynchronize(s));
+    g->next_iter = l;
+    if (stats) {
+        stats->iterations = l;
+        stats->converged = converged ? 1 : 0;
+        stats->probe_fallbacks = (int64_t)fb;
+        stats->launches = launches;
+        cudaEventElapsedTime(&stats->total_ms, run0, run1);
+        for (int r = 0; r < l - start && r < LPA_STATS_MAX_ITERS; ++r) {
+            const unsigned long long *hc = g->h_ctr + per * r;
+            int64_t act = 0, edg = 0, mv = 0, mk = 0;
+            for (int k = 0; k < LPA_NUM_KERNELS; ++k) {
+                act += (int64_t)hc[k * kCtrFields + CTR_ACTIVE];
+                edg += (int64_t)hc[k * kCtrFields + CTR_EDGES];
+                mv += (int64_t)hc[k * kCtrFields + CTR_MOVED];
+                mk += (int64_t)hc[k * kCtrFields + CTR_MARKS];
+                stats->kernel_edges[r][k] = (int64_t)hc[k * kCtrFields + CTR_EDGES];
+                stats->kernel_active[r][k] = (int64_t)hc[k * kCtrFields + CTR_ACTIVE];
+            }
+            stats->changed[r] = mv;
+            stats->active[r] = act;
+            stats->edges[r] = edg;
+            stats->marks[r] = mk;
+            cudaEventElapsedTime(&stats->iter_ms[r], g->events[iter_ev[r].first], g->events[iter_ev[r].second]);
+        }
+        for (const Rec &r : recs) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, g->events[r.ev0], g->events[r.ev1]);
+            stats->kernel_ms[r.iter][r.slot] += ms;
+        }
+    }
+    return LPA_OK;
+}
+
+size_t lpa_struct_size(int which)
+{
+    switch (which) {
+    case 0: return sizeof(lpa_stats);
+    case 1: return sizeof(lpa_tuning);
+    default: return 0;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,645 @@
+// Sweep kernels of liblpa.so: one label-propagation sweep (Algorithm 1, lpaMove) over the
+// vertices of one degree bucket, with per-vertex open-addressing hashtables probed by the
+// hybrid quadratic-double sequence of Algorithm 2.
+//
+// Buckets (by degree D, thresholds in lpa_tuning):
+//   thread     one thread per vertex, private table in shared memory (no atomics)
+//   group      2..16 lanes per vertex, table in shared memory (shared-memory atomics)
+//   warp       one warp per vertex, table in shared memory
+//   cta        one thread block per vertex, table in shared memory (up to 16383 slots)
+//   hub        several blocks per vertex, table in HBM (global atomics), followed by a
+//              block-parallel max-reduce and a move/mark kernel
+// Every table has p1 = 2^b - 1 >= D slots (Section 4.2: capacity nextPow2(D) - 1, read
+// with nextPow2 as the next power of two strictly above D); the secondary modulus is
+// p2 = 2 p1 + 1.  Labels are the keys, float32 weight sums the values.  The winner is
+// the max of (weight bits << 32 | ~label) over the table, i.e. the largest weight and,
+// among equal weights, the smallest label.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lpa_internal.h"
+
+namespace lpa {
+
+// Multipliers for remainders by Mersenne numbers: c_magic[b] = ceil(2^64 / (2^b - 1))
+// (0 for b = 1, where every remainder is 0).  a mod d = mulhi64(M * a, d) for 32-bit a
+// and d (Lemire, Kaser and Kurz, "Faster remainder by direct computation", 2019).
+__constant__ unsigned long long c_magic[33];
+
+cudaError_t sweep_init_constants()
+{
+    unsigned long long h[33];
+    h[0] = 0;
+    for (int b = 1; b <= 32; ++b) {
+        unsigned long long p = (b == 32) ? 0xFFFFFFFFull : ((1ull << b) - 1);
+        h[b] = (p == 1) ? 0ull : (0xFFFFFFFFFFFFFFFFull / p + 1);
+    }
+    return cudaMemcpyToSymbol(c_magic, h, sizeof(h));
+}
+
+__device__ __forceinline__ uint32_t mod_mersenne(uint32_t a, uint32_t b, uint32_t p)
+{
+    unsigned long long low = c_magic[b] * (unsigned long long)a;
+    return (uint32_t)__umul64hi(low, (unsigned long long)p);
+}
+
+__device__ __forceinline__ unsigned long long pack_kv(float w, int32_t k)
+{
+    return ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(~(uint32_t)k);
+}
+
+__device__ __forceinline__ int32_t unpack_key(unsigned long long p)
+{
+    return (int32_t)(~(uint32_t)(p & 0xFFFFFFFFull));
+}
+
+// capacity 2^b - 1 >= D (D >= 1)
+__device__ __forceinline__ uint32_t cap_bits(uint32_t D) { return 32u - __clz(D); }
+__device__ __forceinline__ uint32_t cap_of_bits(uint32_t b) { return b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u); }
+
+// One slot attempt of Algorithm 2: take slot s if it is empty or already holds k.
+template <bool SHARED>
+__device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32_t k, float v)
+{
+    if (!SHARED) {                                    // single owner: plain accesses
+        int32_t kk = Hk[s];
+        if (kk == k || kk == kEmpty) {
+            Hk[s] = k;
+            Hv[s] += v;
+            return true;
+        }
+        return false;
+    }
+    int32_t kk = *((volatile int32_t *)(Hk + s));
+    if (kk == kEmpty) {
+        int32_t old = atomicCAS(Hk + s, kEmpty, k);
+        kk = (old == kEmpty) ? k : old;
+    }
+    if (kk == k) {
+        atomicAdd(Hv + s, v);
+        return true;
+    }
+    return false;
+}
+
+// hashtableAccumulate (Algorithm 2) with i and delta kept reduced mod p1 (same slots),
+// then a linear scan from the last probed slot once the probe budget is spent.
+template <bool SHARED>
+__device__ __forceinline__ void ht_accumulate(int32_t *Hk, float *Hv, int stride, uint32_t p1, uint32_t b,
+                                              int32_t k, float v, unsigned &fallbacks)
+{
+    const uint32_t uk = (uint32_t)k;
+    uint32_t i = mod_mersenne(uk, b, p1);
+    uint32_t delta = (p1 > 1u) ? 1u : 0u;
+    uint32_t step = 0xFFFFFFFFu;                      // (k mod p2) mod p1, on first collision
+    uint32_t s = i;
+#pragma unroll 1
+    for (int t = 0; t < kMaxRetries; ++t) {
+        s = i;
+        if (try_slot<SHARED>(Hk, Hv, (size_t)s * stride, k, v)) return;
+        if (step == 0xFFFFFFFFu) {
+            uint32_t q = mod_mersenne(uk, b + 1, 2u * p1 + 1u);
+            if (q >= p1) q -= p1;
+            if (q >= p1) q -= p1;
+            step = q;
+        }
+        i += delta;
+        if (i >= p1) i -= p1;
+        unsigned long long d2 = 2ull * delta + step;    // < 3 p1
+        if (d2 >= p1) d2 -= p1;
+        if (d2 >= p1) d2 -= p1;
+        delta = (uint32_t)d2;
+    }
+    ++fallbacks;
+#pragma unroll 1
+    for (uint32_t u = 1; u <= p1; ++u) {
+        uint32_t q = s + u;
+        if (q >= p1) q -= p1;
+        if (try_slot<SHARED>(Hk, Hv, (size_t)q * stride, k, v)) return;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask()
+{
+    if (G >= 32) return 0xFFFFFFFFu;
+    const unsigned lane = threadIdx.x & 31u;
+    return ((1u << (G & 31)) - 1u) << (lane & ~(unsigned)(G - 1));
+}
+
+template <int G>
+__device__ __forceinline__ void group_sync()
+{
+    if (G > 1) __syncwarp(group_mask<G>());
+}
+
+// Warp-aggregated append of (v, c) to the synchronous mover list.  Every lane of the
+// warp must call it.
+__device__ __forceinline__ void append_movers(const SweepArgs &a, bool pred, int32_t v, int32_t c)
+{
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
+    if (!bal) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(bal) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(a.mover_count, (unsigned long long)__popc(bal));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (pred) {
+        unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+        a.mover_v[pos] = v;
+        a.mover_c[pos] = c;
+    }
+}
+
+// Warp sum of four per-lane counters into block counters (every lane calls).
+__device__ __forceinline__ void warp_count(unsigned long long *bctr, unsigned act, unsigned edges,
+                                           unsigned moved, unsigned marks)
+{
+    act = __reduce_add_sync(0xFFFFFFFFu, act);
+    edges = __reduce_add_sync(0xFFFFFFFFu, edges);
+    moved = __reduce_add_sync(0xFFFFFFFFu, moved);
+    marks = __reduce_add_sync(0xFFFFFFFFu, marks);
+    if ((threadIdx.x & 31) == 0) {
+        if (act) atomicAdd(&bctr[CTR_ACTIVE], (unsigned long long)act);
+        if (edges) atomicAdd(&bctr[CTR_EDGES], (unsigned long long)edges);
+        if (moved) atomicAdd(&bctr[CTR_MOVED], (unsigned long long)moved);
+        if (marks) atomicAdd(&bctr[CTR_MARKS], (unsigned long long)marks);
+    }
+}
+
+__device__ __forceinline__ void flush_block_counts(const SweepArgs &a, unsigned long long *bctr,
+                                                   unsigned *bfb, int kslot)
+{
+    __syncthreads();
+    if (threadIdx.x < kCtrFields) {
+        unsigned long long x = bctr[threadIdx.x];
+        if (x) atomicAdd(&a.ctr[kslot * kCtrFields + threadIdx.x], x);
+    } else if (threadIdx.x == kCtrFields) {
+        if (*bfb) atomicAdd(a.fallbacks, (unsigned long long)*bfb);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// G lanes per vertex (G = 1: thread per vertex with a private table; G = 32: warp per
+// vertex).  Each block handles TPB / G consecutive entries of the bucket list.
+template <int G, int TPB>
+__global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list, int64_t count, SweepArgs a,
+                                               int slots, int kslot)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NG = TPB / G;
+    __shared__ unsigned long long bctr[kCtrFields];
+    __shared__ unsigned bfb;
+    if (threadIdx.x < kCtrFields) bctr[threadIdx.x] = 0;
+    if (threadIdx.x == 0) bfb = 0;
+    __syncthreads();
+
+    const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
+    const int grp = threadIdx.x / G;
+    int32_t *Hk;
+    float *Hv;
+    int stride;
+    if (G == 1) {                      // interleaved: slot s of thread t at s * TPB + t
+        Hk = (int32_t *)smem + threadIdx.x;
+        Hv = (float *)(smem + (size_t)TPB * slots * sizeof(int32_t)) + threadIdx.x;
+        stride = TPB;
+    } else {
+        Hk = (int32_t *)smem + (size_t)grp * slots;
+        Hv = (float *)(smem + (size_t)NG * slots * sizeof(int32_t)) + (size_t)grp * slots;
+        stride = 1;
+    }
+
+    const int64_t gi = (int64_t)blockIdx.x * NG + grp;
+    int32_t v = -1;
+    bool act = false;
+    if (gi < count) {
+        v = __ldg(list + gi);
+        if (lane == 0) {
+            act = a.flag_cur[v] != 0;
+            if (act) a.flag_cur[v] = 0;                   // mark processed
+        }
+        if (G > 1) act = __shfl_sync(group_mask<G>(), act, 0, G);
+    }
+
+    unsigned fb = 0;
+    int64_t o0 = 0, o1 = 0;
+    int32_t cur = 0, cstar = -1;
+    bool moved = false;
+    if (act) {
+        o0 = a.off[v];
+        o1 = a.off[v + 1];
+        const uint32_t D = (uint32_t)(o1 - o0);
+        const uint32_t b = cap_bits(D);
+        const uint32_t p1 = cap_of_bits(b);
+        for (uint32_t s = lane; s < p1; s += G) {          // hashtableClear
+            Hk[(size_t)s * stride] = kEmpty;
+            Hv[(size_t)s * stride] = 0.0f;
+        }
+        group_sync<G>();
+        cur = a.C[v];
+        for (int64_t e = o0 + lane; e < o1; e += G) {      // scan neighbours
+            const int32_t j = a.idx[e];
+            if (j == v) continue;                           // skip self-loops
+            const int32_t k = a.C[j];
+            const float wv = a.w ? a.w[e] : 1.0f;
+            ht_accumulate<(G > 1)>(Hk, Hv, stride, p1, b, k, wv, fb);
+        }
+        group_sync<G>();
+        unsigned long long best = 0;
+        for (uint32_t s = lane; s < p1; s += G) {          // hashtableMaxKey
+            const int32_t kk = Hk[(size_t)s * stride];
+            if (kk != kEmpty) {
+                const unsigned long long pk = pack_kv(Hv[(size_t)s * stride], kk);
+                best = pk > best ? pk : best;
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(group_mask<G>(), best, o, G);
+            best = other > best ? other : best;
+        }
+        if (best != 0) {
+            cstar = unpack_key(best);
+            moved = (cstar != cur) && (!a.pl || cstar < cur);
+        }
+        if (moved) {
+            if (a.async_mode && lane == 0) {
+                a.C[v] = cstar;
+                __threadfence();
+            }
+            group_sync<G>();
+            for (int64_t e = o0 + lane; e < o1; e += G) a.flag_next[a.idx[e]] = 1;   // mark neighbours
+        }
+    }
+    if (!a.async_mode) append_movers(a, moved && lane == 0, v, cstar);
+    const bool lead = (lane == 0);
+    const unsigned deg = (unsigned)(o1 - o0);
+    warp_count(bctr, (act && lead) ? 1u : 0u, (act && lead) ? deg : 0u, (moved && lead) ? 1u : 0u,
+               (moved && lead) ? deg : 0u);
+    if (fb) atomicAdd(&bfb, fb);
+    flush_block_counts(a, bctr, &bfb, kslot);
+}
+
+// ---------------------------------------------------------------------------------
+// One thread block per vertex; the table (up to slots entries) lives in dynamic smem.
+template <int TPB>
+__global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, int64_t count, SweepArgs a,
+                                             int slots, int kslot)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    int32_t *Hk = (int32_t *)smem;
+    float *Hv = (float *)(smem + (size_t)slots * sizeof(int32_t));
+    __shared__ int s_act;
+    __shared__ unsigned long long s_best[TPB / 32];
+    __shared__ unsigned s_fb;
+    const int64_t gi = blockIdx.x;
+    if (gi >= count) return;
+    const int32_t v = __ldg(list + gi);
+    if (threadIdx.x == 0) {
+        int act = a.flag_cur[v] != 0;
+        if (act) a.flag_cur[v] = 0;
+        s_act = act;
+        s_fb = 0;
+    }
+    __syncthreads();
+    if (!s_act) return;                                // uniform for the block
+
+    const int64_t o0 = a.off[v], o1 = a.off[v + 1];
+    const uint32_t D = (uint32_t)(o1 - o0);
+    const uint32_t b = cap_bits(D);
+    const uint32_t p1 = cap_of_bits(b);
+    for (uint32_t s = threadIdx.x; s < p1; s += TPB) {
+        Hk[s] = kEmpty;
+        Hv[s] = 0.0f;
+    }
+    __syncthreads();
+    const int32_t cur = a.C[v];
+    unsigned fb = 0;
+    for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) {
+        const int32_t j = a.idx[e];
+        if (j == v) continue;
+        const int32_t k = a.C[j];
+        const float wv = a.w ? a.w[e] : 1.0f;
+        ht_accumulate<true>(Hk, Hv, 1, p1, b, k, wv, fb);
+    }
+    if (fb) atomicAdd(&s_fb, fb);
+    __syncthreads();
+    unsigned long long best = 0;
+    for (uint32_t s = threadIdx.x; s < p1; s += TPB) {
+        const int32_t kk = Hk[s];
+        if (kk != kEmpty) {
+            const unsigned long long pk = pack_kv(Hv[s], kk);
+            best = pk > best ? pk : best;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+        best = other > best ? other : best;
+    }
+    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    best = 0;
+#pragma unroll
+    for (int w = 0; w < TPB / 32; ++w) best = s_best[w] > best ? s_best[w] : best;
+    bool moved = false;
+    int32_t cstar = -1;
+    if (best != 0) {
+        cstar = unpack_key(best);
+        moved = (cstar != cur) && (!a.pl || cstar < cur);
+    }
+    if (moved) {
+        if (threadIdx.x == 0) {
+            if (a.async_mode) {
+                a.C[v] = cstar;
+                __threadfence();
+            } else {
+                const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
+                a.mover_v[pos] = v;
+                a.mover_c[pos] = cstar;
+            }
+        }
+        __syncthreads();
+        for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
+    }
+    if (threadIdx.x == 0) {
+        unsigned long long *c = a.ctr + kslot * kCtrFields;
+        atomicAdd(c + CTR_ACTIVE, 1ull);
+        atomicAdd(c + CTR_EDGES, (unsigned long long)D);
+        if (moved) {
+            atomicAdd(c + CTR_MOVED, 1ull);
+            atomicAdd(c + CTR_MARKS, (unsigned long long)D);
+        }
+        if (s_fb) atomicAdd(a.fallbacks, (unsigned long long)s_fb);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Hubs: tables in HBM shared by several blocks.
+__global__ void k_hub_begin(HubArgs h, SweepArgs a)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= h.n_hubs) return;
+    const int32_t v = h.hub_v[t];
+    const uint8_t act = a.flag_cur[v] != 0;
+    if (act) a.flag_cur[v] = 0;                       // mark processed
+    h.hub_act[t] = act;
+    h.hub_best[t] = 0ull;
+}
+
+template <int TPB>
+__global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a)
+{
+    const int hh = h.chunk_h[blockIdx.x];
+    if (!h.hub_act[hh]) return;
+    const int32_t v = h.hub_v[hh];
+    const uint32_t p1 = h.hub_p1[hh], b = h.hub_b[hh];
+    int32_t *Hk = h.tab_k + h.hub_tab[hh];
+    float *Hv = h.tab_v + h.hub_tab[hh];
+    const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
+    unsigned fb = 0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
+        const int32_t j = a.idx[e];
+        if (j == v) continue;
+        const int32_t k = a.C[j];
+        const float wv = a.w ? a.w[e] : 1.0f;
+        ht_accumulate<true>(Hk, Hv, 1, p1, b, k, wv, fb);
+    }
+    if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
+}
+
+template <int TPB>
+__global__ void __launch_bounds__(TPB) k_hub_argmax(HubArgs h, SweepArgs a)
+{
+    __shared__ unsigned long long s_best[TPB / 32];
+    const int hh = h.slice_h[blockIdx.x];
+    if (!h.hub_act[hh]) return;
+    const int64_t s0 = h.slice_s0[blockIdx.x], s1 = h.slice_s1[blockIdx.x];
+    unsigned long long best = 0;
+    for (int64_t s = s0 + threadIdx.x; s < s1; s += TPB) {
+        const int32_t kk = h.tab_k[s];
+        if (kk != kEmpty) {
+            const unsigned long long pk = pack_kv(h.tab_v[s], kk);
+            best = pk > best ? pk : best;
+            h.tab_k[s] = kEmpty;                       // leave the table clear for the next sweep
+            h.tab_v[s] = 0.0f;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+        best = other > best ? other : best;
+    }
+    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < TPB / 32; ++w) best = s_best[w] > best ? s_best[w] : best;
+        if (best) atomicMax(h.hub_best + hh, best);
+    }
+}
+
+template <int TPB>
+__global__ void __launch_bounds__(TPB) k_hub_move(HubArgs h, SweepArgs a)
+{
+    const int hh = blockIdx.x;
+    if (!h.hub_act[hh]) return;
+    const int32_t v = h.hub_v[hh];
+    const unsigned long long best = h.hub_best[hh];
+    const int32_t cur = a.C[v];
+    bool moved = false;
+    int32_t cstar = -1;
+    if (best != 0) {
+        cstar = unpack_key(best);
+        moved = (cstar != cur) && (!a.pl || cstar < cur);
+    }
+    const int64_t o0 = a.off[v], o1 = a.off[v + 1];
+    if (moved) {
+        if (threadIdx.x == 0) {
+            if (a.async_mode) {
+                a.C[v] = cstar;
+                __threadfence();
+            } else {
+                const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
+                a.mover_v[pos] = v;
+                a.mover_c[pos] = cstar;
+            }
+        }
+        __syncthreads();
+        for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
+    }
+    if (threadIdx.x == 0) {
+        const int kslot = LPA_K_HUB_ACC;
+        unsigned long long *c = a.ctr + kslot * kCtrFields;
+        atomicAdd(c + CTR_ACTIVE, 1ull);
+        atomicAdd(c + CTR_EDGES, (unsigned long long)(o1 - o0));
+        if (moved) {
+            atomicAdd(c + CTR_MOVED, 1ull);
+            atomicAdd(c + CTR_MARKS, (unsigned long long)(o1 - o0));
+        }
+    }
+}
+
+// Synchronous mode: publish the labels recorded during the sweep.
+__global__ void k_apply(SweepArgs a)
+{
+    const unsigned long long n = *a.mover_count;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        a.C[a.mover_v[i]] = a.mover_c[i];
+}
+
+__global__ void k_table_clear(int32_t *k, float *v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        k[i] = kEmpty;
+        v[i] = 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// launchers
+
+static int g_num_sms = 0;
+static size_t g_max_smem = 0;
+
+static void query_device()
+{
+    if (g_num_sms) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    int smem = 0;
+    cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    g_max_smem = (size_t)smem;
+}
+
+size_t max_dynamic_smem()
+{
+    query_device();
+    return g_max_smem;
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int G, int TPB>
+static cudaError_t launch_g(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
+                            cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    constexpr int NG = TPB / G;
+    const size_t smem = (size_t)NG * slots * (sizeof(int32_t) + sizeof(float));
+    cudaError_t e = set_smem(k_group<G, TPB>, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (count + NG - 1) / NG;
+    k_group<G, TPB><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thread_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int slots,
+                                 cudaStream_t s)
+{
+    return launch_g<1, 128>(list, count, a, slots, LPA_K_THREAD, s);
+}
+
+cudaError_t launch_group_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int lanes, int slots,
+                                cudaStream_t s)
+{
+    switch (lanes) {
+    case 2: return launch_g<2, 256>(list, count, a, slots, LPA_K_GROUP, s);
+    case 4: return launch_g<4, 256>(list, count, a, slots, LPA_K_GROUP, s);
+    case 8: return launch_g<8, 256>(list, count, a, slots, LPA_K_GROUP, s);
+    case 16: return launch_g<16, 256>(list, count, a, slots, LPA_K_GROUP, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_warp_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int slots,
+                               cudaStream_t s)
+{
+    return launch_g<32, 256>(list, count, a, slots, LPA_K_WARP, s);
+}
+
+template <int TPB>
+static cudaError_t launch_c(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
+                            cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    const size_t smem = (size_t)slots * (sizeof(int32_t) + sizeof(float));
+    cudaError_t e = set_smem(k_cta<TPB>, smem);
+    if (e != cudaSuccess) return e;
+    k_cta<TPB><<<(unsigned)count, TPB, smem, s>>>(list, count, a, slots, kslot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cta_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int threads, int slots,
+                              int kslot, cudaStream_t s)
+{
+    switch (threads) {
+    case 128: return launch_c<128>(list, count, a, slots, kslot, s);
+    case 256: return launch_c<256>(list, count, a, slots, kslot, s);
+    case 512: return launch_c<512>(list, count, a, slots, kslot, s);
+    case 1024: return launch_c<1024>(list, count, a, slots, kslot, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_hub_begin(const HubArgs &h, const SweepArgs &a, cudaStream_t s)
+{
+    if (h.n_hubs <= 0) return cudaSuccess;
+    k_hub_begin<<<(h.n_hubs + 255) / 256, 256, 0, s>>>(h, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, int threads, cudaStream_t s)
+{
+    if (n_chunks <= 0) return cudaSuccess;
+    switch (threads) {
+    case 256: k_hub_acc<256><<<(unsigned)n_chunks, 256, 0, s>>>(h, a); break;
+    case 512: k_hub_acc<512><<<(unsigned)n_chunks, 512, 0, s>>>(h, a); break;
+    default: k_hub_acc<1024><<<(unsigned)n_chunks, 1024, 0, s>>>(h, a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hub_argmax(const HubArgs &h, const SweepArgs &a, int64_t n_slices, cudaStream_t s)
+{
+    if (n_slices <= 0) return cudaSuccess;
+    k_hub_argmax<256><<<(unsigned)n_slices, 256, 0, s>>>(h, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hub_move(const HubArgs &h, const SweepArgs &a, cudaStream_t s)
+{
+    if (h.n_hubs <= 0) return cudaSuccess;
+    k_hub_move<1024><<<h.n_hubs, 1024, 0, s>>>(h, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const SweepArgs &a, int64_t n, cudaStream_t s)
+{
+    query_device();
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = (int64_t)g_num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_apply<<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, cudaStream_t s)
+{
+    if (slots <= 0) return cudaSuccess;
+    query_device();
+    int64_t blocks = (slots + 255) / 256;
+    const int64_t cap = (int64_t)g_num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    k_table_clear<<<(unsigned)blocks, 256, 0, s>>>(k, v, slots);
+    return cudaGetLastError();
+}
+
+}  // namespace lpa

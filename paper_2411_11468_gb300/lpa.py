@@ -1,0 +1,274 @@
+"""Python binding of liblpa.so (ctypes): argument marshalling only.
+
+Every step of label propagation runs in the library's CUDA kernels; this module passes
+pointers, sizes and the current torch CUDA stream.  It raises if liblpa.so is missing:
+there is no CPU fallback.
+
+    from paper_2411_11468_gb300 import lpa
+    g = lpa.Graph(offsets, indices, weights)          # torch tensors (CPU or CUDA)
+    st = g.run(tolerance=0.05, max_iters=20, pl_period=4, mode=lpa.SYNC)
+    labels = g.labels()                                # torch.int32 on the graph's device
+    q = g.modularity()
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblpa.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
+SYNC, ASYNC, RESUME = 0, 1, 16
+OFFSETS_I32, OFFSETS_I64, HOST_PTRS, DEVICE_PTRS, CHECK_SYMMETRIC = 0, 1, 0, 2, 4
+STATS_MAX_ITERS = 64
+NUM_KERNELS = 12
+KERNEL_NAMES = ["thread", "group", "warp", "cta", "cta_large", "hub_begin", "hub_acc", "hub_argmax",
+                "hub_move", "apply", "other", "unused"]
+
+SYMBOLS = ["lpa_create", "lpa_run", "lpa_labels", "lpa_modularity", "lpa_set_labels", "lpa_get_state",
+           "lpa_set_state", "lpa_set_stream", "lpa_get_tuning", "lpa_set_tuning", "lpa_num_vertices",
+           "lpa_num_entries", "lpa_device_bytes", "lpa_destroy", "lpa_strerror", "lpa_last_error",
+           "lpa_kernel_name", "lpa_struct_size"]
+
+
+class LpaError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {_strerror(status)} ({status}){': ' + detail if detail else ''}")
+
+
+class Stats(ct.Structure):
+    _fields_ = [
+        ("time_kernels", ct.c_int32),
+        ("iterations", ct.c_int32),
+        ("converged", ct.c_int32),
+        ("first_iter", ct.c_int32),
+        ("changed", ct.c_int64 * STATS_MAX_ITERS),
+        ("active", ct.c_int64 * STATS_MAX_ITERS),
+        ("edges", ct.c_int64 * STATS_MAX_ITERS),
+        ("marks", ct.c_int64 * STATS_MAX_ITERS),
+        ("iter_ms", ct.c_float * STATS_MAX_ITERS),
+        ("total_ms", ct.c_float),
+        ("launches", ct.c_int32),
+        ("probe_fallbacks", ct.c_int64),
+        ("kernel_ms", (ct.c_float * NUM_KERNELS) * STATS_MAX_ITERS),
+        ("kernel_edges", (ct.c_int64 * NUM_KERNELS) * STATS_MAX_ITERS),
+        ("kernel_active", (ct.c_int64 * NUM_KERNELS) * STATS_MAX_ITERS),
+    ]
+
+    @property
+    def count(self) -> int:
+        return min(self.iterations - self.first_iter, STATS_MAX_ITERS)
+
+    def dN(self) -> list[int]:
+        return [int(self.changed[i]) for i in range(self.count)]
+
+    def to_dict(self) -> dict:
+        k = self.count
+        d = dict(iterations=self.iterations, converged=bool(self.converged), first_iter=self.first_iter,
+                 changed=self.dN(), active=[int(self.active[i]) for i in range(k)],
+                 edges=[int(self.edges[i]) for i in range(k)], marks=[int(self.marks[i]) for i in range(k)],
+                 iter_ms=[float(self.iter_ms[i]) for i in range(k)], total_ms=float(self.total_ms),
+                 probe_fallbacks=int(self.probe_fallbacks), launches=int(self.launches))
+        if self.time_kernels:
+            d["kernel_ms"] = [[float(self.kernel_ms[i][j]) for j in range(NUM_KERNELS)] for i in range(k)]
+            d["kernel_edges"] = [[int(self.kernel_edges[i][j]) for j in range(NUM_KERNELS)] for i in range(k)]
+            d["kernel_active"] = [[int(self.kernel_active[i][j]) for j in range(NUM_KERNELS)] for i in range(k)]
+        return d
+
+
+class Tuning(ct.Structure):
+    _fields_ = [(name, ct.c_int32) for name in (
+        "thread_max", "group_max", "group_lanes", "warp_max", "cta_max", "cta_threads", "cta_large_max",
+        "cta_large_threads", "hub_chunk", "hub_table_shift")] + [("reserved", ct.c_int32 * 6)]
+
+    def to_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+_lib = None
+
+
+def load() -> ct.CDLL:
+    """Loads liblpa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"liblpa.so not built at {LIB_PATH}; run paper_2411_11468_gb300.build.build()")
+    L = ct.CDLL(LIB_PATH)
+    P, i64, i32 = ct.c_void_p, ct.c_int64, ct.c_int
+    L.lpa_create.argtypes = [P, P, P, i64, i64, i32, P, ct.POINTER(P)]
+    L.lpa_run.argtypes = [P, ct.c_double, i32, i32, i32, ct.POINTER(Stats)]
+    L.lpa_labels.argtypes = [P, P, i64, i32]
+    L.lpa_modularity.argtypes = [P, ct.POINTER(ct.c_double)]
+    L.lpa_set_labels.argtypes = [P, P, i64, i32]
+    L.lpa_get_state.argtypes = [P, P, P, ct.POINTER(ct.c_int32), i64, i32]
+    L.lpa_set_state.argtypes = [P, P, P, ct.c_int32, i64, i32]
+    L.lpa_set_stream.argtypes = [P, P]
+    L.lpa_get_tuning.argtypes = [P, ct.POINTER(Tuning)]
+    L.lpa_set_tuning.argtypes = [P, ct.POINTER(Tuning)]
+    for f in ("lpa_num_vertices", "lpa_num_entries", "lpa_device_bytes"):
+        getattr(L, f).argtypes = [P]
+        getattr(L, f).restype = i64
+    L.lpa_destroy.argtypes = [P]
+    L.lpa_destroy.restype = None
+    L.lpa_strerror.argtypes = [i32]
+    L.lpa_strerror.restype = ct.c_char_p
+    L.lpa_last_error.argtypes = []
+    L.lpa_last_error.restype = ct.c_char_p
+    L.lpa_kernel_name.argtypes = [i32]
+    L.lpa_kernel_name.restype = ct.c_char_p
+    L.lpa_struct_size.argtypes = [i32]
+    L.lpa_struct_size.restype = ct.c_size_t
+    if L.lpa_struct_size(0) != ct.sizeof(Stats) or L.lpa_struct_size(1) != ct.sizeof(Tuning):
+        raise RuntimeError("liblpa.so struct layout does not match the binding")
+    _lib = L
+    return L
+
+
+def _strerror(status: int) -> str:
+    try:
+        return load().lpa_strerror(status).decode()
+    except Exception:
+        return "error"
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        detail = load().lpa_last_error().decode(errors="replace")
+        raise LpaError(status, where, detail)
+
+
+def _ptr(t):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def _stream_handle(device) -> ct.c_void_p:
+    if device.type != "cuda":
+        return ct.c_void_p(None)
+    return ct.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Graph:
+    """A CSR graph resident on the current CUDA device (owned by liblpa.so).
+
+    offsets: int32 or int64 [n+1]; indices: int32 [m]; weights: float32 [m] or None (unit).
+    Tensors may live on the host (copied to the device) or on the current CUDA device.
+    The handle uses torch's current CUDA stream at creation (or `stream`).
+    """
+
+    def __init__(self, offsets, indices, weights=None, check_symmetric: bool = False, stream=None):
+        L = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblpa needs a CUDA device")
+        offsets = offsets.contiguous()
+        indices = indices.contiguous()
+        if indices.dtype != torch.int32:
+            raise TypeError("indices must be int32")
+        if offsets.dtype not in (torch.int32, torch.int64):
+            raise TypeError("offsets must be int32 or int64")
+        if weights is not None:
+            weights = weights.contiguous()
+            if weights.dtype != torch.float32:
+                raise TypeError("weights must be float32")
+        on_dev = offsets.is_cuda
+        for t in (indices, weights):
+            if t is not None and t.is_cuda != on_dev:
+                raise ValueError("offsets, indices and weights must be on the same device")
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.n = offsets.numel() - 1
+        self.m = indices.numel()
+        flags = (OFFSETS_I64 if offsets.dtype == torch.int64 else OFFSETS_I32)
+        flags |= DEVICE_PTRS if on_dev else HOST_PTRS
+        if check_symmetric:
+            flags |= CHECK_SYMMETRIC
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = ct.c_void_p()
+        _check(L.lpa_create(_ptr(offsets), _ptr(indices), _ptr(weights), self.n, self.m, flags,
+                            ct.c_void_p(stream.cuda_stream), ct.byref(h)), "lpa_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().lpa_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- algorithm ------------------------------------------------------------------
+    def run(self, tolerance: float = 0.05, max_iters: int = 20, pl_period: int = 4, mode: int = SYNC,
+            resume: bool = False, time_kernels: bool = False) -> Stats:
+        st = Stats()
+        st.time_kernels = 1 if time_kernels else 0
+        _check(load().lpa_run(self._h, float(tolerance), int(max_iters), int(pl_period),
+                              int(mode) | (RESUME if resume else 0), ct.byref(st)), "lpa_run")
+        return st
+
+    def labels(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        if out.dtype != torch.int32 or out.numel() != self.n or not out.is_contiguous():
+            raise ValueError("out must be a contiguous int32 tensor of n elements")
+        _check(load().lpa_labels(self._h, _ptr(out), self.n, 1 if out.is_cuda else 0), "lpa_labels")
+        return out
+
+    def modularity(self) -> float:
+        q = ct.c_double()
+        _check(load().lpa_modularity(self._h, ct.byref(q)), "lpa_modularity")
+        return q.value
+
+    def set_labels(self, labels: torch.Tensor):
+        labels = labels.to(torch.int32).contiguous()
+        _check(load().lpa_set_labels(self._h, _ptr(labels), labels.numel(), 1 if labels.is_cuda else 0),
+               "lpa_set_labels")
+
+    def get_state(self):
+        C = torch.empty(self.n, dtype=torch.int32)
+        A = torch.empty(self.n, dtype=torch.uint8)
+        it = ct.c_int32()
+        _check(load().lpa_get_state(self._h, _ptr(C), _ptr(A), ct.byref(it), self.n, 0), "lpa_get_state")
+        return C, A, it.value
+
+    def set_state(self, labels, unprocessed, next_iter: int):
+        labels = None if labels is None else labels.to(torch.int32).contiguous()
+        unprocessed = None if unprocessed is None else unprocessed.to(torch.uint8).contiguous()
+        dev = [t.is_cuda for t in (labels, unprocessed) if t is not None]
+        on_dev = 1 if (dev and dev[0]) else 0
+        _check(load().lpa_set_state(self._h, _ptr(labels), _ptr(unprocessed), int(next_iter), self.n, on_dev),
+               "lpa_set_state")
+
+    def tuning(self) -> Tuning:
+        t = Tuning()
+        _check(load().lpa_get_tuning(self._h, ct.byref(t)), "lpa_get_tuning")
+        return t
+
+    def set_tuning(self, t: Tuning | None = None, **kw):
+        if t is None:
+            t = self.tuning()
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check(load().lpa_set_tuning(self._h, ct.byref(t)), "lpa_set_tuning")
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(load().lpa_set_stream(self._h, ct.c_void_p(stream.cuda_stream)), "lpa_set_stream")
+
+    def device_bytes(self) -> int:
+        return int(load().lpa_device_bytes(self._h))

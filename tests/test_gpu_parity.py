@@ -1,0 +1,275 @@
+"""CUDA path (through the C ABI) against the CPU oracle, on the same seeded inputs.
+
+Synchronous mode must equal the oracle bit for bit: labels after every iteration and the
+changed-vertex count dN of every iteration (integer weights, weighted degrees < 2^24, so
+every float32 label sum is exact).  Asynchronous mode is racy by design (Section 4 item 1)
+and is judged by the two acceptance bounds: modularity within 0.005 of the oracle's
+asynchronous run and at most a tolerance fraction of vertices whose label is not a
+max-weight neighbour label.
+"""
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2411_11468_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+# thresholds low enough that small graphs reach every bucket, hubs included
+SMALL_BUCKETS = dict(thread_max=3, group_max=7, group_lanes=4, warp_max=31, cta_max=63, cta_threads=128,
+                     cta_large_max=127, cta_large_threads=256, hub_chunk=256, hub_table_shift=0)
+
+
+@pytest.fixture(scope="module")
+def lpa():
+    from paper_2411_11468_gb300 import build
+    build.build()
+    from paper_2411_11468_gb300 import lpa as L
+    L.load()
+    return L
+
+
+def make(lpa, csr, device=True, tuning=None):
+    if device:
+        csr = csr.to("cuda")
+    g = lpa.Graph(csr.offsets, csr.indices, csr.weights)
+    if tuning:
+        g.set_tuning(**tuning)
+    return g
+
+
+def oracle_graph(csr):
+    return oracle.Graph.of(csr)
+
+
+def check_sync_every_iteration(lpa, csr, tol, max_iters, pl, tuning=None, device=True):
+    og = oracle_graph(csr)
+    ref = oracle.lpa_sync(og, tol, max_iters, pl)
+    g = make(lpa, csr, device, tuning)
+    st = g.run(tol, max_iters, pl, lpa.SYNC)
+    assert st.dN() == ref.dN
+    assert st.iterations == ref.iterations
+    assert bool(st.converged) == ref.converged
+    assert g.labels().cpu().numpy().tolist() == ref.labels.tolist()
+    for t in range(1, ref.iterations):
+        rt = oracle.lpa_sync(og, tol, t, pl)
+        g.run(tol, t, pl, lpa.SYNC)
+        assert g.labels().cpu().numpy().tolist() == rt.labels.tolist(), f"iteration {t}"
+    return g, ref
+
+
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["cliques", "bridge6", "bridge12", "knn-noPL", "knn-PL", "star"])
+def test_closed_form_cases_sync(lpa, case):
+    fixtures = {
+        "cliques": (gg.cliques(5, 6), 4),
+        "bridge6": (gg.two_cliques_bridge(6), 4),
+        "bridge12": (gg.two_cliques_bridge(12), 4),
+        "knn-noPL": (gg.complete_bipartite(5), 0),
+        "knn-PL": (gg.complete_bipartite(5), 4),
+        "star": (gg.star(9), 4),
+    }
+    csr, pl = fixtures[case]
+    for tuning in (None, SMALL_BUCKETS):
+        check_sync_every_iteration(lpa, csr, 0.05, 20, pl, tuning)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_sync_random_graphs_all_buckets(lpa, seed):
+    """Random integer-weighted graphs whose degrees span every bucket (with the small
+    thresholds), several tiles and a ragged tail; per-iteration equality."""
+    rnd = random.Random(seed)
+    n = rnd.choice([37, 200, 513, 1500])
+    csr = gg.random_small(n, rnd.choice([0.01, 0.05, 0.15, 0.4]), 1000 + seed, wmax=rnd.choice([1, 4, 8]),
+                          self_loops=(seed % 3 == 0))
+    check_sync_every_iteration(lpa, csr, rnd.choice([0.0, 0.05]), 20, rnd.choice([0, 2, 4]), SMALL_BUCKETS)
+
+
+@pytest.mark.parametrize("scale,weights", [(12, "int8"), (14, "unit"), (15, "int8")])
+def test_sync_rmat_default_buckets(lpa, scale, weights):
+    csr = gg.rmat(scale, weights=weights)
+    check_sync_every_iteration(lpa, csr, 0.05, 20, 4)
+
+
+@pytest.mark.parametrize("scale", [13, 15])
+def test_sync_rmat_small_buckets_with_hubs(lpa, scale):
+    csr = gg.rmat(scale, weights="int8")
+    check_sync_every_iteration(lpa, csr, 0.05, 20, 4, SMALL_BUCKETS)
+
+
+def test_sync_sbm_config(lpa):
+    """Planted partition, 10,000 vertices in 100 blocks, intra-degree 16, inter 2, unit
+    weights, seed 0; tolerance 0.05, 20 iterations, PL every 4th."""
+    csr = gg.sbm(10_000, 100, 16.0, 2.0, seed=0)
+    g, ref = check_sync_every_iteration(lpa, csr, 0.05, 20, 4)
+    q = g.modularity()
+    assert abs(q - oracle.modularity(oracle_graph(csr), ref.labels)) < 1e-12
+
+
+def test_host_and_device_inputs_agree(lpa):
+    csr = gg.rmat(12, weights="int8")
+    a = make(lpa, csr, device=False)
+    b = make(lpa, csr, device=True)
+    sa, sb = a.run(), b.run()
+    assert sa.dN() == sb.dN()
+    assert torch.equal(a.labels().cpu(), b.labels().cpu())
+
+
+def test_int32_offsets(lpa):
+    csr = gg.rmat(12, weights="int8")
+    g = lpa.Graph(csr.offsets.to(torch.int32).cuda(), csr.indices.cuda(), csr.weights.cuda())
+    ref = oracle.lpa_sync(oracle_graph(csr))
+    st = g.run()
+    assert st.dN() == ref.dN and g.labels().cpu().numpy().tolist() == ref.labels.tolist()
+
+
+def test_unit_weights_null_pointer(lpa):
+    csr = gg.rmat(12, weights="unit")
+    g = lpa.Graph(csr.offsets.cuda(), csr.indices.cuda(), None)
+    ref = oracle.lpa_sync(oracle.Graph(csr.offsets, csr.indices, None))
+    st = g.run()
+    assert st.dN() == ref.dN and g.labels().cpu().numpy().tolist() == ref.labels.tolist()
+
+
+def test_sync_is_deterministic(lpa):
+    csr = gg.rmat(14, weights="int8").to("cuda")
+    g = lpa.Graph(csr.offsets, csr.indices, csr.weights)
+    s1 = g.run()
+    l1 = g.labels().clone()
+    s2 = g.run()
+    assert s1.dN() == s2.dN() and torch.equal(l1, g.labels())
+
+
+# ---------------------------------------------------------------------------------------
+# asynchronous mode: acceptance bounds
+
+@pytest.mark.parametrize("which", ["sbm", "rmat14", "rmat14-small"])
+def test_async_bounds(lpa, which):
+    if which == "sbm":
+        csr, tuning = gg.sbm(10_000, 100, 16.0, 2.0, seed=0), None
+    elif which == "rmat14":
+        csr, tuning = gg.rmat(14, weights="int8"), None
+    else:
+        csr, tuning = gg.rmat(14, weights="int8"), SMALL_BUCKETS
+    og = oracle_graph(csr)
+    ref = oracle.lpa_async(og, 0.05, 20, 4)
+    q_ref = oracle.modularity(og, ref.labels)
+    g = make(lpa, csr, True, tuning)
+    g.run(0.05, 20, 4, lpa.ASYNC)
+    lab = g.labels().cpu()
+    q = g.modularity()
+    assert abs(q - oracle.modularity(og, lab)) < 1e-12
+    assert abs(q - q_ref) <= 0.005, (q, q_ref)
+    viol = oracle.violations(og, lab) / og.n
+    assert viol <= 0.05, viol
+
+
+# ---------------------------------------------------------------------------------------
+# modularity (Eq. 1)
+
+@pytest.mark.parametrize("seed", range(4))
+def test_modularity_matches_oracle(lpa, seed):
+    csr = gg.rmat(11 + seed, weights="int8")
+    og = oracle_graph(csr)
+    g = make(lpa, csr)
+    rnd = np.random.default_rng(seed)
+    for labels in (np.zeros(og.n, np.int32), np.arange(og.n, dtype=np.int32),
+                   rnd.integers(0, 7, og.n).astype(np.int32)):
+        g.set_labels(torch.from_numpy(labels))
+        assert abs(g.modularity() - oracle.modularity(og, labels)) < 1e-12
+    g.run()
+    lab = g.labels().cpu()
+    assert abs(g.modularity() - float(oracle.modularity_exact(og, lab))) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# edge cases
+
+def test_empty_graph(lpa):
+    g = lpa.Graph(torch.zeros(1, dtype=torch.int64), torch.zeros(0, dtype=torch.int32))
+    st = g.run()
+    assert st.iterations == 0 and g.labels().numel() == 0
+    assert g.modularity() == 0.0
+
+
+def test_no_edges_and_isolated(lpa):
+    g = lpa.Graph(torch.zeros(6, dtype=torch.int64), torch.zeros(0, dtype=torch.int32))
+    st = g.run()
+    ref0 = oracle.lpa_sync(oracle.Graph(torch.zeros(6, dtype=torch.int64), torch.zeros(0, dtype=torch.int32)))
+    assert st.dN() == ref0.dN == [0, 0]          # l=0 is Pick-Less and cannot stop the loop
+    assert g.labels().cpu().tolist() == list(range(5))
+    csr = gg.from_edges(4, [(0, 0), (1, 2)])
+    ref = oracle.lpa_sync(oracle_graph(csr))
+    g2 = make(lpa, csr)
+    st2 = g2.run()
+    assert st2.dN() == ref.dN and g2.labels().cpu().tolist() == ref.labels.tolist()
+
+
+def test_single_hub_star_large(lpa):
+    """A star whose centre exceeds every smem bucket (HBM hub path)."""
+    csr = gg.star(40_000)
+    check_sync_every_iteration(lpa, csr, 0.05, 20, 4)
+
+
+def test_bucket_boundary_degrees(lpa):
+    """Vertices with degrees 2^k - 1, 2^k, 2^k + 1 around every default threshold."""
+    edges = []
+    n = 0
+    centres = []
+    for d in (7, 8, 9, 15, 16, 31, 32, 33, 255, 256, 257, 4095, 4096, 4097, 16383, 16384, 16385):
+        c = n
+        centres.append(c)
+        for t in range(d):
+            edges.append((c, c + 1 + t))
+        n += d + 1
+    # tie the stars together so labels flow between them
+    for a, b in zip(centres, centres[1:]):
+        edges.append((a + 1, b + 1))
+    csr = gg.from_edges(n, edges, [1 + (k % 5) for k in range(len(edges))])
+    check_sync_every_iteration(lpa, csr, 0.0, 20, 4)
+
+
+def test_invalid_graphs_rejected(lpa):
+    off = torch.tensor([0, 1, 2], dtype=torch.int64)
+    idx = torch.tensor([1, 0], dtype=torch.int32)
+    for bad in (dict(weights=torch.tensor([1.0, -1.0])), dict(weights=torch.tensor([1.0, float("nan")])),
+                dict(weights=torch.tensor([1.0, float("inf")])), dict(indices=torch.tensor([1, 5], dtype=torch.int32)),
+                dict(offsets=torch.tensor([0, 2, 1], dtype=torch.int64)),
+                dict(offsets=torch.tensor([1, 1, 2], dtype=torch.int64))):
+        o = bad.get("offsets", off)
+        i = bad.get("indices", idx)
+        w = bad.get("weights", torch.tensor([1.0, 1.0]))
+        with pytest.raises(lpa.LpaError) as ei:
+            lpa.Graph(o, i, w)
+        assert ei.value.status == lpa.EINVAL
+
+
+def test_check_symmetric_flag(lpa):
+    sym = gg.rmat(10, weights="int8")
+    lpa.Graph(sym.offsets, sym.indices, sym.weights, check_symmetric=True)
+    w = sym.weights.clone()
+    w[3] += 1.0                          # one direction of one edge changes weight
+    with pytest.raises(lpa.LpaError):
+        lpa.Graph(sym.offsets, sym.indices, w, check_symmetric=True)
+
+
+def test_resume_from_checkpoint(lpa):
+    """Run k sweeps, snapshot (labels, unprocessed flags, next sweep index), restore into a
+    fresh handle and finish: identical to one uninterrupted run."""
+    csr = gg.sbm(3000, 50, 10.0, 3.0, seed=4, weights="int8")
+    full = make(lpa, csr)
+    sf = full.run(0.0, 15, 4)
+    part = make(lpa, csr)
+    part.run(0.0, 6, 4)
+    C, A, it = part.get_state()
+    fresh = make(lpa, csr)
+    fresh.set_state(C, A, it)
+    sr = fresh.run(0.0, 15, 4, resume=True)
+    assert torch.equal(fresh.labels().cpu(), full.labels().cpu())
+    assert sr.dN() == sf.dN()[it:]
+    # the oracle agrees with the resumed state as well
+    ref = oracle.lpa_sync(oracle_graph(csr), 0.0, 15, 4, labels=C, active=A, start_iter=it)
+    assert fresh.labels().cpu().numpy().tolist() == ref.labels.tolist()

@@ -428,3 +428,19 @@ def test_empty_and_isolated():
     r = oracle.lpa_sync(g, 0.05, 20, 4)
     assert r.labels.tolist() == [0, 1, 1, 3]
     assert r.dN == [1, 0]
+
+
+def test_sweep_window_equals_first_sync_sweep():
+    """One all-active sweep on a window of rows equals the first iteration of the
+    synchronous run restricted to that window (used for sampled baselines)."""
+    csr = gg.rmat(12, weights="int8")
+    g = G(csr)
+    r1 = oracle.lpa_sync(g, 0.05, 1, 4)              # l = 0 is a Pick-Less sweep
+    labels0 = np.arange(g.n, dtype=np.int32)
+    for v0, v1 in [(0, 1), (0, 300), (1000, 1777), (g.n - 50, g.n)]:
+        out, e = oracle.sweep_window(v0, v1, g.off[v0:v1 + 1], g.idx[g.off[v0]:g.off[v1]],
+                                     g.w[g.off[v0]:g.off[v1]], labels0, pl=True)
+        assert out.tolist() == r1.labels[v0:v1].tolist()
+        assert e == g.off[v1] - g.off[v0]
+        out2, _ = oracle.sweep_range(g, labels0, v0, v1, pl=True)
+        assert out2.tolist() == out.tolist()
