@@ -327,7 +327,13 @@ def run_ours(args):
             "iterations": first["iterations"], "dN": first["changed"], "edges_per_sweep": first["edges"],
             "modularity": q, "processing_rate": ws * csr.m / (ms / 1000.0),
             "roofline": roofline, "gpu_launches": int(statistics.median(s["launches"] for s in stats)) + 2,
-            "clocks": clk}
+            "clocks": clk, "probe_fallbacks": first["probe_fallbacks"],
+            "sweeps": [{"ms": round(first["iter_ms"][i], 3), "edges": first["edges"][i], "active": first["active"][i],
+                        "changed": first["changed"][i],
+                        "kernels": {lpa.KERNEL_NAMES[k]: [round(first["kernel_ms"][i][k], 3), first["kernel_active"][i][k],
+                                                          first["kernel_edges"][i][k]]
+                                    for k in range(lpa.NUM_KERNELS) if first["kernel_ms"][i][k] > 0}}
+                       for i in range(len(first["iter_ms"]))]}
 
     # end to end through the public API with host buffers
     if not args.no_e2e:

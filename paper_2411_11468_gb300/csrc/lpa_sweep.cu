@@ -133,6 +133,40 @@ __device__ __forceinline__ void group_sync()
     if (G > 1) __syncwarp(group_mask<G>());
 }
 
+// Lanes of one group (G lanes, aligned inside the warp) insert their (key, weight) pairs
+// into the group's shared table.  Before the per-lane inserts, up to kPeel rounds take the
+// key of the lowest pending lane, sum the weights of every lane holding that key with a
+// shuffle reduction and insert the sum once: after a few sweeps most neighbours of a vertex
+// share a handful of labels, and same-slot atomics would otherwise serialise.  Integer
+// weights keep every partial sum exact, so the table contents do not depend on the order.
+constexpr int kPeel = 3;
+
+template <int G, bool SHARED>
+__device__ __forceinline__ void group_insert(int32_t *Hk, float *Hv, int stride, uint32_t p1, uint32_t b,
+                                             bool has, int32_t k, float w, unsigned &fb)
+{
+    if (G >= 2) {
+        const unsigned gm = group_mask<G>();
+        const int lane = threadIdx.x & 31;
+        unsigned pend = __ballot_sync(gm, has);
+#pragma unroll 1
+        for (int r = 0; r < kPeel && pend; ++r) {
+            const int leader = __ffs(pend) - 1;
+            const int32_t kl = __shfl_sync(gm, k, leader);
+            const bool mine = has && k == kl;
+            const unsigned same = __ballot_sync(gm, mine);
+            if (__popc(same) < 2) break;
+            float sum = mine ? w : 0.0f;
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gm, sum, o);
+            if (lane == leader) ht_accumulate<SHARED>(Hk, Hv, stride, p1, b, kl, sum, fb);
+            if (mine) has = false;
+            pend &= ~same;
+        }
+    }
+    if (has) ht_accumulate<SHARED>(Hk, Hv, stride, p1, b, k, w, fb);
+}
+
 // Warp-aggregated append of (v, c) to the synchronous mover list.  Every lane of the
 // warp must call it.
 __device__ __forceinline__ void append_movers(const SweepArgs &a, bool pred, int32_t v, int32_t c)
@@ -237,12 +271,20 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
         }
         group_sync<G>();
         cur = a.C[v];
-        for (int64_t e = o0 + lane; e < o1; e += G) {      // scan neighbours
-            const int32_t j = a.idx[e];
-            if (j == v) continue;                           // skip self-loops
-            const int32_t k = a.C[j];
-            const float wv = a.w ? a.w[e] : 1.0f;
-            ht_accumulate<(G > 1)>(Hk, Hv, stride, p1, b, k, wv, fb);
+        for (int64_t eb = o0; eb < o1; eb += G) {          // scan neighbours
+            const int64_t e = eb + lane;
+            bool has = e < o1;
+            int32_t k = 0;
+            float wv = 0.0f;
+            if (has) {
+                const int32_t j = a.idx[e];
+                has = (j != v);                             // skip self-loops
+                if (has) {
+                    k = a.C[j];
+                    wv = a.w ? a.w[e] : 1.0f;
+                }
+            }
+            group_insert<G, (G > 1)>(Hk, Hv, stride, p1, b, has, k, wv, fb);
         }
         group_sync<G>();
         unsigned long long best = 0;
@@ -315,12 +357,20 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
     __syncthreads();
     const int32_t cur = a.C[v];
     unsigned fb = 0;
-    for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) {
-        const int32_t j = a.idx[e];
-        if (j == v) continue;
-        const int32_t k = a.C[j];
-        const float wv = a.w ? a.w[e] : 1.0f;
-        ht_accumulate<true>(Hk, Hv, 1, p1, b, k, wv, fb);
+    for (int64_t eb = o0 + (threadIdx.x & ~31); eb < o1; eb += TPB) {
+        const int64_t e = eb + (threadIdx.x & 31);
+        bool has = e < o1;
+        int32_t k = 0;
+        float wv = 0.0f;
+        if (has) {
+            const int32_t j = a.idx[e];
+            has = (j != v);
+            if (has) {
+                k = a.C[j];
+                wv = a.w ? a.w[e] : 1.0f;
+            }
+        }
+        group_insert<32, true>(Hk, Hv, 1, p1, b, has, k, wv, fb);
     }
     if (fb) atomicAdd(&s_fb, fb);
     __syncthreads();
@@ -398,12 +448,20 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a)
     float *Hv = h.tab_v + h.hub_tab[hh];
     const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
     unsigned fb = 0;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
-        const int32_t j = a.idx[e];
-        if (j == v) continue;
-        const int32_t k = a.C[j];
-        const float wv = a.w ? a.w[e] : 1.0f;
-        ht_accumulate<true>(Hk, Hv, 1, p1, b, k, wv, fb);
+    for (int64_t eb = e0 + (threadIdx.x & ~31); eb < e1; eb += TPB) {
+        const int64_t e = eb + (threadIdx.x & 31);
+        bool has = e < e1;
+        int32_t k = 0;
+        float wv = 0.0f;
+        if (has) {
+            const int32_t j = a.idx[e];
+            has = (j != v);
+            if (has) {
+                k = a.C[j];
+                wv = a.w ? a.w[e] : 1.0f;
+            }
+        }
+        group_insert<32, true>(Hk, Hv, 1, p1, b, has, k, wv, fb);
     }
     if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
 }
