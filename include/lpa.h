@@ -75,9 +75,9 @@ extern "C" {
 #define LPA_K_HUB_BEGIN   5   /* hubs: take the processed flags                        */
 #define LPA_K_HUB_ACC     6   /* hubs: several blocks accumulate into an HBM table     */
 #define LPA_K_HUB_ARGMAX  7   /* hubs: max-reduce and clear the HBM table              */
-#define LPA_K_HUB_MOVE    8   /* hubs: move and mark neighbours                        */
+#define LPA_K_HUB_MOVE    8   /* hubs: move decision                                   */
 #define LPA_K_APPLY       9   /* synchronous mode: publish the sweep's new labels      */
-#define LPA_K_OTHER      10   /* initialisation and bookkeeping                        */
+#define LPA_K_HUB_MARK   10   /* hubs: mark the neighbours of hubs that moved          */
 
 typedef struct lpa_stats {
     /* input */
@@ -102,11 +102,14 @@ typedef struct lpa_stats {
 } lpa_stats;
 
 /* Degree-bucket configuration.  A vertex of degree D is handled by the first bucket
- * whose limit is >= D; vertices above cta_large_max are hubs.  Limits must increase
- * and each smem table must fit: group_max <= 255, warp_max <= 2047,
- * cta_max <= 8191, cta_large_max <= 16383. */
+ * whose limit is >= D; vertices above cta_large_max are hubs.  Limits must not decrease.
+ * Shared-memory tables have capacity nextPow2(D << smem_table_shift) - 1 (shift 0 is the
+ * paper's nextPow2(D) - 1, shift 1 keeps the load factor at or below one half); each
+ * bucket's table, sized for its largest degree, must fit in shared memory, else
+ * lpa_set_tuning returns LPA_EINVAL.  Hub tables live in HBM with capacity
+ * nextPow2(D << hub_table_shift) - 1. */
 typedef struct lpa_tuning {
-    int32_t thread_max;       /* thread per vertex for 1 <= D <= thread_max (<= 15)      */
+    int32_t thread_max;       /* thread per vertex for 1 <= D <= thread_max               */
     int32_t group_max;        /* group of group_lanes lanes per vertex                   */
     int32_t group_lanes;      /* 2, 4, 8 or 16                                           */
     int32_t warp_max;         /* warp per vertex                                         */
@@ -115,8 +118,9 @@ typedef struct lpa_tuning {
     int32_t cta_large_max;    /* block of cta_large_threads per vertex, large smem table */
     int32_t cta_large_threads;
     int32_t hub_chunk;        /* CSR entries per block in the hub accumulate kernel     */
-    int32_t hub_table_shift;  /* hub table capacity = nextPow2(D << shift) - 1 (0 = paper) */
-    int32_t reserved[6];
+    int32_t hub_table_shift;  /* 0..3                                                    */
+    int32_t smem_table_shift; /* 0..2                                                    */
+    int32_t reserved[5];
 } lpa_tuning;
 
 typedef struct lpa_graph lpa_graph;

@@ -319,6 +319,7 @@ struct lpa_graph {
     int64_t n_chunks = 0, n_slices = 0, table_slots = 0;
     int32_t *tab_k = nullptr;
     float *tab_v = nullptr;
+    int32_t *used_list = nullptr;
     int next_iter = 0;
     int64_t bytes = 0, bucket_bytes = 0;
     std::vector<cudaEvent_t> events;
@@ -356,31 +357,42 @@ lpa_tuning default_tuning()
     t.warp_max = 255;
     t.cta_max = 4095;
     t.cta_threads = 512;
-    t.cta_large_max = 16383;
+    t.cta_large_max = 8191;
     t.cta_large_threads = 1024;
     t.hub_chunk = 8192;
     t.hub_table_shift = 1;
+    t.smem_table_shift = 1;
     return t;
+}
+
+// smem slots of a bucket whose largest degree is dmax: capacity(dmax << shift) + 1
+int64_t slots_for(int64_t dmax, int shift)
+{
+    return (int64_t)1 << capacity_bits(std::max<int64_t>(dmax, 1) << shift);
 }
 
 int check_tuning(const lpa_tuning &t)
 {
     auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
-    if (t.thread_max < 0 || t.thread_max > 15) return LPA_EINVAL;
-    if (t.group_max < t.thread_max || t.group_max > 255) return LPA_EINVAL;
+    if (t.smem_table_shift < 0 || t.smem_table_shift > 2) return LPA_EINVAL;
+    if (t.hub_table_shift < 0 || t.hub_table_shift > 3) return LPA_EINVAL;
+    const int sh = t.smem_table_shift;
+    if (t.thread_max < 0 || slots_for(t.thread_max, sh) > 16) return LPA_EINVAL;
+    if (t.group_max < t.thread_max || t.warp_max < t.group_max || t.cta_max < t.warp_max ||
+        t.cta_large_max < t.cta_max)
+        return LPA_EINVAL;
     if (!(t.group_lanes == 2 || t.group_lanes == 4 || t.group_lanes == 8 || t.group_lanes == 16)) return LPA_EINVAL;
-    if (t.warp_max < t.group_max || t.warp_max > 2047) return LPA_EINVAL;
-    if (t.cta_max < t.warp_max || t.cta_max > 8191) return LPA_EINVAL;
-    if (t.cta_large_max < t.cta_max || t.cta_large_max > 16383) return LPA_EINVAL;
     if (!pow2(t.cta_threads) || t.cta_threads < 128 || t.cta_threads > 1024) return LPA_EINVAL;
     if (!pow2(t.cta_large_threads) || t.cta_large_threads < 128 || t.cta_large_threads > 1024) return LPA_EINVAL;
     if (t.hub_chunk < 256 || t.hub_chunk > (1 << 24)) return LPA_EINVAL;
-    if (t.hub_table_shift < 0 || t.hub_table_shift > 3) return LPA_EINVAL;
+    const int64_t smem = (int64_t)max_dynamic_smem();
+    const int64_t bytes_group = (256 / t.group_lanes) * slots_for(t.group_max, sh) * 8;
+    const int64_t bytes_warp = 8 * slots_for(t.warp_max, sh) * 8;
+    const int64_t bytes_cta = slots_for(t.cta_max, sh) * 8;
+    const int64_t bytes_large = slots_for(t.cta_large_max, sh) * 8;
+    if (bytes_group > smem || bytes_warp > smem || bytes_cta > smem || bytes_large > smem) return LPA_EINVAL;
     return LPA_OK;
 }
-
-// smem slots for a bucket whose largest degree is dmax: capacity + 1 (a power of two)
-int slots_for(int dmax) { return (int)((1u << capacity_bits(dmax < 1 ? 1 : dmax))); }
 
 void free_buckets(lpa_graph *g)
 {
@@ -392,6 +404,8 @@ void free_buckets(lpa_graph *g)
     g->tab_k = nullptr;
     dfree(g->tab_v);
     g->tab_v = nullptr;
+    dfree(g->used_list);
+    g->used_list = nullptr;
     g->hub = HubArgs{};
     g->n_chunks = g->n_slices = g->table_slots = 0;
     g->bucket_bytes = 0;
@@ -475,36 +489,36 @@ int build_buckets(lpa_graph *g)
         return LPA_ECUDA;
     }
     const int64_t chunk = g->tuning.hub_chunk;
-    const int64_t slice = 8192;
     std::vector<uint32_t> p1((size_t)H), bb((size_t)H);
-    std::vector<int64_t> tab((size_t)H);
-    std::vector<int32_t> ch, sh;
-    std::vector<int64_t> ce0, ce1, ss0, ss1;
-    int64_t slots = 0;
+    std::vector<int64_t> tab((size_t)H), ubase((size_t)H);
+    std::vector<int32_t> ch, sh, sj;
+    std::vector<int64_t> ce0, ce1;
+    int64_t slots = 0, used_total = 0;
     for (int64_t h = 0; h < H; ++h) {
         const int64_t D = o1[h] - o0[h];
         const int64_t want = std::min<int64_t>(D << g->tuning.hub_table_shift, (int64_t)1 << 31);
         bb[h] = capacity_bits(want);
         p1[h] = (uint32_t)(((int64_t)1 << bb[h]) - 1);
         tab[h] = slots;
+        ubase[h] = used_total;
         for (int64_t e0 = o0[h]; e0 < o1[h]; e0 += chunk) {
             ch.push_back((int32_t)h);
             ce0.push_back(e0);
             ce1.push_back(std::min(o1[h], e0 + chunk));
         }
-        for (int64_t s0 = 0; s0 < (int64_t)p1[h]; s0 += slice) {
+        for (int64_t j = 0; j * kHubSlice < D; ++j) {   // at most D distinct labels
             sh.push_back((int32_t)h);
-            ss0.push_back(slots + s0);
-            ss1.push_back(slots + std::min<int64_t>(p1[h], s0 + slice));
+            sj.push_back((int32_t)j);
         }
         slots += p1[h];
+        used_total += D;
     }
     g->n_chunks = (int64_t)ch.size();
     g->n_slices = (int64_t)sh.size();
     g->table_slots = slots;
     // one allocation for the hub arrays (8-byte fields first)
-    const size_t n8 = (size_t)(H /*tab*/ + H /*best*/ + 2 * g->n_chunks + 2 * g->n_slices);
-    const size_t n4 = (size_t)(H /*v*/ + H /*p1*/ + H /*b*/ + g->n_chunks + g->n_slices);
+    const size_t n8 = (size_t)(3 * H /*tab, best, ubase*/ + 2 * g->n_chunks);
+    const size_t n4 = (size_t)(4 * H /*v, p1, b, used*/ + g->n_chunks + 2 * g->n_slices);
     const size_t bytes = n8 * 8 + n4 * 4 + (size_t)H;
     unsigned char *mem = nullptr;
     LPA_CHECK(dalloc(g, &mem, bytes, &g->bucket_bytes));
@@ -517,30 +531,33 @@ int build_buckets(lpa_graph *g)
     };
     int64_t *d_tab = (int64_t *)take(H * 8);
     unsigned long long *d_best = (unsigned long long *)take(H * 8);
+    int64_t *d_ubase = (int64_t *)take(H * 8);
     int64_t *d_ce0 = (int64_t *)take(g->n_chunks * 8);
     int64_t *d_ce1 = (int64_t *)take(g->n_chunks * 8);
-    int64_t *d_ss0 = (int64_t *)take(g->n_slices * 8);
-    int64_t *d_ss1 = (int64_t *)take(g->n_slices * 8);
     int32_t *d_hv = (int32_t *)take(H * 4);
     uint32_t *d_p1 = (uint32_t *)take(H * 4);
     uint32_t *d_b = (uint32_t *)take(H * 4);
+    uint32_t *d_used = (uint32_t *)take(H * 4);
     int32_t *d_ch = (int32_t *)take(g->n_chunks * 4);
     int32_t *d_sh = (int32_t *)take(g->n_slices * 4);
+    int32_t *d_sj = (int32_t *)take(g->n_slices * 4);
     uint8_t *d_act = (uint8_t *)take(H);
     LPA_CUDA(cudaMemcpyAsync(d_tab, tab.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_ubase, ubase.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
     LPA_CUDA(cudaMemcpyAsync(d_ce0, ce0.data(), g->n_chunks * 8, cudaMemcpyHostToDevice, g->stream));
     LPA_CUDA(cudaMemcpyAsync(d_ce1, ce1.data(), g->n_chunks * 8, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_ss0, ss0.data(), g->n_slices * 8, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_ss1, ss1.data(), g->n_slices * 8, cudaMemcpyHostToDevice, g->stream));
     LPA_CUDA(cudaMemcpyAsync(d_hv, hv.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
     LPA_CUDA(cudaMemcpyAsync(d_p1, p1.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
     LPA_CUDA(cudaMemcpyAsync(d_b, bb.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
     LPA_CUDA(cudaMemcpyAsync(d_ch, ch.data(), g->n_chunks * 4, cudaMemcpyHostToDevice, g->stream));
     LPA_CUDA(cudaMemcpyAsync(d_sh, sh.data(), g->n_slices * 4, cudaMemcpyHostToDevice, g->stream));
+    LPA_CUDA(cudaMemcpyAsync(d_sj, sj.data(), g->n_slices * 4, cudaMemcpyHostToDevice, g->stream));
     LPA_CUDA(cudaMemsetAsync(d_act, 0, H, g->stream));
     LPA_CUDA(cudaMemsetAsync(d_best, 0, H * 8, g->stream));
+    LPA_CUDA(cudaMemsetAsync(d_used, 0, H * 4, g->stream));
     LPA_CHECK(dalloc(g, &g->tab_k, (size_t)slots, &g->bucket_bytes));
     LPA_CHECK(dalloc(g, &g->tab_v, (size_t)slots, &g->bucket_bytes));
+    LPA_CHECK(dalloc(g, &g->used_list, (size_t)used_total, &g->bucket_bytes));
     LPA_CUDA(launch_hub_table_clear(g->tab_k, g->tab_v, slots, g->stream));
     HubArgs &ha = g->hub;
     ha.hub_v = d_hv;
@@ -549,12 +566,14 @@ int build_buckets(lpa_graph *g)
     ha.hub_tab = d_tab;
     ha.hub_act = d_act;
     ha.hub_best = d_best;
+    ha.hub_used = d_used;
+    ha.used_list = g->used_list;
+    ha.used_base = d_ubase;
     ha.chunk_h = d_ch;
     ha.chunk_e0 = d_ce0;
     ha.chunk_e1 = d_ce1;
     ha.slice_h = d_sh;
-    ha.slice_s0 = d_ss0;
-    ha.slice_s1 = d_ss1;
+    ha.slice_j = d_sj;
     ha.tab_k = g->tab_k;
     ha.tab_v = g->tab_v;
     ha.n_hubs = (int32_t)H;
@@ -647,7 +666,7 @@ const char *lpa_last_error(void) { return t_error.c_str(); }
 const char *lpa_kernel_name(int slot)
 {
     static const char *names[LPA_NUM_KERNELS] = {"thread", "group", "warp", "cta", "cta_large", "hub_begin",
-                                                 "hub_acc", "hub_argmax", "hub_move", "apply", "other", "unused"};
+                                                 "hub_acc", "hub_argmax", "hub_move", "apply", "hub_mark", "unused"};
     if (slot < 0 || slot >= LPA_NUM_KERNELS) return "";
     return names[slot];
 }
@@ -796,14 +815,10 @@ int lpa_set_tuning(lpa_graph *g, const lpa_tuning *t)
 {
     if (!g || !t) return LPA_EINVAL;
     if (check_tuning(*t) != LPA_OK) {
-        set_error("lpa_set_tuning: thresholds out of range or not increasing");
+        set_error("lpa_set_tuning: thresholds out of range, decreasing, or a table does not fit in shared memory");
         return LPA_EINVAL;
     }
     DeviceGuard dg(g->device);
-    if (t->cta_large_max > 8191 && max_dynamic_smem() < (size_t)16384 * 8) {
-        set_error("lpa_set_tuning: cta_large table does not fit in shared memory");
-        return LPA_EINVAL;
-    }
     g->tuning = *t;
     return build_buckets(g);
 }
@@ -993,6 +1008,8 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
         a.fallbacks = g->fallbacks;
         a.pl = pl ? 1 : 0;
         a.async_mode = async_mode ? 1 : 0;
+        a.tshift = t.smem_table_shift;
+        const int sh = t.smem_table_shift;
 
         size_t ie0 = evn++, ie1 = evn++;
         if (!event_at(g, ie1)) return LPA_ECUDA;
@@ -1021,27 +1038,29 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
         if (bs[B_GROUP + 1] > bs[B_GROUP])
             LPA_CUDA(timed(LPA_K_GROUP, [&] {
                 return launch_group_bucket(L + bs[B_GROUP], bs[B_GROUP + 1] - bs[B_GROUP], a, t.group_lanes,
-                                           slots_for(t.group_max), s);
+                                           (int)slots_for(t.group_max, sh), s);
             }));
         if (bs[B_WARP + 1] > bs[B_WARP])
             LPA_CUDA(timed(LPA_K_WARP, [&] {
-                return launch_warp_bucket(L + bs[B_WARP], bs[B_WARP + 1] - bs[B_WARP], a, slots_for(t.warp_max), s);
+                return launch_warp_bucket(L + bs[B_WARP], bs[B_WARP + 1] - bs[B_WARP], a,
+                                          (int)slots_for(t.warp_max, sh), s);
             }));
         if (bs[B_CTA + 1] > bs[B_CTA])
             LPA_CUDA(timed(LPA_K_CTA, [&] {
                 return launch_cta_bucket(L + bs[B_CTA], bs[B_CTA + 1] - bs[B_CTA], a, t.cta_threads,
-                                         slots_for(t.cta_max), LPA_K_CTA, s);
+                                         (int)slots_for(t.cta_max, sh), LPA_K_CTA, s);
             }));
         if (bs[B_CTA_LARGE + 1] > bs[B_CTA_LARGE])
             LPA_CUDA(timed(LPA_K_CTA_LARGE, [&] {
                 return launch_cta_bucket(L + bs[B_CTA_LARGE], bs[B_CTA_LARGE + 1] - bs[B_CTA_LARGE], a,
-                                         t.cta_large_threads, slots_for(t.cta_large_max), LPA_K_CTA_LARGE, s);
+                                         t.cta_large_threads, (int)slots_for(t.cta_large_max, sh), LPA_K_CTA_LARGE, s);
             }));
         if (g->hub.n_hubs > 0) {
             LPA_CUDA(timed(LPA_K_HUB_BEGIN, [&] { return launch_hub_begin(g->hub, a, s); }));
             LPA_CUDA(timed(LPA_K_HUB_ACC, [&] { return launch_hub_acc(g->hub, a, g->n_chunks, 1024, s); }));
             LPA_CUDA(timed(LPA_K_HUB_ARGMAX, [&] { return launch_hub_argmax(g->hub, a, g->n_slices, s); }));
             LPA_CUDA(timed(LPA_K_HUB_MOVE, [&] { return launch_hub_move(g->hub, a, s); }));
+            LPA_CUDA(timed(LPA_K_HUB_MARK, [&] { return launch_hub_mark(g->hub, a, g->n_chunks, s); }));
         }
         if (!async_mode) {
             LPA_CUDA(timed(LPA_K_APPLY, [&] { return launch_apply(a, g->n, s); }));

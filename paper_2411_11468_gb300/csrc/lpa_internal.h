@@ -32,6 +32,7 @@ struct SweepArgs {
     unsigned long long *fallbacks;
     int32_t pl;                // Pick-Less active on this sweep
     int32_t async_mode;        // 1: write labels in place (ASYNC), 0: record movers (SYNC)
+    int32_t tshift;            // smem table capacity = nextPow2(D << tshift) - 1
 };
 
 // Hub-bucket device arrays.
@@ -40,18 +41,22 @@ struct HubArgs {
     const uint32_t *hub_p1;    // [H] table capacity (2^b - 1)
     const uint32_t *hub_b;     // [H] b
     const int64_t *hub_tab;    // [H] first slot of the hub's table
-    uint8_t *hub_act;          // [H] processed-flag snapshot of this sweep
+    uint8_t *hub_act;          // [H] this sweep: 0 processed earlier, 1 processing, 2 moved
     unsigned long long *hub_best;  // [H] packed (weight, ~label) maximum
-    const int32_t *chunk_h;    // [n_chunks] hub of each accumulate block
+    uint32_t *hub_used;        // [H] number of table slots taken this sweep
+    int32_t *used_list;        // slots taken, hub h at used_base[h] (at most D_h entries)
+    const int64_t *used_base;  // [H]
+    const int32_t *chunk_h;    // [n_chunks] hub of each accumulate / mark block
     const int64_t *chunk_e0;   // [n_chunks] first CSR entry
     const int64_t *chunk_e1;   // [n_chunks] end CSR entry
     const int32_t *slice_h;    // [n_slices] hub of each argmax block
-    const int64_t *slice_s0;   // [n_slices] first table slot (absolute)
-    const int64_t *slice_s1;   // [n_slices] end table slot (absolute)
+    const int32_t *slice_j;    // [n_slices] slice index within the hub's used list
     int32_t *tab_k;            // hub table keys
     float *tab_v;              // hub table values
     int32_t n_hubs;
 };
+
+constexpr int kHubSlice = 4096;   // used-list entries per argmax block
 
 // Launch helpers implemented in lpa_sweep.cu.
 cudaError_t sweep_init_constants();
@@ -68,6 +73,7 @@ cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunk
                            cudaStream_t s);
 cudaError_t launch_hub_argmax(const HubArgs &h, const SweepArgs &a, int64_t n_slices, cudaStream_t s);
 cudaError_t launch_hub_move(const HubArgs &h, const SweepArgs &a, cudaStream_t s);
+cudaError_t launch_hub_mark(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, cudaStream_t s);
 cudaError_t launch_apply(const SweepArgs &a, int64_t n, cudaStream_t s);
 cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, cudaStream_t s);
 size_t max_dynamic_smem();

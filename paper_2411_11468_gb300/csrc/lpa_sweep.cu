@@ -57,9 +57,11 @@ __device__ __forceinline__ int32_t unpack_key(unsigned long long p)
 __device__ __forceinline__ uint32_t cap_bits(uint32_t D) { return 32u - __clz(D); }
 __device__ __forceinline__ uint32_t cap_of_bits(uint32_t b) { return b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u); }
 
-// One slot attempt of Algorithm 2: take slot s if it is empty or already holds k.
-template <bool SHARED>
-__device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32_t k, float v)
+// One slot attempt of Algorithm 2: take slot s if it is empty or already holds k.  With
+// TRACK, a slot taken from empty is appended to the table's used list.
+template <bool SHARED, bool TRACK>
+__device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32_t k, float v, uint32_t *ucnt,
+                                         int32_t *ulist)
 {
     if (!SHARED) {                                    // single owner: plain accesses
         int32_t kk = Hk[s];
@@ -72,8 +74,13 @@ __device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32
     }
     int32_t kk = *((volatile int32_t *)(Hk + s));
     if (kk == kEmpty) {
-        int32_t old = atomicCAS(Hk + s, kEmpty, k);
-        kk = (old == kEmpty) ? k : old;
+        const int32_t old = atomicCAS(Hk + s, kEmpty, k);
+        if (old == kEmpty) {
+            kk = k;
+            if (TRACK) ulist[atomicAdd(ucnt, 1u)] = (int32_t)s;
+        } else {
+            kk = old;
+        }
     }
     if (kk == k) {
         atomicAdd(Hv + s, v);
@@ -84,9 +91,10 @@ __device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32
 
 // hashtableAccumulate (Algorithm 2) with i and delta kept reduced mod p1 (same slots),
 // then a linear scan from the last probed slot once the probe budget is spent.
-template <bool SHARED>
+template <bool SHARED, bool TRACK = false>
 __device__ __forceinline__ void ht_accumulate(int32_t *Hk, float *Hv, int stride, uint32_t p1, uint32_t b,
-                                              int32_t k, float v, unsigned &fallbacks)
+                                              int32_t k, float v, unsigned &fallbacks, uint32_t *ucnt = nullptr,
+                                              int32_t *ulist = nullptr)
 {
     const uint32_t uk = (uint32_t)k;
     uint32_t i = mod_mersenne(uk, b, p1);
@@ -96,7 +104,7 @@ __device__ __forceinline__ void ht_accumulate(int32_t *Hk, float *Hv, int stride
 #pragma unroll 1
     for (int t = 0; t < kMaxRetries; ++t) {
         s = i;
-        if (try_slot<SHARED>(Hk, Hv, (size_t)s * stride, k, v)) return;
+        if (try_slot<SHARED, TRACK>(Hk, Hv, (size_t)s * stride, k, v, ucnt, ulist)) return;
         if (step == 0xFFFFFFFFu) {
             uint32_t q = mod_mersenne(uk, b + 1, 2u * p1 + 1u);
             if (q >= p1) q -= p1;
@@ -115,7 +123,7 @@ __device__ __forceinline__ void ht_accumulate(int32_t *Hk, float *Hv, int stride
     for (uint32_t u = 1; u <= p1; ++u) {
         uint32_t q = s + u;
         if (q >= p1) q -= p1;
-        if (try_slot<SHARED>(Hk, Hv, (size_t)q * stride, k, v)) return;
+        if (try_slot<SHARED, TRACK>(Hk, Hv, (size_t)q * stride, k, v, ucnt, ulist)) return;
     }
 }
 
@@ -141,9 +149,10 @@ __device__ __forceinline__ void group_sync()
 // weights keep every partial sum exact, so the table contents do not depend on the order.
 constexpr int kPeel = 3;
 
-template <int G, bool SHARED>
+template <int G, bool SHARED, bool TRACK = false>
 __device__ __forceinline__ void group_insert(int32_t *Hk, float *Hv, int stride, uint32_t p1, uint32_t b,
-                                             bool has, int32_t k, float w, unsigned &fb)
+                                             bool has, int32_t k, float w, unsigned &fb, uint32_t *ucnt = nullptr,
+                                             int32_t *ulist = nullptr)
 {
     if (G >= 2) {
         const unsigned gm = group_mask<G>();
@@ -159,12 +168,12 @@ __device__ __forceinline__ void group_insert(int32_t *Hk, float *Hv, int stride,
             float sum = mine ? w : 0.0f;
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gm, sum, o);
-            if (lane == leader) ht_accumulate<SHARED>(Hk, Hv, stride, p1, b, kl, sum, fb);
+            if (lane == leader) ht_accumulate<SHARED, TRACK>(Hk, Hv, stride, p1, b, kl, sum, fb, ucnt, ulist);
             if (mine) has = false;
             pend &= ~same;
         }
     }
-    if (has) ht_accumulate<SHARED>(Hk, Hv, stride, p1, b, k, w, fb);
+    if (has) ht_accumulate<SHARED, TRACK>(Hk, Hv, stride, p1, b, k, w, fb, ucnt, ulist);
 }
 
 // Warp-aggregated append of (v, c) to the synchronous mover list.  Every lane of the
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
         o0 = a.off[v];
         o1 = a.off[v + 1];
         const uint32_t D = (uint32_t)(o1 - o0);
-        const uint32_t b = cap_bits(D);
+        const uint32_t b = cap_bits(D << a.tshift);        // capacity >= D << tshift
         const uint32_t p1 = cap_of_bits(b);
         for (uint32_t s = lane; s < p1; s += G) {          // hashtableClear
             Hk[(size_t)s * stride] = kEmpty;
@@ -348,7 +357,7 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
 
     const int64_t o0 = a.off[v], o1 = a.off[v + 1];
     const uint32_t D = (uint32_t)(o1 - o0);
-    const uint32_t b = cap_bits(D);
+    const uint32_t b = cap_bits(D << a.tshift);
     const uint32_t p1 = cap_of_bits(b);
     for (uint32_t s = threadIdx.x; s < p1; s += TPB) {
         Hk[s] = kEmpty;
@@ -425,7 +434,10 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
 }
 
 // ---------------------------------------------------------------------------------
-// Hubs: tables in HBM shared by several blocks.
+// Hubs: tables in HBM shared by several blocks.  Per sweep: begin (take the processed
+// flag), accumulate (blocks over CSR chunks), argmax (blocks over the used-slot list;
+// the slots are cleared for the next sweep), move (one thread per hub), mark (blocks
+// over CSR chunks of the hubs that moved).
 __global__ void k_hub_begin(HubArgs h, SweepArgs a)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -435,6 +447,7 @@ __global__ void k_hub_begin(HubArgs h, SweepArgs a)
     if (act) a.flag_cur[v] = 0;                       // mark processed
     h.hub_act[t] = act;
     h.hub_best[t] = 0ull;
+    h.hub_used[t] = 0u;
 }
 
 template <int TPB>
@@ -446,6 +459,8 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a)
     const uint32_t p1 = h.hub_p1[hh], b = h.hub_b[hh];
     int32_t *Hk = h.tab_k + h.hub_tab[hh];
     float *Hv = h.tab_v + h.hub_tab[hh];
+    uint32_t *ucnt = h.hub_used + hh;
+    int32_t *ulist = h.used_list + h.used_base[hh];
     const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
     unsigned fb = 0;
     for (int64_t eb = e0 + (threadIdx.x & ~31); eb < e1; eb += TPB) {
@@ -461,7 +476,7 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a)
                 wv = a.w ? a.w[e] : 1.0f;
             }
         }
-        group_insert<32, true>(Hk, Hv, 1, p1, b, has, k, wv, fb);
+        group_insert<32, true, true>(Hk, Hv, 1, p1, b, has, k, wv, fb, ucnt, ulist);
     }
     if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
 }
@@ -472,16 +487,21 @@ __global__ void __launch_bounds__(TPB) k_hub_argmax(HubArgs h, SweepArgs a)
     __shared__ unsigned long long s_best[TPB / 32];
     const int hh = h.slice_h[blockIdx.x];
     if (!h.hub_act[hh]) return;
-    const int64_t s0 = h.slice_s0[blockIdx.x], s1 = h.slice_s1[blockIdx.x];
+    const int64_t lo = (int64_t)h.slice_j[blockIdx.x] * kHubSlice;
+    const int64_t cnt = h.hub_used[hh];
+    if (lo >= cnt) return;                             // uniform for the block
+    const int64_t hi = lo + kHubSlice < cnt ? lo + kHubSlice : cnt;
+    int32_t *Hk = h.tab_k + h.hub_tab[hh];
+    float *Hv = h.tab_v + h.hub_tab[hh];
+    const int32_t *ulist = h.used_list + h.used_base[hh];
     unsigned long long best = 0;
-    for (int64_t s = s0 + threadIdx.x; s < s1; s += TPB) {
-        const int32_t kk = h.tab_k[s];
-        if (kk != kEmpty) {
-            const unsigned long long pk = pack_kv(h.tab_v[s], kk);
-            best = pk > best ? pk : best;
-            h.tab_k[s] = kEmpty;                       // leave the table clear for the next sweep
-            h.tab_v[s] = 0.0f;
-        }
+    for (int64_t q = lo + threadIdx.x; q < hi; q += TPB) {
+        const int32_t s = ulist[q];
+        const int32_t kk = Hk[s];
+        const unsigned long long pk = pack_kv(Hv[s], kk);
+        best = pk > best ? pk : best;
+        Hk[s] = kEmpty;                                // leave the table clear for the next sweep
+        Hv[s] = 0.0f;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -496,11 +516,10 @@ __global__ void __launch_bounds__(TPB) k_hub_argmax(HubArgs h, SweepArgs a)
     }
 }
 
-template <int TPB>
-__global__ void __launch_bounds__(TPB) k_hub_move(HubArgs h, SweepArgs a)
+__global__ void k_hub_move(HubArgs h, SweepArgs a)
 {
-    const int hh = blockIdx.x;
-    if (!h.hub_act[hh]) return;
+    const int hh = blockIdx.x * blockDim.x + threadIdx.x;
+    if (hh >= h.n_hubs || !h.hub_act[hh]) return;
     const int32_t v = h.hub_v[hh];
     const unsigned long long best = h.hub_best[hh];
     const int32_t cur = a.C[v];
@@ -510,31 +529,32 @@ __global__ void __launch_bounds__(TPB) k_hub_move(HubArgs h, SweepArgs a)
         cstar = unpack_key(best);
         moved = (cstar != cur) && (!a.pl || cstar < cur);
     }
-    const int64_t o0 = a.off[v], o1 = a.off[v + 1];
+    const unsigned long long D = (unsigned long long)(a.off[v + 1] - a.off[v]);
+    unsigned long long *c = a.ctr + LPA_K_HUB_ACC * kCtrFields;
+    atomicAdd(c + CTR_ACTIVE, 1ull);
+    atomicAdd(c + CTR_EDGES, D);
     if (moved) {
-        if (threadIdx.x == 0) {
-            if (a.async_mode) {
-                a.C[v] = cstar;
-                __threadfence();
-            } else {
-                const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
-                a.mover_v[pos] = v;
-                a.mover_c[pos] = cstar;
-            }
+        if (a.async_mode) {
+            a.C[v] = cstar;
+            __threadfence();
+        } else {
+            const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
+            a.mover_v[pos] = v;
+            a.mover_c[pos] = cstar;
         }
-        __syncthreads();
-        for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
+        h.hub_act[hh] = 2;
+        atomicAdd(c + CTR_MOVED, 1ull);
+        atomicAdd(c + CTR_MARKS, D);
     }
-    if (threadIdx.x == 0) {
-        const int kslot = LPA_K_HUB_ACC;
-        unsigned long long *c = a.ctr + kslot * kCtrFields;
-        atomicAdd(c + CTR_ACTIVE, 1ull);
-        atomicAdd(c + CTR_EDGES, (unsigned long long)(o1 - o0));
-        if (moved) {
-            atomicAdd(c + CTR_MOVED, 1ull);
-            atomicAdd(c + CTR_MARKS, (unsigned long long)(o1 - o0));
-        }
-    }
+}
+
+template <int TPB>
+__global__ void __launch_bounds__(TPB) k_hub_mark(HubArgs h, SweepArgs a)
+{
+    const int hh = h.chunk_h[blockIdx.x];
+    if (h.hub_act[hh] != 2) return;
+    const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += TPB) a.flag_next[a.idx[e]] = 1;
 }
 
 // Synchronous mode: publish the labels recorded during the sweep.
@@ -674,7 +694,14 @@ cudaError_t launch_hub_argmax(const HubArgs &h, const SweepArgs &a, int64_t n_sl
 cudaError_t launch_hub_move(const HubArgs &h, const SweepArgs &a, cudaStream_t s)
 {
     if (h.n_hubs <= 0) return cudaSuccess;
-    k_hub_move<1024><<<h.n_hubs, 1024, 0, s>>>(h, a);
+    k_hub_move<<<(h.n_hubs + 127) / 128, 128, 0, s>>>(h, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hub_mark(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, cudaStream_t s)
+{
+    if (n_chunks <= 0) return cudaSuccess;
+    k_hub_mark<512><<<(unsigned)n_chunks, 512, 0, s>>>(h, a);
     return cudaGetLastError();
 }
 

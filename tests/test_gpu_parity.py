@@ -21,6 +21,8 @@ pytestmark = pytest.mark.gpu
 # thresholds low enough that small graphs reach every bucket, hubs included
 SMALL_BUCKETS = dict(thread_max=3, group_max=7, group_lanes=4, warp_max=31, cta_max=63, cta_threads=128,
                      cta_large_max=127, cta_large_threads=256, hub_chunk=256, hub_table_shift=0)
+# the paper's table capacity nextPow2(D) - 1 everywhere (load factor up to 1, probe fallbacks)
+PAPER_TABLES = dict(SMALL_BUCKETS, smem_table_shift=0, hub_table_shift=0)
 
 
 @pytest.fixture(scope="module")
@@ -86,7 +88,8 @@ def test_sync_random_graphs_all_buckets(lpa, seed):
     n = rnd.choice([37, 200, 513, 1500])
     csr = gg.random_small(n, rnd.choice([0.01, 0.05, 0.15, 0.4]), 1000 + seed, wmax=rnd.choice([1, 4, 8]),
                           self_loops=(seed % 3 == 0))
-    check_sync_every_iteration(lpa, csr, rnd.choice([0.0, 0.05]), 20, rnd.choice([0, 2, 4]), SMALL_BUCKETS)
+    tuning = PAPER_TABLES if seed % 2 else SMALL_BUCKETS
+    check_sync_every_iteration(lpa, csr, rnd.choice([0.0, 0.05]), 20, rnd.choice([0, 2, 4]), tuning)
 
 
 @pytest.mark.parametrize("scale,weights", [(12, "int8"), (14, "unit"), (15, "int8")])
@@ -95,10 +98,10 @@ def test_sync_rmat_default_buckets(lpa, scale, weights):
     check_sync_every_iteration(lpa, csr, 0.05, 20, 4)
 
 
-@pytest.mark.parametrize("scale", [13, 15])
-def test_sync_rmat_small_buckets_with_hubs(lpa, scale):
+@pytest.mark.parametrize("scale,tables", [(13, "half"), (15, "half"), (14, "paper")])
+def test_sync_rmat_small_buckets_with_hubs(lpa, scale, tables):
     csr = gg.rmat(scale, weights="int8")
-    check_sync_every_iteration(lpa, csr, 0.05, 20, 4, SMALL_BUCKETS)
+    check_sync_every_iteration(lpa, csr, 0.05, 20, 4, SMALL_BUCKETS if tables == "half" else PAPER_TABLES)
 
 
 def test_sync_sbm_config(lpa):
@@ -239,6 +242,16 @@ def test_bucket_boundary_degrees(lpa):
         edges.append((a + 1, b + 1))
     csr = gg.from_edges(n, edges, [1 + (k % 5) for k in range(len(edges))])
     check_sync_every_iteration(lpa, csr, 0.0, 20, 4)
+
+
+def test_tuning_rejected_when_tables_do_not_fit(lpa):
+    csr = gg.rmat(10, weights="int8")
+    g = make(lpa, csr)
+    with pytest.raises(lpa.LpaError):
+        g.set_tuning(cta_large_max=16383, smem_table_shift=2)      # 64K-slot table > smem
+    with pytest.raises(lpa.LpaError):
+        g.set_tuning(warp_max=10, group_max=31)                      # decreasing limits
+    g.run()                                                          # handle still usable
 
 
 def test_invalid_graphs_rejected(lpa):
