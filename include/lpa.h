@@ -70,14 +70,15 @@ extern "C" {
 #define LPA_K_THREAD      0   /* thread per vertex, private table (lowest degrees)     */
 #define LPA_K_GROUP       1   /* small lane group per vertex, shared table in smem     */
 #define LPA_K_WARP        2   /* warp per vertex, table in smem                        */
-#define LPA_K_CTA         3   /* thread block per vertex, table in smem                */
-#define LPA_K_CTA_LARGE   4   /* thread block per vertex, large smem table             */
-#define LPA_K_HUB_BEGIN   5   /* hubs: take the processed flags                        */
-#define LPA_K_HUB_ACC     6   /* hubs: several blocks accumulate into an HBM table     */
-#define LPA_K_HUB_ARGMAX  7   /* hubs: max-reduce and clear the HBM table              */
-#define LPA_K_HUB_MOVE    8   /* hubs: move decision                                   */
-#define LPA_K_APPLY       9   /* synchronous mode: publish the sweep's new labels      */
+#define LPA_K_CTA         3   /* thread block per vertex, table in smem (tier 1)       */
+#define LPA_K_CTA_LARGE   4   /* thread block per vertex, table in smem (tier 2)       */
+#define LPA_K_CTA_XL      5   /* thread block per vertex, table in smem (tier 3)       */
+#define LPA_K_HUB_BEGIN   6   /* hubs: take the processed flags                        */
+#define LPA_K_HUB_ACC     7   /* hubs: several blocks accumulate into an HBM table     */
+#define LPA_K_HUB_CLEAR   8   /* hubs: clear the table slots used in this sweep        */
+#define LPA_K_HUB_MOVE    9   /* hubs: move decision                                   */
 #define LPA_K_HUB_MARK   10   /* hubs: mark the neighbours of hubs that moved          */
+#define LPA_K_APPLY      11   /* synchronous mode: publish the sweep's new labels      */
 
 typedef struct lpa_stats {
     /* input */
@@ -102,7 +103,7 @@ typedef struct lpa_stats {
 } lpa_stats;
 
 /* Degree-bucket configuration.  A vertex of degree D is handled by the first bucket
- * whose limit is >= D; vertices above cta_large_max are hubs.  Limits must not decrease.
+ * whose limit is >= D; vertices above cta_xl_max are hubs.  Limits must not decrease.
  * Shared-memory tables have capacity nextPow2(D << smem_table_shift) - 1 (shift 0 is the
  * paper's nextPow2(D) - 1, shift 1 keeps the load factor at or below one half); each
  * bucket's table, sized for its largest degree, must fit in shared memory, else
@@ -114,13 +115,15 @@ typedef struct lpa_tuning {
     int32_t group_lanes;      /* 2, 4, 8 or 16                                           */
     int32_t warp_max;         /* warp per vertex                                         */
     int32_t cta_max;          /* block of cta_threads per vertex, smem table             */
-    int32_t cta_threads;      /* 128, 256, 512 or 1024                                   */
-    int32_t cta_large_max;    /* block of cta_large_threads per vertex, large smem table */
+    int32_t cta_threads;      /* 64, 128, 256, 512 or 1024 (also for the other tiers)    */
+    int32_t cta_large_max;    /* block of cta_large_threads per vertex                   */
     int32_t cta_large_threads;
     int32_t hub_chunk;        /* CSR entries per block in the hub accumulate kernel     */
     int32_t hub_table_shift;  /* 0..3                                                    */
     int32_t smem_table_shift; /* 0..2                                                    */
-    int32_t reserved[5];
+    int32_t cta_xl_max;       /* block of cta_xl_threads per vertex; above: hubs         */
+    int32_t cta_xl_threads;
+    int32_t reserved[3];
 } lpa_tuning;
 
 typedef struct lpa_graph lpa_graph;

@@ -126,6 +126,7 @@ __device__ __forceinline__ int bucket_of(int64_t D, const lpa_tuning &t)
     if (D <= t.warp_max) return B_WARP;
     if (D <= t.cta_max) return B_CTA;
     if (D <= t.cta_large_max) return B_CTA_LARGE;
+    if (D <= t.cta_xl_max) return B_CTA_XL;
     return B_HUB;
 }
 
@@ -355,10 +356,12 @@ lpa_tuning default_tuning()
     t.group_max = 31;
     t.group_lanes = 8;
     t.warp_max = 255;
-    t.cta_max = 4095;
-    t.cta_threads = 512;
-    t.cta_large_max = 8191;
-    t.cta_large_threads = 1024;
+    t.cta_max = 1023;
+    t.cta_threads = 128;
+    t.cta_large_max = 4095;
+    t.cta_large_threads = 256;
+    t.cta_xl_max = 8191;
+    t.cta_xl_threads = 512;
     t.hub_chunk = 8192;
     t.hub_table_shift = 1;
     t.smem_table_shift = 1;
@@ -379,18 +382,20 @@ int check_tuning(const lpa_tuning &t)
     const int sh = t.smem_table_shift;
     if (t.thread_max < 0 || slots_for(t.thread_max, sh) > 16) return LPA_EINVAL;
     if (t.group_max < t.thread_max || t.warp_max < t.group_max || t.cta_max < t.warp_max ||
-        t.cta_large_max < t.cta_max)
+        t.cta_large_max < t.cta_max || t.cta_xl_max < t.cta_large_max)
         return LPA_EINVAL;
     if (!(t.group_lanes == 2 || t.group_lanes == 4 || t.group_lanes == 8 || t.group_lanes == 16)) return LPA_EINVAL;
-    if (!pow2(t.cta_threads) || t.cta_threads < 128 || t.cta_threads > 1024) return LPA_EINVAL;
-    if (!pow2(t.cta_large_threads) || t.cta_large_threads < 128 || t.cta_large_threads > 1024) return LPA_EINVAL;
+    for (int th : {t.cta_threads, t.cta_large_threads, t.cta_xl_threads})
+        if (!pow2(th) || th < 64 || th > 1024) return LPA_EINVAL;
     if (t.hub_chunk < 256 || t.hub_chunk > (1 << 24)) return LPA_EINVAL;
     const int64_t smem = (int64_t)max_dynamic_smem();
     const int64_t bytes_group = (256 / t.group_lanes) * slots_for(t.group_max, sh) * 8;
     const int64_t bytes_warp = 8 * slots_for(t.warp_max, sh) * 8;
     const int64_t bytes_cta = slots_for(t.cta_max, sh) * 8;
     const int64_t bytes_large = slots_for(t.cta_large_max, sh) * 8;
-    if (bytes_group > smem || bytes_warp > smem || bytes_cta > smem || bytes_large > smem) return LPA_EINVAL;
+    const int64_t bytes_xl = slots_for(t.cta_xl_max, sh) * 8;
+    if (bytes_group > smem || bytes_warp > smem || bytes_cta > smem || bytes_large > smem || bytes_xl > smem)
+        return LPA_EINVAL;
     return LPA_OK;
 }
 
@@ -665,8 +670,8 @@ const char *lpa_last_error(void) { return t_error.c_str(); }
 
 const char *lpa_kernel_name(int slot)
 {
-    static const char *names[LPA_NUM_KERNELS] = {"thread", "group", "warp", "cta", "cta_large", "hub_begin",
-                                                 "hub_acc", "hub_argmax", "hub_move", "apply", "hub_mark", "unused"};
+    static const char *names[LPA_NUM_KERNELS] = {"thread", "group", "warp", "cta", "cta_large", "cta_xl",
+                                                 "hub_begin", "hub_acc", "hub_clear", "hub_move", "hub_mark", "apply"};
     if (slot < 0 || slot >= LPA_NUM_KERNELS) return "";
     return names[slot];
 }
@@ -1055,10 +1060,15 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
                 return launch_cta_bucket(L + bs[B_CTA_LARGE], bs[B_CTA_LARGE + 1] - bs[B_CTA_LARGE], a,
                                          t.cta_large_threads, (int)slots_for(t.cta_large_max, sh), LPA_K_CTA_LARGE, s);
             }));
+        if (bs[B_CTA_XL + 1] > bs[B_CTA_XL])
+            LPA_CUDA(timed(LPA_K_CTA_XL, [&] {
+                return launch_cta_bucket(L + bs[B_CTA_XL], bs[B_CTA_XL + 1] - bs[B_CTA_XL], a, t.cta_xl_threads,
+                                         (int)slots_for(t.cta_xl_max, sh), LPA_K_CTA_XL, s);
+            }));
         if (g->hub.n_hubs > 0) {
             LPA_CUDA(timed(LPA_K_HUB_BEGIN, [&] { return launch_hub_begin(g->hub, a, s); }));
             LPA_CUDA(timed(LPA_K_HUB_ACC, [&] { return launch_hub_acc(g->hub, a, g->n_chunks, 1024, s); }));
-            LPA_CUDA(timed(LPA_K_HUB_ARGMAX, [&] { return launch_hub_argmax(g->hub, a, g->n_slices, s); }));
+            LPA_CUDA(timed(LPA_K_HUB_CLEAR, [&] { return launch_hub_clear(g->hub, g->n_slices, s); }));
             LPA_CUDA(timed(LPA_K_HUB_MOVE, [&] { return launch_hub_move(g->hub, a, s); }));
             LPA_CUDA(timed(LPA_K_HUB_MARK, [&] { return launch_hub_mark(g->hub, a, g->n_chunks, s); }));
         }

@@ -15,7 +15,7 @@ constexpr int32_t kEmpty = -1;     // empty hashtable key (labels are >= 0)
 constexpr int kMaxRetries = 32;    // hybrid probes before the linear fallback (Algorithm 2)
 constexpr int kCtrFields = 4;      // per kernel slot: active, edges, moved, marks
 enum { CTR_ACTIVE = 0, CTR_EDGES = 1, CTR_MOVED = 2, CTR_MARKS = 3 };
-enum Bucket { B_THREAD = 0, B_GROUP, B_WARP, B_CTA, B_CTA_LARGE, B_HUB, B_COUNT };
+enum Bucket { B_THREAD = 0, B_GROUP, B_WARP, B_CTA, B_CTA_LARGE, B_CTA_XL, B_HUB, B_COUNT };
 
 // Arguments of one sweep (Algorithm 1, lpaMove), passed by value to every sweep kernel.
 struct SweepArgs {
@@ -71,7 +71,7 @@ cudaError_t launch_cta_bucket(const int32_t *list, int64_t count, const SweepArg
 cudaError_t launch_hub_begin(const HubArgs &h, const SweepArgs &a, cudaStream_t s);
 cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, int threads,
                            cudaStream_t s);
-cudaError_t launch_hub_argmax(const HubArgs &h, const SweepArgs &a, int64_t n_slices, cudaStream_t s);
+cudaError_t launch_hub_clear(const HubArgs &h, int64_t n_slices, cudaStream_t s);
 cudaError_t launch_hub_move(const HubArgs &h, const SweepArgs &a, cudaStream_t s);
 cudaError_t launch_hub_mark(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, cudaStream_t s);
 cudaError_t launch_apply(const SweepArgs &a, int64_t n, cudaStream_t s);

@@ -3,17 +3,21 @@
 // hybrid quadratic-double sequence of Algorithm 2.
 //
 // Buckets (by degree D, thresholds in lpa_tuning):
-//   thread     one thread per vertex, private table in shared memory (no atomics)
-//   group      2..16 lanes per vertex, table in shared memory (shared-memory atomics)
-//   warp       one warp per vertex, table in shared memory
-//   cta        one thread block per vertex, table in shared memory (up to 16383 slots)
-//   hub        several blocks per vertex, table in HBM (global atomics), followed by a
-//              block-parallel max-reduce and a move/mark kernel
-// Every table has p1 = 2^b - 1 >= D slots (Section 4.2: capacity nextPow2(D) - 1, read
-// with nextPow2 as the next power of two strictly above D); the secondary modulus is
-// p2 = 2 p1 + 1.  Labels are the keys, float32 weight sums the values.  The winner is
-// the max of (weight bits << 32 | ~label) over the table, i.e. the largest weight and,
-// among equal weights, the smallest label.
+//   thread      one thread per vertex, private table in shared memory (no atomics)
+//   group       2..16 lanes per vertex, table in shared memory (shared-memory atomics)
+//   warp        one warp per vertex, table in shared memory
+//   cta tiers   one thread block per vertex (three block sizes), table in shared memory
+//   hub         several blocks per vertex, table in HBM (global atomics)
+// Table capacity is p1 = 2^b - 1 >= D << shift (Section 4.2 uses nextPow2(D) - 1, i.e.
+// shift 0, with nextPow2 read as the next power of two strictly above D); the secondary
+// modulus is p2 = 2 p1 + 1.  Keys are labels, values float32 weight sums.
+//
+// hashtableMaxKey is folded into the accumulation: every add returns the key's new sum,
+// each lane keeps the maximum of (sum bits << 32 | ~label) over the adds it made, and the
+// maxima are reduced over the lanes of the vertex.  A key's final sum is returned to the
+// lane that made its last add and no observed sum exceeds a final sum (weights are >= 0),
+// so the reduction equals the maximum over the table: the largest weight and, among equal
+// weights, the smallest label (Section 4 item 5).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -53,21 +57,29 @@ __device__ __forceinline__ int32_t unpack_key(unsigned long long p)
     return (int32_t)(~(uint32_t)(p & 0xFFFFFFFFull));
 }
 
-// capacity 2^b - 1 >= D (D >= 1)
-__device__ __forceinline__ uint32_t cap_bits(uint32_t D) { return 32u - __clz(D); }
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b)
+{
+    return a > b ? a : b;
+}
+
+// capacity 2^b - 1 >= x (x >= 1)
+__device__ __forceinline__ uint32_t cap_bits(uint32_t x) { return 32u - __clz(x); }
 __device__ __forceinline__ uint32_t cap_of_bits(uint32_t b) { return b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u); }
 
-// One slot attempt of Algorithm 2: take slot s if it is empty or already holds k.  With
-// TRACK, a slot taken from empty is appended to the table's used list.
+// One slot attempt of Algorithm 2: take slot s if it is empty or already holds k, add v
+// and fold the new sum into `best`.  With TRACK a slot taken from empty is appended to the
+// table's used list.
 template <bool SHARED, bool TRACK>
-__device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32_t k, float v, uint32_t *ucnt,
-                                         int32_t *ulist)
+__device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32_t k, float v,
+                                         unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
 {
     if (!SHARED) {                                    // single owner: plain accesses
-        int32_t kk = Hk[s];
+        const int32_t kk = Hk[s];
         if (kk == k || kk == kEmpty) {
             Hk[s] = k;
-            Hv[s] += v;
+            const float nv = Hv[s] + v;
+            Hv[s] = nv;
+            best = umax64(best, pack_kv(nv, k));
             return true;
         }
         return false;
@@ -83,7 +95,8 @@ __device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32
         }
     }
     if (kk == k) {
-        atomicAdd(Hv + s, v);
+        const float nv = atomicAdd(Hv + s, v) + v;
+        best = umax64(best, pack_kv(nv, k));
         return true;
     }
     return false;
@@ -93,8 +106,8 @@ __device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32
 // then a linear scan from the last probed slot once the probe budget is spent.
 template <bool SHARED, bool TRACK = false>
 __device__ __forceinline__ void ht_accumulate(int32_t *Hk, float *Hv, int stride, uint32_t p1, uint32_t b,
-                                              int32_t k, float v, unsigned &fallbacks, uint32_t *ucnt = nullptr,
-                                              int32_t *ulist = nullptr)
+                                              int32_t k, float v, unsigned long long &best, unsigned &fallbacks,
+                                              uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
 {
     const uint32_t uk = (uint32_t)k;
     uint32_t i = mod_mersenne(uk, b, p1);
@@ -104,7 +117,7 @@ __device__ __forceinline__ void ht_accumulate(int32_t *Hk, float *Hv, int stride
 #pragma unroll 1
     for (int t = 0; t < kMaxRetries; ++t) {
         s = i;
-        if (try_slot<SHARED, TRACK>(Hk, Hv, (size_t)s * stride, k, v, ucnt, ulist)) return;
+        if (try_slot<SHARED, TRACK>(Hk, Hv, (size_t)s * stride, k, v, best, ucnt, ulist)) return;
         if (step == 0xFFFFFFFFu) {
             uint32_t q = mod_mersenne(uk, b + 1, 2u * p1 + 1u);
             if (q >= p1) q -= p1;
@@ -123,7 +136,7 @@ __device__ __forceinline__ void ht_accumulate(int32_t *Hk, float *Hv, int stride
     for (uint32_t u = 1; u <= p1; ++u) {
         uint32_t q = s + u;
         if (q >= p1) q -= p1;
-        if (try_slot<SHARED, TRACK>(Hk, Hv, (size_t)q * stride, k, v, ucnt, ulist)) return;
+        if (try_slot<SHARED, TRACK>(Hk, Hv, (size_t)q * stride, k, v, best, ucnt, ulist)) return;
     }
 }
 
@@ -141,6 +154,14 @@ __device__ __forceinline__ void group_sync()
     if (G > 1) __syncwarp(group_mask<G>());
 }
 
+template <int G>
+__device__ __forceinline__ unsigned long long group_max(unsigned long long x)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x = umax64(x, __shfl_xor_sync(group_mask<G>(), x, o, G));
+    return x;
+}
+
 // Lanes of one group (G lanes, aligned inside the warp) insert their (key, weight) pairs
 // into the group's shared table.  Before the per-lane inserts, up to kPeel rounds take the
 // key of the lowest pending lane, sum the weights of every lane holding that key with a
@@ -151,8 +172,8 @@ constexpr int kPeel = 3;
 
 template <int G, bool SHARED, bool TRACK = false>
 __device__ __forceinline__ void group_insert(int32_t *Hk, float *Hv, int stride, uint32_t p1, uint32_t b,
-                                             bool has, int32_t k, float w, unsigned &fb, uint32_t *ucnt = nullptr,
-                                             int32_t *ulist = nullptr)
+                                             bool has, int32_t k, float w, unsigned long long &best, unsigned &fb,
+                                             uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
 {
     if (G >= 2) {
         const unsigned gm = group_mask<G>();
@@ -168,12 +189,25 @@ __device__ __forceinline__ void group_insert(int32_t *Hk, float *Hv, int stride,
             float sum = mine ? w : 0.0f;
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gm, sum, o);
-            if (lane == leader) ht_accumulate<SHARED, TRACK>(Hk, Hv, stride, p1, b, kl, sum, fb, ucnt, ulist);
+            if (lane == leader) ht_accumulate<SHARED, TRACK>(Hk, Hv, stride, p1, b, kl, sum, best, fb, ucnt, ulist);
             if (mine) has = false;
             pend &= ~same;
         }
     }
-    if (has) ht_accumulate<SHARED, TRACK>(Hk, Hv, stride, p1, b, k, w, fb, ucnt, ulist);
+    if (has) ht_accumulate<SHARED, TRACK>(Hk, Hv, stride, p1, b, k, w, best, fb, ucnt, ulist);
+}
+
+// hashtableClear of slots [0, p1] of a contiguous, 16-byte aligned table with 16-byte stores
+// (p1 + 1 is a power of two, at least 4 slots are allocated).
+__device__ __forceinline__ void clear_table_vec(int32_t *Hk, float *Hv, uint32_t p1, int first, int step)
+{
+    const uint32_t chunks = (p1 + 4u) >> 2;
+    int4 *K4 = reinterpret_cast<int4 *>(Hk);
+    float4 *V4 = reinterpret_cast<float4 *>(Hv);
+    for (uint32_t q = first; q < chunks; q += step) {
+        K4[q] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
+        V4[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
 }
 
 // Warp-aggregated append of (v, c) to the synchronous mover list.  Every lane of the
@@ -188,7 +222,7 @@ __device__ __forceinline__ void append_movers(const SweepArgs &a, bool pred, int
     if (lane == leader) base = atomicAdd(a.mover_count, (unsigned long long)__popc(bal));
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
     if (pred) {
-        unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+        const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
         a.mover_v[pos] = v;
         a.mover_c[pos] = c;
     }
@@ -215,11 +249,37 @@ __device__ __forceinline__ void flush_block_counts(const SweepArgs &a, unsigned 
 {
     __syncthreads();
     if (threadIdx.x < kCtrFields) {
-        unsigned long long x = bctr[threadIdx.x];
+        const unsigned long long x = bctr[threadIdx.x];
         if (x) atomicAdd(&a.ctr[kslot * kCtrFields + threadIdx.x], x);
     } else if (threadIdx.x == kCtrFields) {
         if (*bfb) atomicAdd(a.fallbacks, (unsigned long long)*bfb);
     }
+}
+
+// Loads entry e of the row of v: (label of the neighbour, weight); has = false for e past
+// the row end and for self-loops (Algorithm 1 skips j = i).
+__device__ __forceinline__ void load_entry(const SweepArgs &a, int32_t v, int64_t e, int64_t end, bool &has,
+                                           int32_t &k, float &wv)
+{
+    has = e < end;
+    k = 0;
+    wv = 0.0f;
+    if (has) {
+        const int32_t j = a.idx[e];
+        has = (j != v);
+        if (has) {
+            k = a.C[j];
+            wv = a.w ? a.w[e] : 1.0f;
+        }
+    }
+}
+
+// Move rule of Algorithm 1: c* != C[i] and, on Pick-Less sweeps, c* < C[i].
+__device__ __forceinline__ bool decide(unsigned long long best, int32_t cur, int pl, int32_t &cstar)
+{
+    if (best == 0) return false;                   // no neighbour label (isolated / self-loops only)
+    cstar = unpack_key(best);
+    return (cstar != cur) && (!pl || cstar < cur);
 }
 
 // ---------------------------------------------------------------------------------
@@ -266,7 +326,7 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
 
     unsigned fb = 0;
     int64_t o0 = 0, o1 = 0;
-    int32_t cur = 0, cstar = -1;
+    int32_t cstar = -1;
     bool moved = false;
     if (act) {
         o0 = a.off[v];
@@ -274,45 +334,26 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
         const uint32_t D = (uint32_t)(o1 - o0);
         const uint32_t b = cap_bits(D << a.tshift);        // capacity >= D << tshift
         const uint32_t p1 = cap_of_bits(b);
-        for (uint32_t s = lane; s < p1; s += G) {          // hashtableClear
-            Hk[(size_t)s * stride] = kEmpty;
-            Hv[(size_t)s * stride] = 0.0f;
-        }
-        group_sync<G>();
-        cur = a.C[v];
-        for (int64_t eb = o0; eb < o1; eb += G) {          // scan neighbours
-            const int64_t e = eb + lane;
-            bool has = e < o1;
-            int32_t k = 0;
-            float wv = 0.0f;
-            if (has) {
-                const int32_t j = a.idx[e];
-                has = (j != v);                             // skip self-loops
-                if (has) {
-                    k = a.C[j];
-                    wv = a.w ? a.w[e] : 1.0f;
-                }
+        if (G == 1) {
+            for (uint32_t s = 0; s < p1; ++s) {            // hashtableClear
+                Hk[(size_t)s * stride] = kEmpty;
+                Hv[(size_t)s * stride] = 0.0f;
             }
-            group_insert<G, (G > 1)>(Hk, Hv, stride, p1, b, has, k, wv, fb);
+        } else {
+            clear_table_vec(Hk, Hv, p1, lane, G);
+            group_sync<G>();
         }
-        group_sync<G>();
+        const int32_t cur = a.C[v];
         unsigned long long best = 0;
-        for (uint32_t s = lane; s < p1; s += G) {          // hashtableMaxKey
-            const int32_t kk = Hk[(size_t)s * stride];
-            if (kk != kEmpty) {
-                const unsigned long long pk = pack_kv(Hv[(size_t)s * stride], kk);
-                best = pk > best ? pk : best;
-            }
+        for (int64_t eb = o0; eb < o1; eb += G) {          // scan neighbours
+            bool has;
+            int32_t k;
+            float wv;
+            load_entry(a, v, eb + lane, o1, has, k, wv);
+            group_insert<G, (G > 1)>(Hk, Hv, stride, p1, b, has, k, wv, best, fb);
         }
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(group_mask<G>(), best, o, G);
-            best = other > best ? other : best;
-        }
-        if (best != 0) {
-            cstar = unpack_key(best);
-            moved = (cstar != cur) && (!a.pl || cstar < cur);
-        }
+        best = group_max<G>(best);                         // hashtableMaxKey
+        moved = decide(best, cur, a.pl, cstar);
         if (moved) {
             if (a.async_mode && lane == 0) {
                 a.C[v] = cstar;
@@ -347,7 +388,7 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
     if (gi >= count) return;
     const int32_t v = __ldg(list + gi);
     if (threadIdx.x == 0) {
-        int act = a.flag_cur[v] != 0;
+        const int act = a.flag_cur[v] != 0;
         if (act) a.flag_cur[v] = 0;
         s_act = act;
         s_fb = 0;
@@ -359,54 +400,27 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
     const uint32_t D = (uint32_t)(o1 - o0);
     const uint32_t b = cap_bits(D << a.tshift);
     const uint32_t p1 = cap_of_bits(b);
-    for (uint32_t s = threadIdx.x; s < p1; s += TPB) {
-        Hk[s] = kEmpty;
-        Hv[s] = 0.0f;
-    }
+    clear_table_vec(Hk, Hv, p1, threadIdx.x, TPB);
     __syncthreads();
     const int32_t cur = a.C[v];
     unsigned fb = 0;
+    unsigned long long best = 0;
     for (int64_t eb = o0 + (threadIdx.x & ~31); eb < o1; eb += TPB) {
-        const int64_t e = eb + (threadIdx.x & 31);
-        bool has = e < o1;
-        int32_t k = 0;
-        float wv = 0.0f;
-        if (has) {
-            const int32_t j = a.idx[e];
-            has = (j != v);
-            if (has) {
-                k = a.C[j];
-                wv = a.w ? a.w[e] : 1.0f;
-            }
-        }
-        group_insert<32, true>(Hk, Hv, 1, p1, b, has, k, wv, fb);
+        bool has;
+        int32_t k;
+        float wv;
+        load_entry(a, v, eb + (threadIdx.x & 31), o1, has, k, wv);
+        group_insert<32, true>(Hk, Hv, 1, p1, b, has, k, wv, best, fb);
     }
     if (fb) atomicAdd(&s_fb, fb);
-    __syncthreads();
-    unsigned long long best = 0;
-    for (uint32_t s = threadIdx.x; s < p1; s += TPB) {
-        const int32_t kk = Hk[s];
-        if (kk != kEmpty) {
-            const unsigned long long pk = pack_kv(Hv[s], kk);
-            best = pk > best ? pk : best;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-        best = other > best ? other : best;
-    }
+    best = group_max<32>(best);
     if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
     __syncthreads();
     best = 0;
 #pragma unroll
-    for (int w = 0; w < TPB / 32; ++w) best = s_best[w] > best ? s_best[w] : best;
-    bool moved = false;
+    for (int w = 0; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
     int32_t cstar = -1;
-    if (best != 0) {
-        cstar = unpack_key(best);
-        moved = (cstar != cur) && (!a.pl || cstar < cur);
-    }
+    const bool moved = decide(best, cur, a.pl, cstar);
     if (moved) {
         if (threadIdx.x == 0) {
             if (a.async_mode) {
@@ -418,7 +432,7 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
                 a.mover_c[pos] = cstar;
             }
         }
-        __syncthreads();
+        if (a.async_mode) __syncthreads();
         for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
     }
     if (threadIdx.x == 0) {
@@ -435,9 +449,9 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
 
 // ---------------------------------------------------------------------------------
 // Hubs: tables in HBM shared by several blocks.  Per sweep: begin (take the processed
-// flag), accumulate (blocks over CSR chunks), argmax (blocks over the used-slot list;
-// the slots are cleared for the next sweep), move (one thread per hub), mark (blocks
-// over CSR chunks of the hubs that moved).
+// flag), accumulate (blocks over CSR chunks; each block folds its running maximum into
+// hub_best), clear (blocks over the used-slot list), move (one thread per hub), mark
+// (blocks over the CSR chunks of the hubs that moved).
 __global__ void k_hub_begin(HubArgs h, SweepArgs a)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -453,6 +467,7 @@ __global__ void k_hub_begin(HubArgs h, SweepArgs a)
 template <int TPB>
 __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a)
 {
+    __shared__ unsigned long long s_best[TPB / 32];
     const int hh = h.chunk_h[blockIdx.x];
     if (!h.hub_act[hh]) return;
     const int32_t v = h.hub_v[hh];
@@ -463,56 +478,40 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a)
     int32_t *ulist = h.used_list + h.used_base[hh];
     const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
     unsigned fb = 0;
+    unsigned long long best = 0;
     for (int64_t eb = e0 + (threadIdx.x & ~31); eb < e1; eb += TPB) {
-        const int64_t e = eb + (threadIdx.x & 31);
-        bool has = e < e1;
-        int32_t k = 0;
-        float wv = 0.0f;
-        if (has) {
-            const int32_t j = a.idx[e];
-            has = (j != v);
-            if (has) {
-                k = a.C[j];
-                wv = a.w ? a.w[e] : 1.0f;
-            }
-        }
-        group_insert<32, true, true>(Hk, Hv, 1, p1, b, has, k, wv, fb, ucnt, ulist);
+        bool has;
+        int32_t k;
+        float wv;
+        load_entry(a, v, eb + (threadIdx.x & 31), e1, has, k, wv);
+        group_insert<32, true, true>(Hk, Hv, 1, p1, b, has, k, wv, best, fb, ucnt, ulist);
     }
     if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
+    best = group_max<32>(best);
+    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
+        if (best) atomicMax(h.hub_best + hh, best);
+    }
 }
 
 template <int TPB>
-__global__ void __launch_bounds__(TPB) k_hub_argmax(HubArgs h, SweepArgs a)
+__global__ void __launch_bounds__(TPB) k_hub_clear(HubArgs h)
 {
-    __shared__ unsigned long long s_best[TPB / 32];
     const int hh = h.slice_h[blockIdx.x];
     if (!h.hub_act[hh]) return;
     const int64_t lo = (int64_t)h.slice_j[blockIdx.x] * kHubSlice;
     const int64_t cnt = h.hub_used[hh];
-    if (lo >= cnt) return;                             // uniform for the block
+    if (lo >= cnt) return;
     const int64_t hi = lo + kHubSlice < cnt ? lo + kHubSlice : cnt;
     int32_t *Hk = h.tab_k + h.hub_tab[hh];
     float *Hv = h.tab_v + h.hub_tab[hh];
     const int32_t *ulist = h.used_list + h.used_base[hh];
-    unsigned long long best = 0;
     for (int64_t q = lo + threadIdx.x; q < hi; q += TPB) {
         const int32_t s = ulist[q];
-        const int32_t kk = Hk[s];
-        const unsigned long long pk = pack_kv(Hv[s], kk);
-        best = pk > best ? pk : best;
         Hk[s] = kEmpty;                                // leave the table clear for the next sweep
         Hv[s] = 0.0f;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
-        best = other > best ? other : best;
-    }
-    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < TPB / 32; ++w) best = s_best[w] > best ? s_best[w] : best;
-        if (best) atomicMax(h.hub_best + hh, best);
     }
 }
 
@@ -521,14 +520,9 @@ __global__ void k_hub_move(HubArgs h, SweepArgs a)
     const int hh = blockIdx.x * blockDim.x + threadIdx.x;
     if (hh >= h.n_hubs || !h.hub_act[hh]) return;
     const int32_t v = h.hub_v[hh];
-    const unsigned long long best = h.hub_best[hh];
     const int32_t cur = a.C[v];
-    bool moved = false;
     int32_t cstar = -1;
-    if (best != 0) {
-        cstar = unpack_key(best);
-        moved = (cstar != cur) && (!a.pl || cstar < cur);
-    }
+    const bool moved = decide(h.hub_best[hh], cur, a.pl, cstar);
     const unsigned long long D = (unsigned long long)(a.off[v + 1] - a.off[v]);
     unsigned long long *c = a.ctr + LPA_K_HUB_ACC * kCtrFields;
     atomicAdd(c + CTR_ACTIVE, 1ull);
@@ -658,6 +652,7 @@ cudaError_t launch_cta_bucket(const int32_t *list, int64_t count, const SweepArg
                               int kslot, cudaStream_t s)
 {
     switch (threads) {
+    case 64: return launch_c<64>(list, count, a, slots, kslot, s);
     case 128: return launch_c<128>(list, count, a, slots, kslot, s);
     case 256: return launch_c<256>(list, count, a, slots, kslot, s);
     case 512: return launch_c<512>(list, count, a, slots, kslot, s);
@@ -684,10 +679,10 @@ cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunk
     return cudaGetLastError();
 }
 
-cudaError_t launch_hub_argmax(const HubArgs &h, const SweepArgs &a, int64_t n_slices, cudaStream_t s)
+cudaError_t launch_hub_clear(const HubArgs &h, int64_t n_slices, cudaStream_t s)
 {
     if (n_slices <= 0) return cudaSuccess;
-    k_hub_argmax<256><<<(unsigned)n_slices, 256, 0, s>>>(h, a);
+    k_hub_clear<256><<<(unsigned)n_slices, 256, 0, s>>>(h);
     return cudaGetLastError();
 }
 

@@ -26,8 +26,8 @@ SYNC, ASYNC, RESUME = 0, 1, 16
 OFFSETS_I32, OFFSETS_I64, HOST_PTRS, DEVICE_PTRS, CHECK_SYMMETRIC = 0, 1, 0, 2, 4
 STATS_MAX_ITERS = 64
 NUM_KERNELS = 12
-KERNEL_NAMES = ["thread", "group", "warp", "cta", "cta_large", "hub_begin", "hub_acc", "hub_argmax",
-                "hub_move", "apply", "hub_mark", "unused"]
+KERNEL_NAMES = ["thread", "group", "warp", "cta", "cta_large", "cta_xl", "hub_begin", "hub_acc", "hub_clear",
+                "hub_move", "hub_mark", "apply"]
 
 SYMBOLS = ["lpa_create", "lpa_run", "lpa_labels", "lpa_modularity", "lpa_set_labels", "lpa_get_state",
            "lpa_set_state", "lpa_set_stream", "lpa_get_tuning", "lpa_set_tuning", "lpa_num_vertices",
@@ -84,7 +84,8 @@ class Stats(ct.Structure):
 class Tuning(ct.Structure):
     _fields_ = [(name, ct.c_int32) for name in (
         "thread_max", "group_max", "group_lanes", "warp_max", "cta_max", "cta_threads", "cta_large_max",
-        "cta_large_threads", "hub_chunk", "hub_table_shift", "smem_table_shift")] + [("reserved", ct.c_int32 * 5)]
+        "cta_large_threads", "hub_chunk", "hub_table_shift", "smem_table_shift", "cta_xl_max",
+        "cta_xl_threads")] + [("reserved", ct.c_int32 * 3)]
 
     def to_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

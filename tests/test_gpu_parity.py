@@ -19,8 +19,9 @@ from paper_2411_11468_gb300 import graphgen as gg
 pytestmark = pytest.mark.gpu
 
 # thresholds low enough that small graphs reach every bucket, hubs included
-SMALL_BUCKETS = dict(thread_max=3, group_max=7, group_lanes=4, warp_max=31, cta_max=63, cta_threads=128,
-                     cta_large_max=127, cta_large_threads=256, hub_chunk=256, hub_table_shift=0)
+SMALL_BUCKETS = dict(thread_max=3, group_max=7, group_lanes=4, warp_max=31, cta_max=63, cta_threads=64,
+                     cta_large_max=95, cta_large_threads=128, cta_xl_max=127, cta_xl_threads=256, hub_chunk=256,
+                     hub_table_shift=0)
 # the paper's table capacity nextPow2(D) - 1 everywhere (load factor up to 1, probe fallbacks)
 PAPER_TABLES = dict(SMALL_BUCKETS, smem_table_shift=0, hub_table_shift=0)
 
@@ -248,7 +249,7 @@ def test_tuning_rejected_when_tables_do_not_fit(lpa):
     csr = gg.rmat(10, weights="int8")
     g = make(lpa, csr)
     with pytest.raises(lpa.LpaError):
-        g.set_tuning(cta_large_max=16383, smem_table_shift=2)      # 64K-slot table > smem
+        g.set_tuning(cta_xl_max=16383, smem_table_shift=2)         # 64K-slot table > smem
     with pytest.raises(lpa.LpaError):
         g.set_tuning(warp_max=10, group_max=31)                      # decreasing limits
     g.run()                                                          # handle still usable
