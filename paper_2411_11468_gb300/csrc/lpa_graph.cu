@@ -203,7 +203,9 @@ __device__ __forceinline__ double warp_sum_d(double x)
 }
 
 // Eq. 1 numerators: per row i, K_i = sum_j w_ij and the weight of entries with C_j = C_i;
-// Sigma_{C_i} += K_i.  float64 accumulation.
+// Sigma_{C_i} += K_i.  float64 accumulation.  Each warp walks a contiguous range of rows and
+// adds runs of equal labels to Sigma with one atomic per run (labels of a community are
+// often contiguous, and one label may cover most of the graph).
 __global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int32_t *idx, const float *w,
                                                   const int32_t *C, int64_t n, double *Sig, double *acc)
 {
@@ -211,8 +213,11 @@ __global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int3
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double tin = 0.0, tk = 0.0;
-    for (int64_t i = warp; i < n; i += nwarps) {
+    const int64_t per = (n + nwarps - 1) / nwarps;
+    const int64_t r0 = warp * per, r1 = r0 + per < n ? r0 + per : n;
+    double tin = 0.0, tk = 0.0, run = 0.0;
+    int32_t run_c = -1;
+    for (int64_t i = r0; i < r1; ++i) {
         const int64_t o0 = off[i], o1 = off[i + 1];
         if (o0 == o1) continue;
         const int32_t ci = C[i];
@@ -224,12 +229,16 @@ __global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int3
         }
         k = warp_sum_d(k);
         in = warp_sum_d(in);
-        if (lane == 0) {
-            atomicAdd(Sig + ci, k);
-            tin += in;
-            tk += k;
+        tin += in;
+        tk += k;
+        if (ci != run_c) {
+            if (lane == 0 && run_c >= 0) atomicAdd(Sig + run_c, run);
+            run_c = ci;
+            run = 0.0;
         }
+        run += k;
     }
+    if (lane == 0 && run_c >= 0) atomicAdd(Sig + run_c, run);
     if (lane == 0) {
         s_in[threadIdx.x >> 5] = tin;
         s_k[threadIdx.x >> 5] = tk;
@@ -387,7 +396,7 @@ int check_tuning(const lpa_tuning &t)
     if (!(t.group_lanes == 2 || t.group_lanes == 4 || t.group_lanes == 8 || t.group_lanes == 16)) return LPA_EINVAL;
     for (int th : {t.cta_threads, t.cta_large_threads, t.cta_xl_threads})
         if (!pow2(th) || th < 64 || th > 1024) return LPA_EINVAL;
-    if (t.hub_chunk < 256 || t.hub_chunk > (1 << 24)) return LPA_EINVAL;
+    if (t.hub_chunk < 256 || t.hub_chunk > 32768) return LPA_EINVAL;
     const int64_t smem = (int64_t)max_dynamic_smem();
     const int64_t bytes_group = (256 / t.group_lanes) * slots_for(t.group_max, sh) * 8;
     const int64_t bytes_warp = 8 * slots_for(t.warp_max, sh) * 8;
@@ -511,7 +520,7 @@ int build_buckets(lpa_graph *g)
             ce0.push_back(e0);
             ce1.push_back(std::min(o1[h], e0 + chunk));
         }
-        for (int64_t j = 0; j * kHubSlice < D; ++j) {   // at most D distinct labels
+        for (int64_t j = 0; j * kHubSlice < (int64_t)p1[h]; ++j) {   // clear slices cover the table
             sh.push_back((int32_t)h);
             sj.push_back((int32_t)j);
         }
@@ -1067,7 +1076,7 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
             }));
         if (g->hub.n_hubs > 0) {
             LPA_CUDA(timed(LPA_K_HUB_BEGIN, [&] { return launch_hub_begin(g->hub, a, s); }));
-            LPA_CUDA(timed(LPA_K_HUB_ACC, [&] { return launch_hub_acc(g->hub, a, g->n_chunks, 1024, s); }));
+            LPA_CUDA(timed(LPA_K_HUB_ACC, [&] { return launch_hub_acc(g->hub, a, g->n_chunks, t.hub_chunk, s); }));
             LPA_CUDA(timed(LPA_K_HUB_CLEAR, [&] { return launch_hub_clear(g->hub, g->n_slices, s); }));
             LPA_CUDA(timed(LPA_K_HUB_MOVE, [&] { return launch_hub_move(g->hub, a, s); }));
             LPA_CUDA(timed(LPA_K_HUB_MARK, [&] { return launch_hub_mark(g->hub, a, g->n_chunks, s); }));

@@ -69,8 +69,7 @@ cudaError_t launch_warp_bucket(const int32_t *list, int64_t count, const SweepAr
 cudaError_t launch_cta_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int threads,
                               int slots, int kslot, cudaStream_t s);
 cudaError_t launch_hub_begin(const HubArgs &h, const SweepArgs &a, cudaStream_t s);
-cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, int threads,
-                           cudaStream_t s);
+cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, int chunk, cudaStream_t s);
 cudaError_t launch_hub_clear(const HubArgs &h, int64_t n_slices, cudaStream_t s);
 cudaError_t launch_hub_move(const HubArgs &h, const SweepArgs &a, cudaStream_t s);
 cudaError_t launch_hub_mark(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, cudaStream_t s);

@@ -284,13 +284,15 @@ __device__ __forceinline__ bool decide(unsigned long long best, int32_t cur, int
 
 // ---------------------------------------------------------------------------------
 // G lanes per vertex (G = 1: thread per vertex with a private table; G = 32: warp per
-// vertex).  Each block handles TPB / G consecutive entries of the bucket list.
+// vertex).  Persistent: every warp walks the bucket list in steps of 32/G vertices, so the
+// block synchronises only at its start and end.
 template <int G, int TPB>
 __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list, int64_t count, SweepArgs a,
                                                int slots, int kslot)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NG = TPB / G;
+    constexpr int GPW = 32 / G;                        // groups per warp
     __shared__ unsigned long long bctr[kCtrFields];
     __shared__ unsigned bfb;
     if (threadIdx.x < kCtrFields) bctr[threadIdx.x] = 0;
@@ -312,68 +314,77 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
         stride = 1;
     }
 
-    const int64_t gi = (int64_t)blockIdx.x * NG + grp;
-    int32_t v = -1;
-    bool act = false;
-    if (gi < count) {
-        v = __ldg(list + gi);
-        if (lane == 0) {
-            act = a.flag_cur[v] != 0;
-            if (act) a.flag_cur[v] = 0;                   // mark processed
+    unsigned fb = 0, c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
+    const int64_t warp_id = ((int64_t)blockIdx.x * TPB + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * TPB) >> 5;
+    const int gw = (threadIdx.x & 31) / G;             // group within the warp
+    for (int64_t wb = warp_id * GPW; wb < count; wb += n_warps * GPW) {   // uniform per warp
+        const int64_t gi = wb + gw;
+        int32_t v = -1;
+        bool act = false;
+        if (gi < count) {
+            v = __ldg(list + gi);
+            if (lane == 0) {
+                act = a.flag_cur[v] != 0;
+                if (act) a.flag_cur[v] = 0;               // mark processed
+            }
         }
         if (G > 1) act = __shfl_sync(group_mask<G>(), act, 0, G);
-    }
-
-    unsigned fb = 0;
-    int64_t o0 = 0, o1 = 0;
-    int32_t cstar = -1;
-    bool moved = false;
-    if (act) {
-        o0 = a.off[v];
-        o1 = a.off[v + 1];
-        const uint32_t D = (uint32_t)(o1 - o0);
-        const uint32_t b = cap_bits(D << a.tshift);        // capacity >= D << tshift
-        const uint32_t p1 = cap_of_bits(b);
-        if (G == 1) {
-            for (uint32_t s = 0; s < p1; ++s) {            // hashtableClear
-                Hk[(size_t)s * stride] = kEmpty;
-                Hv[(size_t)s * stride] = 0.0f;
+        int32_t cstar = -1;
+        bool moved = false;
+        if (act) {
+            const int64_t o0 = a.off[v], o1 = a.off[v + 1];
+            const uint32_t D = (uint32_t)(o1 - o0);
+            const uint32_t b = cap_bits(D << a.tshift);    // capacity >= D << tshift
+            const uint32_t p1 = cap_of_bits(b);
+            if (G == 1) {
+                for (uint32_t s = 0; s < p1; ++s) {        // hashtableClear
+                    Hk[(size_t)s * stride] = kEmpty;
+                    Hv[(size_t)s * stride] = 0.0f;
+                }
+            } else {
+                group_sync<G>();                           // previous vertex's inserts are done
+                clear_table_vec(Hk, Hv, p1, lane, G);
+                group_sync<G>();
             }
-        } else {
-            clear_table_vec(Hk, Hv, p1, lane, G);
-            group_sync<G>();
-        }
-        const int32_t cur = a.C[v];
-        unsigned long long best = 0;
-        for (int64_t eb = o0; eb < o1; eb += G) {          // scan neighbours
-            bool has;
-            int32_t k;
-            float wv;
-            load_entry(a, v, eb + lane, o1, has, k, wv);
-            group_insert<G, (G > 1)>(Hk, Hv, stride, p1, b, has, k, wv, best, fb);
-        }
-        best = group_max<G>(best);                         // hashtableMaxKey
-        moved = decide(best, cur, a.pl, cstar);
-        if (moved) {
-            if (a.async_mode && lane == 0) {
-                a.C[v] = cstar;
-                __threadfence();
+            const int32_t cur = a.C[v];
+            unsigned long long best = 0;
+            for (int64_t eb = o0; eb < o1; eb += G) {      // scan neighbours
+                bool has;
+                int32_t k;
+                float wv;
+                load_entry(a, v, eb + lane, o1, has, k, wv);
+                group_insert<G, (G > 1)>(Hk, Hv, stride, p1, b, has, k, wv, best, fb);
             }
-            group_sync<G>();
-            for (int64_t e = o0 + lane; e < o1; e += G) a.flag_next[a.idx[e]] = 1;   // mark neighbours
+            best = group_max<G>(best);                     // hashtableMaxKey
+            moved = decide(best, cur, a.pl, cstar);
+            if (moved) {
+                if (a.async_mode && lane == 0) {
+                    a.C[v] = cstar;
+                    __threadfence();
+                }
+                group_sync<G>();
+                for (int64_t e = o0 + lane; e < o1; e += G) a.flag_next[a.idx[e]] = 1;   // mark neighbours
+            }
+            if (lane == 0) {
+                c_act += 1;
+                c_edges += D;
+                if (moved) {
+                    c_moved += 1;
+                    c_marks += D;
+                }
+            }
         }
+        if (!a.async_mode) append_movers(a, moved && lane == 0, v, cstar);
     }
-    if (!a.async_mode) append_movers(a, moved && lane == 0, v, cstar);
-    const bool lead = (lane == 0);
-    const unsigned deg = (unsigned)(o1 - o0);
-    warp_count(bctr, (act && lead) ? 1u : 0u, (act && lead) ? deg : 0u, (moved && lead) ? 1u : 0u,
-               (moved && lead) ? deg : 0u);
+    warp_count(bctr, c_act, c_edges, c_moved, c_marks);
     if (fb) atomicAdd(&bfb, fb);
     flush_block_counts(a, bctr, &bfb, kslot);
 }
 
 // ---------------------------------------------------------------------------------
 // One thread block per vertex; the table (up to slots entries) lives in dynamic smem.
+// Persistent: each block walks the bucket list with a grid stride.
 template <int TPB>
 __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, int64_t count, SweepArgs a,
                                              int slots, int kslot)
@@ -382,69 +393,76 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
     int32_t *Hk = (int32_t *)smem;
     float *Hv = (float *)(smem + (size_t)slots * sizeof(int32_t));
     __shared__ int s_act;
+    __shared__ int32_t s_v;
     __shared__ unsigned long long s_best[TPB / 32];
-    __shared__ unsigned s_fb;
-    const int64_t gi = blockIdx.x;
-    if (gi >= count) return;
-    const int32_t v = __ldg(list + gi);
-    if (threadIdx.x == 0) {
-        const int act = a.flag_cur[v] != 0;
-        if (act) a.flag_cur[v] = 0;
-        s_act = act;
-        s_fb = 0;
-    }
-    __syncthreads();
-    if (!s_act) return;                                // uniform for the block
-
-    const int64_t o0 = a.off[v], o1 = a.off[v + 1];
-    const uint32_t D = (uint32_t)(o1 - o0);
-    const uint32_t b = cap_bits(D << a.tshift);
-    const uint32_t p1 = cap_of_bits(b);
-    clear_table_vec(Hk, Hv, p1, threadIdx.x, TPB);
-    __syncthreads();
-    const int32_t cur = a.C[v];
     unsigned fb = 0;
-    unsigned long long best = 0;
-    for (int64_t eb = o0 + (threadIdx.x & ~31); eb < o1; eb += TPB) {
-        bool has;
-        int32_t k;
-        float wv;
-        load_entry(a, v, eb + (threadIdx.x & 31), o1, has, k, wv);
-        group_insert<32, true>(Hk, Hv, 1, p1, b, has, k, wv, best, fb);
-    }
-    if (fb) atomicAdd(&s_fb, fb);
-    best = group_max<32>(best);
-    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-    __syncthreads();
-    best = 0;
-#pragma unroll
-    for (int w = 0; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
-    int32_t cstar = -1;
-    const bool moved = decide(best, cur, a.pl, cstar);
-    if (moved) {
+    unsigned long long c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
+    for (int64_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
+        __syncthreads();                               // the previous vertex is finished
         if (threadIdx.x == 0) {
-            if (a.async_mode) {
-                a.C[v] = cstar;
-                __threadfence();
-            } else {
-                const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
-                a.mover_v[pos] = v;
-                a.mover_c[pos] = cstar;
+            const int32_t v0 = __ldg(list + gi);
+            const int act = a.flag_cur[v0] != 0;
+            if (act) a.flag_cur[v0] = 0;               // mark processed
+            s_act = act;
+            s_v = v0;
+        }
+        __syncthreads();
+        if (!s_act) continue;                          // uniform for the block
+        const int32_t v = s_v;
+        const int64_t o0 = a.off[v], o1 = a.off[v + 1];
+        const uint32_t D = (uint32_t)(o1 - o0);
+        const uint32_t b = cap_bits(D << a.tshift);
+        const uint32_t p1 = cap_of_bits(b);
+        clear_table_vec(Hk, Hv, p1, threadIdx.x, TPB);
+        __syncthreads();
+        const int32_t cur = a.C[v];
+        unsigned long long best = 0;
+        for (int64_t eb = o0 + (threadIdx.x & ~31); eb < o1; eb += TPB) {
+            bool has;
+            int32_t k;
+            float wv;
+            load_entry(a, v, eb + (threadIdx.x & 31), o1, has, k, wv);
+            group_insert<32, true>(Hk, Hv, 1, p1, b, has, k, wv, best, fb);
+        }
+        best = group_max<32>(best);
+        if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+        __syncthreads();
+        best = 0;
+#pragma unroll
+        for (int w = 0; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
+        int32_t cstar = -1;
+        const bool moved = decide(best, cur, a.pl, cstar);
+        if (moved) {
+            if (threadIdx.x == 0) {
+                if (a.async_mode) {
+                    a.C[v] = cstar;
+                    __threadfence();
+                } else {
+                    const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
+                    a.mover_v[pos] = v;
+                    a.mover_c[pos] = cstar;
+                }
+            }
+            if (a.async_mode) __syncthreads();
+            for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
+        }
+        if (threadIdx.x == 0) {
+            c_act += 1;
+            c_edges += D;
+            if (moved) {
+                c_moved += 1;
+                c_marks += D;
             }
         }
-        if (a.async_mode) __syncthreads();
-        for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
     }
     if (threadIdx.x == 0) {
         unsigned long long *c = a.ctr + kslot * kCtrFields;
-        atomicAdd(c + CTR_ACTIVE, 1ull);
-        atomicAdd(c + CTR_EDGES, (unsigned long long)D);
-        if (moved) {
-            atomicAdd(c + CTR_MOVED, 1ull);
-            atomicAdd(c + CTR_MARKS, (unsigned long long)D);
-        }
-        if (s_fb) atomicAdd(a.fallbacks, (unsigned long long)s_fb);
+        if (c_act) atomicAdd(c + CTR_ACTIVE, c_act);
+        if (c_edges) atomicAdd(c + CTR_EDGES, c_edges);
+        if (c_moved) atomicAdd(c + CTR_MOVED, c_moved);
+        if (c_marks) atomicAdd(c + CTR_MARKS, c_marks);
     }
+    if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
 }
 
 // ---------------------------------------------------------------------------------
@@ -464,18 +482,23 @@ __global__ void k_hub_begin(HubArgs h, SweepArgs a)
     h.hub_used[t] = 0u;
 }
 
+// Slots taken from empty are collected in a block-local list in shared memory and copied to
+// the hub's used list with one global atomic per block.
 template <int TPB>
-__global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a)
+__global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a, int chunk)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int32_t *s_list = (int32_t *)smem;                 // [chunk]
     __shared__ unsigned long long s_best[TPB / 32];
+    __shared__ uint32_t s_cnt, s_base;
     const int hh = h.chunk_h[blockIdx.x];
     if (!h.hub_act[hh]) return;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
     const int32_t v = h.hub_v[hh];
     const uint32_t p1 = h.hub_p1[hh], b = h.hub_b[hh];
     int32_t *Hk = h.tab_k + h.hub_tab[hh];
     float *Hv = h.tab_v + h.hub_tab[hh];
-    uint32_t *ucnt = h.hub_used + hh;
-    int32_t *ulist = h.used_list + h.used_base[hh];
     const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
     unsigned fb = 0;
     unsigned long long best = 0;
@@ -484,7 +507,7 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a)
         int32_t k;
         float wv;
         load_entry(a, v, eb + (threadIdx.x & 31), e1, has, k, wv);
-        group_insert<32, true, true>(Hk, Hv, 1, p1, b, has, k, wv, best, fb, ucnt, ulist);
+        group_insert<32, true, true>(Hk, Hv, 1, p1, b, has, k, wv, best, fb, &s_cnt, s_list);
     }
     if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
     best = group_max<32>(best);
@@ -493,9 +516,15 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a)
     if (threadIdx.x == 0) {
         for (int w = 1; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
         if (best) atomicMax(h.hub_best + hh, best);
+        s_base = s_cnt ? atomicAdd(h.hub_used + hh, s_cnt) : 0u;
     }
+    __syncthreads();
+    int32_t *ulist = h.used_list + h.used_base[hh] + s_base;
+    for (uint32_t q = threadIdx.x; q < s_cnt; q += TPB) ulist[q] = s_list[q];
 }
 
+// Clears the table slots a hub used in this sweep: slot by slot from the used list when
+// few were used, or the whole table with coalesced stores when more than an eighth were.
 template <int TPB>
 __global__ void __launch_bounds__(TPB) k_hub_clear(HubArgs h)
 {
@@ -503,10 +532,20 @@ __global__ void __launch_bounds__(TPB) k_hub_clear(HubArgs h)
     if (!h.hub_act[hh]) return;
     const int64_t lo = (int64_t)h.slice_j[blockIdx.x] * kHubSlice;
     const int64_t cnt = h.hub_used[hh];
-    if (lo >= cnt) return;
-    const int64_t hi = lo + kHubSlice < cnt ? lo + kHubSlice : cnt;
+    const int64_t p1 = h.hub_p1[hh];
     int32_t *Hk = h.tab_k + h.hub_tab[hh];
     float *Hv = h.tab_v + h.hub_tab[hh];
+    if (cnt * 8 > p1) {
+        if (lo >= p1) return;
+        const int64_t hi = lo + kHubSlice < p1 ? lo + kHubSlice : p1;
+        for (int64_t q = lo + threadIdx.x; q < hi; q += TPB) {
+            Hk[q] = kEmpty;
+            Hv[q] = 0.0f;
+        }
+        return;
+    }
+    if (lo >= cnt) return;
+    const int64_t hi = lo + kHubSlice < cnt ? lo + kHubSlice : cnt;
     const int32_t *ulist = h.used_list + h.used_base[hh];
     for (int64_t q = lo + threadIdx.x; q < hi; q += TPB) {
         const int32_t s = ulist[q];
@@ -598,6 +637,17 @@ static cudaError_t set_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <typename K>
+static int64_t persistent_grid(K kernel, int threads, size_t smem, int64_t work_blocks)
+{
+    query_device();
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t cap = (int64_t)g_num_sms * per_sm;
+    return work_blocks < cap ? work_blocks : cap;
+}
+
 template <int G, int TPB>
 static cudaError_t launch_g(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
                             cudaStream_t s)
@@ -607,7 +657,7 @@ static cudaError_t launch_g(const int32_t *list, int64_t count, const SweepArgs 
     const size_t smem = (size_t)NG * slots * (sizeof(int32_t) + sizeof(float));
     cudaError_t e = set_smem(k_group<G, TPB>, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (count + NG - 1) / NG;
+    const int64_t blocks = persistent_grid(k_group<G, TPB>, TPB, smem, (count + NG - 1) / NG);
     k_group<G, TPB><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
     return cudaGetLastError();
 }
@@ -644,7 +694,8 @@ static cudaError_t launch_c(const int32_t *list, int64_t count, const SweepArgs 
     const size_t smem = (size_t)slots * (sizeof(int32_t) + sizeof(float));
     cudaError_t e = set_smem(k_cta<TPB>, smem);
     if (e != cudaSuccess) return e;
-    k_cta<TPB><<<(unsigned)count, TPB, smem, s>>>(list, count, a, slots, kslot);
+    const int64_t blocks = persistent_grid(k_cta<TPB>, TPB, smem, count);
+    k_cta<TPB><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
     return cudaGetLastError();
 }
 
@@ -668,14 +719,13 @@ cudaError_t launch_hub_begin(const HubArgs &h, const SweepArgs &a, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, int threads, cudaStream_t s)
+cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, int chunk, cudaStream_t s)
 {
     if (n_chunks <= 0) return cudaSuccess;
-    switch (threads) {
-    case 256: k_hub_acc<256><<<(unsigned)n_chunks, 256, 0, s>>>(h, a); break;
-    case 512: k_hub_acc<512><<<(unsigned)n_chunks, 512, 0, s>>>(h, a); break;
-    default: k_hub_acc<1024><<<(unsigned)n_chunks, 1024, 0, s>>>(h, a); break;
-    }
+    const size_t smem = (size_t)chunk * sizeof(int32_t);
+    cudaError_t e = set_smem(k_hub_acc<1024>, smem);
+    if (e != cudaSuccess) return e;
+    k_hub_acc<1024><<<(unsigned)n_chunks, 1024, smem, s>>>(h, a, chunk);
     return cudaGetLastError();
 }
 
