@@ -123,7 +123,8 @@ typedef struct lpa_tuning {
     int32_t smem_table_shift; /* 0..2                                                    */
     int32_t cta_xl_max;       /* block of cta_xl_threads per vertex; above: hubs         */
     int32_t cta_xl_threads;
-    int32_t reserved[3];
+    int32_t persistent_mask;  /* bit k (kernel slot k <= LPA_K_CTA_XL): persistent grid  */
+    int32_t reserved[2];
 } lpa_tuning;
 
 typedef struct lpa_graph lpa_graph;

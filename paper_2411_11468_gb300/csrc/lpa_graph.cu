@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -202,24 +203,50 @@ __device__ __forceinline__ double warp_sum_d(double x)
     return x;
 }
 
-// Eq. 1 numerators: per row i, K_i = sum_j w_ij and the weight of entries with C_j = C_i;
-// Sigma_{C_i} += K_i.  float64 accumulation.  Each warp walks a contiguous range of rows and
-// adds runs of equal labels to Sigma with one atomic per run (labels of a community are
-// often contiguous, and one label may cover most of the graph).
-__global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int32_t *idx, const float *w,
-                                                  const int32_t *C, int64_t n, double *Sig, double *acc)
+// Eq. 1 numerators, float64.  Rows of degree <= hub_min: a warp per row (grid stride)
+// computes K_i = sum_j w_ij and the weight of entries with C_j = C_i.  Sigma_c = sum of K_i
+// over i in c is pre-aggregated per block in a small shared-memory table and added to the
+// global Sigma with one atomic per distinct label per block (one label may cover most of
+// the graph, and per-vertex atomics on it would serialise); labels that do not fit go to
+// Sigma directly.
+constexpr int kModSlots = 1024;
+
+__device__ __forceinline__ void mod_sigma_add(int32_t *sk, double *sv, double *Sig, int32_t c, double k)
 {
+    uint32_t s = ((uint32_t)c * 2654435761u) >> 22;          // 10-bit multiplicative hash
+    for (int t = 0; t < 8; ++t, s = (s + 1) & (kModSlots - 1)) {
+        int32_t kk = *((volatile int32_t *)(sk + s));
+        if (kk == -1) {
+            const int32_t old = atomicCAS(sk + s, -1, c);
+            kk = (old == -1) ? c : old;
+        }
+        if (kk == c) {
+            atomicAdd(sv + s, k);
+            return;
+        }
+    }
+    atomicAdd(Sig + c, k);
+}
+
+__global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int32_t *idx, const float *w,
+                                                  const int32_t *C, int64_t n, int64_t hub_min, double *Sig,
+                                                  double *acc)
+{
+    __shared__ int32_t sk[kModSlots];
+    __shared__ double sv[kModSlots];
     __shared__ double s_in[8], s_k[8];
+    for (int q = threadIdx.x; q < kModSlots; q += 256) {
+        sk[q] = -1;
+        sv[q] = 0.0;
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t per = (n + nwarps - 1) / nwarps;
-    const int64_t r0 = warp * per, r1 = r0 + per < n ? r0 + per : n;
-    double tin = 0.0, tk = 0.0, run = 0.0;
-    int32_t run_c = -1;
-    for (int64_t i = r0; i < r1; ++i) {
+    double tin = 0.0, tk = 0.0;
+    for (int64_t i = warp; i < n; i += nwarps) {
         const int64_t o0 = off[i], o1 = off[i + 1];
-        if (o0 == o1) continue;
+        if (o0 == o1 || o1 - o0 > hub_min) continue;
         const int32_t ci = C[i];
         double k = 0.0, in = 0.0;
         for (int64_t e = o0 + lane; e < o1; e += 32) {
@@ -229,19 +256,50 @@ __global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int3
         }
         k = warp_sum_d(k);
         in = warp_sum_d(in);
-        tin += in;
-        tk += k;
-        if (ci != run_c) {
-            if (lane == 0 && run_c >= 0) atomicAdd(Sig + run_c, run);
-            run_c = ci;
-            run = 0.0;
+        if (lane == 0) {
+            tin += in;
+            tk += k;
+            mod_sigma_add(sk, sv, Sig, ci, k);
         }
-        run += k;
     }
-    if (lane == 0 && run_c >= 0) atomicAdd(Sig + run_c, run);
     if (lane == 0) {
         s_in[threadIdx.x >> 5] = tin;
         s_k[threadIdx.x >> 5] = tk;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kModSlots; q += 256)
+        if (sk[q] != -1) atomicAdd(Sig + sk[q], sv[q]);
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < 8; ++q) {
+            a += s_in[q];
+            b += s_k[q];
+        }
+        atomicAdd(acc + 0, a);
+        atomicAdd(acc + 1, b);
+    }
+}
+
+// The same sums for the rows of hubs (degree > hub_min), a block per CSR chunk.
+__global__ void __launch_bounds__(256) k_mod_hubs(const int32_t *idx, const float *w, const int32_t *C,
+                                                  const int32_t *hub_v, const int32_t *chunk_h,
+                                                  const int64_t *chunk_e0, const int64_t *chunk_e1, double *Sig,
+                                                  double *acc)
+{
+    __shared__ double s_in[8], s_k[8];
+    const int32_t v = hub_v[chunk_h[blockIdx.x]];
+    const int32_t ci = C[v];
+    double k = 0.0, in = 0.0;
+    for (int64_t e = chunk_e0[blockIdx.x] + threadIdx.x; e < chunk_e1[blockIdx.x]; e += 256) {
+        const double we = w ? (double)w[e] : 1.0;
+        k += we;
+        if (C[idx[e]] == ci) in += we;
+    }
+    k = warp_sum_d(k);
+    in = warp_sum_d(in);
+    if ((threadIdx.x & 31) == 0) {
+        s_in[threadIdx.x >> 5] = in;
+        s_k[threadIdx.x >> 5] = k;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -252,6 +310,7 @@ __global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int3
         }
         atomicAdd(acc + 0, a);
         atomicAdd(acc + 1, b);
+        atomicAdd(Sig + ci, b);
     }
 }
 
@@ -371,6 +430,7 @@ lpa_tuning default_tuning()
     t.cta_large_threads = 256;
     t.cta_xl_max = 8191;
     t.cta_xl_threads = 512;
+    t.persistent_mask = (1 << LPA_K_WARP) | (1 << LPA_K_CTA) | (1 << LPA_K_CTA_LARGE) | (1 << LPA_K_CTA_XL);
     t.hub_chunk = 8192;
     t.hub_table_shift = 1;
     t.smem_table_shift = 1;
@@ -397,6 +457,7 @@ int check_tuning(const lpa_tuning &t)
     for (int th : {t.cta_threads, t.cta_large_threads, t.cta_xl_threads})
         if (!pow2(th) || th < 64 || th > 1024) return LPA_EINVAL;
     if (t.hub_chunk < 256 || t.hub_chunk > 32768) return LPA_EINVAL;
+    if (t.persistent_mask & ~0x3F) return LPA_EINVAL;
     const int64_t smem = (int64_t)max_dynamic_smem();
     const int64_t bytes_group = (256 / t.group_lanes) * slots_for(t.group_max, sh) * 8;
     const int64_t bytes_warp = 8 * slots_for(t.warp_max, sh) * 8;
@@ -942,7 +1003,12 @@ int lpa_modularity(const lpa_graph *gc, double *q)
         LPA_CUDA(cudaMemsetAsync(g->Sig, 0, (size_t)g->n * sizeof(double), g->stream));
     }
     LPA_CUDA(cudaMemsetAsync(g->macc, 0, 3 * sizeof(double), g->stream));
-    k_mod_rows<<<grid_for(g->n * 32, 256, 16), 256, 0, g->stream>>>(g->off, g->idx, g->w, g->C, g->n, g->Sig, g->macc);
+    const int64_t hub_min = g->hub.n_hubs > 0 ? (int64_t)g->tuning.cta_xl_max : INT64_MAX;
+    k_mod_rows<<<grid_for(g->n * 32, 256, 16), 256, 0, g->stream>>>(g->off, g->idx, g->w, g->C, g->n, hub_min,
+                                                                    g->Sig, g->macc);
+    if (g->hub.n_hubs > 0 && g->n_chunks > 0)
+        k_mod_hubs<<<(unsigned)g->n_chunks, 256, 0, g->stream>>>(g->idx, g->w, g->C, g->hub.hub_v, g->hub.chunk_h,
+                                                                 g->hub.chunk_e0, g->hub.chunk_e1, g->Sig, g->macc);
     k_mod_sq<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->Sig, g->n, g->macc);
     double h[3];
     LPA_CUDA(cudaMemcpyAsync(h, g->macc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
@@ -1023,6 +1089,7 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
         a.pl = pl ? 1 : 0;
         a.async_mode = async_mode ? 1 : 0;
         a.tshift = t.smem_table_shift;
+        a.persist_mask = t.persistent_mask;
         const int sh = t.smem_table_shift;
 
         size_t ie0 = evn++, ie1 = evn++;

@@ -33,6 +33,7 @@ struct SweepArgs {
     int32_t pl;                // Pick-Less active on this sweep
     int32_t async_mode;        // 1: write labels in place (ASYNC), 0: record movers (SYNC)
     int32_t tshift;            // smem table capacity = nextPow2(D << tshift) - 1
+    int32_t persist_mask;      // bit k: kernel slot k runs as a persistent grid
 };
 
 // Hub-bucket device arrays.

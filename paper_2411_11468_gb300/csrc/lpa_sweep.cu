@@ -657,7 +657,9 @@ static cudaError_t launch_g(const int32_t *list, int64_t count, const SweepArgs 
     const size_t smem = (size_t)NG * slots * (sizeof(int32_t) + sizeof(float));
     cudaError_t e = set_smem(k_group<G, TPB>, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = persistent_grid(k_group<G, TPB>, TPB, smem, (count + NG - 1) / NG);
+    const int64_t need = (count + NG - 1) / NG;
+    const bool persist = (a.persist_mask >> kslot) & 1;   // else one pass: a block per NG vertices
+    const int64_t blocks = persist ? persistent_grid(k_group<G, TPB>, TPB, smem, need) : need;
     k_group<G, TPB><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
     return cudaGetLastError();
 }
@@ -694,7 +696,8 @@ static cudaError_t launch_c(const int32_t *list, int64_t count, const SweepArgs 
     const size_t smem = (size_t)slots * (sizeof(int32_t) + sizeof(float));
     cudaError_t e = set_smem(k_cta<TPB>, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = persistent_grid(k_cta<TPB>, TPB, smem, count);
+    const bool persist = (a.persist_mask >> kslot) & 1;
+    const int64_t blocks = persist ? persistent_grid(k_cta<TPB>, TPB, smem, count) : count;
     k_cta<TPB><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
     return cudaGetLastError();
 }
