@@ -15,7 +15,9 @@
  * Input graphs are undirected CSR graphs as in the paper's Preliminaries: every
  * edge {i, j} is stored in row i and in row j with the same weight w_ij >= 0.
  * Vertex ids and labels are int32; weights and label sums are float32 (the
- * paper's Configuration paragraph).  Modularity (Eq. 1) is accumulated in float64.
+ * paper's Configuration paragraph); when every weight is an integer and every weighted
+ * degree is below 2^24 the label sums are kept as uint32, which gives the same sums and
+ * the same winners.  Modularity (Eq. 1) is exact for integer weights, else float64.
  *
  * Conventions for every call:
  *  - Status: every call returns LPA_OK (0) or a negative LPA_E* code; lpa_strerror()
@@ -124,7 +126,8 @@ typedef struct lpa_tuning {
     int32_t cta_xl_max;       /* block of cta_xl_threads per vertex; above: hubs         */
     int32_t cta_xl_threads;
     int32_t persistent_mask;  /* bit k (kernel slot k <= LPA_K_CTA_XL): persistent grid  */
-    int32_t reserved[2];
+    int32_t float_values;     /* 1: float32 label sums even when integer sums would do   */
+    int32_t reserved[1];
 } lpa_tuning;
 
 typedef struct lpa_graph lpa_graph;
@@ -164,7 +167,9 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
 int lpa_labels(const lpa_graph *g, int32_t *out, int64_t n, int out_on_device);
 
 /* Modularity of the current labels, Eq. 1 in its community form
- * Q = sum_c [sigma_c / 2m - (Sigma_c / 2m)^2], accumulated in float64 on the device.
+ * Q = sum_c [sigma_c / 2m - (Sigma_c / 2m)^2].  With integer weights (and weighted degrees
+ * below 2^24) every sum is an exact integer on the device and Q = (2m sigma - sum Sigma_c^2)
+ * / (2m)^2 is rounded once; otherwise the sums are accumulated in float64.
  * A graph with no edge weight (2m = 0) has Q = 0. */
 int lpa_modularity(const lpa_graph *g, double *q);
 

@@ -314,6 +314,174 @@ __global__ void __launch_bounds__(256) k_mod_hubs(const int32_t *idx, const floa
     }
 }
 
+// Weight properties at creation: bit 1 of *flags is cleared when a weight is not an integer
+// in [0, 2^24); *max_k receives the largest row sum (integer rows only).
+__global__ void __launch_bounds__(256) k_weight_props(const int64_t *off, const float *w, int64_t n,
+                                                      unsigned *flags, unsigned long long *max_k)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long mx = 0;
+    bool integral = true;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        unsigned long long k = 0;
+        for (int64_t e = off[i] + lane; e < off[i + 1]; e += 32) {
+            const float x = w ? w[e] : 1.0f;
+            if (!(x >= 0.0f && x < 16777216.0f && truncf(x) == x)) integral = false;
+            k += (unsigned long long)x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xFFFFFFFFu, k, o);
+        mx = k > mx ? k : mx;
+    }
+    if (!integral) atomicAnd(flags, ~2u);
+    if (lane == 0 && mx) atomicMax(max_k, mx);
+}
+
+// Integer-weight modularity: every sum is an exact integer (int64 for sigma, Sigma_c and 2m,
+// 128 bits for sum_c Sigma_c^2), so Q is exact up to the final division and independent of
+// the order of the atomics.
+__device__ __forceinline__ void mod_sigma_add_u(int32_t *sk, unsigned long long *sv, unsigned long long *Sig,
+                                                int32_t c, unsigned long long k)
+{
+    uint32_t s = ((uint32_t)c * 2654435761u) >> 22;
+    for (int t = 0; t < 8; ++t, s = (s + 1) & (kModSlots - 1)) {
+        int32_t kk = *((volatile int32_t *)(sk + s));
+        if (kk == -1) {
+            const int32_t old = atomicCAS(sk + s, -1, c);
+            kk = (old == -1) ? c : old;
+        }
+        if (kk == c) {
+            atomicAdd(sv + s, k);
+            return;
+        }
+    }
+    atomicAdd(Sig + c, k);
+}
+
+__global__ void __launch_bounds__(256) k_mod_rows_int(const int64_t *off, const int32_t *idx, const float *w,
+                                                      const int32_t *C, int64_t n, int64_t hub_min,
+                                                      unsigned long long *Sig, unsigned long long *acc)
+{
+    __shared__ int32_t sk[kModSlots];
+    __shared__ unsigned long long sv[kModSlots];
+    __shared__ unsigned long long s_in[8], s_k[8];
+    for (int q = threadIdx.x; q < kModSlots; q += 256) {
+        sk[q] = -1;
+        sv[q] = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long tin = 0, tk = 0;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int64_t o0 = off[i], o1 = off[i + 1];
+        if (o0 == o1 || o1 - o0 > hub_min) continue;
+        const int32_t ci = C[i];
+        unsigned k = 0, in = 0;                        // row sums < 2^24
+        for (int64_t e = o0 + lane; e < o1; e += 32) {
+            const unsigned we = w ? (unsigned)w[e] : 1u;
+            k += we;
+            if (C[idx[e]] == ci) in += we;
+        }
+        k = __reduce_add_sync(0xFFFFFFFFu, k);
+        in = __reduce_add_sync(0xFFFFFFFFu, in);
+        if (lane == 0) {
+            tin += in;
+            tk += k;
+            mod_sigma_add_u(sk, sv, Sig, ci, k);
+        }
+    }
+    if (lane == 0) {
+        s_in[threadIdx.x >> 5] = tin;
+        s_k[threadIdx.x >> 5] = tk;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kModSlots; q += 256)
+        if (sk[q] != -1) atomicAdd(Sig + sk[q], sv[q]);
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0;
+        for (int q = 0; q < 8; ++q) {
+            a += s_in[q];
+            b += s_k[q];
+        }
+        atomicAdd(acc + 0, a);
+        atomicAdd(acc + 1, b);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mod_hubs_int(const int32_t *idx, const float *w, const int32_t *C,
+                                                      const int32_t *hub_v, const int32_t *chunk_h,
+                                                      const int64_t *chunk_e0, const int64_t *chunk_e1,
+                                                      unsigned long long *Sig, unsigned long long *acc)
+{
+    __shared__ unsigned s_in[8], s_k[8];
+    const int32_t v = hub_v[chunk_h[blockIdx.x]];
+    const int32_t ci = C[v];
+    unsigned k = 0, in = 0;
+    for (int64_t e = chunk_e0[blockIdx.x] + threadIdx.x; e < chunk_e1[blockIdx.x]; e += 256) {
+        const unsigned we = w ? (unsigned)w[e] : 1u;
+        k += we;
+        if (C[idx[e]] == ci) in += we;
+    }
+    k = __reduce_add_sync(0xFFFFFFFFu, k);
+    in = __reduce_add_sync(0xFFFFFFFFu, in);
+    if ((threadIdx.x & 31) == 0) {
+        s_in[threadIdx.x >> 5] = in;
+        s_k[threadIdx.x >> 5] = k;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0;
+        for (int q = 0; q < 8; ++q) {
+            a += s_in[q];
+            b += s_k[q];
+        }
+        atomicAdd(acc + 0, a);
+        atomicAdd(acc + 1, b);
+        atomicAdd(Sig + ci, b);
+    }
+}
+
+// sum_c Sigma_c^2 as a 128-bit integer (acc[2] low word, acc[3] high word); resets Sigma.
+__device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi, unsigned long long xl,
+                                       unsigned long long xh)
+{
+    const unsigned long long r = lo + xl;
+    hi += xh + (r < lo ? 1ull : 0ull);
+    lo = r;
+}
+
+__global__ void __launch_bounds__(256) k_mod_sq_int(unsigned long long *Sig, int64_t n, unsigned long long *acc)
+{
+    __shared__ unsigned long long s_lo[8], s_hi[8];
+    unsigned long long lo = 0, hi = 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long x = Sig[c];
+        if (x) {
+            add128(lo, hi, x * x, __umul64hi(x, x));
+            Sig[c] = 0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        add128(lo, hi, __shfl_xor_sync(0xFFFFFFFFu, lo, o), __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        lo = 0;
+        hi = 0;
+        for (int q = 0; q < 8; ++q) add128(lo, hi, s_lo[q], s_hi[q]);
+        const unsigned long long old = atomicAdd(acc + 2, lo);
+        atomicAdd(acc + 3, hi + (old + lo < old ? 1ull : 0ull));
+    }
+}
+
 __global__ void __launch_bounds__(256) k_mod_sq(double *Sig, int64_t n, double *acc)
 {
     __shared__ double s[8];
@@ -390,6 +558,7 @@ struct lpa_graph {
     float *tab_v = nullptr;
     int32_t *used_list = nullptr;
     int next_iter = 0;
+    bool int_weights = false;         // integer weights, weighted degrees < 2^24
     int64_t bytes = 0, bucket_bytes = 0;
     std::vector<cudaEvent_t> events;
 };
@@ -429,9 +598,9 @@ lpa_tuning default_tuning()
     t.cta_large_max = 4095;
     t.cta_large_threads = 256;
     t.cta_xl_max = 8191;
-    t.cta_xl_threads = 512;
+    t.cta_xl_threads = 1024;
     t.persistent_mask = (1 << LPA_K_WARP) | (1 << LPA_K_CTA) | (1 << LPA_K_CTA_LARGE) | (1 << LPA_K_CTA_XL);
-    t.hub_chunk = 8192;
+    t.hub_chunk = 16384;
     t.hub_table_shift = 1;
     t.smem_table_shift = 1;
     return t;
@@ -458,6 +627,7 @@ int check_tuning(const lpa_tuning &t)
         if (!pow2(th) || th < 64 || th > 1024) return LPA_EINVAL;
     if (t.hub_chunk < 256 || t.hub_chunk > 32768) return LPA_EINVAL;
     if (t.persistent_mask & ~0x3F) return LPA_EINVAL;
+    if (t.float_values != 0 && t.float_values != 1) return LPA_EINVAL;
     const int64_t smem = (int64_t)max_dynamic_smem();
     const int64_t bytes_group = (256 / t.group_lanes) * slots_for(t.group_max, sh) * 8;
     const int64_t bytes_warp = 8 * slots_for(t.warp_max, sh) * 8;
@@ -793,7 +963,7 @@ int lpa_create(const void *offsets, const int32_t *indices, const float *weights
     if ((st = dalloc(g, &g->mover_count, 1)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->fallbacks, 1)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->d_err, 4)) != LPA_OK) return fail(st);
-    if ((st = dalloc(g, &g->macc, 4)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->macc, 4)) != LPA_OK) return fail(st);          // 4 x 8 bytes
     if ((st = ensure_ctr(g, 32)) != LPA_OK) return fail(st);
 
     cudaStream_t s = g->stream;
@@ -841,6 +1011,24 @@ int lpa_create(const void *offsets, const int32_t *indices, const float *weights
         if (err & 16) msg += " weight negative, NaN or Inf;";
         set_error(msg);
         return fail(LPA_EINVAL);
+    }
+    {
+        unsigned long long *mk = nullptr;
+        if ((st = dalloc(g, &mk, 1)) != LPA_OK) return fail(st);
+        unsigned *fl = reinterpret_cast<unsigned *>(g->d_err);
+        cudaMemsetAsync(mk, 0, sizeof(unsigned long long), s);
+        const unsigned two = 2u;
+        cudaMemcpyAsync(fl, &two, sizeof(unsigned), cudaMemcpyHostToDevice, s);
+        k_weight_props<<<grid_for(n * 32, 256, 16), 256, 0, s>>>(g->off, g->w, n, fl, mk);
+        unsigned hf = 0;
+        unsigned long long hk = 0;
+        cudaMemcpyAsync(&hf, fl, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&hk, mk, sizeof(hk), cudaMemcpyDeviceToHost, s);
+        e = cudaStreamSynchronize(s);
+        cudaFree(mk);
+        g->bytes -= (int64_t)sizeof(unsigned long long);
+        if (e != cudaSuccess) return cuda_fail(e, "weight properties");
+        g->int_weights = (hf & 2u) && hk < (1ull << 24);
     }
     if (flags & LPA_CHECK_SYMMETRIC) {
         unsigned long long *acc = nullptr;
@@ -1002,8 +1190,27 @@ int lpa_modularity(const lpa_graph *gc, double *q)
         LPA_CHECK(dalloc(g, &g->Sig, (size_t)g->n));
         LPA_CUDA(cudaMemsetAsync(g->Sig, 0, (size_t)g->n * sizeof(double), g->stream));
     }
-    LPA_CUDA(cudaMemsetAsync(g->macc, 0, 3 * sizeof(double), g->stream));
+    LPA_CUDA(cudaMemsetAsync(g->macc, 0, 4 * sizeof(double), g->stream));
     const int64_t hub_min = g->hub.n_hubs > 0 ? (int64_t)g->tuning.cta_xl_max : INT64_MAX;
+    if (g->int_weights) {
+        unsigned long long *SigU = reinterpret_cast<unsigned long long *>(g->Sig);
+        unsigned long long *acc = reinterpret_cast<unsigned long long *>(g->macc);
+        k_mod_rows_int<<<grid_for(g->n * 32, 256, 16), 256, 0, g->stream>>>(g->off, g->idx, g->w, g->C, g->n, hub_min,
+                                                                            SigU, acc);
+        if (g->hub.n_hubs > 0 && g->n_chunks > 0)
+            k_mod_hubs_int<<<(unsigned)g->n_chunks, 256, 0, g->stream>>>(g->idx, g->w, g->C, g->hub.hub_v,
+                                                                         g->hub.chunk_h, g->hub.chunk_e0,
+                                                                         g->hub.chunk_e1, SigU, acc);
+        k_mod_sq_int<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(SigU, g->n, acc);
+        unsigned long long h[4];
+        LPA_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+        LPA_CUDA(cudaStreamSynchronize(g->stream));
+        const __int128 two_m = (__int128)h[1], in = (__int128)h[0];
+        const __int128 sq = ((__int128)h[3] << 64) | (__int128)h[2];
+        const __int128 num = two_m * in - sq, den = two_m * two_m;
+        *q = (den == 0) ? 0.0 : (double)num / (double)den;
+        return LPA_OK;
+    }
     k_mod_rows<<<grid_for(g->n * 32, 256, 16), 256, 0, g->stream>>>(g->off, g->idx, g->w, g->C, g->n, hub_min,
                                                                     g->Sig, g->macc);
     if (g->hub.n_hubs > 0 && g->n_chunks > 0)
@@ -1090,6 +1297,7 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
         a.async_mode = async_mode ? 1 : 0;
         a.tshift = t.smem_table_shift;
         a.persist_mask = t.persistent_mask;
+        a.int_weights = (g->int_weights && !t.float_values) ? 1 : 0;
         const int sh = t.smem_table_shift;
 
         size_t ie0 = evn++, ie1 = evn++;

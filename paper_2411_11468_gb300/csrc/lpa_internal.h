@@ -34,6 +34,7 @@ struct SweepArgs {
     int32_t async_mode;        // 1: write labels in place (ASYNC), 0: record movers (SYNC)
     int32_t tshift;            // smem table capacity = nextPow2(D << tshift) - 1
     int32_t persist_mask;      // bit k: kernel slot k runs as a persistent grid
+    int32_t int_weights;       // 1: integer weights with weighted degrees < 2^24 (uint32 sums)
 };
 
 // Hub-bucket device arrays.

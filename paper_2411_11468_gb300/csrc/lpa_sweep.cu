@@ -47,9 +47,19 @@ __device__ __forceinline__ uint32_t mod_mersenne(uint32_t a, uint32_t b, uint32_
     return (uint32_t)__umul64hi(low, (unsigned long long)p);
 }
 
-__device__ __forceinline__ unsigned long long pack_kv(float w, int32_t k)
+// Label-weight values are float32, or uint32 when every weight is an integer and every
+// weighted degree is below 2^24 (then each float32 sum is exact and equals the integer sum,
+// and both compare the same way).  vbits gives bits that order like the value (values >= 0).
+__device__ __forceinline__ uint32_t vbits(float w) { return __float_as_uint(w); }
+__device__ __forceinline__ uint32_t vbits(uint32_t w) { return w; }
+template <typename V> __device__ __forceinline__ V to_value(float w);
+template <> __device__ __forceinline__ float to_value<float>(float w) { return w; }
+template <> __device__ __forceinline__ uint32_t to_value<uint32_t>(float w) { return (uint32_t)w; }
+
+template <typename V>
+__device__ __forceinline__ unsigned long long pack_kv(V w, int32_t k)
 {
-    return ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(~(uint32_t)k);
+    return ((unsigned long long)vbits(w) << 32) | (unsigned long long)(~(uint32_t)k);
 }
 
 __device__ __forceinline__ int32_t unpack_key(unsigned long long p)
@@ -69,15 +79,15 @@ __device__ __forceinline__ uint32_t cap_of_bits(uint32_t b) { return b >= 32 ? 0
 // One slot attempt of Algorithm 2: take slot s if it is empty or already holds k, add v
 // and fold the new sum into `best`.  With TRACK a slot taken from empty is appended to the
 // table's used list.
-template <bool SHARED, bool TRACK>
-__device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32_t k, float v,
+template <bool SHARED, bool TRACK, typename V>
+__device__ __forceinline__ bool try_slot(int32_t *Hk, V *Hv, size_t s, int32_t k, V v,
                                          unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
 {
     if (!SHARED) {                                    // single owner: plain accesses
         const int32_t kk = Hk[s];
         if (kk == k || kk == kEmpty) {
             Hk[s] = k;
-            const float nv = Hv[s] + v;
+            const V nv = Hv[s] + v;
             Hv[s] = nv;
             best = umax64(best, pack_kv(nv, k));
             return true;
@@ -95,7 +105,7 @@ __device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32
         }
     }
     if (kk == k) {
-        const float nv = atomicAdd(Hv + s, v) + v;
+        const V nv = atomicAdd(Hv + s, v) + v;
         best = umax64(best, pack_kv(nv, k));
         return true;
     }
@@ -104,9 +114,9 @@ __device__ __forceinline__ bool try_slot(int32_t *Hk, float *Hv, size_t s, int32
 
 // hashtableAccumulate (Algorithm 2) with i and delta kept reduced mod p1 (same slots),
 // then a linear scan from the last probed slot once the probe budget is spent.
-template <bool SHARED, bool TRACK = false>
-__device__ __forceinline__ void ht_accumulate(int32_t *Hk, float *Hv, int stride, uint32_t p1, uint32_t b,
-                                              int32_t k, float v, unsigned long long &best, unsigned &fallbacks,
+template <bool SHARED, bool TRACK, typename V>
+__device__ __forceinline__ void ht_accumulate(int32_t *Hk, V *Hv, int stride, uint32_t p1, uint32_t b,
+                                              int32_t k, V v, unsigned long long &best, unsigned &fallbacks,
                                               uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
 {
     const uint32_t uk = (uint32_t)k;
@@ -170,9 +180,9 @@ __device__ __forceinline__ unsigned long long group_max(unsigned long long x)
 // weights keep every partial sum exact, so the table contents do not depend on the order.
 constexpr int kPeel = 3;
 
-template <int G, bool SHARED, bool TRACK = false>
-__device__ __forceinline__ void group_insert(int32_t *Hk, float *Hv, int stride, uint32_t p1, uint32_t b,
-                                             bool has, int32_t k, float w, unsigned long long &best, unsigned &fb,
+template <int G, bool SHARED, bool TRACK, typename V>
+__device__ __forceinline__ void group_insert(int32_t *Hk, V *Hv, int stride, uint32_t p1, uint32_t b,
+                                             bool has, int32_t k, V w, unsigned long long &best, unsigned &fb,
                                              uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
 {
     if (G >= 2) {
@@ -186,7 +196,7 @@ __device__ __forceinline__ void group_insert(int32_t *Hk, float *Hv, int stride,
             const bool mine = has && k == kl;
             const unsigned same = __ballot_sync(gm, mine);
             if (__popc(same) < 2) break;
-            float sum = mine ? w : 0.0f;
+            V sum = mine ? w : V(0);
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gm, sum, o);
             if (lane == leader) ht_accumulate<SHARED, TRACK>(Hk, Hv, stride, p1, b, kl, sum, best, fb, ucnt, ulist);
@@ -199,14 +209,15 @@ __device__ __forceinline__ void group_insert(int32_t *Hk, float *Hv, int stride,
 
 // hashtableClear of slots [0, p1] of a contiguous, 16-byte aligned table with 16-byte stores
 // (p1 + 1 is a power of two, at least 4 slots are allocated).
-__device__ __forceinline__ void clear_table_vec(int32_t *Hk, float *Hv, uint32_t p1, int first, int step)
+// (Values are cleared to all-zero bits, which is 0 for both value types.)
+__device__ __forceinline__ void clear_table_vec(int32_t *Hk, void *Hv, uint32_t p1, int first, int step)
 {
     const uint32_t chunks = (p1 + 4u) >> 2;
     int4 *K4 = reinterpret_cast<int4 *>(Hk);
-    float4 *V4 = reinterpret_cast<float4 *>(Hv);
+    int4 *V4 = reinterpret_cast<int4 *>(Hv);
     for (uint32_t q = first; q < chunks; q += step) {
         K4[q] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
-        V4[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        V4[q] = make_int4(0, 0, 0, 0);
     }
 }
 
@@ -258,18 +269,19 @@ __device__ __forceinline__ void flush_block_counts(const SweepArgs &a, unsigned 
 
 // Loads entry e of the row of v: (label of the neighbour, weight); has = false for e past
 // the row end and for self-loops (Algorithm 1 skips j = i).
+template <typename V>
 __device__ __forceinline__ void load_entry(const SweepArgs &a, int32_t v, int64_t e, int64_t end, bool &has,
-                                           int32_t &k, float &wv)
+                                           int32_t &k, V &wv)
 {
     has = e < end;
     k = 0;
-    wv = 0.0f;
+    wv = V(0);
     if (has) {
         const int32_t j = a.idx[e];
         has = (j != v);
         if (has) {
             k = a.C[j];
-            wv = a.w ? a.w[e] : 1.0f;
+            wv = a.w ? to_value<V>(a.w[e]) : V(1);
         }
     }
 }
@@ -286,7 +298,7 @@ __device__ __forceinline__ bool decide(unsigned long long best, int32_t cur, int
 // G lanes per vertex (G = 1: thread per vertex with a private table; G = 32: warp per
 // vertex).  Persistent: every warp walks the bucket list in steps of 32/G vertices, so the
 // block synchronises only at its start and end.
-template <int G, int TPB>
+template <int G, int TPB, typename V>
 __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list, int64_t count, SweepArgs a,
                                                int slots, int kslot)
 {
@@ -302,15 +314,15 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
     const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
     const int grp = threadIdx.x / G;
     int32_t *Hk;
-    float *Hv;
+    V *Hv;
     int stride;
     if (G == 1) {                      // interleaved: slot s of thread t at s * TPB + t
         Hk = (int32_t *)smem + threadIdx.x;
-        Hv = (float *)(smem + (size_t)TPB * slots * sizeof(int32_t)) + threadIdx.x;
+        Hv = (V *)(smem + (size_t)TPB * slots * sizeof(int32_t)) + threadIdx.x;
         stride = TPB;
     } else {
         Hk = (int32_t *)smem + (size_t)grp * slots;
-        Hv = (float *)(smem + (size_t)NG * slots * sizeof(int32_t)) + (size_t)grp * slots;
+        Hv = (V *)(smem + (size_t)NG * slots * sizeof(int32_t)) + (size_t)grp * slots;
         stride = 1;
     }
 
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
             if (G == 1) {
                 for (uint32_t s = 0; s < p1; ++s) {        // hashtableClear
                     Hk[(size_t)s * stride] = kEmpty;
-                    Hv[(size_t)s * stride] = 0.0f;
+                    Hv[(size_t)s * stride] = V(0);
                 }
             } else {
                 group_sync<G>();                           // previous vertex's inserts are done
@@ -352,9 +364,9 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
             for (int64_t eb = o0; eb < o1; eb += G) {      // scan neighbours
                 bool has;
                 int32_t k;
-                float wv;
+                V wv;
                 load_entry(a, v, eb + lane, o1, has, k, wv);
-                group_insert<G, (G > 1)>(Hk, Hv, stride, p1, b, has, k, wv, best, fb);
+                group_insert<G, (G > 1), false>(Hk, Hv, stride, p1, b, has, k, wv, best, fb);
             }
             best = group_max<G>(best);                     // hashtableMaxKey
             moved = decide(best, cur, a.pl, cstar);
@@ -385,13 +397,13 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
 // ---------------------------------------------------------------------------------
 // One thread block per vertex; the table (up to slots entries) lives in dynamic smem.
 // Persistent: each block walks the bucket list with a grid stride.
-template <int TPB>
+template <int TPB, typename V>
 __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, int64_t count, SweepArgs a,
                                              int slots, int kslot)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     int32_t *Hk = (int32_t *)smem;
-    float *Hv = (float *)(smem + (size_t)slots * sizeof(int32_t));
+    V *Hv = (V *)(smem + (size_t)slots * sizeof(int32_t));
     __shared__ int s_act;
     __shared__ int32_t s_v;
     __shared__ unsigned long long s_best[TPB / 32];
@@ -420,9 +432,9 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
         for (int64_t eb = o0 + (threadIdx.x & ~31); eb < o1; eb += TPB) {
             bool has;
             int32_t k;
-            float wv;
+            V wv;
             load_entry(a, v, eb + (threadIdx.x & 31), o1, has, k, wv);
-            group_insert<32, true>(Hk, Hv, 1, p1, b, has, k, wv, best, fb);
+            group_insert<32, true, false>(Hk, Hv, 1, p1, b, has, k, wv, best, fb);
         }
         best = group_max<32>(best);
         if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
@@ -484,7 +496,7 @@ __global__ void k_hub_begin(HubArgs h, SweepArgs a)
 
 // Slots taken from empty are collected in a block-local list in shared memory and copied to
 // the hub's used list with one global atomic per block.
-template <int TPB>
+template <int TPB, typename V>
 __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a, int chunk)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -498,14 +510,14 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a, int chu
     const int32_t v = h.hub_v[hh];
     const uint32_t p1 = h.hub_p1[hh], b = h.hub_b[hh];
     int32_t *Hk = h.tab_k + h.hub_tab[hh];
-    float *Hv = h.tab_v + h.hub_tab[hh];
+    V *Hv = reinterpret_cast<V *>(h.tab_v) + h.hub_tab[hh];
     const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
     unsigned fb = 0;
     unsigned long long best = 0;
     for (int64_t eb = e0 + (threadIdx.x & ~31); eb < e1; eb += TPB) {
         bool has;
         int32_t k;
-        float wv;
+        V wv;
         load_entry(a, v, eb + (threadIdx.x & 31), e1, has, k, wv);
         group_insert<32, true, true>(Hk, Hv, 1, p1, b, has, k, wv, best, fb, &s_cnt, s_list);
     }
@@ -648,20 +660,28 @@ static int64_t persistent_grid(K kernel, int threads, size_t smem, int64_t work_
     return work_blocks < cap ? work_blocks : cap;
 }
 
+template <int G, int TPB, typename V>
+static cudaError_t launch_gv(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
+                             cudaStream_t s)
+{
+    constexpr int NG = TPB / G;
+    const size_t smem = (size_t)NG * slots * (sizeof(int32_t) + sizeof(V));
+    cudaError_t e = set_smem(k_group<G, TPB, V>, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t need = (count + NG - 1) / NG;
+    const bool persist = (a.persist_mask >> kslot) & 1;   // else one pass: a block per NG vertices
+    const int64_t blocks = persist ? persistent_grid(k_group<G, TPB, V>, TPB, smem, need) : need;
+    k_group<G, TPB, V><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
+    return cudaGetLastError();
+}
+
 template <int G, int TPB>
 static cudaError_t launch_g(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
                             cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
-    constexpr int NG = TPB / G;
-    const size_t smem = (size_t)NG * slots * (sizeof(int32_t) + sizeof(float));
-    cudaError_t e = set_smem(k_group<G, TPB>, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t need = (count + NG - 1) / NG;
-    const bool persist = (a.persist_mask >> kslot) & 1;   // else one pass: a block per NG vertices
-    const int64_t blocks = persist ? persistent_grid(k_group<G, TPB>, TPB, smem, need) : need;
-    k_group<G, TPB><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
-    return cudaGetLastError();
+    return a.int_weights ? launch_gv<G, TPB, uint32_t>(list, count, a, slots, kslot, s)
+                         : launch_gv<G, TPB, float>(list, count, a, slots, kslot, s);
 }
 
 cudaError_t launch_thread_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int slots,
@@ -688,18 +708,26 @@ cudaError_t launch_warp_bucket(const int32_t *list, int64_t count, const SweepAr
     return launch_g<32, 256>(list, count, a, slots, LPA_K_WARP, s);
 }
 
+template <int TPB, typename V>
+static cudaError_t launch_cv(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
+                             cudaStream_t s)
+{
+    const size_t smem = (size_t)slots * (sizeof(int32_t) + sizeof(V));
+    cudaError_t e = set_smem(k_cta<TPB, V>, smem);
+    if (e != cudaSuccess) return e;
+    const bool persist = (a.persist_mask >> kslot) & 1;
+    const int64_t blocks = persist ? persistent_grid(k_cta<TPB, V>, TPB, smem, count) : count;
+    k_cta<TPB, V><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
+    return cudaGetLastError();
+}
+
 template <int TPB>
 static cudaError_t launch_c(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
                             cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
-    const size_t smem = (size_t)slots * (sizeof(int32_t) + sizeof(float));
-    cudaError_t e = set_smem(k_cta<TPB>, smem);
-    if (e != cudaSuccess) return e;
-    const bool persist = (a.persist_mask >> kslot) & 1;
-    const int64_t blocks = persist ? persistent_grid(k_cta<TPB>, TPB, smem, count) : count;
-    k_cta<TPB><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
-    return cudaGetLastError();
+    return a.int_weights ? launch_cv<TPB, uint32_t>(list, count, a, slots, kslot, s)
+                         : launch_cv<TPB, float>(list, count, a, slots, kslot, s);
 }
 
 cudaError_t launch_cta_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int threads, int slots,
@@ -726,9 +754,15 @@ cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunk
 {
     if (n_chunks <= 0) return cudaSuccess;
     const size_t smem = (size_t)chunk * sizeof(int32_t);
-    cudaError_t e = set_smem(k_hub_acc<1024>, smem);
-    if (e != cudaSuccess) return e;
-    k_hub_acc<1024><<<(unsigned)n_chunks, 1024, smem, s>>>(h, a, chunk);
+    if (a.int_weights) {
+        cudaError_t e = set_smem(k_hub_acc<1024, uint32_t>, smem);
+        if (e != cudaSuccess) return e;
+        k_hub_acc<1024, uint32_t><<<(unsigned)n_chunks, 1024, smem, s>>>(h, a, chunk);
+    } else {
+        cudaError_t e = set_smem(k_hub_acc<1024, float>, smem);
+        if (e != cudaSuccess) return e;
+        k_hub_acc<1024, float><<<(unsigned)n_chunks, 1024, smem, s>>>(h, a, chunk);
+    }
     return cudaGetLastError();
 }
 

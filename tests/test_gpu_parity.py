@@ -105,6 +105,34 @@ def test_sync_rmat_small_buckets_with_hubs(lpa, scale, tables):
     check_sync_every_iteration(lpa, csr, 0.05, 20, 4, SMALL_BUCKETS if tables == "half" else PAPER_TABLES)
 
 
+@pytest.mark.parametrize("scale,tuning", [(13, "float"), (14, "float-small")])
+def test_sync_float_label_sums(lpa, scale, tuning):
+    """Integer-weight graphs forced onto the float32 label-sum kernels."""
+    csr = gg.rmat(scale, weights="int8")
+    t = dict(float_values=1) if tuning == "float" else dict(SMALL_BUCKETS, float_values=1)
+    check_sync_every_iteration(lpa, csr, 0.05, 20, 4, t)
+
+
+def dyadic(csr, seed):
+    """Same graph, weights from {0.5, 1.25, 2.75, 4.0} (both directions equal): not integers,
+    but every float32 partial sum stays exact for these magnitudes."""
+    n = csr.n
+    u = torch.repeat_interleave(torch.arange(n), csr.degrees())
+    v = csr.indices.long()
+    key = torch.minimum(u, v) * n + torch.maximum(u, v)
+    h = gg.draws53(seed, 9, key) % 4
+    w = torch.tensor([0.5, 1.25, 2.75, 4.0])[h]
+    return gg.CSRGraph(csr.offsets, csr.indices, w.to(torch.float32), "dyadic")
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_sync_non_integer_weights(lpa, seed):
+    csr = dyadic(gg.rmat(12 + seed, weights="unit"), seed)
+    g, ref = check_sync_every_iteration(lpa, csr, 0.05, 20, 4, SMALL_BUCKETS if seed == 1 else None)
+    q = g.modularity()                                  # float64 path (weights not integers)
+    assert abs(q - oracle.modularity(oracle_graph(csr), ref.labels)) < 1e-12
+
+
 def test_sync_sbm_config(lpa):
     """Planted partition, 10,000 vertices in 100 blocks, intra-degree 16, inter 2, unit
     weights, seed 0; tolerance 0.05, 20 iterations, PL every 4th."""
@@ -195,7 +223,7 @@ def test_modularity_matches_oracle(lpa, seed):
         assert abs(g.modularity() - oracle.modularity(og, labels)) < 1e-12
     g.run()
     lab = g.labels().cpu()
-    assert abs(g.modularity() - float(oracle.modularity_exact(og, lab))) < 1e-12
+    assert abs(g.modularity() - float(oracle.modularity_exact(og, lab))) < 1e-15   # exact integer path
 
 
 # ---------------------------------------------------------------------------------------
