@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -203,17 +204,16 @@ __device__ __forceinline__ double warp_sum_d(double x)
     return x;
 }
 
-// Eq. 1 numerators, float64.  Rows of degree <= hub_min: a warp per row (grid stride)
-// computes K_i = sum_j w_ij and the weight of entries with C_j = C_i.  Sigma_c = sum of K_i
-// over i in c is pre-aggregated per block in a small shared-memory table and added to the
-// global Sigma with one atomic per distinct label per block (one label may cover most of
-// the graph, and per-vertex atomics on it would serialise); labels that do not fit go to
-// Sigma directly.
+// Eq. 1 numerators: Sigma_c = sum of K_i over i in c is pre-aggregated per block in a small
+// shared-memory table and added to the global Sigma with one atomic per distinct label per
+// block (one label may cover most of the graph, and per-vertex atomics on it would
+// serialise); labels that do not fit go to Sigma directly.
 constexpr int kModSlots = 1024;
 
-__device__ __forceinline__ void mod_sigma_add(int32_t *sk, double *sv, double *Sig, int32_t c, double k)
+template <typename ACC>
+__device__ __forceinline__ void mod_sigma_add_t(int32_t *sk, ACC *sv, ACC *Sig, int32_t c, ACC k)
 {
-    uint32_t s = ((uint32_t)c * 2654435761u) >> 22;          // 10-bit multiplicative hash
+    uint32_t s = ((uint32_t)c * 2654435761u) >> 22;
     for (int t = 0; t < 8; ++t, s = (s + 1) & (kModSlots - 1)) {
         int32_t kk = *((volatile int32_t *)(sk + s));
         if (kk == -1) {
@@ -228,41 +228,65 @@ __device__ __forceinline__ void mod_sigma_add(int32_t *sk, double *sv, double *S
     atomicAdd(Sig + c, k);
 }
 
-__global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int32_t *idx, const float *w,
-                                                  const int32_t *C, int64_t n, int64_t hub_min, double *Sig,
-                                                  double *acc)
+// Eq. 1 numerators over one degree-bucket vertex list, G lanes per row (G = 4 for rows of
+// at most 31 entries, G = 32 above): ACC = unsigned long long (integer weights, exact) or
+// double.
+template <typename ACC> __device__ __forceinline__ ACC acc_weight(const float *w, int64_t e);
+template <> __device__ __forceinline__ unsigned long long acc_weight<unsigned long long>(const float *w, int64_t e)
+{
+    return w ? (unsigned long long)w[e] : 1ull;
+}
+template <> __device__ __forceinline__ double acc_weight<double>(const float *w, int64_t e)
+{
+    return w ? (double)w[e] : 1.0;
+}
+
+template <int G, typename ACC>
+__global__ void __launch_bounds__(256) k_mod_list(const int64_t *off, const int32_t *idx, const float *w,
+                                                  const int32_t *C, const int32_t *list, int64_t count, ACC *Sig,
+                                                  ACC *acc)
 {
     __shared__ int32_t sk[kModSlots];
-    __shared__ double sv[kModSlots];
-    __shared__ double s_in[8], s_k[8];
+    __shared__ ACC sv[kModSlots];
+    __shared__ ACC s_in[8], s_k[8];
     for (int q = threadIdx.x; q < kModSlots; q += 256) {
         sk[q] = -1;
-        sv[q] = 0.0;
+        sv[q] = ACC(0);
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double tin = 0.0, tk = 0.0;
-    for (int64_t i = warp; i < n; i += nwarps) {
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned gm = (G == 32) ? 0xFFFFFFFFu : (((1u << (G & 31)) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+    const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / G;
+    ACC tin = ACC(0), tk = ACC(0);
+    for (int64_t r = grp; r < count; r += ngrp) {
+        const int32_t i = list[r];
         const int64_t o0 = off[i], o1 = off[i + 1];
-        if (o0 == o1 || o1 - o0 > hub_min) continue;
         const int32_t ci = C[i];
-        double k = 0.0, in = 0.0;
-        for (int64_t e = o0 + lane; e < o1; e += 32) {
-            const double we = w ? (double)w[e] : 1.0;
+        ACC k = ACC(0), in = ACC(0);
+        for (int64_t e = o0 + lane; e < o1; e += G) {
+            const ACC we = acc_weight<ACC>(w, e);
             k += we;
             if (C[idx[e]] == ci) in += we;
         }
-        k = warp_sum_d(k);
-        in = warp_sum_d(in);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            k += __shfl_xor_sync(gm, k, o);
+            in += __shfl_xor_sync(gm, in, o);
+        }
         if (lane == 0) {
             tin += in;
             tk += k;
-            mod_sigma_add(sk, sv, Sig, ci, k);
+            mod_sigma_add_t(sk, sv, Sig, ci, k);
         }
     }
-    if (lane == 0) {
+    // block sums of sigma_in and 2m
+#pragma unroll
+    for (int o = 16; o >= G; o >>= 1) {
+        tin += __shfl_xor_sync(0xFFFFFFFFu, tin, o);
+        tk += __shfl_xor_sync(0xFFFFFFFFu, tk, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
         s_in[threadIdx.x >> 5] = tin;
         s_k[threadIdx.x >> 5] = tk;
     }
@@ -270,7 +294,7 @@ __global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int3
     for (int q = threadIdx.x; q < kModSlots; q += 256)
         if (sk[q] != -1) atomicAdd(Sig + sk[q], sv[q]);
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
+        ACC a = ACC(0), b = ACC(0);
         for (int q = 0; q < 8; ++q) {
             a += s_in[q];
             b += s_k[q];
@@ -280,30 +304,33 @@ __global__ void __launch_bounds__(256) k_mod_rows(const int64_t *off, const int3
     }
 }
 
-// The same sums for the rows of hubs (degree > hub_min), a block per CSR chunk.
-__global__ void __launch_bounds__(256) k_mod_hubs(const int32_t *idx, const float *w, const int32_t *C,
-                                                  const int32_t *hub_v, const int32_t *chunk_h,
-                                                  const int64_t *chunk_e0, const int64_t *chunk_e1, double *Sig,
-                                                  double *acc)
+template <typename ACC>
+__global__ void __launch_bounds__(256) k_mod_hub_chunks(const int32_t *idx, const float *w, const int32_t *C,
+                                                        const int32_t *hub_v, const int32_t *chunk_h,
+                                                        const int64_t *chunk_e0, const int64_t *chunk_e1, ACC *Sig,
+                                                        ACC *acc)
 {
-    __shared__ double s_in[8], s_k[8];
+    __shared__ ACC s_in[8], s_k[8];
     const int32_t v = hub_v[chunk_h[blockIdx.x]];
     const int32_t ci = C[v];
-    double k = 0.0, in = 0.0;
+    ACC k = ACC(0), in = ACC(0);
     for (int64_t e = chunk_e0[blockIdx.x] + threadIdx.x; e < chunk_e1[blockIdx.x]; e += 256) {
-        const double we = w ? (double)w[e] : 1.0;
+        const ACC we = acc_weight<ACC>(w, e);
         k += we;
         if (C[idx[e]] == ci) in += we;
     }
-    k = warp_sum_d(k);
-    in = warp_sum_d(in);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        k += __shfl_xor_sync(0xFFFFFFFFu, k, o);
+        in += __shfl_xor_sync(0xFFFFFFFFu, in, o);
+    }
     if ((threadIdx.x & 31) == 0) {
         s_in[threadIdx.x >> 5] = in;
         s_k[threadIdx.x >> 5] = k;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
+        ACC a = ACC(0), b = ACC(0);
         for (int q = 0; q < 8; ++q) {
             a += s_in[q];
             b += s_k[q];
@@ -342,110 +369,10 @@ __global__ void __launch_bounds__(256) k_weight_props(const int64_t *off, const 
 // Integer-weight modularity: every sum is an exact integer (int64 for sigma, Sigma_c and 2m,
 // 128 bits for sum_c Sigma_c^2), so Q is exact up to the final division and independent of
 // the order of the atomics.
-__device__ __forceinline__ void mod_sigma_add_u(int32_t *sk, unsigned long long *sv, unsigned long long *Sig,
-                                                int32_t c, unsigned long long k)
-{
-    uint32_t s = ((uint32_t)c * 2654435761u) >> 22;
-    for (int t = 0; t < 8; ++t, s = (s + 1) & (kModSlots - 1)) {
-        int32_t kk = *((volatile int32_t *)(sk + s));
-        if (kk == -1) {
-            const int32_t old = atomicCAS(sk + s, -1, c);
-            kk = (old == -1) ? c : old;
-        }
-        if (kk == c) {
-            atomicAdd(sv + s, k);
-            return;
-        }
-    }
-    atomicAdd(Sig + c, k);
-}
-
-__global__ void __launch_bounds__(256) k_mod_rows_int(const int64_t *off, const int32_t *idx, const float *w,
-                                                      const int32_t *C, int64_t n, int64_t hub_min,
-                                                      unsigned long long *Sig, unsigned long long *acc)
-{
-    __shared__ int32_t sk[kModSlots];
-    __shared__ unsigned long long sv[kModSlots];
-    __shared__ unsigned long long s_in[8], s_k[8];
-    for (int q = threadIdx.x; q < kModSlots; q += 256) {
-        sk[q] = -1;
-        sv[q] = 0;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long tin = 0, tk = 0;
-    for (int64_t i = warp; i < n; i += nwarps) {
-        const int64_t o0 = off[i], o1 = off[i + 1];
-        if (o0 == o1 || o1 - o0 > hub_min) continue;
-        const int32_t ci = C[i];
-        unsigned k = 0, in = 0;                        // row sums < 2^24
-        for (int64_t e = o0 + lane; e < o1; e += 32) {
-            const unsigned we = w ? (unsigned)w[e] : 1u;
-            k += we;
-            if (C[idx[e]] == ci) in += we;
-        }
-        k = __reduce_add_sync(0xFFFFFFFFu, k);
-        in = __reduce_add_sync(0xFFFFFFFFu, in);
-        if (lane == 0) {
-            tin += in;
-            tk += k;
-            mod_sigma_add_u(sk, sv, Sig, ci, k);
-        }
-    }
-    if (lane == 0) {
-        s_in[threadIdx.x >> 5] = tin;
-        s_k[threadIdx.x >> 5] = tk;
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < kModSlots; q += 256)
-        if (sk[q] != -1) atomicAdd(Sig + sk[q], sv[q]);
-    if (threadIdx.x == 0) {
-        unsigned long long a = 0, b = 0;
-        for (int q = 0; q < 8; ++q) {
-            a += s_in[q];
-            b += s_k[q];
-        }
-        atomicAdd(acc + 0, a);
-        atomicAdd(acc + 1, b);
-    }
-}
-
-__global__ void __launch_bounds__(256) k_mod_hubs_int(const int32_t *idx, const float *w, const int32_t *C,
-                                                      const int32_t *hub_v, const int32_t *chunk_h,
-                                                      const int64_t *chunk_e0, const int64_t *chunk_e1,
-                                                      unsigned long long *Sig, unsigned long long *acc)
-{
-    __shared__ unsigned s_in[8], s_k[8];
-    const int32_t v = hub_v[chunk_h[blockIdx.x]];
-    const int32_t ci = C[v];
-    unsigned k = 0, in = 0;
-    for (int64_t e = chunk_e0[blockIdx.x] + threadIdx.x; e < chunk_e1[blockIdx.x]; e += 256) {
-        const unsigned we = w ? (unsigned)w[e] : 1u;
-        k += we;
-        if (C[idx[e]] == ci) in += we;
-    }
-    k = __reduce_add_sync(0xFFFFFFFFu, k);
-    in = __reduce_add_sync(0xFFFFFFFFu, in);
-    if ((threadIdx.x & 31) == 0) {
-        s_in[threadIdx.x >> 5] = in;
-        s_k[threadIdx.x >> 5] = k;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long a = 0, b = 0;
-        for (int q = 0; q < 8; ++q) {
-            a += s_in[q];
-            b += s_k[q];
-        }
-        atomicAdd(acc + 0, a);
-        atomicAdd(acc + 1, b);
-        atomicAdd(Sig + ci, b);
-    }
-}
-
-// sum_c Sigma_c^2 as a 128-bit integer (acc[2] low word, acc[3] high word); resets Sigma.
+// Integer weights: every sum is an exact integer (int64 for sigma, Sigma_c and 2m, 128 bits
+// for sum_c Sigma_c^2), so Q is exact up to the final division and independent of the
+// order of the atomics.  sum_c Sigma_c^2 goes to acc[2] (low word) and acc[3] (high word);
+// Sigma is reset for the next call.
 __device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi, unsigned long long xl,
                                        unsigned long long xh)
 {
@@ -1192,15 +1119,25 @@ int lpa_modularity(const lpa_graph *gc, double *q)
     }
     LPA_CUDA(cudaMemsetAsync(g->macc, 0, 4 * sizeof(double), g->stream));
     const int64_t hub_min = g->hub.n_hubs > 0 ? (int64_t)g->tuning.cta_xl_max : INT64_MAX;
+    const int64_t *bs = g->bucket_start;
+    auto run_lists = [&](auto *Sig, auto *acc) {
+        using ACC = std::remove_pointer_t<decltype(Sig)>;
+        const int64_t n_small = bs[B_GROUP + 1] - bs[B_THREAD];
+        const int64_t n_mid = bs[B_CTA_XL + 1] - bs[B_WARP];
+        if (n_small > 0)
+            k_mod_list<4, ACC><<<grid_for(n_small * 4, 256, 16), 256, 0, g->stream>>>(
+                g->off, g->idx, g->w, g->C, g->lists + bs[B_THREAD], n_small, Sig, acc);
+        if (n_mid > 0)
+            k_mod_list<32, ACC><<<grid_for(n_mid * 32, 256, 16), 256, 0, g->stream>>>(
+                g->off, g->idx, g->w, g->C, g->lists + bs[B_WARP], n_mid, Sig, acc);
+        if (g->hub.n_hubs > 0 && g->n_chunks > 0)
+            k_mod_hub_chunks<ACC><<<(unsigned)g->n_chunks, 256, 0, g->stream>>>(
+                g->idx, g->w, g->C, g->hub.hub_v, g->hub.chunk_h, g->hub.chunk_e0, g->hub.chunk_e1, Sig, acc);
+    };
     if (g->int_weights) {
         unsigned long long *SigU = reinterpret_cast<unsigned long long *>(g->Sig);
         unsigned long long *acc = reinterpret_cast<unsigned long long *>(g->macc);
-        k_mod_rows_int<<<grid_for(g->n * 32, 256, 16), 256, 0, g->stream>>>(g->off, g->idx, g->w, g->C, g->n, hub_min,
-                                                                            SigU, acc);
-        if (g->hub.n_hubs > 0 && g->n_chunks > 0)
-            k_mod_hubs_int<<<(unsigned)g->n_chunks, 256, 0, g->stream>>>(g->idx, g->w, g->C, g->hub.hub_v,
-                                                                         g->hub.chunk_h, g->hub.chunk_e0,
-                                                                         g->hub.chunk_e1, SigU, acc);
+        run_lists(SigU, acc);
         k_mod_sq_int<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(SigU, g->n, acc);
         unsigned long long h[4];
         LPA_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
@@ -1211,11 +1148,7 @@ int lpa_modularity(const lpa_graph *gc, double *q)
         *q = (den == 0) ? 0.0 : (double)num / (double)den;
         return LPA_OK;
     }
-    k_mod_rows<<<grid_for(g->n * 32, 256, 16), 256, 0, g->stream>>>(g->off, g->idx, g->w, g->C, g->n, hub_min,
-                                                                    g->Sig, g->macc);
-    if (g->hub.n_hubs > 0 && g->n_chunks > 0)
-        k_mod_hubs<<<(unsigned)g->n_chunks, 256, 0, g->stream>>>(g->idx, g->w, g->C, g->hub.hub_v, g->hub.chunk_h,
-                                                                 g->hub.chunk_e0, g->hub.chunk_e1, g->Sig, g->macc);
+    run_lists(g->Sig, g->macc);
     k_mod_sq<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->Sig, g->n, g->macc);
     double h[3];
     LPA_CUDA(cudaMemcpyAsync(h, g->macc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));

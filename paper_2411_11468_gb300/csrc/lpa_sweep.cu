@@ -286,6 +286,28 @@ __device__ __forceinline__ void load_entry(const SweepArgs &a, int32_t v, int64_
     }
 }
 
+// Scans entries [start, end) of the row of v in rounds: each round covers U * step entries,
+// lane offset `lane` inside each step.  All U entries of a round are loaded (index, weight,
+// gathered label) before any of them is inserted, so U gathers per thread are in flight.
+template <int G, bool SHARED, bool TRACK, int U, typename V>
+__device__ __forceinline__ void scan_row(const SweepArgs &a, int32_t v, int64_t start, int64_t end, int step,
+                                         int lane, int32_t *Hk, V *Hv, int stride, uint32_t p1, uint32_t b,
+                                         unsigned long long &best, unsigned &fb, uint32_t *ucnt = nullptr,
+                                         int32_t *ulist = nullptr, int round = 0)
+{
+    const int64_t adv = round ? round : (int64_t)step * U;   // a block-wide round for the CTA kernels
+    for (int64_t eb = start; eb < end; eb += adv) {
+        bool has[U];
+        int32_t k[U];
+        V wv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_entry(a, v, eb + (int64_t)u * step + lane, end, has[u], k[u], wv[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            group_insert<G, SHARED, TRACK>(Hk, Hv, stride, p1, b, has[u], k[u], wv[u], best, fb, ucnt, ulist);
+    }
+}
+
 // Move rule of Algorithm 1: c* != C[i] and, on Pick-Less sweeps, c* < C[i].
 __device__ __forceinline__ bool decide(unsigned long long best, int32_t cur, int pl, int32_t &cstar)
 {
@@ -361,13 +383,7 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
             }
             const int32_t cur = a.C[v];
             unsigned long long best = 0;
-            for (int64_t eb = o0; eb < o1; eb += G) {      // scan neighbours
-                bool has;
-                int32_t k;
-                V wv;
-                load_entry(a, v, eb + lane, o1, has, k, wv);
-                group_insert<G, (G > 1), false>(Hk, Hv, stride, p1, b, has, k, wv, best, fb);
-            }
+            scan_row<G, (G > 1), false, (G >= 8 ? 2 : 1)>(a, v, o0, o1, G, lane, Hk, Hv, stride, p1, b, best, fb);
             best = group_max<G>(best);                     // hashtableMaxKey
             moved = decide(best, cur, a.pl, cstar);
             if (moved) {
@@ -429,13 +445,8 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
         __syncthreads();
         const int32_t cur = a.C[v];
         unsigned long long best = 0;
-        for (int64_t eb = o0 + (threadIdx.x & ~31); eb < o1; eb += TPB) {
-            bool has;
-            int32_t k;
-            V wv;
-            load_entry(a, v, eb + (threadIdx.x & 31), o1, has, k, wv);
-            group_insert<32, true, false>(Hk, Hv, 1, p1, b, has, k, wv, best, fb);
-        }
+        scan_row<32, true, false, 4>(a, v, o0 + (threadIdx.x & ~31) * 4, o1, 32, threadIdx.x & 31, Hk, Hv, 1, p1,
+                                     b, best, fb, nullptr, nullptr, TPB * 4);
         best = group_max<32>(best);
         if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
         __syncthreads();
@@ -514,13 +525,8 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a, int chu
     const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
     unsigned fb = 0;
     unsigned long long best = 0;
-    for (int64_t eb = e0 + (threadIdx.x & ~31); eb < e1; eb += TPB) {
-        bool has;
-        int32_t k;
-        V wv;
-        load_entry(a, v, eb + (threadIdx.x & 31), e1, has, k, wv);
-        group_insert<32, true, true>(Hk, Hv, 1, p1, b, has, k, wv, best, fb, &s_cnt, s_list);
-    }
+    scan_row<32, true, true, 4>(a, v, e0 + (threadIdx.x & ~31) * 4, e1, 32, threadIdx.x & 31, Hk, Hv, 1, p1, b,
+                                best, fb, &s_cnt, s_list, TPB * 4);
     if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
     best = group_max<32>(best);
     if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
