@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
             }
             const int32_t cur = a.C[v];
             unsigned long long best = 0;
-            scan_row<G, (G > 1), false, (G >= 8 ? 2 : 1)>(a, v, o0, o1, G, lane, Hk, Hv, stride, p1, b, best, fb);
+            scan_row<G, (G > 1), false, 1>(a, v, o0, o1, G, lane, Hk, Hv, stride, p1, b, best, fb);
             best = group_max<G>(best);                     // hashtableMaxKey
             moved = decide(best, cur, a.pl, cstar);
             if (moved) {
@@ -445,8 +445,9 @@ __global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, i
         __syncthreads();
         const int32_t cur = a.C[v];
         unsigned long long best = 0;
-        scan_row<32, true, false, 4>(a, v, o0 + (threadIdx.x & ~31) * 4, o1, 32, threadIdx.x & 31, Hk, Hv, 1, p1,
-                                     b, best, fb, nullptr, nullptr, TPB * 4);
+        constexpr int U = TPB >= 1024 ? 2 : 1;             // loads in flight per thread
+        scan_row<32, true, false, U>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, Hk, Hv, 1, p1,
+                                     b, best, fb, nullptr, nullptr, TPB * U);
         best = group_max<32>(best);
         if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
         __syncthreads();
@@ -525,8 +526,8 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a, int chu
     const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
     unsigned fb = 0;
     unsigned long long best = 0;
-    scan_row<32, true, true, 4>(a, v, e0 + (threadIdx.x & ~31) * 4, e1, 32, threadIdx.x & 31, Hk, Hv, 1, p1, b,
-                                best, fb, &s_cnt, s_list, TPB * 4);
+    scan_row<32, true, true, 2>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, Hk, Hv, 1, p1, b,
+                                best, fb, &s_cnt, s_list, TPB * 2);
     if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
     best = group_max<32>(best);
     if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
