@@ -203,6 +203,32 @@ const char *lpa_strerror(int status);
 const char *lpa_last_error(void);
 const char *lpa_kernel_name(int slot);
 
+/* ---- modularity without device allocation ------------------------------------------ */
+
+/* Largest n_vertices accepted by lpa_modularity_noalloc. */
+#define LPA_NOALLOC_MAX_VERTICES (1 << 20)
+
+/* Modularity (Eq. 1) of a labelled CSR graph that the caller holds on the device, computed
+ * without allocating any device memory.  The paper has no counterpart: this entry point is
+ * for callers that cannot call cudaMalloc, such as code running under another framework's
+ * device memory pool, services that have reserved all device memory up front, or paths that
+ * must avoid the allocator's implicit synchronisation.
+ *  offsets  device, int64_t [n_vertices + 1]; indices device, int32_t [n_entries];
+ *  weights  device, float [n_entries] (finite, >= 0) or NULL for unit weights;
+ *  labels   device, int32_t [n_vertices], each in [0, n_vertices);
+ *  q        host, receives Q (float64 accumulation).
+ * Scratch: one fixed array of LPA_NOALLOC_MAX_VERTICES + 8 doubles (8 MiB) compiled into the
+ * library; every GPU that loads the library holds it until the process exits, and every call
+ * on that GPU uses it.  Calls that overlap on the GPU (other streams or host threads) race on
+ * it; order them.  Each call clears the part it reads first.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) once; make that first call before any
+ * stream capture.  The call works on cuda_stream and synchronises it before returning.
+ * Errors: LPA_EINVAL for n_vertices > LPA_NOALLOC_MAX_VERTICES, NULL arrays, or a graph /
+ * labels that fail the device-side checks; LPA_ECUDA for a failed CUDA call. */
+int lpa_modularity_noalloc(const int64_t *offsets, const int32_t *indices, const float *weights,
+                           const int32_t *labels, int64_t n_vertices, int64_t n_entries,
+                           void *cuda_stream, double *q);
+
 /* sizeof(lpa_stats) for which = 0, sizeof(lpa_tuning) for which = 1 (binding checks). */
 size_t lpa_struct_size(int which);
 
