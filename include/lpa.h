@@ -125,7 +125,7 @@ typedef struct lpa_tuning {
     int32_t smem_table_shift; /* 0..2                                                    */
     int32_t cta_xl_max;       /* block of cta_xl_threads per vertex; above: hubs         */
     int32_t cta_xl_threads;
-    int32_t persistent_mask;  /* bit k (kernel slot k <= LPA_K_CTA_XL): persistent grid  */
+    int32_t item_vertices;    /* vertices per work item of the thread/group/warp kernels (0 = default) */
     int32_t float_values;     /* 1: float32 label sums even when integer sums would do   */
     int32_t reserved[1];
 } lpa_tuning;

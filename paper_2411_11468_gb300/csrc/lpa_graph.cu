@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "lpa_internal.h"
+#include "lpa_graph_internal.h"
 
 namespace lpa {
 
@@ -454,63 +454,117 @@ uint32_t capacity_bits(int64_t x)
 }
 
 }  // namespace
+// ---------------------------------------------------------------------------------------
+// Device memory arena
+
+namespace lpa {
+
+Arena::Arena(size_t bytes)
+{
+    void *p = nullptr;
+    if (bytes == 0 || cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    base_ = static_cast<unsigned char *>(p);
+    cap_ = bytes;
+    free_.push_back({0, bytes});
+}
+
+Arena::~Arena()
+{
+    if (base_) cudaFree(base_);
+}
+
+void *Arena::alloc(size_t bytes)
+{
+    if (!base_) return nullptr;
+    bytes = (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+    for (size_t i = 0; i < free_.size(); ++i) {
+        if (free_[i].size < bytes) continue;
+        const size_t off = free_[i].off;
+        free_[i].off += bytes;
+        free_[i].size -= bytes;
+        if (free_[i].size == 0) free_.erase(free_.begin() + (long)i);
+        const Block b{off, bytes};
+        auto it = std::lower_bound(taken_.begin(), taken_.end(), b,
+                                   [](const Block &x, const Block &y) { return x.off < y.off; });
+        taken_.insert(it, b);
+        used_ += bytes;
+        return base_ + off;
+    }
+    return nullptr;
+}
+
+void Arena::free(void *p)
+{
+    if (!p || !base_) return;
+    const size_t off = static_cast<size_t>(static_cast<unsigned char *>(p) - base_);
+    auto it = std::lower_bound(taken_.begin(), taken_.end(), Block{off, 0},
+                               [](const Block &x, const Block &y) { return x.off < y.off; });
+    if (it == taken_.end() || it->off != off) return;
+    Block b = *it;
+    taken_.erase(it);
+    used_ -= b.size;
+    auto f = std::lower_bound(free_.begin(), free_.end(), b,
+                              [](const Block &x, const Block &y) { return x.off < y.off; });
+    f = free_.insert(f, b);
+    if (f + 1 != free_.end() && f->off + f->size == (f + 1)->off) {   // merge with the next block
+        f->size += (f + 1)->size;
+        free_.erase(f + 1);
+    }
+    if (f != free_.begin() && (f - 1)->off + (f - 1)->size == f->off) {   // merge with the previous one
+        (f - 1)->size += f->size;
+        free_.erase(f);
+    }
+}
+
+size_t Arena::largest_free() const
+{
+    size_t m = 0;
+    for (const Block &b : free_) m = std::max(m, b.size);
+    return m;
+}
+
+}  // namespace lpa
 
 // ---------------------------------------------------------------------------------------
-struct lpa_graph {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int64_t n = 0, m = 0;
-    int64_t *off = nullptr;
-    int32_t *idx = nullptr;
-    float *w = nullptr;
-    int32_t *C = nullptr;
-    uint8_t *flagA = nullptr, *flagB = nullptr;   // flagA: unprocessed flags for the next sweep
-    int32_t *mover_v = nullptr, *mover_c = nullptr;
-    unsigned long long *mover_count = nullptr;
-    unsigned long long *fallbacks = nullptr;
-    unsigned long long *ctr = nullptr;            // [ctr_iters][LPA_NUM_KERNELS][kCtrFields]
-    int ctr_iters = 0;
-    unsigned long long *h_ctr = nullptr;          // pinned mirror
-    unsigned *d_err = nullptr;
-    double *Sig = nullptr, *macc = nullptr;
-    // buckets
-    lpa_tuning tuning{};
-    int32_t *lists = nullptr;
-    int64_t bucket_start[B_COUNT + 1] = {};
-    // hubs
-    HubArgs hub{};
-    void *hub_mem = nullptr;
-    int64_t n_chunks = 0, n_slices = 0, table_slots = 0;
-    int32_t *tab_k = nullptr;
-    float *tab_v = nullptr;
-    int32_t *used_list = nullptr;
-    int next_iter = 0;
-    bool int_weights = false;         // integer weights, weighted degrees < 2^24
-    int64_t bytes = 0, bucket_bytes = 0;
-    std::vector<cudaEvent_t> events;
-};
-
 namespace {
 
 template <typename T>
-int dalloc(lpa_graph *g, T **p, size_t count, int64_t *counter = nullptr)
+int dalloc(lpa_graph *g, T **p, size_t count)
 {
     *p = nullptr;
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    void *q = nullptr;
+    if (g->arena) {
+        q = g->arena->alloc(bytes);
+    } else if (cudaMalloc(&q, bytes) != cudaSuccess) {
         cudaGetLastError();
+        q = nullptr;
+    }
+    if (!q) {
+        set_error("device allocation of " + std::to_string(bytes) + " bytes failed" +
+                  (g->arena ? " (arena full)" : ""));
         return LPA_ENOMEM;
     }
-    *(counter ? counter : &g->bytes) += (int64_t)(count * sizeof(T));
+    g->allocs.push_back({q, bytes});
+    g->bytes += (int64_t)bytes;
+    *p = static_cast<T *>(q);
     return LPA_OK;
 }
 
-void dfree(void *p)
+void dfree(lpa_graph *g, void *p)
 {
-    if (p) cudaFree(p);
+    if (!p) return;
+    for (size_t i = 0; i < g->allocs.size(); ++i) {
+        if (g->allocs[i].first != p) continue;
+        g->bytes -= (int64_t)g->allocs[i].second;
+        g->allocs.erase(g->allocs.begin() + (long)i);
+        break;
+    }
+    if (g->arena) g->arena->free(p);
+    else cudaFree(p);
 }
 
 lpa_tuning default_tuning()
@@ -526,7 +580,7 @@ lpa_tuning default_tuning()
     t.cta_large_threads = 256;
     t.cta_xl_max = 8191;
     t.cta_xl_threads = 1024;
-    t.persistent_mask = (1 << LPA_K_WARP) | (1 << LPA_K_CTA) | (1 << LPA_K_CTA_LARGE) | (1 << LPA_K_CTA_XL);
+    t.item_vertices = 0;
     t.hub_chunk = 16384;
     t.hub_table_shift = 1;
     t.smem_table_shift = 1;
@@ -553,7 +607,7 @@ int check_tuning(const lpa_tuning &t)
     for (int th : {t.cta_threads, t.cta_large_threads, t.cta_xl_threads})
         if (!pow2(th) || th < 64 || th > 1024) return LPA_EINVAL;
     if (t.hub_chunk < 256 || t.hub_chunk > 32768) return LPA_EINVAL;
-    if (t.persistent_mask & ~0x3F) return LPA_EINVAL;
+    if (t.item_vertices < 0 || t.item_vertices > (1 << 20)) return LPA_EINVAL;
     if (t.float_values != 0 && t.float_values != 1) return LPA_EINVAL;
     const int64_t smem = (int64_t)max_dynamic_smem();
     const int64_t bytes_group = (256 / t.group_lanes) * slots_for(t.group_max, sh) * 8;
@@ -566,21 +620,34 @@ int check_tuning(const lpa_tuning &t)
     return LPA_OK;
 }
 
+// Vertices per work item of each vertex kernel (a warp's or a block's unit of queue work).
+int64_t item_size(const lpa_tuning &t, int b)
+{
+    static const int64_t base[B_CTA_XL + 1] = {1024, 256, 64, 16, 8, 4};
+    if (t.item_vertices > 0 && b <= B_WARP) return t.item_vertices;
+    return base[b];
+}
+
 void free_buckets(lpa_graph *g)
 {
-    dfree(g->lists);
+    dfree(g, g->lists);
     g->lists = nullptr;
-    dfree(g->hub_mem);
+    dfree(g, g->hub_mem);
     g->hub_mem = nullptr;
-    dfree(g->tab_k);
+    dfree(g, g->tab_k);
     g->tab_k = nullptr;
-    dfree(g->tab_v);
+    dfree(g, g->tab_v);
     g->tab_v = nullptr;
-    dfree(g->used_list);
+    dfree(g, g->used_list);
     g->used_list = nullptr;
-    g->hub = HubArgs{};
-    g->n_chunks = g->n_slices = g->table_slots = 0;
-    g->bucket_bytes = 0;
+    dfree(g, g->items_d);
+    g->items_d = nullptr;
+    g->gdh.hub = HubArgs{};
+    g->table_slots = 0;
+    for (auto &v : g->items_h) v.clear();
+    g->hub_hubs_h.clear();
+    g->hub_chunks_h.clear();
+    g->hub_slices_h.clear();
 }
 
 int build_buckets(lpa_graph *g)
@@ -592,17 +659,15 @@ int build_buckets(lpa_graph *g)
     std::vector<int64_t> base(cnt.size(), 0);
     int32_t *d_cnt = nullptr;
     int64_t *d_base = nullptr;
-    if (cudaMalloc((void **)&d_cnt, cnt.size() * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc((void **)&d_base, base.size() * sizeof(int64_t)) != cudaSuccess) {
-        cudaGetLastError();
-        dfree(d_cnt);
-        dfree(d_base);
-        set_error("build_buckets: cudaMalloc failed");
-        return LPA_ENOMEM;
+    LPA_CHECK(dalloc(g, &d_cnt, cnt.size()));
+    int st = dalloc(g, &d_base, base.size());
+    if (st != LPA_OK) {
+        dfree(g, d_cnt);
+        return st;
     }
     auto cleanup = [&]() {
-        dfree(d_cnt);
-        dfree(d_base);
+        dfree(g, d_cnt);
+        dfree(g, d_base);
     };
     if (tiles > 0) {
         k_bucket_count<<<(unsigned)tiles, 1024, 0, g->stream>>>(g->off, n, g->tuning, d_cnt);
@@ -626,7 +691,7 @@ int build_buckets(lpa_graph *g)
             base[t * B_COUNT + b] = run[b];
             run[b] += cnt[t * B_COUNT + b];
         }
-    int st = dalloc(g, &g->lists, (size_t)g->bucket_start[B_COUNT], &g->bucket_bytes);
+    st = dalloc(g, &g->lists, (size_t)g->bucket_start[B_COUNT]);
     if (st != LPA_OK) {
         cleanup();
         return st;
@@ -642,133 +707,153 @@ int build_buckets(lpa_graph *g)
         return LPA_ECUDA;
     }
 
-    // hubs: tables in HBM, accumulate chunks and argmax slices
-    const int64_t H = total[B_HUB];
-    if (H == 0) return LPA_OK;
-    const int32_t *hub_list = g->lists + g->bucket_start[B_HUB];
-    std::vector<int32_t> hv((size_t)H);
-    std::vector<int64_t> o0((size_t)H), o1((size_t)H);
-    int64_t *d_o = nullptr;
-    LPA_CUDA(cudaMalloc((void **)&d_o, (size_t)(2 * H) * sizeof(int64_t)));
-    k_gather_rows<<<(unsigned)((H + 255) / 256), 256, 0, g->stream>>>(hub_list, H, g->off, d_o, d_o + H);
-    cudaMemcpyAsync(hv.data(), hub_list, H * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream);
-    cudaMemcpyAsync(o0.data(), d_o, H * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
-    cudaMemcpyAsync(o1.data(), d_o + H, H * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
-    e = cudaStreamSynchronize(g->stream);
-    dfree(d_o);
-    if (e != cudaSuccess) {
-        set_error(std::string("hub rows: ") + cudaGetErrorString(e));
-        return LPA_ECUDA;
+    // vertex work items
+    const int64_t *bs = g->bucket_start;
+    for (int b = B_THREAD; b <= B_CTA_XL; ++b) {
+        const int64_t sz = item_size(g->tuning, b);
+        for (int64_t s = bs[b]; s < bs[b + 1]; s += sz)
+            g->items_h[b].push_back(WorkItem{0, 0, s, std::min(sz, bs[b + 1] - s)});
     }
-    const int64_t chunk = g->tuning.hub_chunk;
-    std::vector<uint32_t> p1((size_t)H), bb((size_t)H);
-    std::vector<int64_t> tab((size_t)H), ubase((size_t)H);
-    std::vector<int32_t> ch, sh, sj;
-    std::vector<int64_t> ce0, ce1;
-    int64_t slots = 0, used_total = 0;
-    for (int64_t h = 0; h < H; ++h) {
-        const int64_t D = o1[h] - o0[h];
-        const int64_t want = std::min<int64_t>(D << g->tuning.hub_table_shift, (int64_t)1 << 31);
-        bb[h] = capacity_bits(want);
-        p1[h] = (uint32_t)(((int64_t)1 << bb[h]) - 1);
-        tab[h] = slots;
-        ubase[h] = used_total;
-        for (int64_t e0 = o0[h]; e0 < o1[h]; e0 += chunk) {
-            ch.push_back((int32_t)h);
-            ce0.push_back(e0);
-            ce1.push_back(std::min(o1[h], e0 + chunk));
-        }
-        for (int64_t j = 0; j * kHubSlice < (int64_t)p1[h]; ++j) {   // clear slices cover the table
-            sh.push_back((int32_t)h);
-            sj.push_back((int32_t)j);
-        }
-        slots += p1[h];
-        used_total += D;
-    }
-    g->n_chunks = (int64_t)ch.size();
-    g->n_slices = (int64_t)sh.size();
-    g->table_slots = slots;
-    // one allocation for the hub arrays (8-byte fields first)
-    const size_t n8 = (size_t)(3 * H /*tab, best, ubase*/ + 2 * g->n_chunks);
-    const size_t n4 = (size_t)(4 * H /*v, p1, b, used*/ + g->n_chunks + 2 * g->n_slices);
-    const size_t bytes = n8 * 8 + n4 * 4 + (size_t)H;
-    unsigned char *mem = nullptr;
-    LPA_CHECK(dalloc(g, &mem, bytes, &g->bucket_bytes));
-    g->hub_mem = mem;
-    unsigned char *p = mem;
-    auto take = [&](size_t b) {
-        unsigned char *r = p;
-        p += b;
-        return r;
-    };
-    int64_t *d_tab = (int64_t *)take(H * 8);
-    unsigned long long *d_best = (unsigned long long *)take(H * 8);
-    int64_t *d_ubase = (int64_t *)take(H * 8);
-    int64_t *d_ce0 = (int64_t *)take(g->n_chunks * 8);
-    int64_t *d_ce1 = (int64_t *)take(g->n_chunks * 8);
-    int32_t *d_hv = (int32_t *)take(H * 4);
-    uint32_t *d_p1 = (uint32_t *)take(H * 4);
-    uint32_t *d_b = (uint32_t *)take(H * 4);
-    uint32_t *d_used = (uint32_t *)take(H * 4);
-    int32_t *d_ch = (int32_t *)take(g->n_chunks * 4);
-    int32_t *d_sh = (int32_t *)take(g->n_slices * 4);
-    int32_t *d_sj = (int32_t *)take(g->n_slices * 4);
-    uint8_t *d_act = (uint8_t *)take(H);
-    LPA_CUDA(cudaMemcpyAsync(d_tab, tab.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_ubase, ubase.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_ce0, ce0.data(), g->n_chunks * 8, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_ce1, ce1.data(), g->n_chunks * 8, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_hv, hv.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_p1, p1.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_b, bb.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_ch, ch.data(), g->n_chunks * 4, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_sh, sh.data(), g->n_slices * 4, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemcpyAsync(d_sj, sj.data(), g->n_slices * 4, cudaMemcpyHostToDevice, g->stream));
-    LPA_CUDA(cudaMemsetAsync(d_act, 0, H, g->stream));
-    LPA_CUDA(cudaMemsetAsync(d_best, 0, H * 8, g->stream));
-    LPA_CUDA(cudaMemsetAsync(d_used, 0, H * 4, g->stream));
-    LPA_CHECK(dalloc(g, &g->tab_k, (size_t)slots, &g->bucket_bytes));
-    LPA_CHECK(dalloc(g, &g->tab_v, (size_t)slots, &g->bucket_bytes));
-    LPA_CHECK(dalloc(g, &g->used_list, (size_t)used_total, &g->bucket_bytes));
-    LPA_CUDA(launch_hub_table_clear(g->tab_k, g->tab_v, slots, g->stream));
-    HubArgs &ha = g->hub;
-    ha.hub_v = d_hv;
-    ha.hub_p1 = d_p1;
-    ha.hub_b = d_b;
-    ha.hub_tab = d_tab;
-    ha.hub_act = d_act;
-    ha.hub_best = d_best;
-    ha.hub_used = d_used;
-    ha.used_list = g->used_list;
-    ha.used_base = d_ubase;
-    ha.chunk_h = d_ch;
-    ha.chunk_e0 = d_ce0;
-    ha.chunk_e1 = d_ce1;
-    ha.slice_h = d_sh;
-    ha.slice_j = d_sj;
-    ha.tab_k = g->tab_k;
-    ha.tab_v = g->tab_v;
-    ha.n_hubs = (int32_t)H;
-    LPA_CUDA(cudaStreamSynchronize(g->stream));
-    return LPA_OK;
-}
 
-int ensure_ctr(lpa_graph *g, int iters)
-{
-    if (iters <= g->ctr_iters) return LPA_OK;
-    dfree(g->ctr);
-    if (g->h_ctr) cudaFreeHost(g->h_ctr);
-    g->ctr = nullptr;
-    g->h_ctr = nullptr;
-    const size_t per = (size_t)LPA_NUM_KERNELS * kCtrFields;
-    LPA_CHECK(dalloc(g, &g->ctr, per * iters));
-    cudaError_t e = cudaMallocHost((void **)&g->h_ctr, per * iters * sizeof(unsigned long long));
-    if (e != cudaSuccess) {
-        set_error(std::string("cudaMallocHost: ") + cudaGetErrorString(e));
-        g->h_ctr = nullptr;
-        return LPA_ENOMEM;
+    // hubs: tables in HBM, accumulate chunks and clear slices
+    HubArgs &ha = g->gdh.hub;
+    const int64_t H = total[B_HUB];
+    if (H > 0) {
+        const int32_t *hub_list = g->lists + bs[B_HUB];
+        std::vector<int32_t> hv((size_t)H);
+        std::vector<int64_t> o0((size_t)H), o1((size_t)H);
+        int64_t *d_o = nullptr;
+        LPA_CHECK(dalloc(g, &d_o, (size_t)(2 * H)));
+        k_gather_rows<<<(unsigned)((H + 255) / 256), 256, 0, g->stream>>>(hub_list, H, g->off, d_o, d_o + H);
+        cudaMemcpyAsync(hv.data(), hub_list, H * sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream);
+        cudaMemcpyAsync(o0.data(), d_o, H * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
+        cudaMemcpyAsync(o1.data(), d_o + H, H * sizeof(int64_t), cudaMemcpyDeviceToHost, g->stream);
+        e = cudaStreamSynchronize(g->stream);
+        dfree(g, d_o);
+        if (e != cudaSuccess) {
+            set_error(std::string("hub rows: ") + cudaGetErrorString(e));
+            return LPA_ECUDA;
+        }
+        const int64_t chunk = g->tuning.hub_chunk;
+        std::vector<uint32_t> p1((size_t)H), bb((size_t)H);
+        std::vector<int64_t> tab((size_t)H), ubase((size_t)H);
+        std::vector<int32_t> ch, sh, sj;
+        std::vector<int64_t> ce0, ce1;
+        int64_t slots = 0, used_total = 0;
+        for (int64_t h = 0; h < H; ++h) {
+            const int64_t D = o1[h] - o0[h];
+            const int64_t want = std::min<int64_t>(D << g->tuning.hub_table_shift, (int64_t)1 << 31);
+            bb[h] = capacity_bits(want);
+            p1[h] = (uint32_t)(((int64_t)1 << bb[h]) - 1);
+            tab[h] = slots;
+            ubase[h] = used_total;
+            for (int64_t e0 = o0[h]; e0 < o1[h]; e0 += chunk) {
+                ch.push_back((int32_t)h);
+                ce0.push_back(e0);
+                ce1.push_back(std::min(o1[h], e0 + chunk));
+            }
+            for (int64_t j = 0; j * kHubSlice < (int64_t)p1[h]; ++j) {   // clear slices cover the table
+                sh.push_back((int32_t)h);
+                sj.push_back((int32_t)j);
+            }
+            slots += p1[h];
+            used_total += D;
+        }
+        const int64_t n_chunks = (int64_t)ch.size(), n_slices = (int64_t)sh.size();
+        g->table_slots = slots;
+        const size_t n8 = (size_t)(3 * H + 2 * n_chunks);
+        const size_t n4 = (size_t)(4 * H + n_chunks + 2 * n_slices);
+        unsigned char *mem = nullptr;
+        LPA_CHECK(dalloc(g, &mem, n8 * 8 + n4 * 4 + (size_t)H));
+        g->hub_mem = mem;
+        unsigned char *p = mem;
+        auto take = [&](size_t b) {
+            unsigned char *r = p;
+            p += b;
+            return r;
+        };
+        int64_t *d_tab = (int64_t *)take(H * 8);
+        unsigned long long *d_best = (unsigned long long *)take(H * 8);
+        int64_t *d_ubase = (int64_t *)take(H * 8);
+        int64_t *d_ce0 = (int64_t *)take(n_chunks * 8);
+        int64_t *d_ce1 = (int64_t *)take(n_chunks * 8);
+        int32_t *d_hv = (int32_t *)take(H * 4);
+        uint32_t *d_p1 = (uint32_t *)take(H * 4);
+        uint32_t *d_b = (uint32_t *)take(H * 4);
+        uint32_t *d_used = (uint32_t *)take(H * 4);
+        int32_t *d_ch = (int32_t *)take(n_chunks * 4);
+        int32_t *d_sh = (int32_t *)take(n_slices * 4);
+        int32_t *d_sj = (int32_t *)take(n_slices * 4);
+        uint8_t *d_act = (uint8_t *)take(H);
+        LPA_CUDA(cudaMemcpyAsync(d_tab, tab.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemcpyAsync(d_ubase, ubase.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemcpyAsync(d_ce0, ce0.data(), n_chunks * 8, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemcpyAsync(d_ce1, ce1.data(), n_chunks * 8, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemcpyAsync(d_hv, hv.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemcpyAsync(d_p1, p1.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemcpyAsync(d_b, bb.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemcpyAsync(d_ch, ch.data(), n_chunks * 4, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemcpyAsync(d_sh, sh.data(), n_slices * 4, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemcpyAsync(d_sj, sj.data(), n_slices * 4, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemsetAsync(d_act, 0, H, g->stream));
+        LPA_CUDA(cudaMemsetAsync(d_best, 0, H * 8, g->stream));
+        LPA_CUDA(cudaMemsetAsync(d_used, 0, H * 4, g->stream));
+        LPA_CHECK(dalloc(g, &g->tab_k, (size_t)slots));
+        LPA_CHECK(dalloc(g, &g->tab_v, (size_t)slots));
+        LPA_CHECK(dalloc(g, &g->used_list, (size_t)used_total));
+        LPA_CUDA(launch_hub_table_clear(g->tab_k, g->tab_v, slots, g->stream));
+        ha.hub_v = d_hv;
+        ha.hub_p1 = d_p1;
+        ha.hub_b = d_b;
+        ha.hub_tab = d_tab;
+        ha.hub_act = d_act;
+        ha.hub_best = d_best;
+        ha.hub_used = d_used;
+        ha.used_list = g->used_list;
+        ha.used_base = d_ubase;
+        ha.chunk_h = d_ch;
+        ha.chunk_e0 = d_ce0;
+        ha.chunk_e1 = d_ce1;
+        ha.slice_h = d_sh;
+        ha.slice_j = d_sj;
+        ha.tab_k = g->tab_k;
+        ha.tab_v = g->tab_v;
+        ha.n_hubs = (int32_t)H;
+        ha.n_chunks = (int32_t)n_chunks;
+        ha.n_slices = (int32_t)n_slices;
+        g->hub_hubs_h.push_back(WorkItem{0, 0, 0, H});
+        for (int64_t c = 0; c < n_chunks; ++c) g->hub_chunks_h.push_back(WorkItem{0, 0, c, 1});
+        for (int64_t j = 0; j < n_slices; ++j) g->hub_slices_h.push_back(WorkItem{0, 0, j, 1});
     }
-    g->ctr_iters = iters;
+
+    // every item of this graph in one device block: vertex items, hub items, one per-graph item
+    size_t total_items = 1 + g->hub_hubs_h.size() + g->hub_chunks_h.size() + g->hub_slices_h.size();
+    for (int b = B_THREAD; b <= B_CTA_XL; ++b) total_items += g->items_h[b].size();
+    std::vector<WorkItem> all;
+    all.reserve(total_items);
+    size_t at[B_COUNT] = {}, at_hh = 0, at_hc = 0, at_hs = 0, at_pg = 0;
+    for (int b = B_THREAD; b <= B_CTA_XL; ++b) {
+        at[b] = all.size();
+        all.insert(all.end(), g->items_h[b].begin(), g->items_h[b].end());
+    }
+    at_hh = all.size();
+    all.insert(all.end(), g->hub_hubs_h.begin(), g->hub_hubs_h.end());
+    at_hc = all.size();
+    all.insert(all.end(), g->hub_chunks_h.begin(), g->hub_chunks_h.end());
+    at_hs = all.size();
+    all.insert(all.end(), g->hub_slices_h.begin(), g->hub_slices_h.end());
+    at_pg = all.size();
+    all.push_back(WorkItem{0, 0, 0, 0});
+    LPA_CHECK(dalloc(g, &g->items_d, all.size()));
+    LPA_CUDA(cudaMemcpyAsync(g->items_d, all.data(), all.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                             g->stream));
+    for (int b = B_THREAD; b <= B_CTA_XL; ++b) g->items_at[b] = g->items_d + at[b];
+    g->hub_hubs_d = g->items_d + at_hh;
+    g->hub_chunks_d = g->items_d + at_hc;
+    g->hub_slices_d = g->items_d + at_hs;
+    g->per_graph_d = g->items_d + at_pg;
+    LPA_CHECK(upload_descriptor(g));
+    LPA_CUDA(cudaStreamSynchronize(g->stream));
     return LPA_OK;
 }
 
@@ -782,69 +867,136 @@ cudaEvent_t event_at(lpa_graph *g, size_t k)
     return g->events[k];
 }
 
+int init_state(lpa_graph *g)
+{
+    if (g->n > 0) {
+        k_init_labels<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->off, g->n, g->C, g->flags[0]);
+        LPA_CUDA(cudaGetLastError());
+        LPA_CUDA(cudaMemsetAsync(g->flags[1], 0, (size_t)g->n, g->stream));
+    }
+    g->active_buf = 0;
+    g->next_iter = 0;
+    return LPA_OK;
+}
+
+// CUDA-event timing of every launch of lpa_run (stats->time_kernels).
+struct EventHook : LaunchHook {
+    lpa_graph *g;
+    size_t *evn;
+    int iter = 0;
+    bool on = false;
+    struct Rec {
+        int iter, slot;
+        size_t e0, e1;
+    };
+    std::vector<Rec> recs;
+    size_t pending = 0;
+    EventHook(lpa_graph *gg, size_t *n) : g(gg), evn(n) {}
+    void before(int slot) override
+    {
+        (void)slot;
+        if (!on) return;
+        pending = (*evn)++;
+        cudaEvent_t e = event_at(g, pending);
+        if (e) cudaEventRecord(e, g->stream);
+    }
+    void after(int slot) override
+    {
+        if (!on) return;
+        const size_t e1 = (*evn)++;
+        cudaEvent_t e = event_at(g, e1);
+        if (e) cudaEventRecord(e, g->stream);
+        recs.push_back({iter, slot, pending, e1});
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+namespace lpa {
+
+int ensure_counters(lpa_graph *g, int iters, bool mirror)
+{
+    if (iters < 1) iters = 1;
+    if (iters > g->ctr_iters) {
+        dfree(g, g->ctr);
+        g->ctr = nullptr;
+        g->ctr_iters = 0;
+        LPA_CHECK(dalloc(g, &g->ctr, (size_t)kPerSweep * iters));
+        g->ctr_iters = iters;
+    }
+    if (mirror && iters > g->h_ctr_iters) {
+        if (g->h_ctr) cudaFreeHost(g->h_ctr);
+        g->h_ctr = nullptr;
+        g->h_ctr_iters = 0;
+        if (cudaMallocHost((void **)&g->h_ctr, (size_t)kPerSweep * iters * sizeof(unsigned long long)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            g->h_ctr = nullptr;
+            set_error("cudaMallocHost failed");
+            return LPA_ENOMEM;
+        }
+        g->h_ctr_iters = iters;
+    }
+    return LPA_OK;
+}
+
+void plan_slots(const lpa_tuning &t, int32_t slots[B_COUNT])
+{
+    const int sh = t.smem_table_shift;
+    slots[B_THREAD] = 16;
+    slots[B_GROUP] = (int32_t)slots_for(t.group_max, sh);
+    slots[B_WARP] = (int32_t)slots_for(t.warp_max, sh);
+    slots[B_CTA] = (int32_t)slots_for(t.cta_max, sh);
+    slots[B_CTA_LARGE] = (int32_t)slots_for(t.cta_large_max, sh);
+    slots[B_CTA_XL] = (int32_t)slots_for(t.cta_xl_max, sh);
+    slots[B_HUB] = 0;
+}
+
+bool plan_int_weights(const lpa_graph *g) { return g->int_weights && !g->tuning.float_values; }
+
+int upload_descriptor(lpa_graph *g)
+{
+    GraphDev &d = g->gdh;
+    d.off = g->off;
+    d.idx = g->idx;
+    d.w = g->w;
+    d.C = g->C;
+    d.flags0 = g->flags[0];
+    d.flags1 = g->flags[1];
+    d.mover_v = g->mover_v;
+    d.mover_c = g->mover_c;
+    d.mover_count = g->mover_count;
+    d.ctr = g->ctr;
+    d.ctr_iters = g->ctr_iters;
+    d.fallbacks = g->fallbacks;
+    d.lists = g->lists;
+    d.rs = g->rs_d;
+    d.tshift = g->tuning.smem_table_shift;
+    d.int_weights = plan_int_weights(g) ? 1 : 0;
+    LPA_CUDA(cudaMemcpyAsync(g->gdd, &g->gdh, sizeof(GraphDev), cudaMemcpyHostToDevice, g->stream));
+    return LPA_OK;
+}
+
 void destroy_graph(lpa_graph *g)
 {
     if (!g) return;
     DeviceGuard dg(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
-    free_buckets(g);
-    dfree(g->off);
-    dfree(g->idx);
-    dfree(g->w);
-    dfree(g->C);
-    dfree(g->flagA);
-    dfree(g->flagB);
-    dfree(g->mover_v);
-    dfree(g->mover_c);
-    dfree(g->mover_count);
-    dfree(g->fallbacks);
-    dfree(g->ctr);
-    dfree(g->d_err);
-    dfree(g->Sig);
-    dfree(g->macc);
+    for (auto &a : g->allocs) {
+        if (g->arena) g->arena->free(a.first);
+        else cudaFree(a.first);
+    }
+    g->allocs.clear();
     if (g->h_ctr) cudaFreeHost(g->h_ctr);
+    if (g->hm) cudaFreeHost(g->hm);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     delete g;
 }
 
-int init_state(lpa_graph *g)
-{
-    k_init_labels<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->off, g->n, g->C, g->flagA);
-    LPA_CUDA(cudaGetLastError());
-    g->next_iter = 0;
-    return LPA_OK;
-}
-
-}  // namespace
-
-// =======================================================================================
-extern "C" {
-
-const char *lpa_strerror(int status)
-{
-    switch (status) {
-    case LPA_OK: return "success";
-    case LPA_EINVAL: return "invalid argument";
-    case LPA_ENOMEM: return "out of memory";
-    case LPA_ECUDA: return "CUDA error";
-    case LPA_ETIMEOUT: return "device wait timed out";
-    case LPA_ESTATE: return "invalid state";
-    default: return "unknown status";
-    }
-}
-
-const char *lpa_last_error(void) { return t_error.c_str(); }
-
-const char *lpa_kernel_name(int slot)
-{
-    static const char *names[LPA_NUM_KERNELS] = {"thread", "group", "warp", "cta", "cta_large", "cta_xl",
-                                                 "hub_begin", "hub_acc", "hub_clear", "hub_move", "hub_mark", "apply"};
-    if (slot < 0 || slot >= LPA_NUM_KERNELS) return "";
-    return names[slot];
-}
-
-int lpa_create(const void *offsets, const int32_t *indices, const float *weights, int64_t n_vertices,
-               int64_t n_entries, int flags, void *cuda_stream, lpa_graph **out)
+int create_graph(const void *offsets, const int32_t *indices, const float *weights, int64_t n_vertices,
+                 int64_t n_entries, int flags, cudaStream_t stream, Arena *arena, const lpa_tuning *tuning,
+                 lpa_graph **out)
 {
     if (!out) {
         set_error("lpa_create: out is NULL");
@@ -862,10 +1014,11 @@ int lpa_create(const void *offsets, const int32_t *indices, const float *weights
     }
     lpa_graph *g = new lpa_graph();
     cudaGetDevice(&g->device);
-    g->stream = (cudaStream_t)cuda_stream;
+    g->stream = stream;
+    g->arena = arena;
     g->n = n_vertices;
     g->m = n_entries;
-    g->tuning = default_tuning();
+    g->tuning = tuning ? *tuning : default_tuning();
     const bool dev_ptrs = (flags & LPA_DEVICE_PTRS) != 0;
     const cudaMemcpyKind kind = dev_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     int st = LPA_OK;
@@ -883,15 +1036,19 @@ int lpa_create(const void *offsets, const int32_t *indices, const float *weights
     if ((st = dalloc(g, &g->idx, (size_t)m)) != LPA_OK) return fail(st);
     if (weights && (st = dalloc(g, &g->w, (size_t)m)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->C, (size_t)n)) != LPA_OK) return fail(st);
-    if ((st = dalloc(g, &g->flagA, (size_t)n)) != LPA_OK) return fail(st);
-    if ((st = dalloc(g, &g->flagB, (size_t)n)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->flags[0], (size_t)n)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->flags[1], (size_t)n)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->mover_v, (size_t)n)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->mover_c, (size_t)n)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->mover_count, 1)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->fallbacks, 1)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->d_err, 4)) != LPA_OK) return fail(st);
-    if ((st = dalloc(g, &g->macc, 4)) != LPA_OK) return fail(st);          // 4 x 8 bytes
-    if ((st = ensure_ctr(g, 32)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->macc, 4)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->gdd, 1)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->rs_d, 1)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->queues, B_COUNT)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->active, 1)) != LPA_OK) return fail(st);
+    if ((st = ensure_counters(g, 1, false)) != LPA_OK) return fail(st);
 
     cudaStream_t s = g->stream;
     auto cuda_fail = [&](cudaError_t e, const char *what) {
@@ -904,14 +1061,13 @@ int lpa_create(const void *offsets, const int32_t *indices, const float *weights
         if (e != cudaSuccess) return cuda_fail(e, "copy offsets");
     } else {
         int32_t *tmp = nullptr;
-        e = cudaMalloc((void **)&tmp, (size_t)(n + 1) * sizeof(int32_t));
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        if ((st = dalloc(g, &tmp, (size_t)(n + 1))) != LPA_OK) return fail(st);
         e = cudaMemcpyAsync(tmp, offsets, (size_t)(n + 1) * sizeof(int32_t), kind, s);
         if (e == cudaSuccess) {
             k_off32to64<<<grid_for(n + 1, 256, 16), 256, 0, s>>>(tmp, g->off, n + 1);
             e = cudaStreamSynchronize(s);
         }
-        cudaFree(tmp);
+        dfree(g, tmp);
         if (e != cudaSuccess) return cuda_fail(e, "copy offsets");
     }
     if (m > 0) {
@@ -952,8 +1108,7 @@ int lpa_create(const void *offsets, const int32_t *indices, const float *weights
         cudaMemcpyAsync(&hf, fl, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&hk, mk, sizeof(hk), cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);
-        cudaFree(mk);
-        g->bytes -= (int64_t)sizeof(unsigned long long);
+        dfree(g, mk);
         if (e != cudaSuccess) return cuda_fail(e, "weight properties");
         g->int_weights = (hf & 2u) && hk < (1ull << 24);
     }
@@ -965,8 +1120,7 @@ int lpa_create(const void *offsets, const int32_t *indices, const float *weights
         unsigned long long h[4];
         cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);
-        cudaFree(acc);
-        g->bytes -= 4 * (int64_t)sizeof(unsigned long long);
+        dfree(g, acc);
         if (e != cudaSuccess) return cuda_fail(e, "symmetry check");
         if (h[0] != h[1] || h[2] != h[3]) {
             set_error("lpa_create: graph is not undirected (entry (i,j,w) without (j,i,w))");
@@ -981,11 +1135,95 @@ int lpa_create(const void *offsets, const int32_t *indices, const float *weights
     return LPA_OK;
 }
 
+int graph_modularity(lpa_graph *g, double *q)
+{
+    *q = 0.0;
+    if (g->n == 0) return LPA_OK;
+    if (!g->Sig) {
+        LPA_CHECK(dalloc(g, &g->Sig, (size_t)g->n));
+        LPA_CUDA(cudaMemsetAsync(g->Sig, 0, (size_t)g->n * sizeof(double), g->stream));
+    }
+    LPA_CUDA(cudaMemsetAsync(g->macc, 0, 4 * sizeof(double), g->stream));
+    const int64_t *bs = g->bucket_start;
+    const HubArgs &ha = g->gdh.hub;
+    auto run_lists = [&](auto *Sig, auto *acc) {
+        using ACC = std::remove_pointer_t<decltype(Sig)>;
+        const int64_t n_small = bs[B_GROUP + 1] - bs[B_THREAD];
+        const int64_t n_mid = bs[B_CTA_XL + 1] - bs[B_WARP];
+        if (n_small > 0)
+            k_mod_list<4, ACC><<<grid_for(n_small * 4, 256, 16), 256, 0, g->stream>>>(
+                g->off, g->idx, g->w, g->C, g->lists + bs[B_THREAD], n_small, Sig, acc);
+        if (n_mid > 0)
+            k_mod_list<32, ACC><<<grid_for(n_mid * 32, 256, 16), 256, 0, g->stream>>>(
+                g->off, g->idx, g->w, g->C, g->lists + bs[B_WARP], n_mid, Sig, acc);
+        if (ha.n_hubs > 0 && ha.n_chunks > 0)
+            k_mod_hub_chunks<ACC><<<(unsigned)ha.n_chunks, 256, 0, g->stream>>>(
+                g->idx, g->w, g->C, ha.hub_v, ha.chunk_h, ha.chunk_e0, ha.chunk_e1, Sig, acc);
+    };
+    if (g->int_weights) {
+        unsigned long long *SigU = reinterpret_cast<unsigned long long *>(g->Sig);
+        unsigned long long *acc = reinterpret_cast<unsigned long long *>(g->macc);
+        run_lists(SigU, acc);
+        k_mod_sq_int<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(SigU, g->n, acc);
+        unsigned long long h[4];
+        LPA_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+        LPA_CUDA(cudaStreamSynchronize(g->stream));
+        const __int128 two_m = (__int128)h[1], in = (__int128)h[0];
+        const __int128 sq = ((__int128)h[3] << 64) | (__int128)h[2];
+        const __int128 num = two_m * in - sq, den = two_m * two_m;
+        *q = (den == 0) ? 0.0 : (double)num / (double)den;
+        return LPA_OK;
+    }
+    run_lists(g->Sig, g->macc);
+    k_mod_sq<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->Sig, g->n, g->macc);
+    double h[3];
+    LPA_CUDA(cudaMemcpyAsync(h, g->macc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    LPA_CUDA(cudaStreamSynchronize(g->stream));
+    const double in = h[0], two_m = h[1], sq = h[2];
+    *q = (two_m == 0.0) ? 0.0 : in / two_m - sq / (two_m * two_m);
+    return LPA_OK;
+}
+
+}  // namespace lpa
+
+// =======================================================================================
+extern "C" {
+
+const char *lpa_strerror(int status)
+{
+    switch (status) {
+    case LPA_OK: return "success";
+    case LPA_EINVAL: return "invalid argument";
+    case LPA_ENOMEM: return "out of memory";
+    case LPA_ECUDA: return "CUDA error";
+    case LPA_ETIMEOUT: return "device wait timed out";
+    case LPA_ESTATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+const char *lpa_last_error(void) { return t_error.c_str(); }
+
+const char *lpa_kernel_name(int slot)
+{
+    static const char *names[LPA_NUM_KERNELS] = {"thread", "group", "warp", "cta", "cta_large", "cta_xl",
+                                                 "hub_begin", "hub_acc", "hub_clear", "hub_move", "hub_mark", "apply"};
+    if (slot < 0 || slot >= LPA_NUM_KERNELS) return "";
+    return names[slot];
+}
+
+int lpa_create(const void *offsets, const int32_t *indices, const float *weights, int64_t n_vertices,
+               int64_t n_entries, int flags, void *cuda_stream, lpa_graph **out)
+{
+    return create_graph(offsets, indices, weights, n_vertices, n_entries, flags, (cudaStream_t)cuda_stream, nullptr,
+                        nullptr, out);
+}
+
 void lpa_destroy(lpa_graph *g) { destroy_graph(g); }
 
 int64_t lpa_num_vertices(const lpa_graph *g) { return g ? g->n : -1; }
 int64_t lpa_num_entries(const lpa_graph *g) { return g ? g->m : -1; }
-int64_t lpa_device_bytes(const lpa_graph *g) { return g ? g->bytes + g->bucket_bytes : -1; }
+int64_t lpa_device_bytes(const lpa_graph *g) { return g ? g->bytes : -1; }
 
 int lpa_set_stream(lpa_graph *g, void *cuda_stream)
 {
@@ -1004,11 +1242,11 @@ int lpa_get_tuning(const lpa_graph *g, lpa_tuning *t)
 int lpa_set_tuning(lpa_graph *g, const lpa_tuning *t)
 {
     if (!g || !t) return LPA_EINVAL;
+    DeviceGuard dg(g->device);
     if (check_tuning(*t) != LPA_OK) {
         set_error("lpa_set_tuning: thresholds out of range, decreasing, or a table does not fit in shared memory");
         return LPA_EINVAL;
     }
-    DeviceGuard dg(g->device);
     g->tuning = *t;
     return build_buckets(g);
 }
@@ -1034,7 +1272,7 @@ int lpa_get_state(const lpa_graph *g, int32_t *labels, uint8_t *unprocessed, int
     DeviceGuard dg(g->device);
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (labels && n) LPA_CUDA(cudaMemcpyAsync(labels, g->C, (size_t)n * 4, k, g->stream));
-    if (unprocessed && n) LPA_CUDA(cudaMemcpyAsync(unprocessed, g->flagA, (size_t)n, k, g->stream));
+    if (unprocessed && n) LPA_CUDA(cudaMemcpyAsync(unprocessed, g->flags[g->active_buf], (size_t)n, k, g->stream));
     LPA_CUDA(cudaStreamSynchronize(g->stream));
     if (next_iter) *next_iter = g->next_iter;
     return LPA_OK;
@@ -1053,13 +1291,15 @@ int lpa_set_state(lpa_graph *g, const int32_t *labels, const uint8_t *unprocesse
         g->next_iter = next_iter;
         return LPA_OK;
     }
-    // stage into the mover buffers so a rejected state leaves the handle unchanged
+    // stage labels in the mover buffer and flags in the idle flag buffer, so that a rejected
+    // state leaves the handle unchanged
+    uint8_t *stage = g->flags[1 - g->active_buf];
     if (labels) LPA_CUDA(cudaMemcpyAsync(g->mover_v, labels, (size_t)n * 4, k, g->stream));
     else LPA_CUDA(cudaMemcpyAsync(g->mover_v, g->C, (size_t)n * 4, cudaMemcpyDeviceToDevice, g->stream));
-    if (unprocessed) LPA_CUDA(cudaMemcpyAsync(g->flagB, unprocessed, (size_t)n, k, g->stream));
-    else LPA_CUDA(cudaMemcpyAsync(g->flagB, g->flagA, (size_t)n, cudaMemcpyDeviceToDevice, g->stream));
+    if (unprocessed) LPA_CUDA(cudaMemcpyAsync(stage, unprocessed, (size_t)n, k, g->stream));
+    else LPA_CUDA(cudaMemcpyAsync(stage, g->flags[g->active_buf], (size_t)n, cudaMemcpyDeviceToDevice, g->stream));
     LPA_CUDA(cudaMemsetAsync(g->d_err, 0, 4, g->stream));
-    k_check_state<<<grid_for(n, 256, 16), 256, 0, g->stream>>>(g->off, n, g->mover_v, g->flagB, g->d_err);
+    k_check_state<<<grid_for(n, 256, 16), 256, 0, g->stream>>>(g->off, n, g->mover_v, stage, g->d_err);
     unsigned err = 0;
     LPA_CUDA(cudaMemcpyAsync(&err, g->d_err, 4, cudaMemcpyDeviceToHost, g->stream));
     LPA_CUDA(cudaStreamSynchronize(g->stream));
@@ -1068,7 +1308,7 @@ int lpa_set_state(lpa_graph *g, const int32_t *labels, const uint8_t *unprocesse
         return LPA_EINVAL;
     }
     LPA_CUDA(cudaMemcpyAsync(g->C, g->mover_v, (size_t)n * 4, cudaMemcpyDeviceToDevice, g->stream));
-    std::swap(g->flagA, g->flagB);
+    g->active_buf = 1 - g->active_buf;
     LPA_CUDA(cudaStreamSynchronize(g->stream));
     g->next_iter = next_iter;
     return LPA_OK;
@@ -1085,8 +1325,9 @@ int lpa_set_labels(lpa_graph *g, const int32_t *labels, int64_t n, int on_device
         g->next_iter = 0;
         return LPA_OK;
     }
-    // every vertex with an edge becomes unprocessed; flags staged in flagB
-    k_init_labels<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->off, g->n, g->mover_c, g->flagB);
+    // every vertex with an edge becomes unprocessed (flags staged in the idle buffer)
+    uint8_t *stage = g->flags[1 - g->active_buf];
+    k_init_labels<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->off, g->n, g->mover_c, stage);
     LPA_CUDA(cudaGetLastError());
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     LPA_CUDA(cudaMemcpyAsync(g->mover_v, labels, (size_t)n * 4, k, g->stream));
@@ -1100,7 +1341,7 @@ int lpa_set_labels(lpa_graph *g, const int32_t *labels, int64_t n, int on_device
         return LPA_EINVAL;
     }
     LPA_CUDA(cudaMemcpyAsync(g->C, g->mover_v, (size_t)n * 4, cudaMemcpyDeviceToDevice, g->stream));
-    std::swap(g->flagA, g->flagB);
+    g->active_buf = 1 - g->active_buf;
     LPA_CUDA(cudaStreamSynchronize(g->stream));
     g->next_iter = 0;
     return LPA_OK;
@@ -1111,51 +1352,7 @@ int lpa_modularity(const lpa_graph *gc, double *q)
     lpa_graph *g = const_cast<lpa_graph *>(gc);
     if (!g || !q) return LPA_EINVAL;
     DeviceGuard dg(g->device);
-    *q = 0.0;
-    if (g->n == 0) return LPA_OK;
-    if (!g->Sig) {
-        LPA_CHECK(dalloc(g, &g->Sig, (size_t)g->n));
-        LPA_CUDA(cudaMemsetAsync(g->Sig, 0, (size_t)g->n * sizeof(double), g->stream));
-    }
-    LPA_CUDA(cudaMemsetAsync(g->macc, 0, 4 * sizeof(double), g->stream));
-    const int64_t hub_min = g->hub.n_hubs > 0 ? (int64_t)g->tuning.cta_xl_max : INT64_MAX;
-    const int64_t *bs = g->bucket_start;
-    auto run_lists = [&](auto *Sig, auto *acc) {
-        using ACC = std::remove_pointer_t<decltype(Sig)>;
-        const int64_t n_small = bs[B_GROUP + 1] - bs[B_THREAD];
-        const int64_t n_mid = bs[B_CTA_XL + 1] - bs[B_WARP];
-        if (n_small > 0)
-            k_mod_list<4, ACC><<<grid_for(n_small * 4, 256, 16), 256, 0, g->stream>>>(
-                g->off, g->idx, g->w, g->C, g->lists + bs[B_THREAD], n_small, Sig, acc);
-        if (n_mid > 0)
-            k_mod_list<32, ACC><<<grid_for(n_mid * 32, 256, 16), 256, 0, g->stream>>>(
-                g->off, g->idx, g->w, g->C, g->lists + bs[B_WARP], n_mid, Sig, acc);
-        if (g->hub.n_hubs > 0 && g->n_chunks > 0)
-            k_mod_hub_chunks<ACC><<<(unsigned)g->n_chunks, 256, 0, g->stream>>>(
-                g->idx, g->w, g->C, g->hub.hub_v, g->hub.chunk_h, g->hub.chunk_e0, g->hub.chunk_e1, Sig, acc);
-    };
-    if (g->int_weights) {
-        unsigned long long *SigU = reinterpret_cast<unsigned long long *>(g->Sig);
-        unsigned long long *acc = reinterpret_cast<unsigned long long *>(g->macc);
-        run_lists(SigU, acc);
-        k_mod_sq_int<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(SigU, g->n, acc);
-        unsigned long long h[4];
-        LPA_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
-        LPA_CUDA(cudaStreamSynchronize(g->stream));
-        const __int128 two_m = (__int128)h[1], in = (__int128)h[0];
-        const __int128 sq = ((__int128)h[3] << 64) | (__int128)h[2];
-        const __int128 num = two_m * in - sq, den = two_m * two_m;
-        *q = (den == 0) ? 0.0 : (double)num / (double)den;
-        return LPA_OK;
-    }
-    run_lists(g->Sig, g->macc);
-    k_mod_sq<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->Sig, g->n, g->macc);
-    double h[3];
-    LPA_CUDA(cudaMemcpyAsync(h, g->macc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
-    LPA_CUDA(cudaStreamSynchronize(g->stream));
-    const double in = h[0], two_m = h[1], sq = h[2];
-    *q = (two_m == 0.0) ? 0.0 : in / two_m - sq / (two_m * two_m);
-    return LPA_OK;
+    return graph_modularity(g, q);
 }
 
 int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mode, lpa_stats *stats)
@@ -1185,141 +1382,107 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
         return LPA_OK;
     }
     const int span = max_iters - start;
-    LPA_CHECK(ensure_ctr(g, span));
-    const size_t per = (size_t)LPA_NUM_KERNELS * kCtrFields;
-    LPA_CUDA(cudaMemsetAsync(g->ctr, 0, per * span * sizeof(unsigned long long), s));
+    LPA_CHECK(ensure_counters(g, span, true));
+    if (!g->hm) {
+        if (cudaMallocHost((void **)&g->hm, sizeof(lpa_graph::HostMirror)) != cudaSuccess) {
+            cudaGetLastError();
+            g->hm = nullptr;
+            set_error("cudaMallocHost failed");
+            return LPA_ENOMEM;
+        }
+    }
+    LPA_CHECK(upload_descriptor(g));
+    LPA_CUDA(cudaMemsetAsync(g->ctr, 0, (size_t)kPerSweep * span * sizeof(unsigned long long), s));
     LPA_CUDA(cudaMemsetAsync(g->fallbacks, 0, sizeof(unsigned long long), s));
     LPA_CUDA(cudaMemsetAsync(g->mover_count, 0, sizeof(unsigned long long), s));
-    if (!async_mode) LPA_CUDA(cudaMemsetAsync(g->flagB, 0, (size_t)g->n, s));
+    // the unprocessed flags of sweep `start` must sit where the kernels read them
+    const int target = async_mode ? 0 : (start & 1);
+    if (g->active_buf != target)
+        LPA_CUDA(cudaMemcpyAsync(g->flags[target], g->flags[g->active_buf], (size_t)g->n, cudaMemcpyDeviceToDevice, s));
+    if (!async_mode) LPA_CUDA(cudaMemsetAsync(g->flags[1 - target], 0, (size_t)g->n, s));
+    g->active_buf = target;
+    RunState &rs = g->hm->rs;
+    rs = RunState{};
+    rs.l = start;
+    rs.first = start;
+    rs.max_iters = max_iters;
+    rs.pl_period = pl_period;
+    rs.async_mode = async_mode ? 1 : 0;
+    rs.tol = tolerance;
+    rs.n = g->n;
+    g->hm->active = 1;
+    LPA_CUDA(cudaMemcpyAsync(g->rs_d, &g->hm->rs, sizeof(RunState), cudaMemcpyHostToDevice, s));
+    LPA_CUDA(cudaMemcpyAsync(g->active, &g->hm->active, sizeof(int32_t), cudaMemcpyHostToDevice, s));
 
-    struct Rec {
-        int iter, slot;
-        size_t ev0, ev1;
-    };
-    std::vector<Rec> recs;
+    SweepPlan p{};
+    p.gd = g->gdd;
+    p.n_graphs = 1;
+    for (int b = B_THREAD; b <= B_CTA_XL; ++b) {
+        p.items[b] = g->items_at[b];
+        p.n_items[b] = (int32_t)g->items_h[b].size();
+        p.n_vertices[b] = g->bucket_start[b + 1] - g->bucket_start[b];
+    }
+    plan_slots(g->tuning, p.slots);
+    p.hub_hubs = g->hub_hubs_d;
+    p.n_hub_hubs = (int32_t)g->hub_hubs_h.size();
+    p.hub_chunks = g->hub_chunks_d;
+    p.n_hub_chunks = (int32_t)g->hub_chunks_h.size();
+    p.hub_slices = g->hub_slices_d;
+    p.n_hub_slices = (int32_t)g->hub_slices_h.size();
+    p.per_graph = g->per_graph_d;
+    p.queues = g->queues;
+    p.active_count = g->active;
+    p.group_lanes = g->tuning.group_lanes;
+    p.cta_threads = g->tuning.cta_threads;
+    p.cta_large_threads = g->tuning.cta_large_threads;
+    p.cta_xl_threads = g->tuning.cta_xl_threads;
+    p.hub_chunk = g->tuning.hub_chunk;
+    p.int_weights = plan_int_weights(g) ? 1 : 0;
+
     size_t evn = 0;
     cudaEvent_t run0 = event_at(g, evn++), run1 = event_at(g, evn++);
     if (!run0 || !run1) {
         set_error("cudaEventCreate failed");
         return LPA_ECUDA;
     }
+    EventHook hook(g, &evn);
     std::vector<std::pair<size_t, size_t>> iter_ev;
-    LPA_CUDA(cudaEventRecord(run0, s));
-
-    const lpa_tuning &t = g->tuning;
-    const int64_t *bs = g->bucket_start;
     int launches = 0;
-    int l = start;
-    bool converged = false;
-    for (; l < max_iters; ++l) {
-        const int rel = l - start;
-        const bool pl = pl_period > 0 && (l % pl_period) == 0;
-        SweepArgs a{};
-        a.off = g->off;
-        a.idx = g->idx;
-        a.w = g->w;
-        a.C = g->C;
-        a.flag_cur = g->flagA;
-        a.flag_next = async_mode ? g->flagA : g->flagB;
-        a.mover_v = g->mover_v;
-        a.mover_c = g->mover_c;
-        a.mover_count = g->mover_count;
-        a.ctr = g->ctr + per * rel;
-        a.fallbacks = g->fallbacks;
-        a.pl = pl ? 1 : 0;
-        a.async_mode = async_mode ? 1 : 0;
-        a.tshift = t.smem_table_shift;
-        a.persist_mask = t.persistent_mask;
-        a.int_weights = (g->int_weights && !t.float_values) ? 1 : 0;
-        const int sh = t.smem_table_shift;
-
-        size_t ie0 = evn++, ie1 = evn++;
+    LPA_CUDA(cudaEventRecord(run0, s));
+    int ran = 0;
+    for (; ran < span; ++ran) {
+        const size_t ie0 = evn++, ie1 = evn++;
         if (!event_at(g, ie1)) return LPA_ECUDA;
+        hook.iter = ran;
+        hook.on = timing && ran < LPA_STATS_MAX_ITERS;
         LPA_CUDA(cudaEventRecord(g->events[ie0], s));
-        auto timed = [&](int slot, auto &&launch) -> cudaError_t {
-            ++launches;
-            size_t e0 = 0, e1 = 0;
-            if (timing && rel < LPA_STATS_MAX_ITERS) {
-                e0 = evn++;
-                e1 = evn++;
-                if (!event_at(g, e1)) return cudaErrorUnknown;
-                cudaEventRecord(g->events[e0], s);
-            }
-            cudaError_t e = launch();
-            if (timing && rel < LPA_STATS_MAX_ITERS) {
-                cudaEventRecord(g->events[e1], s);
-                recs.push_back({rel, slot, e0, e1});
-            }
-            return e;
-        };
-        const int32_t *L = g->lists;
-        if (bs[B_THREAD + 1] > bs[B_THREAD])
-            LPA_CUDA(timed(LPA_K_THREAD, [&] {
-                return launch_thread_bucket(L + bs[B_THREAD], bs[B_THREAD + 1] - bs[B_THREAD], a, 16, s);
-            }));
-        if (bs[B_GROUP + 1] > bs[B_GROUP])
-            LPA_CUDA(timed(LPA_K_GROUP, [&] {
-                return launch_group_bucket(L + bs[B_GROUP], bs[B_GROUP + 1] - bs[B_GROUP], a, t.group_lanes,
-                                           (int)slots_for(t.group_max, sh), s);
-            }));
-        if (bs[B_WARP + 1] > bs[B_WARP])
-            LPA_CUDA(timed(LPA_K_WARP, [&] {
-                return launch_warp_bucket(L + bs[B_WARP], bs[B_WARP + 1] - bs[B_WARP], a,
-                                          (int)slots_for(t.warp_max, sh), s);
-            }));
-        if (bs[B_CTA + 1] > bs[B_CTA])
-            LPA_CUDA(timed(LPA_K_CTA, [&] {
-                return launch_cta_bucket(L + bs[B_CTA], bs[B_CTA + 1] - bs[B_CTA], a, t.cta_threads,
-                                         (int)slots_for(t.cta_max, sh), LPA_K_CTA, s);
-            }));
-        if (bs[B_CTA_LARGE + 1] > bs[B_CTA_LARGE])
-            LPA_CUDA(timed(LPA_K_CTA_LARGE, [&] {
-                return launch_cta_bucket(L + bs[B_CTA_LARGE], bs[B_CTA_LARGE + 1] - bs[B_CTA_LARGE], a,
-                                         t.cta_large_threads, (int)slots_for(t.cta_large_max, sh), LPA_K_CTA_LARGE, s);
-            }));
-        if (bs[B_CTA_XL + 1] > bs[B_CTA_XL])
-            LPA_CUDA(timed(LPA_K_CTA_XL, [&] {
-                return launch_cta_bucket(L + bs[B_CTA_XL], bs[B_CTA_XL + 1] - bs[B_CTA_XL], a, t.cta_xl_threads,
-                                         (int)slots_for(t.cta_xl_max, sh), LPA_K_CTA_XL, s);
-            }));
-        if (g->hub.n_hubs > 0) {
-            LPA_CUDA(timed(LPA_K_HUB_BEGIN, [&] { return launch_hub_begin(g->hub, a, s); }));
-            LPA_CUDA(timed(LPA_K_HUB_ACC, [&] { return launch_hub_acc(g->hub, a, g->n_chunks, t.hub_chunk, s); }));
-            LPA_CUDA(timed(LPA_K_HUB_CLEAR, [&] { return launch_hub_clear(g->hub, g->n_slices, s); }));
-            LPA_CUDA(timed(LPA_K_HUB_MOVE, [&] { return launch_hub_move(g->hub, a, s); }));
-            LPA_CUDA(timed(LPA_K_HUB_MARK, [&] { return launch_hub_mark(g->hub, a, g->n_chunks, s); }));
-        }
-        if (!async_mode) {
-            LPA_CUDA(timed(LPA_K_APPLY, [&] { return launch_apply(a, g->n, s); }));
-            LPA_CUDA(cudaMemsetAsync(g->mover_count, 0, sizeof(unsigned long long), s));
-            std::swap(g->flagA, g->flagB);        // next sweep reads the marks; old flags are all clear
-        }
+        LPA_CUDA(enqueue_sweep(p, s, &hook, &launches));
         LPA_CUDA(cudaEventRecord(g->events[ie1], s));
         iter_ev.push_back({ie0, ie1});
-        unsigned long long *hc = g->h_ctr + per * rel;
-        LPA_CUDA(cudaMemcpyAsync(hc, a.ctr, per * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        LPA_CUDA(cudaMemcpyAsync(&g->hm->rs, g->rs_d, sizeof(RunState), cudaMemcpyDeviceToHost, s));
         LPA_CUDA(cudaStreamSynchronize(s));
-        int64_t dn = 0;
-        for (int k = 0; k < LPA_NUM_KERNELS; ++k) dn += (int64_t)hc[k * kCtrFields + CTR_MOVED];
-        if (!pl && (double)dn / (double)g->n < tolerance) {
-            converged = true;
-            ++l;
+        if (g->hm->rs.done) {
+            ++ran;
             break;
         }
     }
     LPA_CUDA(cudaEventRecord(run1, s));
     unsigned long long fb = 0;
     LPA_CUDA(cudaMemcpyAsync(&fb, g->fallbacks, sizeof(fb), cudaMemcpyDeviceToHost, s));
+    LPA_CUDA(cudaMemcpyAsync(g->h_ctr, g->ctr, (size_t)kPerSweep * ran * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, s));
     LPA_CUDA(cudaStreamSynchronize(s));
-    g->next_iter = l;
+    const int l_end = g->hm->rs.l;
+    g->next_iter = l_end;
+    g->active_buf = async_mode ? 0 : (l_end & 1);
     if (stats) {
-        stats->iterations = l;
-        stats->converged = converged ? 1 : 0;
+        stats->iterations = l_end;
+        stats->converged = g->hm->rs.converged;
         stats->probe_fallbacks = (int64_t)fb;
         stats->launches = launches;
         cudaEventElapsedTime(&stats->total_ms, run0, run1);
-        for (int r = 0; r < l - start && r < LPA_STATS_MAX_ITERS; ++r) {
-            const unsigned long long *hc = g->h_ctr + per * r;
+        for (int r = 0; r < ran && r < LPA_STATS_MAX_ITERS; ++r) {
+            const unsigned long long *hc = g->h_ctr + (size_t)kPerSweep * r;
             int64_t act = 0, edg = 0, mv = 0, mk = 0;
             for (int k = 0; k < LPA_NUM_KERNELS; ++k) {
                 act += (int64_t)hc[k * kCtrFields + CTR_ACTIVE];
@@ -1335,9 +1498,9 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
             stats->marks[r] = mk;
             cudaEventElapsedTime(&stats->iter_ms[r], g->events[iter_ev[r].first], g->events[iter_ev[r].second]);
         }
-        for (const Rec &r : recs) {
+        for (const auto &r : hook.recs) {
             float ms = 0.0f;
-            cudaEventElapsedTime(&ms, g->events[r.ev0], g->events[r.ev1]);
+            cudaEventElapsedTime(&ms, g->events[r.e0], g->events[r.e1]);
             stats->kernel_ms[r.iter][r.slot] += ms;
         }
     }

@@ -16,28 +16,26 @@ constexpr int kMaxRetries = 32;    // hybrid probes before the linear fallback (
 constexpr int kCtrFields = 4;      // per kernel slot: active, edges, moved, marks
 enum { CTR_ACTIVE = 0, CTR_EDGES = 1, CTR_MOVED = 2, CTR_MARKS = 3 };
 enum Bucket { B_THREAD = 0, B_GROUP, B_WARP, B_CTA, B_CTA_LARGE, B_CTA_XL, B_HUB, B_COUNT };
+constexpr int kHubSlice = 4096;    // table slots / used-list entries per hub clear block
+constexpr int kPerSweep = LPA_NUM_KERNELS * kCtrFields;   // counter words per sweep
 
-// Arguments of one sweep (Algorithm 1, lpaMove), passed by value to every sweep kernel.
-struct SweepArgs {
-    const int64_t *off;        // CSR offsets [n+1]
-    const int32_t *idx;        // CSR neighbour ids [m]
-    const float *w;            // CSR weights [m] or nullptr (unit)
-    int32_t *C;                // labels [n]
-    uint8_t *flag_cur;         // unprocessed flags read (and cleared) by this sweep
-    uint8_t *flag_next;        // flags set for the next sweep (== flag_cur in ASYNC mode)
-    int32_t *mover_v;          // SYNC: vertices that moved this sweep
-    int32_t *mover_c;          // SYNC: their new labels
-    unsigned long long *mover_count;
-    unsigned long long *ctr;   // this sweep's counters [LPA_NUM_KERNELS][kCtrFields]
-    unsigned long long *fallbacks;
-    int32_t pl;                // Pick-Less active on this sweep
-    int32_t async_mode;        // 1: write labels in place (ASYNC), 0: record movers (SYNC)
-    int32_t tshift;            // smem table capacity = nextPow2(D << tshift) - 1
-    int32_t persist_mask;      // bit k: kernel slot k runs as a persistent grid
-    int32_t int_weights;       // 1: integer weights with weighted degrees < 2^24 (uint32 sums)
+// Run state of one graph, device-resident.  Sweep kernels read it; k_decide (after each
+// sweep) applies the stop rule of Algorithm 1 and advances l.
+struct RunState {
+    int32_t l;            // absolute index of the sweep about to run
+    int32_t first;        // absolute index of this run's first sweep (counter slot 0)
+    int32_t max_iters;
+    int32_t pl_period;
+    int32_t async_mode;
+    int32_t done;         // the run has stopped (tolerance or cap); no more work for this graph
+    int32_t converged;    // stopped by the tolerance test
+    int32_t pad;
+    double tol;
+    int64_t n;            // vertices (dN / n)
+    int64_t last_dn;
 };
 
-// Hub-bucket device arrays.
+// Hub-bucket device arrays of one graph.
 struct HubArgs {
     const int32_t *hub_v;      // [H] vertex of each hub
     const uint32_t *hub_p1;    // [H] table capacity (2^b - 1)
@@ -51,33 +49,108 @@ struct HubArgs {
     const int32_t *chunk_h;    // [n_chunks] hub of each accumulate / mark block
     const int64_t *chunk_e0;   // [n_chunks] first CSR entry
     const int64_t *chunk_e1;   // [n_chunks] end CSR entry
-    const int32_t *slice_h;    // [n_slices] hub of each argmax block
-    const int32_t *slice_j;    // [n_slices] slice index within the hub's used list
+    const int32_t *slice_h;    // [n_slices] hub of each clear block
+    const int32_t *slice_j;    // [n_slices] slice index within the hub's table / used list
     int32_t *tab_k;            // hub table keys
-    float *tab_v;              // hub table values
+    float *tab_v;              // hub table values (float32 or uint32 bits)
     int32_t n_hubs;
+    int32_t n_chunks;
+    int32_t n_slices;
+    int32_t pad;
 };
 
-constexpr int kHubSlice = 4096;   // used-list entries per argmax block
+// Static description of one resident graph, device-resident (an array of them per launch).
+struct GraphDev {
+    const int64_t *off;        // CSR offsets [n+1]
+    const int32_t *idx;        // CSR neighbour ids [m]
+    const float *w;            // CSR weights [m] or nullptr (unit)
+    int32_t *C;                // labels [n]
+    uint8_t *flags0, *flags1;  // processed flags; sweep l reads flags[l & 1] (sync) or flags0 (async)
+    int32_t *mover_v;          // sync: vertices that moved this sweep
+    int32_t *mover_c;          // sync: their new labels
+    unsigned long long *mover_count;
+    unsigned long long *ctr;   // [ctr_iters][kPerSweep] per-sweep counters of this run
+    unsigned long long *fallbacks;
+    const int32_t *lists;      // degree-bucket vertex lists
+    RunState *rs;
+    int32_t ctr_iters;
+    int32_t tshift;            // smem table capacity = nextPow2(D << tshift) - 1
+    int32_t int_weights;       // integer weights with weighted degrees < 2^24 (uint32 sums)
+    int32_t pad;
+    HubArgs hub;
+};
 
-// Launch helpers implemented in lpa_sweep.cu.
+// A unit of work of one kernel kind: for vertex kernels, entries [start, start + count) of
+// graph g's bucket list; for hub kernels, hubs / chunks / slices [start, start + count).
+struct WorkItem {
+    int32_t g;
+    int32_t pad;
+    int64_t start;
+    int64_t count;
+};
+
+// One launch of every kernel of a sweep over a set of graphs (one graph for lpa_run, many
+// for batches and the server).  Launch shapes are uniform over the set.
+struct SweepPlan {
+    const GraphDev *gd;        // device array of graph descriptors
+    int32_t n_graphs;
+    const WorkItem *items[B_COUNT];    // vertex items per bucket (B_HUB unused)
+    int32_t n_items[B_COUNT];
+    int64_t n_vertices[B_COUNT];       // vertices covered by the items of each bucket
+    int32_t slots[B_COUNT];    // smem slots per table for each vertex kernel
+    const WorkItem *hub_hubs;  // items over hubs (begin, move)
+    int32_t n_hub_hubs;
+    const WorkItem *hub_chunks;        // one item per hub chunk (acc, mark)
+    int32_t n_hub_chunks;
+    const WorkItem *hub_slices;        // one item per hub clear slice
+    int32_t n_hub_slices;
+    const WorkItem *per_graph;         // one item per graph (apply, decide)
+    unsigned *queues;          // [B_COUNT] work-queue counters, zeroed before each sweep
+    int32_t *active_count;     // device counter written by k_decide (graphs still running)
+    int32_t group_lanes, cta_threads, cta_large_threads, cta_xl_threads, hub_chunk;
+    int32_t persist_mask;
+    int32_t int_weights;       // 1: every graph of the plan uses uint32 sums (else float32)
+};
+
+// Optional hook around each kernel launch (CUDA-event timing per kernel slot).
+struct LaunchHook {
+    virtual void before(int slot) = 0;
+    virtual void after(int slot) = 0;
+    virtual ~LaunchHook() {}
+};
+
 cudaError_t sweep_init_constants();
-cudaError_t launch_thread_bucket(const int32_t *list, int64_t count, const SweepArgs &a,
-                                 int slots, cudaStream_t s);
-cudaError_t launch_group_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int lanes,
-                                int slots, cudaStream_t s);
-cudaError_t launch_warp_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int slots,
-                               cudaStream_t s);
-cudaError_t launch_cta_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int threads,
-                              int slots, int kslot, cudaStream_t s);
-cudaError_t launch_hub_begin(const HubArgs &h, const SweepArgs &a, cudaStream_t s);
-cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, int chunk, cudaStream_t s);
-cudaError_t launch_hub_clear(const HubArgs &h, int64_t n_slices, cudaStream_t s);
-cudaError_t launch_hub_move(const HubArgs &h, const SweepArgs &a, cudaStream_t s);
-cudaError_t launch_hub_mark(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, cudaStream_t s);
-cudaError_t launch_apply(const SweepArgs &a, int64_t n, cudaStream_t s);
+// Enqueues one sweep of every graph of the plan (graphs whose run has stopped do no work),
+// the synchronous label publication and k_decide.  *launches counts kernel launches.
+cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, int *launches);
 cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, cudaStream_t s);
 size_t max_dynamic_smem();
+int num_sms();
+
+// Device memory arena: one reservation carved into 256-byte aligned blocks (first fit with
+// coalescing free list).  Batches and the server allocate their graphs from it, so thousands
+// of graphs do not each cost a dozen cudaMalloc calls and admission can be decided by
+// footprint.
+class Arena {
+  public:
+    explicit Arena(size_t bytes);
+    ~Arena();
+    bool ok() const { return base_ != nullptr; }
+    void *alloc(size_t bytes);
+    void free(void *p);
+    size_t capacity() const { return cap_; }
+    size_t used() const { return used_; }
+    size_t largest_free() const;
+
+  private:
+    struct Block {
+        size_t off, size;
+    };
+    unsigned char *base_ = nullptr;
+    size_t cap_ = 0, used_ = 0;
+    std::vector<Block> free_;        // sorted by offset, coalesced
+    std::vector<Block> taken_;       // sorted by offset
+};
 
 // Thread-local error message.
 void set_error(const std::string &msg);

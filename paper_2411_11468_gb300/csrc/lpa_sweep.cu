@@ -221,9 +221,57 @@ __device__ __forceinline__ void clear_table_vec(int32_t *Hk, void *Hv, uint32_t 
     }
 }
 
+// The per-sweep view of one graph: what the sweep kernels read and write for an item of
+// graph g, derived from its descriptor and run state.
+struct SweepView {
+    const int64_t *off;
+    const int32_t *idx;
+    const float *w;
+    int32_t *C;
+    uint8_t *flag_cur;         // unprocessed flags read (and cleared) by this sweep
+    uint8_t *flag_next;        // flags set for the next sweep (== flag_cur in ASYNC mode)
+    int32_t *mover_v, *mover_c;
+    unsigned long long *mover_count;
+    unsigned long long *ctr;   // this sweep's counters [LPA_NUM_KERNELS][kCtrFields]
+    unsigned long long *fallbacks;
+    const int32_t *lists;
+    int32_t pl, async_mode, tshift, done;
+};
+
+__device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
+{
+    const GraphDev &G = gd[g];
+    const RunState *rs = G.rs;
+    SweepView v;
+    const int l = rs->l;
+    v.done = rs->done;
+    v.pl = (rs->pl_period > 0) && (l % rs->pl_period == 0);
+    v.async_mode = rs->async_mode;
+    v.off = G.off;
+    v.idx = G.idx;
+    v.w = G.w;
+    v.C = G.C;
+    if (v.async_mode) {
+        v.flag_cur = G.flags0;
+        v.flag_next = G.flags0;
+    } else {
+        v.flag_cur = (l & 1) ? G.flags1 : G.flags0;
+        v.flag_next = (l & 1) ? G.flags0 : G.flags1;
+    }
+    v.mover_v = G.mover_v;
+    v.mover_c = G.mover_c;
+    v.mover_count = G.mover_count;
+    const int slot = (l - rs->first) % (G.ctr_iters > 0 ? G.ctr_iters : 1);
+    v.ctr = G.ctr + (size_t)(slot < 0 ? 0 : slot) * kPerSweep;
+    v.fallbacks = G.fallbacks;
+    v.lists = G.lists;
+    v.tshift = G.tshift;
+    return v;
+}
+
 // Warp-aggregated append of (v, c) to the synchronous mover list.  Every lane of the
 // warp must call it.
-__device__ __forceinline__ void append_movers(const SweepArgs &a, bool pred, int32_t v, int32_t c)
+__device__ __forceinline__ void append_movers(const SweepView &a, bool pred, int32_t v, int32_t c)
 {
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
     if (!bal) return;
@@ -239,38 +287,10 @@ __device__ __forceinline__ void append_movers(const SweepArgs &a, bool pred, int
     }
 }
 
-// Warp sum of four per-lane counters into block counters (every lane calls).
-__device__ __forceinline__ void warp_count(unsigned long long *bctr, unsigned act, unsigned edges,
-                                           unsigned moved, unsigned marks)
-{
-    act = __reduce_add_sync(0xFFFFFFFFu, act);
-    edges = __reduce_add_sync(0xFFFFFFFFu, edges);
-    moved = __reduce_add_sync(0xFFFFFFFFu, moved);
-    marks = __reduce_add_sync(0xFFFFFFFFu, marks);
-    if ((threadIdx.x & 31) == 0) {
-        if (act) atomicAdd(&bctr[CTR_ACTIVE], (unsigned long long)act);
-        if (edges) atomicAdd(&bctr[CTR_EDGES], (unsigned long long)edges);
-        if (moved) atomicAdd(&bctr[CTR_MOVED], (unsigned long long)moved);
-        if (marks) atomicAdd(&bctr[CTR_MARKS], (unsigned long long)marks);
-    }
-}
-
-__device__ __forceinline__ void flush_block_counts(const SweepArgs &a, unsigned long long *bctr,
-                                                   unsigned *bfb, int kslot)
-{
-    __syncthreads();
-    if (threadIdx.x < kCtrFields) {
-        const unsigned long long x = bctr[threadIdx.x];
-        if (x) atomicAdd(&a.ctr[kslot * kCtrFields + threadIdx.x], x);
-    } else if (threadIdx.x == kCtrFields) {
-        if (*bfb) atomicAdd(a.fallbacks, (unsigned long long)*bfb);
-    }
-}
-
 // Loads entry e of the row of v: (label of the neighbour, weight); has = false for e past
 // the row end and for self-loops (Algorithm 1 skips j = i).
 template <typename V>
-__device__ __forceinline__ void load_entry(const SweepArgs &a, int32_t v, int64_t e, int64_t end, bool &has,
+__device__ __forceinline__ void load_entry(const SweepView &a, int32_t v, int64_t e, int64_t end, bool &has,
                                            int32_t &k, V &wv)
 {
     has = e < end;
@@ -290,7 +310,7 @@ __device__ __forceinline__ void load_entry(const SweepArgs &a, int32_t v, int64_
 // lane offset `lane` inside each step.  All U entries of a round are loaded (index, weight,
 // gathered label) before any of them is inserted, so U gathers per thread are in flight.
 template <int G, bool SHARED, bool TRACK, int U, typename V>
-__device__ __forceinline__ void scan_row(const SweepArgs &a, int32_t v, int64_t start, int64_t end, int step,
+__device__ __forceinline__ void scan_row(const SweepView &a, int32_t v, int64_t start, int64_t end, int step,
                                          int lane, int32_t *Hk, V *Hv, int stride, uint32_t p1, uint32_t b,
                                          unsigned long long &best, unsigned &fb, uint32_t *ucnt = nullptr,
                                          int32_t *ulist = nullptr, int round = 0)
@@ -317,84 +337,199 @@ __device__ __forceinline__ bool decide(unsigned long long best, int32_t cur, int
 }
 
 // ---------------------------------------------------------------------------------
-// G lanes per vertex (G = 1: thread per vertex with a private table; G = 32: warp per
-// vertex).  Persistent: every warp walks the bucket list in steps of 32/G vertices, so the
-// block synchronises only at its start and end.
-template <int G, int TPB, typename V>
-__global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list, int64_t count, SweepArgs a,
-                                               int slots, int kslot)
+// Kernel arguments common to the vertex kernels: the plan's graphs, this kernel's work items
+// and work-queue counter, and the number of graphs still running (0: return at once).
+struct KArgs {
+    const GraphDev *gd;
+    const WorkItem *items;
+    int32_t n_items;
+    int32_t slots;
+    unsigned *queue;
+    const int32_t *active;
+    int32_t kslot;
+    int32_t pad;
+};
+
+// Adds a warp's four counters and its fallback count to graph counters (every lane calls).
+__device__ __forceinline__ void warp_flush(const SweepView &a, int kslot, unsigned act, unsigned edges,
+                                           unsigned moved, unsigned marks, unsigned fb)
 {
+    act = __reduce_add_sync(0xFFFFFFFFu, act);
+    edges = __reduce_add_sync(0xFFFFFFFFu, edges);
+    moved = __reduce_add_sync(0xFFFFFFFFu, moved);
+    marks = __reduce_add_sync(0xFFFFFFFFu, marks);
+    fb = __reduce_add_sync(0xFFFFFFFFu, fb);
+    if ((threadIdx.x & 31) == 0) {
+        unsigned long long *c = a.ctr + kslot * kCtrFields;
+        if (act) atomicAdd(c + CTR_ACTIVE, (unsigned long long)act);
+        if (edges) atomicAdd(c + CTR_EDGES, (unsigned long long)edges);
+        if (moved) atomicAdd(c + CTR_MOVED, (unsigned long long)moved);
+        if (marks) atomicAdd(c + CTR_MARKS, (unsigned long long)marks);
+        if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
+    }
+}
+
+// G lanes per vertex (G = 1: thread per vertex with a private table; G = 32: warp per
+// vertex).  Persistent: each warp takes work items (a range of one graph's bucket list) from
+// the queue and walks them 32/G vertices at a time.
+template <int G, int TPB, typename V>
+__global__ void __launch_bounds__(TPB) k_group(KArgs k)
+{
+    if (*k.active == 0) return;                        // every graph has stopped
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NG = TPB / G;
     constexpr int GPW = 32 / G;                        // groups per warp
-    __shared__ unsigned long long bctr[kCtrFields];
-    __shared__ unsigned bfb;
-    if (threadIdx.x < kCtrFields) bctr[threadIdx.x] = 0;
-    if (threadIdx.x == 0) bfb = 0;
-    __syncthreads();
-
+    const int lane_w = threadIdx.x & 31;
     const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
     const int grp = threadIdx.x / G;
+    const int gw = lane_w / G;                         // group within the warp
     int32_t *Hk;
     V *Hv;
     int stride;
     if (G == 1) {                      // interleaved: slot s of thread t at s * TPB + t
         Hk = (int32_t *)smem + threadIdx.x;
-        Hv = (V *)(smem + (size_t)TPB * slots * sizeof(int32_t)) + threadIdx.x;
+        Hv = (V *)(smem + (size_t)TPB * k.slots * sizeof(int32_t)) + threadIdx.x;
         stride = TPB;
     } else {
-        Hk = (int32_t *)smem + (size_t)grp * slots;
-        Hv = (V *)(smem + (size_t)NG * slots * sizeof(int32_t)) + (size_t)grp * slots;
+        Hk = (int32_t *)smem + (size_t)grp * k.slots;
+        Hv = (V *)(smem + (size_t)NG * k.slots * sizeof(int32_t)) + (size_t)grp * k.slots;
         stride = 1;
     }
-
-    unsigned fb = 0, c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
-    const int64_t warp_id = ((int64_t)blockIdx.x * TPB + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * TPB) >> 5;
-    const int gw = (threadIdx.x & 31) / G;             // group within the warp
-    for (int64_t wb = warp_id * GPW; wb < count; wb += n_warps * GPW) {   // uniform per warp
-        const int64_t gi = wb + gw;
-        int32_t v = -1;
-        bool act = false;
-        if (gi < count) {
-            v = __ldg(list + gi);
-            if (lane == 0) {
-                act = a.flag_cur[v] != 0;
-                if (act) a.flag_cur[v] = 0;               // mark processed
+    for (;;) {
+        int it = 0;
+        if (lane_w == 0) it = (int)atomicAdd(k.queue, 1u);
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it >= k.n_items) break;
+        const WorkItem item = k.items[it];
+        const SweepView a = view_of(k.gd, item.g);
+        if (a.done) continue;
+        unsigned fb = 0, c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
+        for (int64_t wb = 0; wb < item.count; wb += GPW) {          // uniform per warp
+            const int64_t gi = wb + gw;
+            int32_t v = -1;
+            bool act = false;
+            if (gi < item.count) {
+                v = __ldg(a.lists + item.start + gi);
+                if (lane == 0) {
+                    act = a.flag_cur[v] != 0;
+                    if (act) a.flag_cur[v] = 0;           // mark processed
+                }
             }
+            if (G > 1) act = __shfl_sync(group_mask<G>(), act, 0, G);
+            int32_t cstar = -1;
+            bool moved = false;
+            if (act) {
+                const int64_t o0 = a.off[v], o1 = a.off[v + 1];
+                const uint32_t D = (uint32_t)(o1 - o0);
+                const uint32_t b = cap_bits(D << a.tshift);    // capacity >= D << tshift
+                const uint32_t p1 = cap_of_bits(b);
+                if (G == 1) {
+                    for (uint32_t s = 0; s < p1; ++s) {        // hashtableClear
+                        Hk[(size_t)s * stride] = kEmpty;
+                        Hv[(size_t)s * stride] = V(0);
+                    }
+                } else {
+                    group_sync<G>();                           // previous vertex's inserts are done
+                    clear_table_vec(Hk, Hv, p1, lane, G);
+                    group_sync<G>();
+                }
+                const int32_t cur = a.C[v];
+                unsigned long long best = 0;
+                scan_row<G, (G > 1), false, 1>(a, v, o0, o1, G, lane, Hk, Hv, stride, p1, b, best, fb);
+                best = group_max<G>(best);                     // hashtableMaxKey
+                moved = decide(best, cur, a.pl, cstar);
+                if (moved) {
+                    if (a.async_mode && lane == 0) {
+                        a.C[v] = cstar;
+                        __threadfence();
+                    }
+                    group_sync<G>();
+                    for (int64_t e = o0 + lane; e < o1; e += G) a.flag_next[a.idx[e]] = 1;   // mark neighbours
+                }
+                if (lane == 0) {
+                    c_act += 1;
+                    c_edges += D;
+                    if (moved) {
+                        c_moved += 1;
+                        c_marks += D;
+                    }
+                }
+            }
+            if (!a.async_mode) append_movers(a, moved && lane == 0, v, cstar);
         }
-        if (G > 1) act = __shfl_sync(group_mask<G>(), act, 0, G);
-        int32_t cstar = -1;
-        bool moved = false;
-        if (act) {
+        warp_flush(a, k.kslot, c_act, c_edges, c_moved, c_marks, fb);
+    }
+}
+
+// One thread block per vertex; the table (up to k.slots entries) lives in dynamic smem.
+// Persistent: each block takes work items from the queue and walks their vertices.
+template <int TPB, typename V>
+__global__ void __launch_bounds__(TPB) k_cta(KArgs k)
+{
+    if (*k.active == 0) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int32_t *Hk = (int32_t *)smem;
+    V *Hv = (V *)(smem + (size_t)k.slots * sizeof(int32_t));
+    __shared__ int s_item, s_act;
+    __shared__ int32_t s_v;
+    __shared__ unsigned long long s_best[TPB / 32];
+    for (;;) {
+        __syncthreads();                               // s_item and s_best of the last round are consumed
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(k.queue, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= k.n_items) break;
+        const WorkItem item = k.items[it];
+        const SweepView a = view_of(k.gd, item.g);
+        if (a.done) continue;
+        unsigned fb = 0;
+        unsigned long long c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
+        for (int64_t gi = 0; gi < item.count; ++gi) {
+            __syncthreads();                           // the previous vertex is finished
+            if (threadIdx.x == 0) {
+                const int32_t v0 = __ldg(a.lists + item.start + gi);
+                const int act = a.flag_cur[v0] != 0;
+                if (act) a.flag_cur[v0] = 0;           // mark processed
+                s_act = act;
+                s_v = v0;
+            }
+            __syncthreads();
+            if (!s_act) continue;                      // uniform for the block
+            const int32_t v = s_v;
             const int64_t o0 = a.off[v], o1 = a.off[v + 1];
             const uint32_t D = (uint32_t)(o1 - o0);
-            const uint32_t b = cap_bits(D << a.tshift);    // capacity >= D << tshift
+            const uint32_t b = cap_bits(D << a.tshift);
             const uint32_t p1 = cap_of_bits(b);
-            if (G == 1) {
-                for (uint32_t s = 0; s < p1; ++s) {        // hashtableClear
-                    Hk[(size_t)s * stride] = kEmpty;
-                    Hv[(size_t)s * stride] = V(0);
-                }
-            } else {
-                group_sync<G>();                           // previous vertex's inserts are done
-                clear_table_vec(Hk, Hv, p1, lane, G);
-                group_sync<G>();
-            }
+            clear_table_vec(Hk, Hv, p1, threadIdx.x, TPB);
+            __syncthreads();
             const int32_t cur = a.C[v];
             unsigned long long best = 0;
-            scan_row<G, (G > 1), false, 1>(a, v, o0, o1, G, lane, Hk, Hv, stride, p1, b, best, fb);
-            best = group_max<G>(best);                     // hashtableMaxKey
-            moved = decide(best, cur, a.pl, cstar);
+            constexpr int U = TPB >= 1024 ? 2 : 1;         // loads in flight per thread
+            scan_row<32, true, false, U>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, Hk, Hv, 1,
+                                         p1, b, best, fb, nullptr, nullptr, TPB * U);
+            best = group_max<32>(best);
+            if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+            __syncthreads();
+            best = 0;
+#pragma unroll
+            for (int w = 0; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
+            int32_t cstar = -1;
+            const bool moved = decide(best, cur, a.pl, cstar);
             if (moved) {
-                if (a.async_mode && lane == 0) {
-                    a.C[v] = cstar;
-                    __threadfence();
+                if (threadIdx.x == 0) {
+                    if (a.async_mode) {
+                        a.C[v] = cstar;
+                        __threadfence();
+                    } else {
+                        const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
+                        a.mover_v[pos] = v;
+                        a.mover_c[pos] = cstar;
+                    }
                 }
-                group_sync<G>();
-                for (int64_t e = o0 + lane; e < o1; e += G) a.flag_next[a.idx[e]] = 1;   // mark neighbours
+                if (a.async_mode) __syncthreads();
+                for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
             }
-            if (lane == 0) {
+            if (threadIdx.x == 0) {
                 c_act += 1;
                 c_edges += D;
                 if (moved) {
@@ -403,119 +538,64 @@ __global__ void __launch_bounds__(TPB) k_group(const int32_t *__restrict__ list,
                 }
             }
         }
-        if (!a.async_mode) append_movers(a, moved && lane == 0, v, cstar);
-    }
-    warp_count(bctr, c_act, c_edges, c_moved, c_marks);
-    if (fb) atomicAdd(&bfb, fb);
-    flush_block_counts(a, bctr, &bfb, kslot);
-}
-
-// ---------------------------------------------------------------------------------
-// One thread block per vertex; the table (up to slots entries) lives in dynamic smem.
-// Persistent: each block walks the bucket list with a grid stride.
-template <int TPB, typename V>
-__global__ void __launch_bounds__(TPB) k_cta(const int32_t *__restrict__ list, int64_t count, SweepArgs a,
-                                             int slots, int kslot)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    int32_t *Hk = (int32_t *)smem;
-    V *Hv = (V *)(smem + (size_t)slots * sizeof(int32_t));
-    __shared__ int s_act;
-    __shared__ int32_t s_v;
-    __shared__ unsigned long long s_best[TPB / 32];
-    unsigned fb = 0;
-    unsigned long long c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
-    for (int64_t gi = blockIdx.x; gi < count; gi += gridDim.x) {
-        __syncthreads();                               // the previous vertex is finished
         if (threadIdx.x == 0) {
-            const int32_t v0 = __ldg(list + gi);
-            const int act = a.flag_cur[v0] != 0;
-            if (act) a.flag_cur[v0] = 0;               // mark processed
-            s_act = act;
-            s_v = v0;
+            unsigned long long *c = a.ctr + k.kslot * kCtrFields;
+            if (c_act) atomicAdd(c + CTR_ACTIVE, c_act);
+            if (c_edges) atomicAdd(c + CTR_EDGES, c_edges);
+            if (c_moved) atomicAdd(c + CTR_MOVED, c_moved);
+            if (c_marks) atomicAdd(c + CTR_MARKS, c_marks);
         }
-        __syncthreads();
-        if (!s_act) continue;                          // uniform for the block
-        const int32_t v = s_v;
-        const int64_t o0 = a.off[v], o1 = a.off[v + 1];
-        const uint32_t D = (uint32_t)(o1 - o0);
-        const uint32_t b = cap_bits(D << a.tshift);
-        const uint32_t p1 = cap_of_bits(b);
-        clear_table_vec(Hk, Hv, p1, threadIdx.x, TPB);
-        __syncthreads();
-        const int32_t cur = a.C[v];
-        unsigned long long best = 0;
-        constexpr int U = TPB >= 1024 ? 2 : 1;             // loads in flight per thread
-        scan_row<32, true, false, U>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, Hk, Hv, 1, p1,
-                                     b, best, fb, nullptr, nullptr, TPB * U);
-        best = group_max<32>(best);
-        if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-        __syncthreads();
-        best = 0;
-#pragma unroll
-        for (int w = 0; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
-        int32_t cstar = -1;
-        const bool moved = decide(best, cur, a.pl, cstar);
-        if (moved) {
-            if (threadIdx.x == 0) {
-                if (a.async_mode) {
-                    a.C[v] = cstar;
-                    __threadfence();
-                } else {
-                    const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
-                    a.mover_v[pos] = v;
-                    a.mover_c[pos] = cstar;
-                }
-            }
-            if (a.async_mode) __syncthreads();
-            for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
-        }
-        if (threadIdx.x == 0) {
-            c_act += 1;
-            c_edges += D;
-            if (moved) {
-                c_moved += 1;
-                c_marks += D;
-            }
-        }
+        if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
     }
-    if (threadIdx.x == 0) {
-        unsigned long long *c = a.ctr + kslot * kCtrFields;
-        if (c_act) atomicAdd(c + CTR_ACTIVE, c_act);
-        if (c_edges) atomicAdd(c + CTR_EDGES, c_edges);
-        if (c_moved) atomicAdd(c + CTR_MOVED, c_moved);
-        if (c_marks) atomicAdd(c + CTR_MARKS, c_marks);
-    }
-    if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
 }
 
 // ---------------------------------------------------------------------------------
 // Hubs: tables in HBM shared by several blocks.  Per sweep: begin (take the processed
-// flag), accumulate (blocks over CSR chunks; each block folds its running maximum into
-// hub_best), clear (blocks over the used-slot list), move (one thread per hub), mark
-// (blocks over the CSR chunks of the hubs that moved).
-__global__ void k_hub_begin(HubArgs h, SweepArgs a)
+// flag), accumulate (a block per CSR chunk; each block folds its running maximum into
+// hub_best), clear (a block per slice of the used-slot list or of the table), move (the
+// decision), mark (a block per CSR chunk of the hubs that moved).  Items: begin and move take
+// a graph's hubs [start, start + count); accumulate, clear and mark take one chunk / slice.
+struct HArgs {
+    const GraphDev *gd;
+    const WorkItem *items;
+    const int32_t *active;
+    int32_t chunk;
+    int32_t pad;
+};
+
+__global__ void k_hub_begin(HArgs k)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= h.n_hubs) return;
-    const int32_t v = h.hub_v[t];
-    const uint8_t act = a.flag_cur[v] != 0;
-    if (act) a.flag_cur[v] = 0;                       // mark processed
-    h.hub_act[t] = act;
-    h.hub_best[t] = 0ull;
-    h.hub_used[t] = 0u;
+    if (*k.active == 0) return;
+    const WorkItem item = k.items[blockIdx.x];
+    const SweepView a = view_of(k.gd, item.g);
+    if (a.done) return;
+    const HubArgs &h = k.gd[item.g].hub;
+    for (int64_t t = item.start + threadIdx.x; t < item.start + item.count; t += blockDim.x) {
+        const int32_t v = h.hub_v[t];
+        const uint8_t act = a.flag_cur[v] != 0;
+        if (act) a.flag_cur[v] = 0;                   // mark processed
+        h.hub_act[t] = act;
+        h.hub_best[t] = 0ull;
+        h.hub_used[t] = 0u;
+    }
 }
 
 // Slots taken from empty are collected in a block-local list in shared memory and copied to
 // the hub's used list with one global atomic per block.
 template <int TPB, typename V>
-__global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a, int chunk)
+__global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
 {
+    if (*k.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
     int32_t *s_list = (int32_t *)smem;                 // [chunk]
     __shared__ unsigned long long s_best[TPB / 32];
     __shared__ uint32_t s_cnt, s_base;
-    const int hh = h.chunk_h[blockIdx.x];
+    const WorkItem item = k.items[blockIdx.x];
+    const SweepView a = view_of(k.gd, item.g);
+    if (a.done) return;
+    const HubArgs &h = k.gd[item.g].hub;
+    const int64_t c = item.start;
+    const int hh = h.chunk_h[c];
     if (!h.hub_act[hh]) return;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
@@ -523,7 +603,7 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a, int chu
     const uint32_t p1 = h.hub_p1[hh], b = h.hub_b[hh];
     int32_t *Hk = h.tab_k + h.hub_tab[hh];
     V *Hv = reinterpret_cast<V *>(h.tab_v) + h.hub_tab[hh];
-    const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
+    const int64_t e0 = h.chunk_e0[c], e1 = h.chunk_e1[c];
     unsigned fb = 0;
     unsigned long long best = 0;
     scan_row<32, true, true, 2>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, Hk, Hv, 1, p1, b,
@@ -545,11 +625,16 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HubArgs h, SweepArgs a, int chu
 // Clears the table slots a hub used in this sweep: slot by slot from the used list when
 // few were used, or the whole table with coalesced stores when more than an eighth were.
 template <int TPB>
-__global__ void __launch_bounds__(TPB) k_hub_clear(HubArgs h)
+__global__ void __launch_bounds__(TPB) k_hub_clear(HArgs k)
 {
-    const int hh = h.slice_h[blockIdx.x];
+    if (*k.active == 0) return;
+    const WorkItem item = k.items[blockIdx.x];
+    const SweepView a = view_of(k.gd, item.g);
+    if (a.done) return;
+    const HubArgs &h = k.gd[item.g].hub;
+    const int hh = h.slice_h[item.start];
     if (!h.hub_act[hh]) return;
-    const int64_t lo = (int64_t)h.slice_j[blockIdx.x] * kHubSlice;
+    const int64_t lo = (int64_t)h.slice_j[item.start] * kHubSlice;
     const int64_t cnt = h.hub_used[hh];
     const int64_t p1 = h.hub_p1[hh];
     int32_t *Hk = h.tab_k + h.hub_tab[hh];
@@ -573,49 +658,94 @@ __global__ void __launch_bounds__(TPB) k_hub_clear(HubArgs h)
     }
 }
 
-__global__ void k_hub_move(HubArgs h, SweepArgs a)
+__global__ void k_hub_move(HArgs k)
 {
-    const int hh = blockIdx.x * blockDim.x + threadIdx.x;
-    if (hh >= h.n_hubs || !h.hub_act[hh]) return;
-    const int32_t v = h.hub_v[hh];
-    const int32_t cur = a.C[v];
-    int32_t cstar = -1;
-    const bool moved = decide(h.hub_best[hh], cur, a.pl, cstar);
-    const unsigned long long D = (unsigned long long)(a.off[v + 1] - a.off[v]);
-    unsigned long long *c = a.ctr + LPA_K_HUB_ACC * kCtrFields;
-    atomicAdd(c + CTR_ACTIVE, 1ull);
-    atomicAdd(c + CTR_EDGES, D);
-    if (moved) {
-        if (a.async_mode) {
-            a.C[v] = cstar;
-            __threadfence();
-        } else {
-            const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
-            a.mover_v[pos] = v;
-            a.mover_c[pos] = cstar;
+    if (*k.active == 0) return;
+    const WorkItem item = k.items[blockIdx.x];
+    const SweepView a = view_of(k.gd, item.g);
+    if (a.done) return;
+    const HubArgs &h = k.gd[item.g].hub;
+    unsigned long long n_act = 0, n_edges = 0, n_moved = 0, n_marks = 0;
+    for (int64_t hh = item.start + threadIdx.x; hh < item.start + item.count; hh += blockDim.x) {
+        if (!h.hub_act[hh]) continue;
+        const int32_t v = h.hub_v[hh];
+        const int32_t cur = a.C[v];
+        int32_t cstar = -1;
+        const bool moved = decide(h.hub_best[hh], cur, a.pl, cstar);
+        const unsigned long long D = (unsigned long long)(a.off[v + 1] - a.off[v]);
+        n_act += 1;
+        n_edges += D;
+        if (moved) {
+            if (a.async_mode) {
+                a.C[v] = cstar;
+                __threadfence();
+            } else {
+                const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
+                a.mover_v[pos] = v;
+                a.mover_c[pos] = cstar;
+            }
+            h.hub_act[hh] = 2;
+            n_moved += 1;
+            n_marks += D;
         }
-        h.hub_act[hh] = 2;
-        atomicAdd(c + CTR_MOVED, 1ull);
-        atomicAdd(c + CTR_MARKS, D);
     }
+    unsigned long long *c = a.ctr + LPA_K_HUB_ACC * kCtrFields;
+    if (n_act) atomicAdd(c + CTR_ACTIVE, n_act);
+    if (n_edges) atomicAdd(c + CTR_EDGES, n_edges);
+    if (n_moved) atomicAdd(c + CTR_MOVED, n_moved);
+    if (n_marks) atomicAdd(c + CTR_MARKS, n_marks);
 }
 
 template <int TPB>
-__global__ void __launch_bounds__(TPB) k_hub_mark(HubArgs h, SweepArgs a)
+__global__ void __launch_bounds__(TPB) k_hub_mark(HArgs k)
 {
-    const int hh = h.chunk_h[blockIdx.x];
-    if (h.hub_act[hh] != 2) return;
-    const int64_t e0 = h.chunk_e0[blockIdx.x], e1 = h.chunk_e1[blockIdx.x];
+    if (*k.active == 0) return;
+    const WorkItem item = k.items[blockIdx.x];
+    const SweepView a = view_of(k.gd, item.g);
+    if (a.done) return;
+    const HubArgs &h = k.gd[item.g].hub;
+    const int64_t c = item.start;
+    if (h.hub_act[h.chunk_h[c]] != 2) return;
+    const int64_t e0 = h.chunk_e0[c], e1 = h.chunk_e1[c];
     for (int64_t e = e0 + threadIdx.x; e < e1; e += TPB) a.flag_next[a.idx[e]] = 1;
 }
 
-// Synchronous mode: publish the labels recorded during the sweep.
-__global__ void k_apply(SweepArgs a)
+// Synchronous mode: publish the labels recorded during the sweep (a block per graph).
+__global__ void k_apply(HArgs k)
 {
+    if (*k.active == 0) return;
+    const WorkItem item = k.items[blockIdx.x];
+    const SweepView a = view_of(k.gd, item.g);
+    if (a.done || a.async_mode) return;
     const unsigned long long n = *a.mover_count;
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        a.C[a.mover_v[i]] = a.mover_c[i];
+    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) a.C[a.mover_v[i]] = a.mover_c[i];
+}
+
+// After each sweep, per graph: the stop test of Algorithm 1 (after a sweep without Pick-Less,
+// stop when dN / n < tolerance; stop at max_iters), then advance to the next sweep.
+__global__ void k_decide(const GraphDev *gd, int n_graphs, int32_t *active)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_graphs) return;
+    RunState *rs = gd[g].rs;
+    if (rs->done) return;
+    const SweepView a = view_of(gd, g);
+    long long dn = 0;
+    for (int q = 0; q < LPA_NUM_KERNELS; ++q) dn += (long long)a.ctr[q * kCtrFields + CTR_MOVED];
+    const int l = rs->l;
+    int done = 0, conv = 0;
+    if (!a.pl && (double)dn / (double)rs->n < rs->tol) {
+        done = 1;
+        conv = 1;
+    } else if (l + 1 >= rs->max_iters) {
+        done = 1;
+    }
+    rs->l = l + 1;
+    rs->last_dn = dn;
+    rs->done = done;
+    rs->converged = conv;
+    *gd[g].mover_count = 0ull;
+    if (!done) atomicAdd(active, 1);
 }
 
 __global__ void k_table_clear(int32_t *k, float *v, int64_t n)
@@ -649,6 +779,12 @@ size_t max_dynamic_smem()
     return g_max_smem;
 }
 
+int num_sms()
+{
+    query_device();
+    return g_num_sms;
+}
+
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes)
 {
@@ -668,140 +804,146 @@ static int64_t persistent_grid(K kernel, int threads, size_t smem, int64_t work_
 }
 
 template <int G, int TPB, typename V>
-static cudaError_t launch_gv(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
-                             cudaStream_t s)
+static cudaError_t launch_gv(const KArgs &k, cudaStream_t s)
 {
     constexpr int NG = TPB / G;
-    const size_t smem = (size_t)NG * slots * (sizeof(int32_t) + sizeof(V));
+    const size_t smem = (size_t)NG * k.slots * (sizeof(int32_t) + sizeof(V));
     cudaError_t e = set_smem(k_group<G, TPB, V>, smem);
     if (e != cudaSuccess) return e;
-    const int64_t need = (count + NG - 1) / NG;
-    const bool persist = (a.persist_mask >> kslot) & 1;   // else one pass: a block per NG vertices
-    const int64_t blocks = persist ? persistent_grid(k_group<G, TPB, V>, TPB, smem, need) : need;
-    k_group<G, TPB, V><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
+    const int64_t blocks = persistent_grid(k_group<G, TPB, V>, TPB, smem, ((int64_t)k.n_items + 7) / 8 * 8);
+    k_group<G, TPB, V><<<(unsigned)(blocks < 1 ? 1 : blocks), TPB, smem, s>>>(k);
     return cudaGetLastError();
 }
 
 template <int G, int TPB>
-static cudaError_t launch_g(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
-                            cudaStream_t s)
+static cudaError_t launch_g(const KArgs &k, bool int_w, cudaStream_t s)
 {
-    if (count <= 0) return cudaSuccess;
-    return a.int_weights ? launch_gv<G, TPB, uint32_t>(list, count, a, slots, kslot, s)
-                         : launch_gv<G, TPB, float>(list, count, a, slots, kslot, s);
-}
-
-cudaError_t launch_thread_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int slots,
-                                 cudaStream_t s)
-{
-    return launch_g<1, 128>(list, count, a, slots, LPA_K_THREAD, s);
-}
-
-cudaError_t launch_group_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int lanes, int slots,
-                                cudaStream_t s)
-{
-    switch (lanes) {
-    case 2: return launch_g<2, 256>(list, count, a, slots, LPA_K_GROUP, s);
-    case 4: return launch_g<4, 256>(list, count, a, slots, LPA_K_GROUP, s);
-    case 8: return launch_g<8, 256>(list, count, a, slots, LPA_K_GROUP, s);
-    case 16: return launch_g<16, 256>(list, count, a, slots, LPA_K_GROUP, s);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-cudaError_t launch_warp_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int slots,
-                               cudaStream_t s)
-{
-    return launch_g<32, 256>(list, count, a, slots, LPA_K_WARP, s);
+    return int_w ? launch_gv<G, TPB, uint32_t>(k, s) : launch_gv<G, TPB, float>(k, s);
 }
 
 template <int TPB, typename V>
-static cudaError_t launch_cv(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
-                             cudaStream_t s)
+static cudaError_t launch_cv(const KArgs &k, cudaStream_t s)
 {
-    const size_t smem = (size_t)slots * (sizeof(int32_t) + sizeof(V));
+    const size_t smem = (size_t)k.slots * (sizeof(int32_t) + sizeof(V));
     cudaError_t e = set_smem(k_cta<TPB, V>, smem);
     if (e != cudaSuccess) return e;
-    const bool persist = (a.persist_mask >> kslot) & 1;
-    const int64_t blocks = persist ? persistent_grid(k_cta<TPB, V>, TPB, smem, count) : count;
-    k_cta<TPB, V><<<(unsigned)blocks, TPB, smem, s>>>(list, count, a, slots, kslot);
+    const int64_t blocks = persistent_grid(k_cta<TPB, V>, TPB, smem, k.n_items);
+    k_cta<TPB, V><<<(unsigned)(blocks < 1 ? 1 : blocks), TPB, smem, s>>>(k);
     return cudaGetLastError();
 }
 
-template <int TPB>
-static cudaError_t launch_c(const int32_t *list, int64_t count, const SweepArgs &a, int slots, int kslot,
-                            cudaStream_t s)
-{
-    if (count <= 0) return cudaSuccess;
-    return a.int_weights ? launch_cv<TPB, uint32_t>(list, count, a, slots, kslot, s)
-                         : launch_cv<TPB, float>(list, count, a, slots, kslot, s);
-}
-
-cudaError_t launch_cta_bucket(const int32_t *list, int64_t count, const SweepArgs &a, int threads, int slots,
-                              int kslot, cudaStream_t s)
+static cudaError_t launch_cta(const KArgs &k, int threads, bool int_w, cudaStream_t s)
 {
     switch (threads) {
-    case 64: return launch_c<64>(list, count, a, slots, kslot, s);
-    case 128: return launch_c<128>(list, count, a, slots, kslot, s);
-    case 256: return launch_c<256>(list, count, a, slots, kslot, s);
-    case 512: return launch_c<512>(list, count, a, slots, kslot, s);
-    case 1024: return launch_c<1024>(list, count, a, slots, kslot, s);
+    case 64: return int_w ? launch_cv<64, uint32_t>(k, s) : launch_cv<64, float>(k, s);
+    case 128: return int_w ? launch_cv<128, uint32_t>(k, s) : launch_cv<128, float>(k, s);
+    case 256: return int_w ? launch_cv<256, uint32_t>(k, s) : launch_cv<256, float>(k, s);
+    case 512: return int_w ? launch_cv<512, uint32_t>(k, s) : launch_cv<512, float>(k, s);
+    case 1024: return int_w ? launch_cv<1024, uint32_t>(k, s) : launch_cv<1024, float>(k, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_hub_begin(const HubArgs &h, const SweepArgs &a, cudaStream_t s)
+static cudaError_t launch_vertex(const SweepPlan &p, int b, cudaStream_t s)
 {
-    if (h.n_hubs <= 0) return cudaSuccess;
-    k_hub_begin<<<(h.n_hubs + 255) / 256, 256, 0, s>>>(h, a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_hub_acc(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, int chunk, cudaStream_t s)
-{
-    if (n_chunks <= 0) return cudaSuccess;
-    const size_t smem = (size_t)chunk * sizeof(int32_t);
-    if (a.int_weights) {
-        cudaError_t e = set_smem(k_hub_acc<1024, uint32_t>, smem);
-        if (e != cudaSuccess) return e;
-        k_hub_acc<1024, uint32_t><<<(unsigned)n_chunks, 1024, smem, s>>>(h, a, chunk);
-    } else {
-        cudaError_t e = set_smem(k_hub_acc<1024, float>, smem);
-        if (e != cudaSuccess) return e;
-        k_hub_acc<1024, float><<<(unsigned)n_chunks, 1024, smem, s>>>(h, a, chunk);
+    KArgs k{};
+    k.gd = p.gd;
+    k.items = p.items[b];
+    k.n_items = p.n_items[b];
+    k.slots = p.slots[b];
+    k.queue = p.queues + b;
+    k.active = p.active_count;
+    k.kslot = b;                                       // bucket index == kernel slot
+    const bool iw = p.int_weights != 0;
+    switch (b) {
+    case B_THREAD: return launch_g<1, 128>(k, iw, s);
+    case B_GROUP:
+        switch (p.group_lanes) {
+        case 2: return launch_g<2, 256>(k, iw, s);
+        case 4: return launch_g<4, 256>(k, iw, s);
+        case 8: return launch_g<8, 256>(k, iw, s);
+        case 16: return launch_g<16, 256>(k, iw, s);
+        default: return cudaErrorInvalidValue;
+        }
+    case B_WARP: return launch_g<32, 256>(k, iw, s);
+    case B_CTA: return launch_cta(k, p.cta_threads, iw, s);
+    case B_CTA_LARGE: return launch_cta(k, p.cta_large_threads, iw, s);
+    case B_CTA_XL: return launch_cta(k, p.cta_xl_threads, iw, s);
+    default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
-cudaError_t launch_hub_clear(const HubArgs &h, int64_t n_slices, cudaStream_t s)
+cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, int *launches)
 {
-    if (n_slices <= 0) return cudaSuccess;
-    k_hub_clear<256><<<(unsigned)n_slices, 256, 0, s>>>(h);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_hub_move(const HubArgs &h, const SweepArgs &a, cudaStream_t s)
-{
-    if (h.n_hubs <= 0) return cudaSuccess;
-    k_hub_move<<<(h.n_hubs + 127) / 128, 128, 0, s>>>(h, a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_hub_mark(const HubArgs &h, const SweepArgs &a, int64_t n_chunks, cudaStream_t s)
-{
-    if (n_chunks <= 0) return cudaSuccess;
-    k_hub_mark<512><<<(unsigned)n_chunks, 512, 0, s>>>(h, a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_apply(const SweepArgs &a, int64_t n, cudaStream_t s)
-{
-    query_device();
-    int64_t blocks = (n + 255) / 256;
-    const int64_t cap = (int64_t)g_num_sms * 8;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_apply<<<(unsigned)blocks, 256, 0, s>>>(a);
+    cudaError_t e = cudaMemsetAsync(p.queues, 0, sizeof(unsigned) * B_COUNT, s);
+    if (e != cudaSuccess) return e;
+    auto timed = [&](int slot, auto &&fn) -> cudaError_t {
+        if (hook) hook->before(slot);
+        cudaError_t r = fn();
+        if (hook) hook->after(slot);
+        if (launches) ++*launches;
+        return r;
+    };
+    for (int b = B_THREAD; b <= B_CTA_XL; ++b) {
+        if (p.n_items[b] <= 0) continue;
+        e = timed(b, [&] { return launch_vertex(p, b, s); });
+        if (e != cudaSuccess) return e;
+    }
+    HArgs h{};
+    h.gd = p.gd;
+    h.active = p.active_count;
+    h.chunk = p.hub_chunk;
+    if (p.n_hub_hubs > 0) {
+        h.items = p.hub_hubs;
+        e = timed(LPA_K_HUB_BEGIN, [&] {
+            k_hub_begin<<<p.n_hub_hubs, 256, 0, s>>>(h);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+        h.items = p.hub_chunks;
+        e = timed(LPA_K_HUB_ACC, [&] {
+            const size_t smem = (size_t)p.hub_chunk * sizeof(int32_t);
+            if (p.int_weights) {
+                cudaError_t r = set_smem(k_hub_acc<1024, uint32_t>, smem);
+                if (r != cudaSuccess) return r;
+                k_hub_acc<1024, uint32_t><<<p.n_hub_chunks, 1024, smem, s>>>(h);
+            } else {
+                cudaError_t r = set_smem(k_hub_acc<1024, float>, smem);
+                if (r != cudaSuccess) return r;
+                k_hub_acc<1024, float><<<p.n_hub_chunks, 1024, smem, s>>>(h);
+            }
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+        h.items = p.hub_slices;
+        e = timed(LPA_K_HUB_CLEAR, [&] {
+            k_hub_clear<256><<<p.n_hub_slices, 256, 0, s>>>(h);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+        h.items = p.hub_hubs;
+        e = timed(LPA_K_HUB_MOVE, [&] {
+            k_hub_move<<<p.n_hub_hubs, 128, 0, s>>>(h);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+        h.items = p.hub_chunks;
+        e = timed(LPA_K_HUB_MARK, [&] {
+            k_hub_mark<512><<<p.n_hub_chunks, 512, 0, s>>>(h);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+    }
+    h.items = p.per_graph;
+    e = timed(LPA_K_APPLY, [&] {
+        k_apply<<<p.n_graphs, 256, 0, s>>>(h);
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p.active_count, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    k_decide<<<(p.n_graphs + 127) / 128, 128, 0, s>>>(p.gd, p.n_graphs, p.active_count);
+    if (launches) ++*launches;
     return cudaGetLastError();
 }
 
