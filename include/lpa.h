@@ -203,6 +203,92 @@ const char *lpa_strerror(int status);
 const char *lpa_last_error(void);
 const char *lpa_kernel_name(int slot);
 
+/* ---- batches: many independent graphs solved together -------------------------------- */
+
+/* One input graph of a batch or a server request: same conventions as lpa_create. */
+typedef struct lpa_graph_desc {
+    const void *offsets;       /* int32_t or int64_t [n_vertices + 1] (per flags)          */
+    const int32_t *indices;    /* [n_entries]                                               */
+    const float *weights;      /* [n_entries] or NULL (unit weights)                        */
+    int64_t n_vertices;
+    int64_t n_entries;
+} lpa_graph_desc;
+
+/* Outcome of one graph's run in a batch or a server request. */
+typedef struct lpa_result {
+    int32_t iterations;        /* sweeps run                                                */
+    int32_t converged;         /* 1 when the tolerance test ended the run                   */
+    int64_t last_changed;      /* dN of the last sweep                                      */
+} lpa_result;
+
+typedef struct lpa_batch lpa_batch;
+
+/* Copies n_graphs independent graphs to the device (one memory arena for all of them) and
+ * prepares one combined launch plan: every sweep kernel covers the vertices of every graph,
+ * so thousands of small graphs cost the launches of one.  Each graph keeps its own run state
+ * (sweep index, Pick-Less phase, changed count, stop decision), so results are the same as
+ * running each graph alone with lpa_run.  1 <= n_graphs <= 65535; flags as lpa_create
+ * (offset width and host/device pointers apply to every graph).  Errors as lpa_create. */
+int lpa_batch_create(int n_graphs, const lpa_graph_desc *descs, int flags, void *cuda_stream, lpa_batch **out);
+
+/* Runs every graph of the batch from fresh labels (Algorithm 1 for each graph, same
+ * tolerance, cap, Pick-Less period and mode).  The max_iters sweeps are recorded once into a
+ * CUDA graph and replayed; graphs that stop early do no further work.
+ *  results   optional, [n_graphs]; device_ms optional (device time of the run). */
+int lpa_batch_run(lpa_batch *b, double tolerance, int max_iters, int pl_period, int mode, lpa_result *results,
+                  float *device_ms);
+
+/* Labels of graph `graph` (its own vertex ids), n = its n_vertices; host or device out. */
+int lpa_batch_labels(const lpa_batch *b, int graph, int32_t *out, int64_t n, int out_on_device);
+
+/* Modularity of every graph, q [n_graphs]. */
+int lpa_batch_modularity(lpa_batch *b, double *q);
+
+/* A borrowed handle of graph `graph` (valid until lpa_batch_destroy; do not destroy it): its
+ * lpa_run solves that graph alone on the same device data. */
+int lpa_batch_graph(lpa_batch *b, int graph, lpa_graph **out);
+
+int lpa_batch_size(const lpa_batch *b);
+int64_t lpa_batch_device_bytes(const lpa_batch *b);
+void lpa_batch_destroy(lpa_batch *b);
+
+/* ---- server: continuous batching of label-propagation requests ----------------------- */
+
+typedef struct lpa_server lpa_server;
+
+/* A request server on the current device.  Resident requests live in one device arena of
+ * hbm_budget_bytes; a request is admitted when its graph fits in the arena (and fewer than
+ * max_resident requests are running), in arrival order, later requests passing one that does
+ * not fit yet.  Each lpa_server_step admits what fits, runs one sweep of every running request
+ * in the same kernel launches (each request at its own sweep index), and retires the requests
+ * whose run stopped. */
+int lpa_server_create(size_t hbm_budget_bytes, int max_resident, void *cuda_stream, lpa_server **out);
+
+/* Queues a request: the graph (host arrays, copied at submission, flags: offset width) and its
+ * run parameters (as lpa_run; mode LPA_SYNC or LPA_ASYNC).  *request_id receives its id.
+ * LPA_EINVAL when the graph alone can never fit the budget. */
+int lpa_server_submit(lpa_server *s, const lpa_graph_desc *graph, int flags, double tolerance, int max_iters,
+                      int pl_period, int mode, int64_t *request_id);
+
+/* One scheduling step (admission, one sweep of every running request, retirement).
+ * *n_running and *n_queued (optional) report the state after the step; *n_completed (optional)
+ * the requests that finished in this step. */
+int lpa_server_step(lpa_server *s, int *n_completed, int *n_running, int *n_queued);
+
+/* Ids of finished requests not yet collected (at most max_ids); *n receives how many. */
+int lpa_server_poll(lpa_server *s, int64_t *ids, int max_ids, int *n);
+
+/* Collects a finished request: labels [n] (host), its result, and its timeline in seconds
+ * on the server's clock (submitted, admitted, finished; each may be NULL).  The request is
+ * forgotten afterwards.  LPA_ESTATE when the request has not finished. */
+int lpa_server_result(lpa_server *s, int64_t request_id, int32_t *labels, int64_t n, lpa_result *result,
+                      double *t_submit, double *t_admit, double *t_finish);
+
+/* Seconds on the server's clock (the clock of the timelines above). */
+double lpa_server_clock(const lpa_server *s);
+int64_t lpa_server_device_bytes(const lpa_server *s);
+void lpa_server_destroy(lpa_server *s);
+
 /* ---- modularity without device allocation ------------------------------------------ */
 
 /* Largest n_vertices accepted by lpa_modularity_noalloc. */

@@ -459,70 +459,106 @@ uint32_t capacity_bits(int64_t x)
 
 namespace lpa {
 
-Arena::Arena(size_t bytes)
+Arena::Arena(size_t bytes, bool grow, size_t grow_chunk) : grow_(grow), grow_chunk_(grow_chunk)
 {
-    void *p = nullptr;
-    if (bytes == 0 || cudaMalloc(&p, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-    }
-    base_ = static_cast<unsigned char *>(p);
-    cap_ = bytes;
-    free_.push_back({0, bytes});
+    if (bytes > 0) add_region(bytes);
 }
 
 Arena::~Arena()
 {
-    if (base_) cudaFree(base_);
+    for (Region &r : regions_)
+        if (r.base) cudaFree(r.base);
 }
 
-void *Arena::alloc(size_t bytes)
+bool Arena::add_region(size_t bytes)
 {
-    if (!base_) return nullptr;
-    bytes = (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
-    for (size_t i = 0; i < free_.size(); ++i) {
-        if (free_[i].size < bytes) continue;
-        const size_t off = free_[i].off;
-        free_[i].off += bytes;
-        free_[i].size -= bytes;
-        if (free_[i].size == 0) free_.erase(free_.begin() + (long)i);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    Region r;
+    r.base = static_cast<unsigned char *>(p);
+    r.cap = bytes;
+    r.free_.push_back({0, bytes});
+    regions_.push_back(std::move(r));
+    return true;
+}
+
+void *Arena::region_alloc(Region &r, size_t bytes)
+{
+    for (size_t i = 0; i < r.free_.size(); ++i) {
+        if (r.free_[i].size < bytes) continue;
+        const size_t off = r.free_[i].off;
+        r.free_[i].off += bytes;
+        r.free_[i].size -= bytes;
+        if (r.free_[i].size == 0) r.free_.erase(r.free_.begin() + (long)i);
         const Block b{off, bytes};
-        auto it = std::lower_bound(taken_.begin(), taken_.end(), b,
+        auto it = std::lower_bound(r.taken_.begin(), r.taken_.end(), b,
                                    [](const Block &x, const Block &y) { return x.off < y.off; });
-        taken_.insert(it, b);
-        used_ += bytes;
-        return base_ + off;
+        r.taken_.insert(it, b);
+        r.used += bytes;
+        return r.base + off;
     }
     return nullptr;
 }
 
+void *Arena::alloc(size_t bytes)
+{
+    bytes = (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+    for (Region &r : regions_)
+        if (void *p = region_alloc(r, bytes)) return p;
+    if (!grow_ || !add_region(std::max(bytes, grow_chunk_))) return nullptr;
+    return region_alloc(regions_.back(), bytes);
+}
+
 void Arena::free(void *p)
 {
-    if (!p || !base_) return;
-    const size_t off = static_cast<size_t>(static_cast<unsigned char *>(p) - base_);
-    auto it = std::lower_bound(taken_.begin(), taken_.end(), Block{off, 0},
-                               [](const Block &x, const Block &y) { return x.off < y.off; });
-    if (it == taken_.end() || it->off != off) return;
-    Block b = *it;
-    taken_.erase(it);
-    used_ -= b.size;
-    auto f = std::lower_bound(free_.begin(), free_.end(), b,
-                              [](const Block &x, const Block &y) { return x.off < y.off; });
-    f = free_.insert(f, b);
-    if (f + 1 != free_.end() && f->off + f->size == (f + 1)->off) {   // merge with the next block
-        f->size += (f + 1)->size;
-        free_.erase(f + 1);
+    if (!p) return;
+    unsigned char *q = static_cast<unsigned char *>(p);
+    for (Region &r : regions_) {
+        if (q < r.base || q >= r.base + r.cap) continue;
+        const size_t off = (size_t)(q - r.base);
+        auto it = std::lower_bound(r.taken_.begin(), r.taken_.end(), Block{off, 0},
+                                   [](const Block &x, const Block &y) { return x.off < y.off; });
+        if (it == r.taken_.end() || it->off != off) return;
+        Block b = *it;
+        r.taken_.erase(it);
+        r.used -= b.size;
+        auto f = std::lower_bound(r.free_.begin(), r.free_.end(), b,
+                                  [](const Block &x, const Block &y) { return x.off < y.off; });
+        f = r.free_.insert(f, b);
+        if (f + 1 != r.free_.end() && f->off + f->size == (f + 1)->off) {   // merge with the next block
+            f->size += (f + 1)->size;
+            r.free_.erase(f + 1);
+        }
+        if (f != r.free_.begin() && (f - 1)->off + (f - 1)->size == f->off) {   // and with the previous one
+            (f - 1)->size += f->size;
+            r.free_.erase(f);
+        }
+        return;
     }
-    if (f != free_.begin() && (f - 1)->off + (f - 1)->size == f->off) {   // merge with the previous one
-        (f - 1)->size += f->size;
-        free_.erase(f);
-    }
+}
+
+size_t Arena::capacity() const
+{
+    size_t c = 0;
+    for (const Region &r : regions_) c += r.cap;
+    return c;
+}
+
+size_t Arena::used() const
+{
+    size_t u = 0;
+    for (const Region &r : regions_) u += r.used;
+    return u;
 }
 
 size_t Arena::largest_free() const
 {
     size_t m = 0;
-    for (const Block &b : free_) m = std::max(m, b.size);
+    for (const Region &r : regions_)
+        for (const Block &b : r.free_) m = std::max(m, b.size);
     return m;
 }
 
@@ -821,7 +857,7 @@ int build_buckets(lpa_graph *g)
         ha.n_hubs = (int32_t)H;
         ha.n_chunks = (int32_t)n_chunks;
         ha.n_slices = (int32_t)n_slices;
-        g->hub_hubs_h.push_back(WorkItem{0, 0, 0, H});
+        for (int64_t h0 = 0; h0 < H; h0 += 256) g->hub_hubs_h.push_back(WorkItem{0, 0, h0, std::min<int64_t>(256, H - h0)});
         for (int64_t c = 0; c < n_chunks; ++c) g->hub_chunks_h.push_back(WorkItem{0, 0, c, 1});
         for (int64_t j = 0; j < n_slices; ++j) g->hub_slices_h.push_back(WorkItem{0, 0, j, 1});
     }

@@ -127,29 +127,36 @@ cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, cudaStre
 size_t max_dynamic_smem();
 int num_sms();
 
-// Device memory arena: one reservation carved into 256-byte aligned blocks (first fit with
+// Device memory arena: reservations carved into 256-byte aligned blocks (first fit with a
 // coalescing free list).  Batches and the server allocate their graphs from it, so thousands
-// of graphs do not each cost a dozen cudaMalloc calls and admission can be decided by
-// footprint.
+// of graphs do not each cost a dozen cudaMalloc calls, and a fixed arena turns admission by
+// footprint into "the allocation fits".  A growing arena adds reservations on demand.
 class Arena {
   public:
-    explicit Arena(size_t bytes);
+    Arena(size_t bytes, bool grow, size_t grow_chunk = (size_t)1 << 30);
     ~Arena();
-    bool ok() const { return base_ != nullptr; }
+    bool ok() const { return !regions_.empty(); }
     void *alloc(size_t bytes);
     void free(void *p);
-    size_t capacity() const { return cap_; }
-    size_t used() const { return used_; }
+    size_t capacity() const;
+    size_t used() const;
     size_t largest_free() const;
 
   private:
     struct Block {
         size_t off, size;
     };
-    unsigned char *base_ = nullptr;
-    size_t cap_ = 0, used_ = 0;
-    std::vector<Block> free_;        // sorted by offset, coalesced
-    std::vector<Block> taken_;       // sorted by offset
+    struct Region {
+        unsigned char *base = nullptr;
+        size_t cap = 0, used = 0;
+        std::vector<Block> free_;        // sorted by offset, coalesced
+        std::vector<Block> taken_;       // sorted by offset
+    };
+    bool add_region(size_t bytes);
+    static void *region_alloc(Region &r, size_t bytes);
+    std::vector<Region> regions_;
+    bool grow_ = false;
+    size_t grow_chunk_ = 0;
 };
 
 // Thread-local error message.

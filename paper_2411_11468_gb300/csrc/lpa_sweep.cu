@@ -710,15 +710,18 @@ __global__ void __launch_bounds__(TPB) k_hub_mark(HArgs k)
     for (int64_t e = e0 + threadIdx.x; e < e1; e += TPB) a.flag_next[a.idx[e]] = 1;
 }
 
-// Synchronous mode: publish the labels recorded during the sweep (a block per graph).
+// Synchronous mode: publish the labels recorded during the sweep (blockIdx.y: graph,
+// blockIdx.x: stride over its movers).
 __global__ void k_apply(HArgs k)
 {
     if (*k.active == 0) return;
-    const WorkItem item = k.items[blockIdx.x];
+    const WorkItem item = k.items[blockIdx.y];
     const SweepView a = view_of(k.gd, item.g);
     if (a.done || a.async_mode) return;
     const unsigned long long n = *a.mover_count;
-    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) a.C[a.mover_v[i]] = a.mover_c[i];
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        a.C[a.mover_v[i]] = a.mover_c[i];
 }
 
 // After each sweep, per graph: the stop test of Algorithm 1 (after a sweep without Pick-Less,
@@ -936,7 +939,8 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
     }
     h.items = p.per_graph;
     e = timed(LPA_K_APPLY, [&] {
-        k_apply<<<p.n_graphs, 256, 0, s>>>(h);
+        const unsigned bx = p.n_graphs == 1 ? (unsigned)(num_sms() * 4) : 8u;
+        k_apply<<<dim3(bx, (unsigned)p.n_graphs), 256, 0, s>>>(h);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;

@@ -32,7 +32,10 @@ KERNEL_NAMES = ["thread", "group", "warp", "cta", "cta_large", "cta_xl", "hub_be
 SYMBOLS = ["lpa_create", "lpa_run", "lpa_labels", "lpa_modularity", "lpa_set_labels", "lpa_get_state",
            "lpa_set_state", "lpa_set_stream", "lpa_get_tuning", "lpa_set_tuning", "lpa_num_vertices",
            "lpa_num_entries", "lpa_device_bytes", "lpa_destroy", "lpa_strerror", "lpa_last_error",
-           "lpa_kernel_name", "lpa_struct_size"]
+           "lpa_kernel_name", "lpa_struct_size", "lpa_batch_create", "lpa_batch_run", "lpa_batch_labels",
+           "lpa_batch_modularity", "lpa_batch_graph", "lpa_batch_size", "lpa_batch_device_bytes", "lpa_batch_destroy",
+           "lpa_server_create", "lpa_server_submit", "lpa_server_step", "lpa_server_poll", "lpa_server_result",
+           "lpa_server_clock", "lpa_server_device_bytes", "lpa_server_destroy"]
 
 
 class LpaError(RuntimeError):
@@ -273,3 +276,198 @@ class Graph:
 
     def device_bytes(self) -> int:
         return int(load().lpa_device_bytes(self._h))
+
+
+# ----------------------------------------------------------------------------------------
+# batches and the request server
+
+class GraphDesc(ct.Structure):
+    _fields_ = [("offsets", ct.c_void_p), ("indices", ct.c_void_p), ("weights", ct.c_void_p),
+                ("n_vertices", ct.c_int64), ("n_entries", ct.c_int64)]
+
+
+class Result(ct.Structure):
+    _fields_ = [("iterations", ct.c_int32), ("converged", ct.c_int32), ("last_changed", ct.c_int64)]
+
+    def to_dict(self):
+        return dict(iterations=self.iterations, converged=bool(self.converged), last_changed=self.last_changed)
+
+
+_multi_ready = False
+
+
+def _load_multi():
+    global _multi_ready
+    L = load()
+    if _multi_ready:
+        return L
+    P, i32, i64 = ct.c_void_p, ct.c_int, ct.c_int64
+    L.lpa_batch_create.argtypes = [i32, ct.POINTER(GraphDesc), i32, P, ct.POINTER(P)]
+    L.lpa_batch_run.argtypes = [P, ct.c_double, i32, i32, i32, ct.POINTER(Result), ct.POINTER(ct.c_float)]
+    L.lpa_batch_labels.argtypes = [P, i32, P, i64, i32]
+    L.lpa_batch_modularity.argtypes = [P, ct.POINTER(ct.c_double)]
+    L.lpa_batch_graph.argtypes = [P, i32, ct.POINTER(P)]
+    L.lpa_batch_size.argtypes = [P]
+    L.lpa_batch_device_bytes.argtypes = [P]
+    L.lpa_batch_device_bytes.restype = i64
+    L.lpa_batch_destroy.argtypes = [P]
+    L.lpa_batch_destroy.restype = None
+    L.lpa_server_create.argtypes = [ct.c_size_t, i32, P, ct.POINTER(P)]
+    L.lpa_server_submit.argtypes = [P, ct.POINTER(GraphDesc), i32, ct.c_double, i32, i32, i32, ct.POINTER(ct.c_int64)]
+    L.lpa_server_step.argtypes = [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
+    L.lpa_server_poll.argtypes = [P, ct.POINTER(ct.c_int64), i32, ct.POINTER(ct.c_int)]
+    L.lpa_server_result.argtypes = [P, i64, P, i64, ct.POINTER(Result), ct.POINTER(ct.c_double),
+                                    ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
+    L.lpa_server_clock.argtypes = [P]
+    L.lpa_server_clock.restype = ct.c_double
+    L.lpa_server_device_bytes.argtypes = [P]
+    L.lpa_server_device_bytes.restype = i64
+    L.lpa_server_destroy.argtypes = [P]
+    L.lpa_server_destroy.restype = None
+    _multi_ready = True
+    return L
+
+
+def _desc(offsets, indices, weights):
+    return GraphDesc(offsets.data_ptr(), indices.data_ptr(), None if weights is None else weights.data_ptr(),
+                     offsets.numel() - 1, indices.numel())
+
+
+class _Borrowed(Graph):
+    """A graph handle owned by a batch (not destroyed by this object)."""
+
+    def __init__(self, handle, n, m, device):
+        self._h = handle
+        self.n, self.m, self.device = n, m, device
+
+    def close(self):
+        self._h = ct.c_void_p()
+
+
+class Batch:
+    """Many independent CSR graphs on the device, solved together (lpa_batch_*).
+
+    graphs: list of (offsets, indices, weights) tensors, all on the host or all on the device,
+    all offsets of one dtype (int32 or int64)."""
+
+    def __init__(self, graphs, stream=None):
+        L = _load_multi()
+        self._keep = [tuple(t.contiguous() if t is not None else None for t in g) for g in graphs]
+        if not self._keep:
+            raise ValueError("empty batch")
+        o0 = self._keep[0][0]
+        flags = (OFFSETS_I64 if o0.dtype == torch.int64 else OFFSETS_I32) | (DEVICE_PTRS if o0.is_cuda else HOST_PTRS)
+        descs = (GraphDesc * len(self._keep))(*[_desc(*g) for g in self._keep])
+        self.sizes = [(g[0].numel() - 1, g[1].numel()) for g in self._keep]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        h = ct.c_void_p()
+        _check(L.lpa_batch_create(len(self._keep), descs, flags, ct.c_void_p(stream.cuda_stream), ct.byref(h)),
+               "lpa_batch_create")
+        self._h = h
+        if not o0.is_cuda:
+            self._keep = None
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def run(self, tolerance=0.05, max_iters=20, pl_period=4, mode=SYNC):
+        res = (Result * len(self))()
+        ms = ct.c_float()
+        _check(_load_multi().lpa_batch_run(self._h, float(tolerance), int(max_iters), int(pl_period), int(mode),
+                                           res, ct.byref(ms)), "lpa_batch_run")
+        return [r.to_dict() for r in res], ms.value
+
+    def labels(self, i, out=None):
+        n = self.sizes[i][0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=self.device)
+        _check(_load_multi().lpa_batch_labels(self._h, i, _ptr(out), n, 1 if out.is_cuda else 0), "lpa_batch_labels")
+        return out
+
+    def modularity(self):
+        q = (ct.c_double * len(self))()
+        _check(_load_multi().lpa_batch_modularity(self._h, q), "lpa_batch_modularity")
+        return list(q)
+
+    def graph(self, i) -> Graph:
+        """Borrowed handle of graph i (lpa_run solves it alone on the same device data)."""
+        h = ct.c_void_p()
+        _check(_load_multi().lpa_batch_graph(self._h, i, ct.byref(h)), "lpa_batch_graph")
+        return _Borrowed(h, self.sizes[i][0], self.sizes[i][1], self.device)
+
+    def device_bytes(self):
+        return int(_load_multi().lpa_batch_device_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _load_multi().lpa_batch_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (lpa_server_*): submit host CSR graphs, call step()
+    repeatedly, collect finished requests."""
+
+    def __init__(self, hbm_budget_bytes, max_resident=256):
+        L = _load_multi()
+        h = ct.c_void_p()
+        _check(L.lpa_server_create(int(hbm_budget_bytes), int(max_resident), None, ct.byref(h)), "lpa_server_create")
+        self._h = h
+        self._sizes = {}
+
+    def submit(self, offsets, indices, weights=None, tolerance=0.05, max_iters=20, pl_period=4, mode=SYNC) -> int:
+        offsets = offsets.contiguous().cpu()
+        indices = indices.contiguous().cpu()
+        weights = None if weights is None else weights.contiguous().cpu()
+        flags = OFFSETS_I64 if offsets.dtype == torch.int64 else OFFSETS_I32
+        d = _desc(offsets, indices, weights)
+        rid = ct.c_int64()
+        _check(_load_multi().lpa_server_submit(self._h, ct.byref(d), flags, float(tolerance), int(max_iters),
+                                               int(pl_period), int(mode), ct.byref(rid)), "lpa_server_submit")
+        self._sizes[rid.value] = offsets.numel() - 1
+        return rid.value
+
+    def step(self):
+        c, r, q = ct.c_int(), ct.c_int(), ct.c_int()
+        _check(_load_multi().lpa_server_step(self._h, ct.byref(c), ct.byref(r), ct.byref(q)), "lpa_server_step")
+        return c.value, r.value, q.value
+
+    def poll(self, max_ids=4096):
+        ids = (ct.c_int64 * max_ids)()
+        n = ct.c_int()
+        _check(_load_multi().lpa_server_poll(self._h, ids, max_ids, ct.byref(n)), "lpa_server_poll")
+        return [ids[i] for i in range(n.value)]
+
+    def result(self, rid):
+        n = self._sizes.pop(rid)
+        lab = torch.empty(n, dtype=torch.int32)
+        res = Result()
+        ts, ta, tf = ct.c_double(), ct.c_double(), ct.c_double()
+        _check(_load_multi().lpa_server_result(self._h, rid, _ptr(lab), n, ct.byref(res), ct.byref(ts), ct.byref(ta),
+                                               ct.byref(tf)), "lpa_server_result")
+        return lab, res.to_dict(), (ts.value, ta.value, tf.value)
+
+    def clock(self):
+        return float(_load_multi().lpa_server_clock(self._h))
+
+    def device_bytes(self):
+        return int(_load_multi().lpa_server_device_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _load_multi().lpa_server_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

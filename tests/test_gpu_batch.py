@@ -1,0 +1,190 @@
+"""Batches (many graphs in shared launches) and the continuous-batching server, through the
+C ABI, against the CPU oracle and against each graph run alone.
+
+Synchronous mode is deterministic, so every graph of a batch and every server request must
+give the oracle's labels bit for bit, and the same labels as a run of that graph alone; the
+asynchronous mode is checked with the same bounds as single graphs."""
+import random
+
+import pytest
+import torch
+
+import oracle
+from paper_2411_11468_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lpa():
+    from paper_2411_11468_gb300 import build
+    build.build()
+    from paper_2411_11468_gb300 import lpa as L
+    L.load()
+    return L
+
+
+def mixed_graphs(seed=0, count=24, with_hub=True):
+    """Graphs of uneven sizes and degree profiles (SBM of the batched recipe, R-MAT, fixtures),
+    including a hub above every shared-memory bucket and an edgeless graph."""
+    rnd = random.Random(seed)
+    out = []
+    specs = gg.batch_specs(count, seed=seed, n_hi=3000)
+    for k in range(count):
+        pick = k % 4
+        if pick == 0:
+            out.append(gg.batch_graph(specs[k], weights="int8"))
+        elif pick == 1:
+            out.append(gg.rmat(rnd.choice([9, 10, 11, 12]), weights="int8"))
+        elif pick == 2:
+            out.append(gg.sbm(rnd.randint(200, 3000), rnd.choice([20, 50, 100]), 10.0, 2.0, seed=100 + k))
+        else:
+            out.append(gg.cliques(rnd.randint(2, 6), rnd.randint(3, 9)))
+    if with_hub:
+        out.append(gg.star(20_000))
+    out.append(gg.from_edges(5, []))
+    return out
+
+
+def as_tuple(csr, device="cuda"):
+    return (csr.offsets.to(device), csr.indices.to(device), None if csr.weights is None else csr.weights.to(device))
+
+
+def test_batch_sync_equals_oracle_and_single_runs(lpa):
+    graphs = mixed_graphs(1)
+    b = lpa.Batch([as_tuple(g) for g in graphs])
+    results, ms = b.run(0.05, 20, 4, lpa.SYNC)
+    assert ms > 0
+    for i, g in enumerate(graphs):
+        ref = oracle.lpa_sync(oracle.Graph.of(g), 0.05, 20, 4)
+        assert b.labels(i).cpu().numpy().tolist() == ref.labels.tolist(), f"graph {i}"
+        assert results[i]["iterations"] == ref.iterations, f"graph {i}"
+        assert results[i]["converged"] == ref.converged
+        if ref.dN:
+            assert results[i]["last_changed"] == ref.dN[-1]
+    # the same graphs solved one at a time through their borrowed handles
+    for i in range(len(graphs)):
+        h = b.graph(i)
+        st = h.run(0.05, 20, 4, lpa.SYNC)
+        assert st.iterations == results[i]["iterations"]
+        assert torch.equal(h.labels().cpu(), b.labels(i).cpu())
+    # replaying the recorded sweeps gives the same labels again
+    labels0 = [b.labels(i).cpu().clone() for i in range(len(graphs))]
+    results2, _ = b.run(0.05, 20, 4, lpa.SYNC)
+    assert results2 == results
+    assert all(torch.equal(labels0[i], b.labels(i).cpu()) for i in range(len(graphs)))
+
+
+def test_batch_modularity_and_other_parameters(lpa):
+    graphs = mixed_graphs(2, count=12, with_hub=False)
+    b = lpa.Batch([as_tuple(g) for g in graphs])
+    b.run(0.0, 7, 3, lpa.SYNC)
+    q = b.modularity()
+    for i, g in enumerate(graphs):
+        og = oracle.Graph.of(g)
+        ref = oracle.lpa_sync(og, 0.0, 7, 3)
+        lab = b.labels(i).cpu()
+        assert lab.numpy().tolist() == ref.labels.tolist()
+        assert abs(q[i] - oracle.modularity(og, lab)) < 1e-12
+
+
+def test_batch_from_host_arrays(lpa):
+    graphs = mixed_graphs(3, count=8, with_hub=False)
+    b = lpa.Batch([as_tuple(g, "cpu") for g in graphs])
+    b.run()
+    for i, g in enumerate(graphs):
+        ref = oracle.lpa_sync(oracle.Graph.of(g))
+        assert b.labels(i).cpu().numpy().tolist() == ref.labels.tolist()
+
+
+def test_batch_async_bounds(lpa):
+    graphs = [gg.sbm(3000, 60, 12.0, 2.0, seed=s, weights="int8") for s in range(4)] + \
+             [gg.rmat(11 + s % 2, weights="int8") for s in range(4)]
+    b = lpa.Batch([as_tuple(g) for g in graphs])
+    b.run(0.05, 20, 4, lpa.ASYNC)
+    for i, g in enumerate(graphs):
+        og = oracle.Graph.of(g)
+        lab = b.labels(i).cpu()
+        q = oracle.modularity(og, lab)
+        q_ref = oracle.modularity(og, oracle.lpa_async(og, 0.05, 20, 4).labels)
+        assert q >= q_ref - 0.005, (i, q, q_ref)
+        assert oracle.violations(og, lab) / og.n <= 0.05
+
+
+def drain(server, limit=10_000):
+    done = {}
+    for _ in range(limit):
+        c, running, queued = server.step()
+        for rid in server.poll():
+            done[rid] = server.result(rid)
+        if running == 0 and queued == 0:
+            break
+    return done
+
+
+def test_server_results_equal_alone_and_in_the_mix(lpa):
+    graphs = mixed_graphs(4, count=16)
+    params = [(0.05, 20, 4), (0.0, 9, 4), (0.05, 20, 0), (0.1, 20, 2)]
+    # all requests in one server: they join and leave the shared sweeps at different times
+    srv = lpa.Server(1 << 30, max_resident=8)
+    ids = {}
+    for i, g in enumerate(graphs):
+        tol, mi, pl = params[i % len(params)]
+        ids[srv.submit(g.offsets, g.indices, g.weights, tol, mi, pl, lpa.SYNC)] = i
+        if i % 3 == 2:
+            srv.step()                     # requests arrive while others run
+    done = drain(srv)
+    assert sorted(done) == sorted(ids)
+    for rid, i in ids.items():
+        lab, res, (ts, ta, tf) = done[rid]
+        tol, mi, pl = params[i % len(params)]
+        ref = oracle.lpa_sync(oracle.Graph.of(graphs[i]), tol, mi, pl)
+        assert lab.numpy().tolist() == ref.labels.tolist(), f"request {i}"
+        assert res["iterations"] == ref.iterations
+        assert ts <= ta <= tf
+        # alone: a fresh server with this request only
+        solo = lpa.Server(1 << 28, max_resident=1)
+        sid = solo.submit(graphs[i].offsets, graphs[i].indices, graphs[i].weights, tol, mi, pl, lpa.SYNC)
+        lab2, res2, _ = drain(solo)[sid]
+        assert torch.equal(lab, lab2) and res2 == res
+        solo.close()
+    srv.close()
+
+
+def test_server_admission_by_footprint(lpa):
+    """A budget that holds about two of the graphs at a time: requests wait in the queue and
+    are admitted as memory frees up; results are unchanged."""
+    graphs = [gg.rmat(12, weights="int8") for _ in range(6)]
+    one = 2 * (graphs[0].n + 1) * 8 + graphs[0].m * 8 + graphs[0].n * 40
+    srv = lpa.Server(int(2.5 * one) + (4 << 20), max_resident=16)
+    ids = [srv.submit(g.offsets, g.indices, g.weights) for g in graphs]
+    c, running, queued = srv.step()
+    assert queued > 0                      # not everything fits at once
+    done = drain(srv)
+    ref = oracle.lpa_sync(oracle.Graph.of(graphs[0]))
+    for rid in ids:
+        assert done[rid][0].numpy().tolist() == ref.labels.tolist()
+    srv.close()
+
+
+def test_server_rejects_graph_that_never_fits(lpa):
+    srv = lpa.Server(1 << 20, max_resident=4)
+    g = gg.rmat(14, weights="int8")
+    with pytest.raises(lpa.LpaError):
+        srv.submit(g.offsets, g.indices, g.weights)
+    srv.close()
+
+
+def test_server_async_requests(lpa):
+    graphs = [gg.sbm(2000, 40, 10.0, 2.0, seed=s, weights="int8") for s in range(5)]
+    srv = lpa.Server(1 << 28, max_resident=3)
+    ids = {srv.submit(g.offsets, g.indices, g.weights, 0.05, 20, 4, lpa.ASYNC): i for i, g in enumerate(graphs)}
+    done = drain(srv)
+    for rid, i in ids.items():
+        og = oracle.Graph.of(graphs[i])
+        lab = done[rid][0]
+        q = oracle.modularity(og, lab)
+        q_ref = oracle.modularity(og, oracle.lpa_async(og, 0.05, 20, 4).labels)
+        assert q >= q_ref - 0.005
+        assert oracle.violations(og, lab) / og.n <= 0.05
+    srv.close()
