@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import platform
 import statistics
@@ -207,6 +208,8 @@ def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
+    if args.workload in ("batch", "serve"):
+        return run_reference_multi(args)
     device = "cuda" if torch.cuda.is_available() else "cpu"
     csr = make_graph(args.workload, device)
     w = WORKLOADS[args.workload]
@@ -224,6 +227,53 @@ def run_reference(args):
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": vals[-1]["sample"], "value": value,
                              "unit": "edges/s", "host": vals[-1]["host"]},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_multi(args):
+    """The oracle (synchronous, single thread) on the batched or served workload's graphs, in
+    order, until about --ref-seconds of oracle time per step: graphs or requests per second."""
+    import oracle
+    from paper_2411_11468_gb300 import graphgen as gg
+    import numpy as np
+    if args.workload == "batch":
+        specs = gg.batch_specs(args.batch_graphs)
+        make = lambda k: gg.batch_graph(specs[k], weights="unit")
+        order = list(range(len(specs)))
+        unit, metric = "graphs/s", "batched LPA graphs solved per second (4,096 SBM graphs)"
+    else:
+        specs = gg.serve_specs(args.serve_pool)
+        make = lambda k: gg.serve_graph(specs[k])
+        rng = np.random.default_rng(12345)
+        order = [int(x) for x in rng.integers(0, len(specs), args.serve_requests)]
+        unit, metric = "requests/s", "served LPA requests per second (Poisson stream, continuous batching)"
+    vals, secs, counts = [], [], []
+    pos = 0
+    for step in range(args.warmup + args.steps):
+        t, k = 0.0, 0
+        while t < args.ref_seconds and k < len(order):
+            g = oracle.Graph.of(make(order[(pos + k) % len(order)]))
+            t0 = time.perf_counter()
+            oracle.lpa_sync(g, ALG["tolerance"], ALG["max_iters"], ALG["pl_period"])
+            t += time.perf_counter() - t0
+            k += 1
+        pos += k
+        if step >= args.warmup:
+            vals.append(k / t)
+            secs.append(t)
+            counts.append(k)
+    value = statistics.median(vals)
+    sample = (f"the first {sum(counts)} {'graphs' if args.workload == 'batch' else 'requests'} of the workload in "
+              f"order, whole synchronous runs (tolerance 0.05, cap 20, Pick-Less every 4th sweep), single-threaded C "
+              f"oracle, about {args.ref_seconds:.0f} s of oracle time per step; graph generation not timed")
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": dist_env()[0],
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(secs) * 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "mode": "sync", **ALG},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value, "unit": unit,
+                             "host": dict(machine=platform.machine(), nproc=os.cpu_count(), cpu=_cpu_model())},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -336,12 +386,13 @@ def run_ours(args):
                        for i in range(len(first["iter_ms"]))]}
 
     # end to end through the public API with host buffers
+    h_off = h_idx = h_w = h_lab = None
     if not args.no_e2e:
         h_off = csr.offsets.cpu().pin_memory()
         h_idx = csr.indices.cpu().pin_memory()
         h_w = None if csr.weights is None else csr.weights.cpu().pin_memory()
         h_lab = torch.empty(csr.n, dtype=torch.int32).pin_memory()
-        del g
+        g = None
         torch.cuda.synchronize()
         times = []
         edges = []
@@ -369,10 +420,252 @@ def run_ours(args):
                                    "lpa_labels to pinned host, lpa_modularity, lpa_destroy"}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(csr, target_s=args.ref_seconds)
+    # the batched and served workloads, summarised in the same line (one GPU only)
+    if ws == 1 and not args.no_extras:
+        h_off = h_idx = h_w = h_lab = None
+        csr = g = None
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        clocks = Clocks(local)
+        clocks.start()
+        line["batch"] = bench_batch(args, dev, lpa, mode)
+        line["serve"] = bench_serve(args, dev, lpa, mode)
+        line["clocks_extras"] = clocks.stop()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# batched and served workloads
+
+def _pinned(t):
+    return None if t is None else t.cpu().pin_memory()
+
+
+def _pct(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(math.ceil(p / 100.0 * len(xs))) - 1))
+    return xs[k]
+
+
+def bench_batch(args, dev, lpa, mode):
+    """4,096 SBM graphs (vertex counts log-uniform in [100, 1e5], block sizes log-uniform in
+    [10, 1000], mean degree uniform in [4, 32], unit float32 weights) solved by lpa_batch_run
+    (every sweep of every graph in shared launches, replayed from a CUDA graph), against a
+    serial loop of lpa_run over the same resident graphs; labels must be identical."""
+    from paper_2411_11468_gb300 import graphgen as gg
+    t0 = time.time()
+    specs = gg.batch_specs(args.batch_graphs)
+    graphs = [gg.batch_graph(sp, weights="unit", device=dev) for sp in specs]
+    torch.cuda.synchronize()
+    n_tot = sum(g.n for g in graphs)
+    m_tot = sum(g.m for g in graphs)
+    log(f"[bench] batch: {len(graphs)} graphs, {n_tot} vertices, {m_tot} entries, generated in {time.time() - t0:.1f}s")
+    b = lpa.Batch([(g.offsets, g.indices, g.weights) for g in graphs])
+    run_args = (ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode)
+    tuned = None
+    if not args.no_autotune:
+        t1 = time.time()
+        default_ms = min(b.run(*run_args)[1] for _ in range(2))
+        best, best_ms, count = b.autotune(*run_args, reps=2)
+        tuned = {"tuning": best, "device_ms": best_ms, "default_device_ms": default_ms, "configurations": count,
+                 "seconds": time.time() - t1}
+        log(f"[bench] batch autotune: {default_ms:.1f} -> {best_ms:.1f} ms in {tuned['seconds']:.1f}s ({count} configs)")
+    for _ in range(args.warmup):
+        res, dms = b.run(*run_args)
+    times, dev_ms = [], []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        res, dms = b.run(*run_args)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t1)
+        dev_ms.append(dms)
+    batch_s = statistics.median(times)
+    iters = [r["iterations"] for r in res]
+    scanned_bound = sum(g.m * it for g, it in zip(graphs, iters))
+    saved = [b.labels(i).clone() for i in range(len(graphs))]
+    q = b.modularity()
+    # serial loop over the same resident graphs (borrowed handles, one lpa_run each)
+    handles = [b.graph(i) for i in range(len(graphs))]
+    for h in handles[: min(64, len(handles))]:
+        h.run(*run_args)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    serial_iters = [h.run(*run_args).iterations for h in handles]
+    torch.cuda.synchronize()
+    serial_s = time.perf_counter() - t1
+    identical = all(torch.equal(saved[i], b.labels(i)) for i in range(len(graphs))) and serial_iters == iters
+    out = {"graphs": len(graphs), "vertices": n_tot, "entries": m_tot,
+           "graphs_per_s": len(graphs) / batch_s, "ms_per_step": batch_s * 1000.0,
+           "device_ms_per_step": statistics.median(dev_ms),
+           "serial_graphs_per_s": len(graphs) / serial_s, "serial_ms": serial_s * 1000.0,
+           "speedup_vs_serial": serial_s / batch_s, "identical_labels": bool(identical),
+           "iterations_mean": sum(iters) / len(iters), "iterations_max": max(iters),
+           "entries_x_iterations_per_s": scanned_bound / batch_s,
+           "modularity_mean": sum(q) / len(q), "autotune": tuned,
+           "graph_recipe": "SBM, n log-uniform [100, 1e5], block log-uniform [10, 1000], mean degree uniform "
+                           "[4, 32] split 8:1 intra:inter, unit float32 weights, seeds 0..count-1"}
+    # end to end: pinned host CSR in, labels out, through the public batch API
+    if not args.no_e2e:
+        host = [(_pinned(g.offsets), _pinned(g.indices), _pinned(g.weights)) for g in graphs]
+        labs = [torch.empty(g.n, dtype=torch.int32).pin_memory() for g in graphs]
+        del b, handles, saved
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        b2 = lpa.Batch(host)
+        b2.run(*run_args)
+        for i in range(len(graphs)):
+            b2.labels(i, labs[i])
+        b2.modularity()
+        b2.close()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t1
+        h2d = sum(h[0].numel() * h[0].element_size() + h[1].numel() * 4 + (0 if h[2] is None else h[2].numel() * 4)
+                  for h in host)
+        out["e2e"] = {"value": len(graphs) / e2e_s, "unit": "graphs/s", "ms_per_step": e2e_s * 1000.0,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4 * n_tot + 8 * len(graphs),
+                      "includes": "lpa_batch_create from pinned host CSR, lpa_batch_run, lpa_batch_labels to pinned "
+                                  "host for every graph, lpa_batch_modularity, lpa_batch_destroy"}
+    return out
+
+
+def bench_serve(args, dev, lpa, mode):
+    """A Poisson stream of requests drawn from a pool of seeded SBM / R-MAT graphs with 1e3..1e7
+    CSR entries (integer weights 1..8) into lpa_server (continuous batching, admission by HBM
+    footprint under the budget); p50/p99 latency from arrival to finish and throughput.  A
+    sample of the stream is also run one request at a time (lpa_create, lpa_run, lpa_labels,
+    lpa_destroy) and through the server with every request queued at once; the labels of
+    both must be identical."""
+    from paper_2411_11468_gb300 import graphgen as gg
+    import numpy as np
+    t0 = time.time()
+    specs = gg.serve_specs(args.serve_pool)
+    pool = []
+    for sp in specs:
+        g = gg.serve_graph(sp, device=dev)
+        pool.append((_pinned(g.offsets), _pinned(g.indices), _pinned(g.weights)))
+        del g
+    torch.cuda.synchronize()
+    sizes = [p[1].numel() for p in pool]
+    log(f"[bench] serve: pool of {len(pool)} graphs, {sum(sizes)} entries, built in {time.time() - t0:.1f}s")
+    rng = np.random.default_rng(12345)
+    picks = rng.integers(0, len(pool), args.serve_requests)
+    budget = int(args.serve_budget_gb * (1 << 30))
+    run_args = (ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode)
+
+    def drive(req_ids, arrivals):
+        """Feeds requests at their arrival times (seconds from start) into a fresh server; returns
+        per-request (latency s, iterations, labels or None), wall seconds and server steps."""
+        srv = lpa.Server(budget, max_resident=args.serve_resident)
+        keep_labels = arrivals is None
+        lat, its = {}, {}
+        labels = {}
+        t_arr = {}
+        steps = 0
+        i = 0
+        total = len(req_ids)
+        start = time.perf_counter()
+        while len(lat) < total:
+            now = time.perf_counter() - start
+            while i < total and (arrivals is None or arrivals[i] <= now):
+                p = pool[req_ids[i]]
+                rid = srv.submit(p[0], p[1], p[2], *run_args, borrow=True)
+                t_arr[rid] = (start + (0.0 if arrivals is None else arrivals[i]), i)
+                i += 1
+            c, running, queued = srv.step()
+            steps += 1
+            for rid in srv.poll():
+                lab, res, _ = srv.result(rid)
+                t_done = time.perf_counter()
+                ta, k = t_arr.pop(rid)
+                lat[k] = t_done - ta
+                its[k] = res["iterations"]
+                if keep_labels:
+                    labels[k] = lab
+            if running == 0 and queued == 0 and i < total and arrivals is not None:
+                time.sleep(max(0.0, min(0.01, arrivals[i] - (time.perf_counter() - start))))
+        wall = time.perf_counter() - start
+        srv.close()
+        return lat, its, labels, wall, steps
+
+    # one request at a time on a sample, and the same sample through the server at once
+    sample = [int(x) for x in picks[: args.serve_sample]]
+    for k in sample[:8]:
+        gw = lpa.Graph(*pool[k])
+        gw.run(*run_args)
+        gw.close()
+    torch.cuda.synchronize()
+    serial_labels = []
+    t1 = time.perf_counter()
+    for k in sample:
+        gs = lpa.Graph(*pool[k])
+        gs.run(*run_args)
+        serial_labels.append(gs.labels(torch.empty(pool[k][0].numel() - 1, dtype=torch.int32)))
+        gs.close()
+    torch.cuda.synchronize()
+    serial_s = time.perf_counter() - t1
+    lat_b, its_b, labels_b, wall_b, steps_b = drive(sample, None)
+    identical = all(torch.equal(labels_b[k], serial_labels[k]) for k in range(len(sample)))
+    sample_entries = sum(sizes[k] for k in sample)
+    # the Poisson stream
+    rate = args.serve_rate if args.serve_rate > 0 else 0.7 * len(sample) / wall_b
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, args.serve_requests))
+    req = [int(x) for x in picks]
+    lat, its, _, wall, steps = drive(req, arrivals)
+    lats = [lat[k] * 1000.0 for k in range(len(req))]
+    entries = sum(sizes[k] for k in req)
+    return {"requests": len(req), "rate_per_s": rate, "p50_ms": _pct(lats, 50), "p99_ms": _pct(lats, 99),
+            "mean_ms": sum(lats) / len(lats), "wall_s": wall, "requests_per_s": len(req) / wall,
+            "entries_per_s": entries / wall,
+            "entries_x_iterations_per_s": sum(sizes[k] * its[j] for j, k in enumerate(req)) / wall,
+            "server_steps": steps, "budget_gb": args.serve_budget_gb, "max_resident": args.serve_resident,
+            "saturated_sample": {"requests": len(sample), "entries": sample_entries,
+                                 "server_requests_per_s": len(sample) / wall_b,
+                                 "serial_requests_per_s": len(sample) / serial_s,
+                                 "speedup_vs_serial": serial_s / wall_b, "identical_labels": bool(identical),
+                                 "server_p50_ms": _pct([v * 1000 for v in lat_b.values()], 50),
+                                 "server_p99_ms": _pct([v * 1000 for v in lat_b.values()], 99)},
+            "pool": {"graphs": len(pool), "entries": sum(sizes),
+                     "recipe": "alternating SBM / R-MAT, target entries log-uniform [1e3, 1e7], integer weights "
+                               "1..8 as float32; requests pick pool graphs uniformly; latency = finish - arrival"}}
+
+
+def run_multi(args):
+    """--workload batch | serve: one JSON line for the batched or the served workload."""
+    from paper_2411_11468_gb300 import build, lpa
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    lpa.load()
+    mode = lpa.SYNC if args.mode == "sync" else lpa.ASYNC
+    clocks = Clocks(local)
+    clocks.start()
+    if args.workload == "batch":
+        r = bench_batch(args, dev, lpa, mode)
+        metric, value, unit, ms = "batched LPA graphs solved per second (4,096 SBM graphs)", r["graphs_per_s"], \
+            "graphs/s", r["ms_per_step"]
+    else:
+        r = bench_serve(args, dev, lpa, mode)
+        metric, value, unit, ms = "served LPA requests per second (Poisson stream, continuous batching)", \
+            r["requests_per_s"], "requests/s", r["wall_s"] * 1000.0
+    clk = clocks.stop()
+    line = {"metric": metric, "value": value * ws, "unit": unit, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "mode": args.mode, **ALG}, args.workload: r, "clocks": clk}
+    if "e2e" in r:
+        line["e2e"] = r["e2e"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -382,17 +675,28 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat26")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve"], default="rmat26")
     ap.add_argument("--mode", choices=["sync", "async"], default="sync")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and served summaries")
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the default buckets")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=20_000)
+    ap.add_argument("--serve-pool", type=int, default=512)
+    ap.add_argument("--serve-sample", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=0.0, help="arrivals/s (0: 70%% of saturated throughput)")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-resident", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("[bench] warning: fewer than 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("batch", "serve"):
+        return run_multi(args)
     return run_ours(args)
 
 

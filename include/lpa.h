@@ -63,6 +63,7 @@ extern "C" {
 #define LPA_HOST_PTRS        0   /* input arrays are host pointers                     */
 #define LPA_DEVICE_PTRS      2   /* input arrays are device pointers                   */
 #define LPA_CHECK_SYMMETRIC  4   /* also verify that the graph is undirected           */
+#define LPA_BORROW_INPUTS    8   /* lpa_server_submit: read the host arrays at admission  */
 
 /* ---- statistics ------------------------------------------------------------------- */
 #define LPA_STATS_MAX_ITERS 64   /* per-iteration arrays hold the first 64 iterations  */
@@ -248,6 +249,11 @@ int lpa_batch_modularity(lpa_batch *b, double *q);
  * lpa_run solves that graph alone on the same device data. */
 int lpa_batch_graph(lpa_batch *b, int graph, lpa_graph **out);
 
+/* Degree-bucket configuration shared by every graph of the batch (lpa_tuning above); setting
+ * it rebuilds every graph's buckets (labels untouched).  LPA_EINVAL as lpa_set_tuning. */
+int lpa_batch_get_tuning(const lpa_batch *b, lpa_tuning *t);
+int lpa_batch_set_tuning(lpa_batch *b, const lpa_tuning *t);
+
 int lpa_batch_size(const lpa_batch *b);
 int64_t lpa_batch_device_bytes(const lpa_batch *b);
 void lpa_batch_destroy(lpa_batch *b);
@@ -264,8 +270,11 @@ typedef struct lpa_server lpa_server;
  * whose run stopped. */
 int lpa_server_create(size_t hbm_budget_bytes, int max_resident, void *cuda_stream, lpa_server **out);
 
-/* Queues a request: the graph (host arrays, copied at submission, flags: offset width) and its
- * run parameters (as lpa_run; mode LPA_SYNC or LPA_ASYNC).  *request_id receives its id.
+/* Queues a request: the graph (host arrays; flags: offset width) and its run parameters (as
+ * lpa_run; mode LPA_SYNC or LPA_ASYNC).  *request_id receives its id.  The arrays are copied at
+ * submission, unless flags has LPA_BORROW_INPUTS: then they are read when the request is
+ * admitted, and the caller keeps them alive and unchanged until lpa_server_poll lists the
+ * request (pinned host memory makes admission's copy fastest).
  * LPA_EINVAL when the graph alone can never fit the budget. */
 int lpa_server_submit(lpa_server *s, const lpa_graph_desc *graph, int flags, double tolerance, int max_iters,
                       int pl_period, int mode, int64_t *request_id);
@@ -290,6 +299,29 @@ int64_t lpa_server_device_bytes(const lpa_server *s);
 void lpa_server_destroy(lpa_server *s);
 
 /* ---- modularity without device allocation ------------------------------------------ */
+
+/* ---- autotuning of the degree buckets ---------------------------------------------- */
+
+/* Picks the handle's degree-bucket configuration by timing: a coordinate descent over fixed
+ * candidates for each lpa_tuning field (hub chunk, block sizes and thresholds of the three
+ * block tiers, warp and group thresholds, lanes per group, thread threshold), starting from
+ * the current configuration.  Every candidate is applied (lpa_set_tuning) and timed on the
+ * run given by tolerance / max_iters / pl_period / mode (as lpa_run, from fresh labels; best
+ * of reps CUDA-event timings); a candidate is kept when it is at least 2% faster.  Section 4.3
+ * chooses its one switch degree (thread vs block per vertex) by timing a range of thresholds
+ * offline; this makes that choice per graph, for every bucket boundary and block size.
+ * On return the best configuration is installed and copied to *best (optional), its time to
+ * *best_ms (optional), the number of timed configurations to *evaluated (optional); the
+ * labels are those of the last timed run.  Tuning changes only which kernel handles a vertex
+ * and launch shapes: synchronous labels do not depend on it.  LPA_EINVAL for bad arguments
+ * (max_iters >= 1, 1 <= reps <= 16). */
+int lpa_autotune(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mode, int reps,
+                 lpa_tuning *best, float *best_ms, int *evaluated);
+
+/* The same search for a batch: every candidate is applied to all graphs
+ * (lpa_batch_set_tuning) and timed by lpa_batch_run's device time. */
+int lpa_batch_autotune(lpa_batch *b, double tolerance, int max_iters, int pl_period, int mode, int reps,
+                       lpa_tuning *best, float *best_ms, int *evaluated);
 
 /* Largest n_vertices accepted by lpa_modularity_noalloc. */
 #define LPA_NOALLOC_MAX_VERTICES (1 << 20)

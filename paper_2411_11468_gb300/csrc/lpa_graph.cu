@@ -22,21 +22,6 @@ void set_error(const std::string &msg) { t_error = msg; }
 
 using namespace lpa;
 
-#define LPA_CUDA(call)                                                                       \
-    do {                                                                                     \
-        cudaError_t _e = (call);                                                             \
-        if (_e != cudaSuccess) {                                                             \
-            set_error(std::string(#call) + ": " + cudaGetErrorString(_e));                   \
-            return _e == cudaErrorMemoryAllocation ? LPA_ENOMEM : LPA_ECUDA;                 \
-        }                                                                                    \
-    } while (0)
-
-#define LPA_CHECK(st)                                                                        \
-    do {                                                                                     \
-        int _s = (st);                                                                       \
-        if (_s != LPA_OK) return _s;                                                         \
-    } while (0)
-
 namespace {
 
 struct DeviceGuard {

@@ -163,3 +163,20 @@ class Arena {
 void set_error(const std::string &msg);
 
 }  // namespace lpa
+
+// Early returns on a failed CUDA call (message recorded, status LPA_ENOMEM or LPA_ECUDA) or
+// on a failed library status.
+#define LPA_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t _e = (call);                                                             \
+        if (_e != cudaSuccess) {                                                             \
+            ::lpa::set_error(std::string(#call) + ": " + cudaGetErrorString(_e));            \
+            return _e == cudaErrorMemoryAllocation ? LPA_ENOMEM : LPA_ECUDA;                 \
+        }                                                                                    \
+    } while (0)
+
+#define LPA_CHECK(st)                                                                        \
+    do {                                                                                     \
+        int _s = (st);                                                                       \
+        if (_s != LPA_OK) return _s;                                                         \
+    } while (0)

@@ -18,21 +18,6 @@
 
 using namespace lpa;
 
-#define LPA_CUDA(call)                                                                       \
-    do {                                                                                     \
-        cudaError_t _e = (call);                                                             \
-        if (_e != cudaSuccess) {                                                             \
-            set_error(std::string(#call) + ": " + cudaGetErrorString(_e));                   \
-            return _e == cudaErrorMemoryAllocation ? LPA_ENOMEM : LPA_ECUDA;                 \
-        }                                                                                    \
-    } while (0)
-
-#define LPA_CHECK(st)                                                                        \
-    do {                                                                                     \
-        int _s = (st);                                                                       \
-        if (_s != LPA_OK) return _s;                                                         \
-    } while (0)
-
 namespace {
 
 // Fresh run of every graph of a plan (blockIdx.y: graph): labels = vertex ids, every vertex
@@ -467,6 +452,34 @@ int lpa_batch_graph(lpa_batch *b, int graph, lpa_graph **out)
     return LPA_OK;
 }
 
+int lpa_batch_get_tuning(const lpa_batch *b, lpa_tuning *t)
+{
+    if (!b || !t) return LPA_EINVAL;
+    *t = b->tuning;
+    return LPA_OK;
+}
+
+int lpa_batch_set_tuning(lpa_batch *b, const lpa_tuning *t)
+{
+    if (!b || !t) return LPA_EINVAL;
+    DeviceGuard dg(b->device);
+    LPA_CUDA(cudaStreamSynchronize(b->stream));
+    const lpa_tuning old = b->tuning;
+    for (size_t i = 0; i < b->graphs.size(); ++i) {
+        const int st = lpa_set_tuning(b->graphs[i], t);
+        if (st != LPA_OK) {                            // the first graph rejects an invalid tuning
+            for (size_t j = 0; j < i; ++j) lpa_set_tuning(b->graphs[j], &old);
+            return st;
+        }
+    }
+    b->tuning = *t;
+    if (b->exec) {                                     // launch shapes are recorded in the graph
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    return LPA_OK;
+}
+
 int lpa_batch_size(const lpa_batch *b) { return b ? (int)b->graphs.size() : -1; }
 
 int64_t lpa_batch_device_bytes(const lpa_batch *b) { return b ? (int64_t)b->arena->capacity() : -1; }
@@ -486,6 +499,10 @@ struct Request {
     std::vector<int32_t> idx;
     std::vector<float> w;
     bool has_w = false;
+    const void *b_off = nullptr;       // borrowed inputs (LPA_BORROW_INPUTS)
+    const int32_t *b_idx = nullptr;
+    const float *b_w = nullptr;
+    int b_flags = 0;
     int64_t n = 0, m = 0;
     double tol = 0.0;
     int max_iters = 0, pl_period = 0;
@@ -611,17 +628,24 @@ int lpa_server_submit(lpa_server *s, const lpa_graph_desc *graph, int flags, dou
     Request *r = new Request();
     r->n = n;
     r->m = m;
-    r->off.resize((size_t)n + 1);
-    if (flags & LPA_OFFSETS_I64) {
-        memcpy(r->off.data(), graph->offsets, ((size_t)n + 1) * sizeof(int64_t));
+    if (flags & LPA_BORROW_INPUTS) {
+        r->b_off = graph->offsets;
+        r->b_idx = graph->indices;
+        r->b_w = graph->weights;
+        r->b_flags = flags & LPA_OFFSETS_I64;
     } else {
-        const int32_t *o = static_cast<const int32_t *>(graph->offsets);
-        for (int64_t i = 0; i <= n; ++i) r->off[(size_t)i] = o[i];
-    }
-    r->idx.assign(graph->indices, graph->indices + m);
-    if (graph->weights) {
-        r->has_w = true;
-        r->w.assign(graph->weights, graph->weights + m);
+        r->off.resize((size_t)n + 1);
+        if (flags & LPA_OFFSETS_I64) {
+            memcpy(r->off.data(), graph->offsets, ((size_t)n + 1) * sizeof(int64_t));
+        } else {
+            const int32_t *o = static_cast<const int32_t *>(graph->offsets);
+            for (int64_t i = 0; i <= n; ++i) r->off[(size_t)i] = o[i];
+        }
+        r->idx.assign(graph->indices, graph->indices + m);
+        if (graph->weights) {
+            r->has_w = true;
+            r->w.assign(graph->weights, graph->weights + m);
+        }
     }
     r->tol = tolerance;
     r->max_iters = max_iters;
@@ -645,8 +669,11 @@ int lpa_server_step(lpa_server *s, int *n_completed, int *n_running, int *n_queu
     for (auto it = s->queue.begin(); it != s->queue.end() && (int)s->running.size() < s->max_resident;) {
         Request *r = *it;
         lpa_graph *g = nullptr;
-        const int st = create_graph(r->off.data(), r->idx.data(), r->has_w ? r->w.data() : nullptr, r->n, r->m,
-                                    LPA_OFFSETS_I64 | LPA_HOST_PTRS, s->stream, s->arena, &s->tuning, &g);
+        const int st = r->b_off
+            ? create_graph(r->b_off, r->b_idx, r->b_w, r->n, r->m, r->b_flags | LPA_HOST_PTRS, s->stream, s->arena,
+                           &s->tuning, &g)
+            : create_graph(r->off.data(), r->idx.data(), r->has_w ? r->w.data() : nullptr, r->n, r->m,
+                           LPA_OFFSETS_I64 | LPA_HOST_PTRS, s->stream, s->arena, &s->tuning, &g);
         if (st == LPA_ENOMEM && !s->running.empty()) {
             ++it;                                      // waits for memory to free up
             continue;

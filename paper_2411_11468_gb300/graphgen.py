@@ -39,6 +39,7 @@ STREAM_SBM_IN_V = 4
 STREAM_SBM_OUT_U = 5
 STREAM_SBM_OUT_V = 6
 STREAM_BATCH = 7
+STREAM_SERVE = 8
 
 
 def _s64(x: int) -> int:
@@ -308,6 +309,40 @@ def batch_specs(count: int = 4096, seed: int = 0, n_lo: int = 100, n_hi: int = 1
 def batch_graph(spec: dict, weights: str = "unit", device="cpu") -> CSRGraph:
     return sbm(spec["n"], spec["block"], spec["d_in"], spec["d_out"], seed=spec["seed"],
                weights=weights, device=device)
+
+
+def serve_specs(count: int = 512, seed: int = 0, e_lo: float = 1e3, e_hi: float = 1e7):
+    """Request graphs of the serving workload: half SBM, half R-MAT (alternating), each with a
+    target of directed CSR entries log-uniform in [e_lo, e_hi] and integer weights 1..8.
+
+    R-MAT: the smallest scale whose edge factor (target / 2^(scale+1)) is at most 32 (scale at
+    least 5).  SBM: mean degree uniform in [4, 32] split 8:1 intra:inter, block size
+    log-uniform in [10, 1000].  Duplicate removal makes the realised counts somewhat lower."""
+    ctr = torch.arange(count, dtype=torch.int64) * 4
+    r = draws53(seed, STREAM_SERVE, torch.stack([ctr, ctr + 1, ctr + 2], 1)).to(torch.float64) / float(1 << 53)
+    specs = []
+    for k in range(count):
+        e = math.exp(math.log(e_lo) + r[k, 0].item() * (math.log(e_hi) - math.log(e_lo)))
+        if k % 2 == 0:
+            d = 4.0 + r[k, 1].item() * 28.0
+            n = max(16, int(round(e / d)))
+            s = int(round(math.exp(math.log(10) + r[k, 2].item() * (math.log(1000) - math.log(10)))))
+            specs.append(dict(kind="sbm", n=n, block=max(2, min(s, n)), d_in=d * 8.0 / 9.0, d_out=d / 9.0,
+                              seed=seed * 1_000_003 + k, target_entries=e))
+        else:
+            scale = 5
+            while e / float(1 << (scale + 1)) > 32.0:
+                scale += 1
+            ef = max(1, int(round(e / float(1 << (scale + 1)))))
+            specs.append(dict(kind="rmat", scale=scale, edge_factor=ef, seed=seed * 1_000_003 + k, target_entries=e))
+    return specs
+
+
+def serve_graph(spec: dict, device="cpu") -> CSRGraph:
+    if spec["kind"] == "sbm":
+        return sbm(spec["n"], spec["block"], spec["d_in"], spec["d_out"], seed=spec["seed"], weights="int8",
+                   device=device)
+    return rmat(spec["scale"], edge_factor=spec["edge_factor"], seed=spec["seed"], weights="int8", device=device)
 
 
 # ----------------------------------------------------------------------------------------

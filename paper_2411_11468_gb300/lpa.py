@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "liblpa.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
 SYNC, ASYNC, RESUME = 0, 1, 16
 OFFSETS_I32, OFFSETS_I64, HOST_PTRS, DEVICE_PTRS, CHECK_SYMMETRIC = 0, 1, 0, 2, 4
+BORROW_INPUTS = 8
 STATS_MAX_ITERS = 64
 NUM_KERNELS = 12
 KERNEL_NAMES = ["thread", "group", "warp", "cta", "cta_large", "cta_xl", "hub_begin", "hub_acc", "hub_clear",
@@ -35,7 +36,8 @@ SYMBOLS = ["lpa_create", "lpa_run", "lpa_labels", "lpa_modularity", "lpa_set_lab
            "lpa_kernel_name", "lpa_struct_size", "lpa_batch_create", "lpa_batch_run", "lpa_batch_labels",
            "lpa_batch_modularity", "lpa_batch_graph", "lpa_batch_size", "lpa_batch_device_bytes", "lpa_batch_destroy",
            "lpa_server_create", "lpa_server_submit", "lpa_server_step", "lpa_server_poll", "lpa_server_result",
-           "lpa_server_clock", "lpa_server_device_bytes", "lpa_server_destroy"]
+           "lpa_server_clock", "lpa_server_device_bytes", "lpa_server_destroy", "lpa_batch_get_tuning",
+           "lpa_batch_set_tuning", "lpa_autotune", "lpa_batch_autotune", "lpa_modularity_noalloc"]
 
 
 class LpaError(RuntimeError):
@@ -270,6 +272,14 @@ class Graph:
             setattr(t, k, int(v))
         _check(load().lpa_set_tuning(self._h, ct.byref(t)), "lpa_set_tuning")
 
+    def autotune(self, tolerance=0.05, max_iters=20, pl_period=4, mode=SYNC, reps=2):
+        """lpa_autotune: returns (tuning dict, best ms, configurations timed); the best tuning
+        stays installed."""
+        t, ms, k = Tuning(), ct.c_float(), ct.c_int()
+        _check(_load_multi().lpa_autotune(self._h, float(tolerance), int(max_iters), int(pl_period), int(mode),
+                                          int(reps), ct.byref(t), ct.byref(ms), ct.byref(k)), "lpa_autotune")
+        return t.to_dict(), ms.value, k.value
+
     def set_stream(self, stream):
         self.stream = stream
         _check(load().lpa_set_stream(self._h, ct.c_void_p(stream.cuda_stream)), "lpa_set_stream")
@@ -307,6 +317,12 @@ def _load_multi():
     L.lpa_batch_labels.argtypes = [P, i32, P, i64, i32]
     L.lpa_batch_modularity.argtypes = [P, ct.POINTER(ct.c_double)]
     L.lpa_batch_graph.argtypes = [P, i32, ct.POINTER(P)]
+    L.lpa_batch_get_tuning.argtypes = [P, ct.POINTER(Tuning)]
+    L.lpa_batch_set_tuning.argtypes = [P, ct.POINTER(Tuning)]
+    L.lpa_autotune.argtypes = [P, ct.c_double, i32, i32, i32, i32, ct.POINTER(Tuning), ct.POINTER(ct.c_float),
+                               ct.POINTER(ct.c_int)]
+    L.lpa_batch_autotune.argtypes = [P, ct.c_double, i32, i32, i32, i32, ct.POINTER(Tuning),
+                                     ct.POINTER(ct.c_float), ct.POINTER(ct.c_int)]
     L.lpa_batch_size.argtypes = [P]
     L.lpa_batch_device_bytes.argtypes = [P]
     L.lpa_batch_device_bytes.restype = i64
@@ -400,6 +416,26 @@ class Batch:
     def device_bytes(self):
         return int(_load_multi().lpa_batch_device_bytes(self._h))
 
+    def tuning(self) -> Tuning:
+        t = Tuning()
+        _check(_load_multi().lpa_batch_get_tuning(self._h, ct.byref(t)), "lpa_batch_get_tuning")
+        return t
+
+    def set_tuning(self, t: Tuning | None = None, **kw):
+        if t is None:
+            t = self.tuning()
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check(_load_multi().lpa_batch_set_tuning(self._h, ct.byref(t)), "lpa_batch_set_tuning")
+
+    def autotune(self, tolerance=0.05, max_iters=20, pl_period=4, mode=SYNC, reps=2):
+        """lpa_batch_autotune: returns (tuning dict, best device ms, configurations timed)."""
+        t, ms, k = Tuning(), ct.c_float(), ct.c_int()
+        _check(_load_multi().lpa_batch_autotune(self._h, float(tolerance), int(max_iters), int(pl_period), int(mode),
+                                                int(reps), ct.byref(t), ct.byref(ms), ct.byref(k)),
+               "lpa_batch_autotune")
+        return t.to_dict(), ms.value, k.value
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             _load_multi().lpa_batch_destroy(self._h)
@@ -422,17 +458,24 @@ class Server:
         _check(L.lpa_server_create(int(hbm_budget_bytes), int(max_resident), None, ct.byref(h)), "lpa_server_create")
         self._h = h
         self._sizes = {}
+        self._borrowed = {}
 
-    def submit(self, offsets, indices, weights=None, tolerance=0.05, max_iters=20, pl_period=4, mode=SYNC) -> int:
+    def submit(self, offsets, indices, weights=None, tolerance=0.05, max_iters=20, pl_period=4, mode=SYNC,
+               borrow=False) -> int:
+        """Queues a request.  borrow=True passes LPA_BORROW_INPUTS: the server reads the host
+        tensors at admission (keep them unchanged; this object holds a reference until the
+        result is collected)."""
         offsets = offsets.contiguous().cpu()
         indices = indices.contiguous().cpu()
         weights = None if weights is None else weights.contiguous().cpu()
-        flags = OFFSETS_I64 if offsets.dtype == torch.int64 else OFFSETS_I32
+        flags = (OFFSETS_I64 if offsets.dtype == torch.int64 else OFFSETS_I32) | (BORROW_INPUTS if borrow else 0)
         d = _desc(offsets, indices, weights)
         rid = ct.c_int64()
         _check(_load_multi().lpa_server_submit(self._h, ct.byref(d), flags, float(tolerance), int(max_iters),
                                                int(pl_period), int(mode), ct.byref(rid)), "lpa_server_submit")
         self._sizes[rid.value] = offsets.numel() - 1
+        if borrow:
+            self._borrowed[rid.value] = (offsets, indices, weights)
         return rid.value
 
     def step(self):
@@ -453,6 +496,7 @@ class Server:
         ts, ta, tf = ct.c_double(), ct.c_double(), ct.c_double()
         _check(_load_multi().lpa_server_result(self._h, rid, _ptr(lab), n, ct.byref(res), ct.byref(ts), ct.byref(ta),
                                                ct.byref(tf)), "lpa_server_result")
+        self._borrowed.pop(rid, None)
         return lab, res.to_dict(), (ts.value, ta.value, tf.value)
 
     def clock(self):
