@@ -655,9 +655,8 @@ void free_buckets(lpa_graph *g)
     g->lists = nullptr;
     dfree(g, g->hub_mem);
     g->hub_mem = nullptr;
-    dfree(g, g->tab_k);
+    dfree(g, g->tab_k);                               // tab_v lives in the same block
     g->tab_k = nullptr;
-    dfree(g, g->tab_v);
     g->tab_v = nullptr;
     dfree(g, g->used_list);
     g->used_list = nullptr;
@@ -819,10 +818,11 @@ int build_buckets(lpa_graph *g)
         LPA_CUDA(cudaMemsetAsync(d_act, 0, H, g->stream));
         LPA_CUDA(cudaMemsetAsync(d_best, 0, H * 8, g->stream));
         LPA_CUDA(cudaMemsetAsync(d_used, 0, H * 4, g->stream));
-        LPA_CHECK(dalloc(g, &g->tab_k, (size_t)slots));
-        LPA_CHECK(dalloc(g, &g->tab_v, (size_t)slots));
+        // 8 bytes per slot in one block: split keys then values, or packed 64-bit slots
+        LPA_CHECK(dalloc(g, &g->tab_k, (size_t)slots * 2));
+        g->tab_v = reinterpret_cast<float *>(g->tab_k + slots);
         LPA_CHECK(dalloc(g, &g->used_list, (size_t)used_total));
-        LPA_CUDA(launch_hub_table_clear(g->tab_k, g->tab_v, slots, g->stream));
+        LPA_CUDA(launch_hub_table_clear(g->tab_k, g->tab_v, slots, plan_int_weights(g), g->stream));
         ha.hub_v = d_hv;
         ha.hub_p1 = d_p1;
         ha.hub_b = d_b;

@@ -51,8 +51,8 @@ struct HubArgs {
     const int64_t *chunk_e1;   // [n_chunks] end CSR entry
     const int32_t *slice_h;    // [n_slices] hub of each clear block
     const int32_t *slice_j;    // [n_slices] slice index within the hub's table / used list
-    int32_t *tab_k;            // hub table keys
-    float *tab_v;              // hub table values (float32 or uint32 bits)
+    int32_t *tab_k;            // hub tables: keys (split layout) or 64-bit slots over tab_k and tab_v (packed)
+    float *tab_v;              // hub table values (split layout; directly after tab_k)
     int32_t n_hubs;
     int32_t n_chunks;
     int32_t n_slices;
@@ -123,7 +123,8 @@ cudaError_t sweep_init_constants();
 // Enqueues one sweep of every graph of the plan (graphs whose run has stopped do no work),
 // the synchronous label publication and k_decide.  *launches counts kernel launches.
 cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, int *launches);
-cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, cudaStream_t s);
+// Clears `slots` hub-table slots: packed (one 64-bit word per slot over k) or split (k, v).
+cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, bool packed, cudaStream_t s);
 size_t max_dynamic_smem();
 int num_sms();
 

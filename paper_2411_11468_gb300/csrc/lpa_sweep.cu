@@ -76,13 +76,36 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
 __device__ __forceinline__ uint32_t cap_bits(uint32_t x) { return 32u - __clz(x); }
 __device__ __forceinline__ uint32_t cap_of_bits(uint32_t b) { return b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u); }
 
+// Table layouts.  Split: keys and values in two arrays (slot s at index s * stride).  Packed
+// (integer sums only): one 64-bit word per slot, key in the high half and the uint32 sum in
+// the low half, so taking an empty slot is one compare-and-swap that also stores the first
+// weight, and adding to a present key is one add (sums stay below 2^24, so the low half
+// never carries into the key).  Both hold the same (key, sum) pairs at the same slots.
+template <typename V>
+struct SplitTable {
+    using Val = V;
+    int32_t *k;
+    V *v;
+    int stride;
+};
+
+struct PackedTable {
+    using Val = uint32_t;
+    unsigned long long *h;
+    int stride;
+};
+
+constexpr unsigned long long kEmptySlot = 0xFFFFFFFF00000000ull;   // key -1, sum 0
+
 // One slot attempt of Algorithm 2: take slot s if it is empty or already holds k, add v
 // and fold the new sum into `best`.  With TRACK a slot taken from empty is appended to the
 // table's used list.
 template <bool SHARED, bool TRACK, typename V>
-__device__ __forceinline__ bool try_slot(int32_t *Hk, V *Hv, size_t s, int32_t k, V v,
-                                         unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
+__device__ __forceinline__ bool try_slot(const SplitTable<V> &T, size_t s, int32_t k, V v, unsigned long long &best,
+                                         uint32_t *ucnt, int32_t *ulist)
 {
+    int32_t *Hk = T.k;
+    V *Hv = T.v;
     if (!SHARED) {                                    // single owner: plain accesses
         const int32_t kk = Hk[s];
         if (kk == k || kk == kEmpty) {
@@ -112,11 +135,50 @@ __device__ __forceinline__ bool try_slot(int32_t *Hk, V *Hv, size_t s, int32_t k
     return false;
 }
 
+template <bool SHARED, bool TRACK>
+__device__ __forceinline__ bool try_slot(const PackedTable &T, size_t s, int32_t k, uint32_t v,
+                                         unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
+{
+    unsigned long long *p = T.h + s;
+    const uint32_t uk = (uint32_t)k;
+    const unsigned long long mine = ((unsigned long long)uk << 32) | v;
+    if (!SHARED) {
+        const unsigned long long cur = *p;
+        const uint32_t ck = (uint32_t)(cur >> 32);
+        if (ck == uk || ck == 0xFFFFFFFFu) {
+            const uint32_t nv = (uint32_t)cur + v;       // an empty slot holds sum 0
+            *p = ((unsigned long long)uk << 32) | nv;
+            best = umax64(best, pack_kv(nv, k));
+            return true;
+        }
+        return false;
+    }
+    uint32_t ck = (uint32_t)(*((volatile unsigned long long *)p) >> 32);
+    if (ck == 0xFFFFFFFFu) {
+        const unsigned long long old = atomicCAS(p, kEmptySlot, mine);
+        if (old == kEmptySlot) {
+            if (TRACK) ulist[atomicAdd(ucnt, 1u)] = (int32_t)s;
+            best = umax64(best, pack_kv(v, k));
+            return true;
+        }
+        ck = (uint32_t)(old >> 32);
+    }
+    if (ck == uk) {
+        // 32-bit add on the sum half (the low word, at the lower address): native in shared
+        // memory, unlike a 64-bit add.  The key half never changes once the slot is taken, so
+        // a concurrent compare-and-swap on the slot fails on the key whatever the sum.
+        const uint32_t nv = atomicAdd(reinterpret_cast<uint32_t *>(p), v) + v;
+        best = umax64(best, pack_kv(nv, k));
+        return true;
+    }
+    return false;
+}
+
 // hashtableAccumulate (Algorithm 2) with i and delta kept reduced mod p1 (same slots),
 // then a linear scan from the last probed slot once the probe budget is spent.
-template <bool SHARED, bool TRACK, typename V>
-__device__ __forceinline__ void ht_accumulate(int32_t *Hk, V *Hv, int stride, uint32_t p1, uint32_t b,
-                                              int32_t k, V v, unsigned long long &best, unsigned &fallbacks,
+template <bool SHARED, bool TRACK, typename T>
+__device__ __forceinline__ void ht_accumulate(const T &tab, uint32_t p1, uint32_t b, int32_t k, typename T::Val v,
+                                              unsigned long long &best, unsigned &fallbacks,
                                               uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
 {
     const uint32_t uk = (uint32_t)k;
@@ -127,7 +189,7 @@ __device__ __forceinline__ void ht_accumulate(int32_t *Hk, V *Hv, int stride, ui
 #pragma unroll 1
     for (int t = 0; t < kMaxRetries; ++t) {
         s = i;
-        if (try_slot<SHARED, TRACK>(Hk, Hv, (size_t)s * stride, k, v, best, ucnt, ulist)) return;
+        if (try_slot<SHARED, TRACK>(tab, (size_t)s * tab.stride, k, v, best, ucnt, ulist)) return;
         if (step == 0xFFFFFFFFu) {
             uint32_t q = mod_mersenne(uk, b + 1, 2u * p1 + 1u);
             if (q >= p1) q -= p1;
@@ -146,7 +208,7 @@ __device__ __forceinline__ void ht_accumulate(int32_t *Hk, V *Hv, int stride, ui
     for (uint32_t u = 1; u <= p1; ++u) {
         uint32_t q = s + u;
         if (q >= p1) q -= p1;
-        if (try_slot<SHARED, TRACK>(Hk, Hv, (size_t)q * stride, k, v, best, ucnt, ulist)) return;
+        if (try_slot<SHARED, TRACK>(tab, (size_t)q * tab.stride, k, v, best, ucnt, ulist)) return;
     }
 }
 
@@ -180,11 +242,12 @@ __device__ __forceinline__ unsigned long long group_max(unsigned long long x)
 // weights keep every partial sum exact, so the table contents do not depend on the order.
 constexpr int kPeel = 3;
 
-template <int G, bool SHARED, bool TRACK, typename V>
-__device__ __forceinline__ void group_insert(int32_t *Hk, V *Hv, int stride, uint32_t p1, uint32_t b,
-                                             bool has, int32_t k, V w, unsigned long long &best, unsigned &fb,
+template <int G, bool SHARED, bool TRACK, typename T>
+__device__ __forceinline__ void group_insert(const T &tab, uint32_t p1, uint32_t b, bool has, int32_t k,
+                                             typename T::Val w, unsigned long long &best, unsigned &fb,
                                              uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
 {
+    using V = typename T::Val;
     if (G >= 2) {
         const unsigned gm = group_mask<G>();
         const int lane = threadIdx.x & 31;
@@ -199,26 +262,49 @@ __device__ __forceinline__ void group_insert(int32_t *Hk, V *Hv, int stride, uin
             V sum = mine ? w : V(0);
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gm, sum, o);
-            if (lane == leader) ht_accumulate<SHARED, TRACK>(Hk, Hv, stride, p1, b, kl, sum, best, fb, ucnt, ulist);
+            if (lane == leader) ht_accumulate<SHARED, TRACK>(tab, p1, b, kl, sum, best, fb, ucnt, ulist);
             if (mine) has = false;
             pend &= ~same;
         }
     }
-    if (has) ht_accumulate<SHARED, TRACK>(Hk, Hv, stride, p1, b, k, w, best, fb, ucnt, ulist);
+    if (has) ht_accumulate<SHARED, TRACK>(tab, p1, b, k, w, best, fb, ucnt, ulist);
 }
 
 // hashtableClear of slots [0, p1] of a contiguous, 16-byte aligned table with 16-byte stores
 // (p1 + 1 is a power of two, at least 4 slots are allocated).
 // (Values are cleared to all-zero bits, which is 0 for both value types.)
-__device__ __forceinline__ void clear_table_vec(int32_t *Hk, void *Hv, uint32_t p1, int first, int step)
+template <typename V>
+__device__ __forceinline__ void clear_table_vec(const SplitTable<V> &T, uint32_t p1, int first, int step)
 {
     const uint32_t chunks = (p1 + 4u) >> 2;
-    int4 *K4 = reinterpret_cast<int4 *>(Hk);
-    int4 *V4 = reinterpret_cast<int4 *>(Hv);
+    int4 *K4 = reinterpret_cast<int4 *>(T.k);
+    int4 *V4 = reinterpret_cast<int4 *>(T.v);
     for (uint32_t q = first; q < chunks; q += step) {
         K4[q] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
         V4[q] = make_int4(0, 0, 0, 0);
     }
+}
+
+__device__ __forceinline__ void clear_table_vec(const PackedTable &T, uint32_t p1, int first, int step)
+{
+    const uint32_t chunks = (p1 + 2u) >> 1;          // two slots per 16 bytes
+    int4 *H4 = reinterpret_cast<int4 *>(T.h);
+    for (uint32_t q = first; q < chunks; q += step) H4[q] = make_int4(0, kEmpty, 0, kEmpty);
+}
+
+// Clear of a thread's private interleaved table (slot s at s * stride).
+template <typename V>
+__device__ __forceinline__ void clear_table_private(const SplitTable<V> &T, uint32_t p1)
+{
+    for (uint32_t s = 0; s < p1; ++s) {
+        T.k[(size_t)s * T.stride] = kEmpty;
+        T.v[(size_t)s * T.stride] = V(0);
+    }
+}
+
+__device__ __forceinline__ void clear_table_private(const PackedTable &T, uint32_t p1)
+{
+    for (uint32_t s = 0; s < p1; ++s) T.h[(size_t)s * T.stride] = kEmptySlot;
 }
 
 // The per-sweep view of one graph: what the sweep kernels read and write for an item of
@@ -269,22 +355,35 @@ __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
     return v;
 }
 
-// Warp-aggregated append of (v, c) to the synchronous mover list.  Every lane of the
-// warp must call it.
-__device__ __forceinline__ void append_movers(const SweepView &a, bool pred, int32_t v, int32_t c)
+// Synchronous movers are staged per warp in shared memory (32 (v, c) pairs) and appended to
+// the graph's mover list with one atomic per 32 movers: a per-vertex atomic on the single
+// list counter would serialise in L2.  Every lane of the warp calls these; n is uniform.
+__device__ __forceinline__ void movers_flush(unsigned long long *count, int32_t *mv, int32_t *mc, int2 *sbuf, int &n)
+{
+    if (n == 0) return;
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(count, (unsigned long long)n);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (lane < n) {
+        const int2 m = sbuf[lane];
+        mv[base + lane] = m.x;
+        mc[base + lane] = m.y;
+    }
+    __syncwarp();
+    n = 0;
+}
+
+__device__ __forceinline__ void movers_push(const SweepView &a, int2 *sbuf, int &n, bool pred, int32_t v, int32_t c)
 {
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
     if (!bal) return;
+    const int cnt = __popc(bal);
+    if (n + cnt > 32) movers_flush(a.mover_count, a.mover_v, a.mover_c, sbuf, n);
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(bal) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(a.mover_count, (unsigned long long)__popc(bal));
-    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (pred) {
-        const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
-        a.mover_v[pos] = v;
-        a.mover_c[pos] = c;
-    }
+    if (pred) sbuf[n + __popc(bal & ((1u << lane) - 1u))] = make_int2(v, c);
+    n += cnt;
 }
 
 // Loads entry e of the row of v: (label of the neighbour, weight); has = false for e past
@@ -309,12 +408,13 @@ __device__ __forceinline__ void load_entry(const SweepView &a, int32_t v, int64_
 // Scans entries [start, end) of the row of v in rounds: each round covers U * step entries,
 // lane offset `lane` inside each step.  All U entries of a round are loaded (index, weight,
 // gathered label) before any of them is inserted, so U gathers per thread are in flight.
-template <int G, bool SHARED, bool TRACK, int U, typename V>
+template <int G, bool SHARED, bool TRACK, int U, typename T>
 __device__ __forceinline__ void scan_row(const SweepView &a, int32_t v, int64_t start, int64_t end, int step,
-                                         int lane, int32_t *Hk, V *Hv, int stride, uint32_t p1, uint32_t b,
+                                         int lane, const T &tab, uint32_t p1, uint32_t b,
                                          unsigned long long &best, unsigned &fb, uint32_t *ucnt = nullptr,
                                          int32_t *ulist = nullptr, int round = 0)
 {
+    using V = typename T::Val;
     const int64_t adv = round ? round : (int64_t)step * U;   // a block-wide round for the CTA kernels
     for (int64_t eb = start; eb < end; eb += adv) {
         bool has[U];
@@ -324,7 +424,7 @@ __device__ __forceinline__ void scan_row(const SweepView &a, int32_t v, int64_t 
         for (int u = 0; u < U; ++u) load_entry(a, v, eb + (int64_t)u * step + lane, end, has[u], k[u], wv[u]);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            group_insert<G, SHARED, TRACK>(Hk, Hv, stride, p1, b, has[u], k[u], wv[u], best, fb, ucnt, ulist);
+            group_insert<G, SHARED, TRACK>(tab, p1, b, has[u], k[u], wv[u], best, fb, ucnt, ulist);
     }
 }
 
@@ -334,6 +434,45 @@ __device__ __forceinline__ bool decide(unsigned long long best, int32_t cur, int
     if (best == 0) return false;                   // no neighbour label (isolated / self-loops only)
     cstar = unpack_key(best);
     return (cstar != cur) && (!pl || cstar < cur);
+}
+
+// Shared-memory tables use the packed layout when the sums are integers.
+constexpr bool kPackShared = true;
+template <typename V, bool PACK> struct TableFor {
+    using type = SplitTable<V>;
+};
+template <> struct TableFor<uint32_t, true> {
+    using type = PackedTable;
+};
+
+// Table t of n_tables tables of `slots` slots at `base` (8 bytes per slot in both layouts):
+// interleaved (slot s of table t at s * n_tables + t) or one table after another.
+template <typename V>
+__device__ __forceinline__ void table_at(SplitTable<V> &T, unsigned char *base, int n_tables, int slots, int t,
+                                         bool interleaved)
+{
+    V *vbase = (V *)(base + (size_t)n_tables * slots * sizeof(int32_t));
+    if (interleaved) {
+        T.k = (int32_t *)base + t;
+        T.v = vbase + t;
+        T.stride = n_tables;
+    } else {
+        T.k = (int32_t *)base + (size_t)t * slots;
+        T.v = vbase + (size_t)t * slots;
+        T.stride = 1;
+    }
+}
+
+__device__ __forceinline__ void table_at(PackedTable &T, unsigned char *base, int n_tables, int slots, int t,
+                                         bool interleaved)
+{
+    if (interleaved) {
+        T.h = (unsigned long long *)base + t;
+        T.stride = n_tables;
+    } else {
+        T.h = (unsigned long long *)base + (size_t)t * slots;
+        T.stride = 1;
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -369,175 +508,192 @@ __device__ __forceinline__ void warp_flush(const SweepView &a, int kslot, unsign
     }
 }
 
+// Entries loaded per lane and round by the G-lane kernels: enough that one round covers the
+// default degree range of each bucket (G = 1: D <= 8, G = 8: D <= 32, G = 32: D <= 256), so
+// a row's index, weight and label loads are all in flight together.
+constexpr int kUnrollThread = 2;      // G = 1
+constexpr int kUnrollSmall = 4;       // G = 2, 4
+constexpr int kUnrollGroup = 2;       // G = 8, 16
+constexpr int kUnrollWarp = 4;        // G = 32
+constexpr int kMinBlocksThread = 6;   // resident blocks per SM asked of the register allocator (128 threads)
+constexpr int kMinBlocks = 3;         // (256 threads)
+template <int G> struct GroupUnroll {
+    static constexpr int U = G == 1 ? kUnrollThread : (G <= 4 ? kUnrollSmall : (G <= 16 ? kUnrollGroup : kUnrollWarp));
+    static constexpr int kMinBlocks = G == 1 ? ::lpa::kMinBlocksThread : ::lpa::kMinBlocks;
+};
+
 // G lanes per vertex (G = 1: thread per vertex with a private table; G = 32: warp per
 // vertex).  Persistent: each warp takes work items (a range of one graph's bucket list) from
-// the queue and walks them 32/G vertices at a time.
+// the queue.  The warp fetches the list entry, processed flag and row bounds of 32 vertices
+// at once (one per lane), then its groups take them 32/G at a time: the per-vertex chain of
+// dependent loads (list, flag, offsets) is paid once per 32 vertices.  Neighbour ids of a
+// row that fits one round stay in registers for the marks.
 template <int G, int TPB, typename V>
-__global__ void __launch_bounds__(TPB) k_group(KArgs k)
+__global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs k)
 {
     if (*k.active == 0) return;                        // every graph has stopped
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NG = TPB / G;
     constexpr int GPW = 32 / G;                        // groups per warp
+    constexpr int U = GroupUnroll<G>::U;
     const int lane_w = threadIdx.x & 31;
     const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
     const int grp = threadIdx.x / G;
     const int gw = lane_w / G;                         // group within the warp
-    int32_t *Hk;
-    V *Hv;
-    int stride;
-    if (G == 1) {                      // interleaved: slot s of thread t at s * TPB + t
-        Hk = (int32_t *)smem + threadIdx.x;
-        Hv = (V *)(smem + (size_t)TPB * k.slots * sizeof(int32_t)) + threadIdx.x;
-        stride = TPB;
-    } else {
-        Hk = (int32_t *)smem + (size_t)grp * k.slots;
-        Hv = (V *)(smem + (size_t)NG * k.slots * sizeof(int32_t)) + (size_t)grp * k.slots;
-        stride = 1;
-    }
+    using Tab = typename TableFor<V, kPackShared>::type;
+    Tab tab;
+    if (G == 1) table_at(tab, smem, TPB, k.slots, threadIdx.x, true);      // private, interleaved
+    else table_at(tab, smem, NG, k.slots, grp, false);
+    __shared__ int2 s_mov[TPB / 32][32];
+    int2 *mbuf = s_mov[threadIdx.x >> 5];
+    int nmov = 0;
+    // counters and movers are kept per warp while consecutive items belong to one graph
+    int cur_g = -1;
+    SweepView a{};
+    unsigned fb = 0, c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
     for (;;) {
         int it = 0;
         if (lane_w == 0) it = (int)atomicAdd(k.queue, 1u);
         it = __shfl_sync(0xFFFFFFFFu, it, 0);
         if (it >= k.n_items) break;
         const WorkItem item = k.items[it];
-        const SweepView a = view_of(k.gd, item.g);
-        if (a.done) continue;
-        unsigned fb = 0, c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
-        for (int64_t wb = 0; wb < item.count; wb += GPW) {          // uniform per warp
-            const int64_t gi = wb + gw;
-            int32_t v = -1;
-            bool act = false;
-            if (gi < item.count) {
-                v = __ldg(a.lists + item.start + gi);
-                if (lane == 0) {
-                    act = a.flag_cur[v] != 0;
-                    if (act) a.flag_cur[v] = 0;           // mark processed
-                }
+        if (item.g != cur_g) {
+            if (cur_g >= 0) {
+                movers_flush(a.mover_count, a.mover_v, a.mover_c, mbuf, nmov);
+                warp_flush(a, k.kslot, c_act, c_edges, c_moved, c_marks, fb);
+                fb = c_act = c_edges = c_moved = c_marks = 0;
             }
-            if (G > 1) act = __shfl_sync(group_mask<G>(), act, 0, G);
-            int32_t cstar = -1;
-            bool moved = false;
-            if (act) {
-                const int64_t o0 = a.off[v], o1 = a.off[v + 1];
-                const uint32_t D = (uint32_t)(o1 - o0);
-                const uint32_t b = cap_bits(D << a.tshift);    // capacity >= D << tshift
-                const uint32_t p1 = cap_of_bits(b);
-                if (G == 1) {
-                    for (uint32_t s = 0; s < p1; ++s) {        // hashtableClear
-                        Hk[(size_t)s * stride] = kEmpty;
-                        Hv[(size_t)s * stride] = V(0);
-                    }
-                } else {
-                    group_sync<G>();                           // previous vertex's inserts are done
-                    clear_table_vec(Hk, Hv, p1, lane, G);
-                    group_sync<G>();
-                }
-                const int32_t cur = a.C[v];
-                unsigned long long best = 0;
-                scan_row<G, (G > 1), false, 1>(a, v, o0, o1, G, lane, Hk, Hv, stride, p1, b, best, fb);
-                best = group_max<G>(best);                     // hashtableMaxKey
-                moved = decide(best, cur, a.pl, cstar);
-                if (moved) {
-                    if (a.async_mode && lane == 0) {
-                        a.C[v] = cstar;
-                        __threadfence();
-                    }
-                    group_sync<G>();
-                    for (int64_t e = o0 + lane; e < o1; e += G) a.flag_next[a.idx[e]] = 1;   // mark neighbours
-                }
-                if (lane == 0) {
-                    c_act += 1;
-                    c_edges += D;
-                    if (moved) {
-                        c_moved += 1;
-                        c_marks += D;
-                    }
-                }
-            }
-            if (!a.async_mode) append_movers(a, moved && lane == 0, v, cstar);
+            cur_g = item.g;
+            a = view_of(k.gd, item.g);
         }
+        if (a.done) continue;
+        for (int64_t base = 0; base < item.count; base += 32) {       // uniform per warp
+            // lane L: vertex base + L of the item (its flag is taken here: mark processed)
+            int32_t mv = -1;
+            int64_t mo0 = 0, mo1 = 0;
+            if (base + lane_w < item.count) {
+                mv = __ldg(a.lists + item.start + base + lane_w);
+                if (a.flag_cur[mv] != 0) {
+                    a.flag_cur[mv] = 0;
+                    mo0 = a.off[mv];
+                    mo1 = a.off[mv + 1];
+                } else {
+                    mv = -1;                                   // not active in this sweep
+                }
+            }
+#pragma unroll 1
+            for (int st = 0; st < 32 && base + st < item.count; st += GPW) {    // uniform per warp
+                const int src = st + gw;
+                const int32_t v = __shfl_sync(0xFFFFFFFFu, mv, src);
+                const int64_t o0 = __shfl_sync(0xFFFFFFFFu, mo0, src);
+                const int64_t o1 = __shfl_sync(0xFFFFFFFFu, mo1, src);
+                const bool act = v >= 0 && o1 > o0;
+                int32_t cstar = -1;
+                bool moved = false;
+                if (act) {
+                    const uint32_t D = (uint32_t)(o1 - o0);
+                    const uint32_t b = cap_bits(D << a.tshift);    // capacity >= D << tshift
+                    const uint32_t p1 = cap_of_bits(b);
+                    const int32_t cur = a.C[v];
+                    if (G == 1) {
+                        clear_table_private(tab, p1);              // hashtableClear
+                    } else {
+                        group_sync<G>();                           // previous vertex's inserts are done
+                        clear_table_vec(tab, p1, lane, G);
+                        group_sync<G>();
+                    }
+                    unsigned long long best = 0;
+                    int32_t jr[U];                                 // neighbour ids of the first round
+#pragma unroll
+                    for (int u = 0; u < U; ++u) jr[u] = -1;
+                    for (int64_t eb = o0; eb < o1; eb += (int64_t)U * G) {
+                        bool has[U];
+                        int32_t kk[U];
+                        V wv[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {              // indices and weights
+                            const int64_t e = eb + (int64_t)u * G + lane;
+                            has[u] = e < o1;
+                            jr[u] = has[u] ? a.idx[e] : -1;
+                            wv[u] = (has[u] && a.w) ? to_value<V>(a.w[e]) : V(1);
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {              // labels (self-loops skipped)
+                            has[u] = has[u] && jr[u] != v;
+                            kk[u] = has[u] ? a.C[jr[u]] : 0;
+                        }
+                        // inserts one slot at a time (rolled loop, entries shifted down in
+                        // registers) so that the probe loop is not replicated U times
+#pragma unroll 1
+                        for (int u = 0; u < U; ++u) {
+                            if (!__any_sync(group_mask<G>(), has[0])) break;     // lanes of this group only
+                            group_insert<G, (G > 1), false>(tab, p1, b, has[0], kk[0], wv[0], best, fb);
+#pragma unroll
+                            for (int q = 0; q + 1 < U; ++q) {
+                                has[q] = has[q + 1];
+                                kk[q] = kk[q + 1];
+                                wv[q] = wv[q + 1];
+                            }
+                            has[U - 1] = false;
+                        }
+                    }
+                    best = group_max<G>(best);                     // hashtableMaxKey
+                    moved = decide(best, cur, a.pl, cstar);
+                    if (moved) {
+                        if (a.async_mode && lane == 0) {
+                            a.C[v] = cstar;
+                            __threadfence();
+                        }
+                        if (D <= (uint32_t)(U * G)) {              // mark neighbours (ids in registers)
+#pragma unroll
+                            for (int u = 0; u < U; ++u)
+                                if (jr[u] >= 0) a.flag_next[jr[u]] = 1;
+                        } else {
+                            for (int64_t e = o0 + lane; e < o1; e += G) a.flag_next[a.idx[e]] = 1;
+                        }
+                    }
+                    if (lane == 0) {
+                        c_act += 1;
+                        c_edges += D;
+                        if (moved) {
+                            c_moved += 1;
+                            c_marks += D;
+                        }
+                    }
+                }
+                if (!a.async_mode) movers_push(a, mbuf, nmov, moved && lane == 0, v, cstar);
+            }
+        }
+    }
+    if (cur_g >= 0) {
+        movers_flush(a.mover_count, a.mover_v, a.mover_c, mbuf, nmov);
         warp_flush(a, k.kslot, c_act, c_edges, c_moved, c_marks, fb);
     }
 }
 
 // One thread block per vertex; the table (up to k.slots entries) lives in dynamic smem.
-// Persistent: each block takes work items from the queue and walks their vertices.
+// Persistent: each block takes work items from the queue; the list entries, processed flags
+// and row bounds of up to 32 vertices of the item are fetched at once into shared memory.
 template <int TPB, typename V>
 __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
 {
     if (*k.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    int32_t *Hk = (int32_t *)smem;
-    V *Hv = (V *)(smem + (size_t)k.slots * sizeof(int32_t));
-    __shared__ int s_item, s_act;
-    __shared__ int32_t s_v;
-    __shared__ unsigned long long s_best[TPB / 32];
-    for (;;) {
-        __syncthreads();                               // s_item and s_best of the last round are consumed
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(k.queue, 1u);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= k.n_items) break;
-        const WorkItem item = k.items[it];
-        const SweepView a = view_of(k.gd, item.g);
-        if (a.done) continue;
-        unsigned fb = 0;
-        unsigned long long c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
-        for (int64_t gi = 0; gi < item.count; ++gi) {
-            __syncthreads();                           // the previous vertex is finished
-            if (threadIdx.x == 0) {
-                const int32_t v0 = __ldg(a.lists + item.start + gi);
-                const int act = a.flag_cur[v0] != 0;
-                if (act) a.flag_cur[v0] = 0;           // mark processed
-                s_act = act;
-                s_v = v0;
-            }
-            __syncthreads();
-            if (!s_act) continue;                      // uniform for the block
-            const int32_t v = s_v;
-            const int64_t o0 = a.off[v], o1 = a.off[v + 1];
-            const uint32_t D = (uint32_t)(o1 - o0);
-            const uint32_t b = cap_bits(D << a.tshift);
-            const uint32_t p1 = cap_of_bits(b);
-            clear_table_vec(Hk, Hv, p1, threadIdx.x, TPB);
-            __syncthreads();
-            const int32_t cur = a.C[v];
-            unsigned long long best = 0;
-            constexpr int U = TPB >= 1024 ? 2 : 1;         // loads in flight per thread
-            scan_row<32, true, false, U>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, Hk, Hv, 1,
-                                         p1, b, best, fb, nullptr, nullptr, TPB * U);
-            best = group_max<32>(best);
-            if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-            __syncthreads();
-            best = 0;
-#pragma unroll
-            for (int w = 0; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
-            int32_t cstar = -1;
-            const bool moved = decide(best, cur, a.pl, cstar);
-            if (moved) {
-                if (threadIdx.x == 0) {
-                    if (a.async_mode) {
-                        a.C[v] = cstar;
-                        __threadfence();
-                    } else {
-                        const unsigned long long pos = atomicAdd(a.mover_count, 1ull);
-                        a.mover_v[pos] = v;
-                        a.mover_c[pos] = cstar;
-                    }
-                }
-                if (a.async_mode) __syncthreads();
-                for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
-            }
-            if (threadIdx.x == 0) {
-                c_act += 1;
-                c_edges += D;
-                if (moved) {
-                    c_moved += 1;
-                    c_marks += D;
-                }
-            }
-        }
+    using Tab = typename TableFor<V, kPackShared>::type;
+    Tab tab;
+    table_at(tab, smem, 1, k.slots, 0, false);
+    __shared__ int s_item, s_nmov;
+    __shared__ int32_t s_mv[32];
+    __shared__ int64_t s_mo0[32], s_mo1[32];
+    __shared__ int2 s_mov[32];
+    __shared__ unsigned long long s_best[TPB / 32], s_mbase;
+    if (threadIdx.x == 0) s_nmov = 0;
+    // counters (thread 0) are kept while consecutive items belong to one graph
+    int cur_g = -1;
+    SweepView a{};
+    unsigned fb = 0;
+    unsigned long long c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
+    auto flush_counts = [&]() {
         if (threadIdx.x == 0) {
             unsigned long long *c = a.ctr + k.kslot * kCtrFields;
             if (c_act) atomicAdd(c + CTR_ACTIVE, c_act);
@@ -546,7 +702,101 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
             if (c_marks) atomicAdd(c + CTR_MARKS, c_marks);
         }
         if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
+        fb = 0;
+        c_act = c_edges = c_moved = c_marks = 0;
+    };
+    for (;;) {
+        __syncthreads();                               // s_item and s_best of the last round are consumed
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(k.queue, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= k.n_items) break;
+        const WorkItem item = k.items[it];
+        if (item.g != cur_g) {
+            if (cur_g >= 0) flush_counts();
+            cur_g = item.g;
+            a = view_of(k.gd, item.g);
+        }
+        if (a.done) continue;
+        for (int64_t base = 0; base < item.count; base += 32) {
+            __syncthreads();                           // the previous batch is finished
+            if (threadIdx.x < 32 && base + threadIdx.x < item.count) {
+                int32_t v0 = __ldg(a.lists + item.start + base + threadIdx.x);
+                int64_t m0 = 0, m1 = 0;
+                if (a.flag_cur[v0] != 0) {
+                    a.flag_cur[v0] = 0;                // mark processed
+                    m0 = a.off[v0];
+                    m1 = a.off[v0 + 1];
+                } else {
+                    v0 = -1;
+                }
+                s_mv[threadIdx.x] = v0;
+                s_mo0[threadIdx.x] = m0;
+                s_mo1[threadIdx.x] = m1;
+            }
+            __syncthreads();
+            const int nb = (int)(item.count - base < 32 ? item.count - base : 32);
+            for (int q = 0; q < nb; ++q) {
+                const int32_t v = s_mv[q];
+                if (v < 0) continue;                   // uniform for the block
+                const int64_t o0 = s_mo0[q], o1 = s_mo1[q];
+                const uint32_t D = (uint32_t)(o1 - o0);
+                const uint32_t b = cap_bits(D << a.tshift);
+                const uint32_t p1 = cap_of_bits(b);
+                const int32_t cur = a.C[v];
+                __syncthreads();                       // the previous vertex is finished
+                clear_table_vec(tab, p1, threadIdx.x, TPB);
+                __syncthreads();
+                unsigned long long best = 0;
+                constexpr int U = TPB >= 1024 ? 2 : 1;     // loads in flight per thread
+                scan_row<32, true, false, U>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, tab, p1,
+                                             b, best, fb, nullptr, nullptr, TPB * U);
+                best = group_max<32>(best);
+                if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+                __syncthreads();
+                best = 0;
+#pragma unroll
+                for (int w = 0; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
+                int32_t cstar = -1;
+                const bool moved = decide(best, cur, a.pl, cstar);
+                if (moved) {
+                    if (threadIdx.x == 0) {
+                        if (a.async_mode) {
+                            a.C[v] = cstar;
+                            __threadfence();
+                        } else {
+                            s_mov[s_nmov++] = make_int2(v, cstar);     // at most 32 per batch
+                        }
+                    }
+                    if (a.async_mode) __syncthreads();
+                    for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
+                }
+                if (threadIdx.x == 0) {
+                    c_act += 1;
+                    c_edges += D;
+                    if (moved) {
+                        c_moved += 1;
+                        c_marks += D;
+                    }
+                }
+            }
+            // append the batch's synchronous movers with one atomic
+            __syncthreads();
+            const int nm = s_nmov;
+            if (nm > 0) {
+                if (threadIdx.x == 0) s_mbase = atomicAdd(a.mover_count, (unsigned long long)nm);
+                __syncthreads();
+                if (threadIdx.x < nm) {
+                    const int2 m = s_mov[threadIdx.x];
+                    a.mover_v[s_mbase + threadIdx.x] = m.x;
+                    a.mover_c[s_mbase + threadIdx.x] = m.y;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) s_nmov = 0;
+            }
+        }
     }
+    if (cur_g >= 0) flush_counts();
 }
 
 // ---------------------------------------------------------------------------------
@@ -581,8 +831,35 @@ __global__ void k_hub_begin(HArgs k)
 }
 
 // Slots taken from empty are collected in a block-local list in shared memory and copied to
-// the hub's used list with one global atomic per block.
-template <int TPB, typename V>
+// the hub's used list with one global atomic per block.  A graph with integer sums keeps its
+// hub tables in the packed layout, any other graph in the split float layout.
+template <int TPB, typename T>
+__device__ __forceinline__ void hub_accumulate(const SweepView &a, const HubArgs &h, int hh, int64_t c, const T &tab,
+                                               int32_t *s_list, uint32_t &s_cnt, uint32_t &s_base,
+                                               unsigned long long *s_best)
+{
+    const int32_t v = h.hub_v[hh];
+    const uint32_t p1 = h.hub_p1[hh], b = h.hub_b[hh];
+    const int64_t e0 = h.chunk_e0[c], e1 = h.chunk_e1[c];
+    unsigned fb = 0;
+    unsigned long long best = 0;
+    scan_row<32, true, true, 2>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab, p1, b, best, fb,
+                                &s_cnt, s_list, TPB * 2);
+    if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
+    best = group_max<32>(best);
+    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
+        if (best) atomicMax(h.hub_best + hh, best);
+        s_base = s_cnt ? atomicAdd(h.hub_used + hh, s_cnt) : 0u;
+    }
+    __syncthreads();
+    int32_t *ulist = h.used_list + h.used_base[hh] + s_base;
+    for (uint32_t q = threadIdx.x; q < s_cnt; q += TPB) ulist[q] = s_list[q];
+}
+
+template <int TPB>
 __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
 {
     if (*k.active == 0) return;
@@ -599,27 +876,13 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
     if (!h.hub_act[hh]) return;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    const int32_t v = h.hub_v[hh];
-    const uint32_t p1 = h.hub_p1[hh], b = h.hub_b[hh];
-    int32_t *Hk = h.tab_k + h.hub_tab[hh];
-    V *Hv = reinterpret_cast<V *>(h.tab_v) + h.hub_tab[hh];
-    const int64_t e0 = h.chunk_e0[c], e1 = h.chunk_e1[c];
-    unsigned fb = 0;
-    unsigned long long best = 0;
-    scan_row<32, true, true, 2>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, Hk, Hv, 1, p1, b,
-                                best, fb, &s_cnt, s_list, TPB * 2);
-    if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
-    best = group_max<32>(best);
-    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
-        if (best) atomicMax(h.hub_best + hh, best);
-        s_base = s_cnt ? atomicAdd(h.hub_used + hh, s_cnt) : 0u;
+    if (k.gd[item.g].int_weights) {
+        PackedTable tab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1};
+        hub_accumulate<TPB>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
+    } else {
+        SplitTable<float> tab{h.tab_k + h.hub_tab[hh], h.tab_v + h.hub_tab[hh], 1};
+        hub_accumulate<TPB>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
     }
-    __syncthreads();
-    int32_t *ulist = h.used_list + h.used_base[hh] + s_base;
-    for (uint32_t q = threadIdx.x; q < s_cnt; q += TPB) ulist[q] = s_list[q];
 }
 
 // Clears the table slots a hub used in this sweep: slot by slot from the used list when
@@ -634,28 +897,31 @@ __global__ void __launch_bounds__(TPB) k_hub_clear(HArgs k)
     const HubArgs &h = k.gd[item.g].hub;
     const int hh = h.slice_h[item.start];
     if (!h.hub_act[hh]) return;
+    const bool packed = k.gd[item.g].int_weights != 0;
     const int64_t lo = (int64_t)h.slice_j[item.start] * kHubSlice;
     const int64_t cnt = h.hub_used[hh];
     const int64_t p1 = h.hub_p1[hh];
     int32_t *Hk = h.tab_k + h.hub_tab[hh];
     float *Hv = h.tab_v + h.hub_tab[hh];
-    if (cnt * 8 > p1) {
-        if (lo >= p1) return;
-        const int64_t hi = lo + kHubSlice < p1 ? lo + kHubSlice : p1;
-        for (int64_t q = lo + threadIdx.x; q < hi; q += TPB) {
+    unsigned long long *H = (unsigned long long *)h.tab_k + h.hub_tab[hh];
+    auto clear = [&](int64_t q) {
+        if (packed) {
+            H[q] = kEmptySlot;
+        } else {
             Hk[q] = kEmpty;
             Hv[q] = 0.0f;
         }
+    };
+    if (cnt * 8 > p1) {
+        if (lo >= p1) return;
+        const int64_t hi = lo + kHubSlice < p1 ? lo + kHubSlice : p1;
+        for (int64_t q = lo + threadIdx.x; q < hi; q += TPB) clear(q);
         return;
     }
     if (lo >= cnt) return;
     const int64_t hi = lo + kHubSlice < cnt ? lo + kHubSlice : cnt;
     const int32_t *ulist = h.used_list + h.used_base[hh];
-    for (int64_t q = lo + threadIdx.x; q < hi; q += TPB) {
-        const int32_t s = ulist[q];
-        Hk[s] = kEmpty;                                // leave the table clear for the next sweep
-        Hv[s] = 0.0f;
-    }
+    for (int64_t q = lo + threadIdx.x; q < hi; q += TPB) clear(ulist[q]);    // leave the table clear
 }
 
 __global__ void k_hub_move(HArgs k)
@@ -751,11 +1017,17 @@ __global__ void k_decide(const GraphDev *gd, int n_graphs, int32_t *active)
     if (!done) atomicAdd(active, 1);
 }
 
-__global__ void k_table_clear(int32_t *k, float *v, int64_t n)
+// Initial clear of all hub tables of a graph: `n` slots in the packed or the split layout.
+__global__ void k_table_clear(int32_t *k, float *v, int64_t n, int packed)
 {
+    unsigned long long *h = (unsigned long long *)k;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        k[i] = kEmpty;
-        v[i] = 0.0f;
+        if (packed) {
+            h[i] = kEmptySlot;
+        } else {
+            k[i] = kEmpty;
+            v[i] = 0.0f;
+        }
     }
 }
 
@@ -906,15 +1178,9 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
         h.items = p.hub_chunks;
         e = timed(LPA_K_HUB_ACC, [&] {
             const size_t smem = (size_t)p.hub_chunk * sizeof(int32_t);
-            if (p.int_weights) {
-                cudaError_t r = set_smem(k_hub_acc<1024, uint32_t>, smem);
-                if (r != cudaSuccess) return r;
-                k_hub_acc<1024, uint32_t><<<p.n_hub_chunks, 1024, smem, s>>>(h);
-            } else {
-                cudaError_t r = set_smem(k_hub_acc<1024, float>, smem);
-                if (r != cudaSuccess) return r;
-                k_hub_acc<1024, float><<<p.n_hub_chunks, 1024, smem, s>>>(h);
-            }
+            cudaError_t r = set_smem(k_hub_acc<1024>, smem);
+            if (r != cudaSuccess) return r;
+            k_hub_acc<1024><<<p.n_hub_chunks, 1024, smem, s>>>(h);
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
@@ -951,14 +1217,14 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, cudaStream_t s)
+cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, bool packed, cudaStream_t s)
 {
     if (slots <= 0) return cudaSuccess;
     query_device();
     int64_t blocks = (slots + 255) / 256;
     const int64_t cap = (int64_t)g_num_sms * 16;
     if (blocks > cap) blocks = cap;
-    k_table_clear<<<(unsigned)blocks, 256, 0, s>>>(k, v, slots);
+    k_table_clear<<<(unsigned)blocks, 256, 0, s>>>(k, v, slots, packed ? 1 : 0);
     return cudaGetLastError();
 }
 
