@@ -598,7 +598,7 @@ lpa_tuning default_tuning()
     t.cta_max = 1023;
     t.cta_threads = 128;
     t.cta_large_max = 4095;
-    t.cta_large_threads = 256;
+    t.cta_large_threads = 512;
     t.cta_xl_max = 8191;
     t.cta_xl_threads = 1024;
     t.item_vertices = 0;
@@ -784,7 +784,7 @@ int build_buckets(lpa_graph *g)
         const size_t n8 = (size_t)(3 * H + 2 * n_chunks);
         const size_t n4 = (size_t)(4 * H + n_chunks + 2 * n_slices);
         unsigned char *mem = nullptr;
-        LPA_CHECK(dalloc(g, &mem, n8 * 8 + n4 * 4 + (size_t)H));
+        LPA_CHECK(dalloc(g, &mem, n8 * 8 + n4 * 4 + 2 * (size_t)H));
         g->hub_mem = mem;
         unsigned char *p = mem;
         auto take = [&](size_t b) {
@@ -805,6 +805,7 @@ int build_buckets(lpa_graph *g)
         int32_t *d_sh = (int32_t *)take(n_slices * 4);
         int32_t *d_sj = (int32_t *)take(n_slices * 4);
         uint8_t *d_act = (uint8_t *)take(H);
+        uint8_t *d_seen = (uint8_t *)take(H);
         LPA_CUDA(cudaMemcpyAsync(d_tab, tab.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
         LPA_CUDA(cudaMemcpyAsync(d_ubase, ubase.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
         LPA_CUDA(cudaMemcpyAsync(d_ce0, ce0.data(), n_chunks * 8, cudaMemcpyHostToDevice, g->stream));
@@ -815,7 +816,7 @@ int build_buckets(lpa_graph *g)
         LPA_CUDA(cudaMemcpyAsync(d_ch, ch.data(), n_chunks * 4, cudaMemcpyHostToDevice, g->stream));
         LPA_CUDA(cudaMemcpyAsync(d_sh, sh.data(), n_slices * 4, cudaMemcpyHostToDevice, g->stream));
         LPA_CUDA(cudaMemcpyAsync(d_sj, sj.data(), n_slices * 4, cudaMemcpyHostToDevice, g->stream));
-        LPA_CUDA(cudaMemsetAsync(d_act, 0, H, g->stream));
+        LPA_CUDA(cudaMemsetAsync(d_act, 0, 2 * H, g->stream));     // hub_act and hub_seen
         LPA_CUDA(cudaMemsetAsync(d_best, 0, H * 8, g->stream));
         LPA_CUDA(cudaMemsetAsync(d_used, 0, H * 4, g->stream));
         // 8 bytes per slot in one block: split keys then values, or packed 64-bit slots
@@ -828,6 +829,7 @@ int build_buckets(lpa_graph *g)
         ha.hub_b = d_b;
         ha.hub_tab = d_tab;
         ha.hub_act = d_act;
+        ha.hub_seen = d_seen;
         ha.hub_best = d_best;
         ha.hub_used = d_used;
         ha.used_list = g->used_list;
@@ -986,6 +988,7 @@ int upload_descriptor(lpa_graph *g)
     d.flags0 = g->flags[0];
     d.flags1 = g->flags[1];
     d.mover_v = g->mover_v;
+    d.mover_v1 = g->mover_v1;
     d.mover_c = g->mover_c;
     d.mover_count = g->mover_count;
     d.ctr = g->ctr;
@@ -1060,14 +1063,15 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
     if ((st = dalloc(g, &g->flags[0], (size_t)n)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->flags[1], (size_t)n)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->mover_v, (size_t)n)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->mover_v1, (size_t)n)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->mover_c, (size_t)n)) != LPA_OK) return fail(st);
-    if ((st = dalloc(g, &g->mover_count, 1)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->mover_count, 2)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->fallbacks, 1)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->d_err, 4)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->macc, 4)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->gdd, 1)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->rs_d, 1)) != LPA_OK) return fail(st);
-    if ((st = dalloc(g, &g->queues, B_COUNT)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->queues, 2 * B_COUNT)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->active, 1)) != LPA_OK) return fail(st);
     if ((st = ensure_counters(g, 1, false)) != LPA_OK) return fail(st);
 
@@ -1415,7 +1419,7 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
     LPA_CHECK(upload_descriptor(g));
     LPA_CUDA(cudaMemsetAsync(g->ctr, 0, (size_t)kPerSweep * span * sizeof(unsigned long long), s));
     LPA_CUDA(cudaMemsetAsync(g->fallbacks, 0, sizeof(unsigned long long), s));
-    LPA_CUDA(cudaMemsetAsync(g->mover_count, 0, sizeof(unsigned long long), s));
+    LPA_CUDA(cudaMemsetAsync(g->mover_count, 0, 2 * sizeof(unsigned long long), s));
     // the unprocessed flags of sweep `start` must sit where the kernels read them
     const int target = async_mode ? 0 : (start & 1);
     if (g->active_buf != target)
@@ -1429,6 +1433,9 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
     rs.max_iters = max_iters;
     rs.pl_period = pl_period;
     rs.async_mode = async_mode ? 1 : 0;
+    // a fresh synchronous run starts without marks (the first sweep moves most vertices); a
+    // resumed run starts from its processed flags
+    rs.mark = (async_mode || (mode & LPA_RESUME)) ? 1 : 0;
     rs.tol = tolerance;
     rs.n = g->n;
     g->hm->active = 1;
@@ -1477,6 +1484,7 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
         hook.iter = ran;
         hook.on = timing && ran < LPA_STATS_MAX_ITERS;
         LPA_CUDA(cudaEventRecord(g->events[ie0], s));
+        p.pull_mode = g->hm->rs.pull ? 1 : 0;           // the state read back after the last sweep
         LPA_CUDA(enqueue_sweep(p, s, &hook, &launches));
         LPA_CUDA(cudaEventRecord(g->events[ie1], s));
         iter_ev.push_back({ie0, ie1});

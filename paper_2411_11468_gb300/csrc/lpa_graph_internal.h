@@ -19,8 +19,8 @@ struct lpa_graph {
     int32_t *C = nullptr;
     uint8_t *flags[2] = {nullptr, nullptr};
     int active_buf = 0;                              // flags[active_buf]: unprocessed flags of the next sweep
-    int32_t *mover_v = nullptr, *mover_c = nullptr;
-    unsigned long long *mover_count = nullptr;
+    int32_t *mover_v = nullptr, *mover_v1 = nullptr, *mover_c = nullptr;
+    unsigned long long *mover_count = nullptr;       // [2]
     unsigned long long *fallbacks = nullptr;
     unsigned long long *ctr = nullptr;               // [ctr_iters][kPerSweep]
     int ctr_iters = 0;

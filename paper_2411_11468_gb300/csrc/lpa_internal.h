@@ -29,11 +29,20 @@ struct RunState {
     int32_t async_mode;
     int32_t done;         // the run has stopped (tolerance or cap); no more work for this graph
     int32_t converged;    // stopped by the tolerance test
-    int32_t pad;
+    int32_t mark;         // this sweep marks the neighbours of its movers (else movers get the moved bit)
     double tol;
     int64_t n;            // vertices (dN / n)
     int64_t last_dn;
+    int32_t pull;         // this sweep takes activity from the previous sweep's moved bits
+    int32_t fin;          // stopped after a sweep that set moved bits: k_finalize turns them into marks
 };
+
+// Synchronous mode, sweeps that move many vertices: instead of marking the neighbours of each
+// mover, the mover's label word gets bit 31 (labels are below 2^31), and the next sweep
+// processes every vertex and takes as active those with a neighbour whose bit is set: the
+// same active set as the marks give (a vertex is active iff a neighbour moved).
+constexpr uint32_t kMovedBit = 0x80000000u;
+constexpr uint32_t kLabelMask = 0x7FFFFFFFu;
 
 // Hub-bucket device arrays of one graph.
 struct HubArgs {
@@ -42,6 +51,7 @@ struct HubArgs {
     const uint32_t *hub_b;     // [H] b
     const int64_t *hub_tab;    // [H] first slot of the hub's table
     uint8_t *hub_act;          // [H] this sweep: 0 processed earlier, 1 processing, 2 moved
+    uint8_t *hub_seen;         // [H] pull sweeps: a neighbour's moved bit was seen
     unsigned long long *hub_best;  // [H] packed (weight, ~label) maximum
     uint32_t *hub_used;        // [H] number of table slots taken this sweep
     int32_t *used_list;        // slots taken, hub h at used_base[h] (at most D_h entries)
@@ -66,9 +76,10 @@ struct GraphDev {
     const float *w;            // CSR weights [m] or nullptr (unit)
     int32_t *C;                // labels [n]
     uint8_t *flags0, *flags1;  // processed flags; sweep l reads flags[l & 1] (sync) or flags0 (async)
-    int32_t *mover_v;          // sync: vertices that moved this sweep
-    int32_t *mover_c;          // sync: their new labels
-    unsigned long long *mover_count;
+    int32_t *mover_v;          // sync: vertices that moved in an even sweep
+    int32_t *mover_v1;         // sync: vertices that moved in an odd sweep
+    int32_t *mover_c;          // sync: new labels of this sweep's movers
+    unsigned long long *mover_count;   // [2]: movers of the even / odd sweep
     unsigned long long *ctr;   // [ctr_iters][kPerSweep] per-sweep counters of this run
     unsigned long long *fallbacks;
     const int32_t *lists;      // degree-bucket vertex lists
@@ -105,10 +116,10 @@ struct SweepPlan {
     const WorkItem *hub_slices;        // one item per hub clear slice
     int32_t n_hub_slices;
     const WorkItem *per_graph;         // one item per graph (apply, decide)
-    unsigned *queues;          // [B_COUNT] work-queue counters, zeroed before each sweep
+    unsigned *queues;          // [2 * B_COUNT] work-queue counters (push, pull launches), zeroed per sweep
     int32_t *active_count;     // device counter written by k_decide (graphs still running)
     int32_t group_lanes, cta_threads, cta_large_threads, cta_xl_threads, hub_chunk;
-    int32_t persist_mask;
+    int32_t pull_mode;         // kernels launched for this sweep: 0 push only, 1 pull only, 2 both
     int32_t int_weights;       // 1: every graph of the plan uses uint32 sums (else float32)
 };
 

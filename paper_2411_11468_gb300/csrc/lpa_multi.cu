@@ -37,7 +37,8 @@ __global__ void k_init_multi(const GraphDev *gd)
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < words; q += (int64_t)gridDim.x * blockDim.x)
         G.ctr[q] = 0ull;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *G.mover_count = 0ull;
+        G.mover_count[0] = 0ull;
+        G.mover_count[1] = 0ull;
         *G.fallbacks = 0ull;
     }
 }
@@ -119,7 +120,7 @@ struct MultiPlan {
         LPA_CHECK(grow(&gd, &gd_cap, n));
         LPA_CHECK(grow(&rs, &rs_cap, n));
         LPA_CHECK(ensure_host(n));
-        if (!queues && cudaMalloc((void **)&queues, sizeof(unsigned) * B_COUNT) != cudaSuccess) {
+        if (!queues && cudaMalloc((void **)&queues, sizeof(unsigned) * 2 * B_COUNT) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaMalloc failed");
             return LPA_ENOMEM;
@@ -217,6 +218,7 @@ RunState fresh_state(int64_t n, double tol, int max_iters, int pl_period, bool a
     r.max_iters = max_iters;
     r.pl_period = pl_period;
     r.async_mode = async_mode ? 1 : 0;
+    r.mark = async_mode ? 1 : 0;                    // see lpa_run: a fresh synchronous run starts without marks
     r.tol = tol;
     r.n = n;
     r.done = (n == 0 || max_iters <= 0) ? 1 : 0;
@@ -248,7 +250,7 @@ lpa_tuning multi_tuning()
     t.cta_max = 1023;
     t.cta_threads = 128;
     t.cta_large_max = 4095;
-    t.cta_large_threads = 256;
+    t.cta_large_threads = 512;
     t.cta_xl_max = 8191;
     t.cta_xl_threads = 1024;
     t.hub_chunk = 16384;
@@ -389,7 +391,14 @@ int lpa_batch_run(lpa_batch *b, double tolerance, int max_iters, int pl_period, 
         cudaGraph_t graph = nullptr;
         LPA_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
         cudaError_t e = cudaSuccess;
-        for (int it = 0; it < span && e == cudaSuccess; ++it) e = enqueue_sweep(b->mp.plan, b->stream, nullptr, nullptr);
+        // Every run of a batch starts fresh at sweep 0, and only sweep 1 of a fresh synchronous
+        // run takes its active vertices from moved bits: that sweep launches both kernel
+        // variants (asynchronous runs replay the same recording and use the push variant).
+        for (int it = 0; it < span && e == cudaSuccess; ++it) {
+            SweepPlan p = b->mp.plan;
+            p.pull_mode = it == 1 ? 2 : 0;
+            e = enqueue_sweep(p, b->stream, nullptr, nullptr);
+        }
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
         if (e != cudaSuccess || e2 != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -709,8 +718,13 @@ int lpa_server_step(lpa_server *s, int *n_completed, int *n_running, int *n_queu
             LPA_CHECK(s->mp.build(gs, s->tuning));
             s->dirty = false;
         }
-        for (size_t i = 0; i < n; ++i) s->mp.rs_h[i] = s->running[i]->rs;
+        bool any_pull = false, any_push = false;
+        for (size_t i = 0; i < n; ++i) {
+            s->mp.rs_h[i] = s->running[i]->rs;
+            (s->running[i]->rs.pull ? any_pull : any_push) = true;
+        }
         LPA_CHECK(s->mp.upload_states(n));
+        s->mp.plan.pull_mode = any_pull ? (any_push ? 2 : 1) : 0;
         LPA_CUDA(enqueue_sweep(s->mp.plan, s->stream, nullptr, nullptr));
         LPA_CHECK(s->mp.download_states(n));
         std::vector<Request *> still;

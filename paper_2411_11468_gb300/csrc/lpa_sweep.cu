@@ -322,6 +322,7 @@ struct SweepView {
     unsigned long long *fallbacks;
     const int32_t *lists;
     int32_t pl, async_mode, tshift, done;
+    int32_t mark, pull;        // marks written this sweep; activity from moved bits (sync)
 };
 
 __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
@@ -344,9 +345,11 @@ __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
         v.flag_cur = (l & 1) ? G.flags1 : G.flags0;
         v.flag_next = (l & 1) ? G.flags0 : G.flags1;
     }
-    v.mover_v = G.mover_v;
+    v.mover_v = (l & 1) ? G.mover_v1 : G.mover_v;
     v.mover_c = G.mover_c;
-    v.mover_count = G.mover_count;
+    v.mover_count = G.mover_count + (l & 1);
+    v.mark = rs->mark;
+    v.pull = rs->pull;
     const int slot = (l - rs->first) % (G.ctr_iters > 0 ? G.ctr_iters : 1);
     v.ctr = G.ctr + (size_t)(slot < 0 ? 0 : slot) * kPerSweep;
     v.fallbacks = G.fallbacks;
@@ -387,20 +390,30 @@ __device__ __forceinline__ void movers_push(const SweepView &a, int2 *sbuf, int 
 }
 
 // Loads entry e of the row of v: (label of the neighbour, weight); has = false for e past
-// the row end and for self-loops (Algorithm 1 skips j = i).
-template <typename V>
+// the row end and for self-loops (Algorithm 1 skips j = i).  With SEEN (pull sweeps) the raw
+// label words are or-ed into `seen` (bit 31: the neighbour moved in the previous sweep),
+// self-loops included; push sweeps never see the bit and skip that work.
+template <bool SEEN, typename V>
 __device__ __forceinline__ void load_entry(const SweepView &a, int32_t v, int64_t e, int64_t end, bool &has,
-                                           int32_t &k, V &wv)
+                                           int32_t &k, V &wv, uint32_t &seen)
 {
     has = e < end;
     k = 0;
     wv = V(0);
     if (has) {
         const int32_t j = a.idx[e];
-        has = (j != v);
-        if (has) {
-            k = a.C[j];
-            wv = a.w ? to_value<V>(a.w[e]) : V(1);
+        if (SEEN) {
+            const uint32_t cj = (uint32_t)a.C[j];
+            seen |= cj;
+            has = (j != v);
+            k = (int32_t)(cj & kLabelMask);
+            if (has) wv = a.w ? to_value<V>(a.w[e]) : V(1);
+        } else {
+            has = (j != v);
+            if (has) {
+                k = a.C[j];
+                wv = a.w ? to_value<V>(a.w[e]) : V(1);
+            }
         }
     }
 }
@@ -408,11 +421,11 @@ __device__ __forceinline__ void load_entry(const SweepView &a, int32_t v, int64_
 // Scans entries [start, end) of the row of v in rounds: each round covers U * step entries,
 // lane offset `lane` inside each step.  All U entries of a round are loaded (index, weight,
 // gathered label) before any of them is inserted, so U gathers per thread are in flight.
-template <int G, bool SHARED, bool TRACK, int U, typename T>
+template <int G, bool SHARED, bool TRACK, int U, bool SEEN, typename T>
 __device__ __forceinline__ void scan_row(const SweepView &a, int32_t v, int64_t start, int64_t end, int step,
                                          int lane, const T &tab, uint32_t p1, uint32_t b,
-                                         unsigned long long &best, unsigned &fb, uint32_t *ucnt = nullptr,
-                                         int32_t *ulist = nullptr, int round = 0)
+                                         unsigned long long &best, unsigned &fb, uint32_t &seen,
+                                         uint32_t *ucnt = nullptr, int32_t *ulist = nullptr, int round = 0)
 {
     using V = typename T::Val;
     const int64_t adv = round ? round : (int64_t)step * U;   // a block-wide round for the CTA kernels
@@ -421,7 +434,7 @@ __device__ __forceinline__ void scan_row(const SweepView &a, int32_t v, int64_t 
         int32_t k[U];
         V wv[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) load_entry(a, v, eb + (int64_t)u * step + lane, end, has[u], k[u], wv[u]);
+        for (int u = 0; u < U; ++u) load_entry<SEEN>(a, v, eb + (int64_t)u * step + lane, end, has[u], k[u], wv[u], seen);
 #pragma unroll
         for (int u = 0; u < U; ++u)
             group_insert<G, SHARED, TRACK>(tab, p1, b, has[u], k[u], wv[u], best, fb, ucnt, ulist);
@@ -528,7 +541,7 @@ template <int G> struct GroupUnroll {
 // at once (one per lane), then its groups take them 32/G at a time: the per-vertex chain of
 // dependent loads (list, flag, offsets) is paid once per 32 vertices.  Neighbour ids of a
 // row that fits one round stay in registers for the marks.
-template <int G, int TPB, typename V>
+template <int G, int TPB, typename V, bool PULL>
 __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs k)
 {
     if (*k.active == 0) return;                        // every graph has stopped
@@ -566,15 +579,20 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
             cur_g = item.g;
             a = view_of(k.gd, item.g);
         }
-        if (a.done) continue;
+        if (a.done || (a.pull != 0) != PULL) continue;                // the other launch takes it
         for (int64_t base = 0; base < item.count; base += 32) {       // uniform per warp
-            // lane L: vertex base + L of the item (its flag is taken here: mark processed)
+            // lane L: vertex base + L of the item (its flag is taken here: mark processed; in a
+            // pull sweep every vertex is a candidate and its activity is known after the scan)
             int32_t mv = -1;
             int64_t mo0 = 0, mo1 = 0;
             if (base + lane_w < item.count) {
                 mv = __ldg(a.lists + item.start + base + lane_w);
-                if (a.flag_cur[mv] != 0) {
+                bool cand = PULL;
+                if (!PULL && a.flag_cur[mv] != 0) {
                     a.flag_cur[mv] = 0;
+                    cand = true;
+                }
+                if (cand) {
                     mo0 = a.off[mv];
                     mo1 = a.off[mv + 1];
                 } else {
@@ -587,14 +605,15 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                 const int32_t v = __shfl_sync(0xFFFFFFFFu, mv, src);
                 const int64_t o0 = __shfl_sync(0xFFFFFFFFu, mo0, src);
                 const int64_t o1 = __shfl_sync(0xFFFFFFFFu, mo1, src);
-                const bool act = v >= 0 && o1 > o0;
+                const bool cand = v >= 0 && o1 > o0;
                 int32_t cstar = -1;
                 bool moved = false;
-                if (act) {
+                if (cand) {
                     const uint32_t D = (uint32_t)(o1 - o0);
                     const uint32_t b = cap_bits(D << a.tshift);    // capacity >= D << tshift
                     const uint32_t p1 = cap_of_bits(b);
-                    const int32_t cur = a.C[v];
+                    const int32_t cur = PULL ? (int32_t)((uint32_t)a.C[v] & kLabelMask) : a.C[v];
+                    uint32_t seen = 0;
                     if (G == 1) {
                         clear_table_private(tab, p1);              // hashtableClear
                     } else {
@@ -618,9 +637,16 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                             wv[u] = (has[u] && a.w) ? to_value<V>(a.w[e]) : V(1);
                         }
 #pragma unroll
-                        for (int u = 0; u < U; ++u) {              // labels (self-loops skipped)
-                            has[u] = has[u] && jr[u] != v;
-                            kk[u] = has[u] ? a.C[jr[u]] : 0;
+                        for (int u = 0; u < U; ++u) {              // labels (self-loops not inserted)
+                            if (PULL) {
+                                const uint32_t cj = has[u] ? (uint32_t)a.C[jr[u]] : 0u;
+                                seen |= cj;
+                                has[u] = has[u] && jr[u] != v;
+                                kk[u] = (int32_t)(cj & kLabelMask);
+                            } else {
+                                has[u] = has[u] && jr[u] != v;
+                                kk[u] = has[u] ? a.C[jr[u]] : 0;
+                            }
                         }
                         // inserts one slot at a time (rolled loop, entries shifted down in
                         // registers) so that the probe loop is not replicated U times
@@ -638,13 +664,19 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                         }
                     }
                     best = group_max<G>(best);                     // hashtableMaxKey
-                    moved = decide(best, cur, a.pl, cstar);
+                    bool act = true;
+                    if (PULL) {                                    // a neighbour moved in the last sweep
+                        if (G > 1) seen = __reduce_or_sync(group_mask<G>(), seen);
+                        act = (seen & kMovedBit) != 0;
+                    }
+                    moved = act && decide(best, cur, a.pl, cstar);
                     if (moved) {
                         if (a.async_mode && lane == 0) {
                             a.C[v] = cstar;
                             __threadfence();
                         }
-                        if (D <= (uint32_t)(U * G)) {              // mark neighbours (ids in registers)
+                        if (!a.mark) {
+                        } else if (D <= (uint32_t)(U * G)) {       // mark neighbours (ids in registers)
 #pragma unroll
                             for (int u = 0; u < U; ++u)
                                 if (jr[u] >= 0) a.flag_next[jr[u]] = 1;
@@ -652,12 +684,12 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                             for (int64_t e = o0 + lane; e < o1; e += G) a.flag_next[a.idx[e]] = 1;
                         }
                     }
-                    if (lane == 0) {
+                    if (lane == 0 && act) {
                         c_act += 1;
                         c_edges += D;
                         if (moved) {
                             c_moved += 1;
-                            c_marks += D;
+                            if (a.mark) c_marks += D;
                         }
                     }
                 }
@@ -674,7 +706,7 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
 // One thread block per vertex; the table (up to k.slots entries) lives in dynamic smem.
 // Persistent: each block takes work items from the queue; the list entries, processed flags
 // and row bounds of up to 32 vertices of the item are fetched at once into shared memory.
-template <int TPB, typename V>
+template <int TPB, typename V, bool PULL>
 __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
 {
     if (*k.active == 0) return;
@@ -717,14 +749,18 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
             cur_g = item.g;
             a = view_of(k.gd, item.g);
         }
-        if (a.done) continue;
+        if (a.done || (a.pull != 0) != PULL) continue;        // the other launch takes it
         for (int64_t base = 0; base < item.count; base += 32) {
             __syncthreads();                           // the previous batch is finished
             if (threadIdx.x < 32 && base + threadIdx.x < item.count) {
                 int32_t v0 = __ldg(a.lists + item.start + base + threadIdx.x);
                 int64_t m0 = 0, m1 = 0;
-                if (a.flag_cur[v0] != 0) {
+                bool cand = PULL;                      // pull sweep: activity known after the scan
+                if (!PULL && a.flag_cur[v0] != 0) {
                     a.flag_cur[v0] = 0;                // mark processed
+                    cand = true;
+                }
+                if (cand) {
                     m0 = a.off[v0];
                     m1 = a.off[v0 + 1];
                 } else {
@@ -743,22 +779,25 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
                 const uint32_t D = (uint32_t)(o1 - o0);
                 const uint32_t b = cap_bits(D << a.tshift);
                 const uint32_t p1 = cap_of_bits(b);
-                const int32_t cur = a.C[v];
+                const int32_t cur = PULL ? (int32_t)((uint32_t)a.C[v] & kLabelMask) : a.C[v];
                 __syncthreads();                       // the previous vertex is finished
                 clear_table_vec(tab, p1, threadIdx.x, TPB);
                 __syncthreads();
                 unsigned long long best = 0;
+                uint32_t seen = 0;
                 constexpr int U = TPB >= 1024 ? 2 : 1;     // loads in flight per thread
-                scan_row<32, true, false, U>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, tab, p1,
-                                             b, best, fb, nullptr, nullptr, TPB * U);
+                scan_row<32, true, false, U, PULL>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, tab,
+                                                   p1, b, best, fb, seen, nullptr, nullptr, TPB * U);
                 best = group_max<32>(best);
                 if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-                __syncthreads();
+                bool act = true;
+                if (PULL) act = __syncthreads_or((seen & kMovedBit) != 0) != 0;   // a neighbour moved
+                else __syncthreads();
                 best = 0;
 #pragma unroll
                 for (int w = 0; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
                 int32_t cstar = -1;
-                const bool moved = decide(best, cur, a.pl, cstar);
+                const bool moved = act && decide(best, cur, a.pl, cstar);
                 if (moved) {
                     if (threadIdx.x == 0) {
                         if (a.async_mode) {
@@ -769,14 +808,15 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
                         }
                     }
                     if (a.async_mode) __syncthreads();
-                    for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
+                    if (a.mark)
+                        for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
                 }
-                if (threadIdx.x == 0) {
+                if (threadIdx.x == 0 && act) {
                     c_act += 1;
                     c_edges += D;
                     if (moved) {
                         c_moved += 1;
-                        c_marks += D;
+                        if (a.mark) c_marks += D;
                     }
                 }
             }
@@ -822,9 +862,13 @@ __global__ void k_hub_begin(HArgs k)
     const HubArgs &h = k.gd[item.g].hub;
     for (int64_t t = item.start + threadIdx.x; t < item.start + item.count; t += blockDim.x) {
         const int32_t v = h.hub_v[t];
-        const uint8_t act = a.flag_cur[v] != 0;
-        if (act) a.flag_cur[v] = 0;                   // mark processed
+        uint8_t act = 1;                              // pull sweep: every hub is a candidate
+        if (!a.pull) {
+            act = a.flag_cur[v] != 0;
+            if (act) a.flag_cur[v] = 0;               // mark processed
+        }
         h.hub_act[t] = act;
+        h.hub_seen[t] = 0;
         h.hub_best[t] = 0ull;
         h.hub_used[t] = 0u;
     }
@@ -833,7 +877,7 @@ __global__ void k_hub_begin(HArgs k)
 // Slots taken from empty are collected in a block-local list in shared memory and copied to
 // the hub's used list with one global atomic per block.  A graph with integer sums keeps its
 // hub tables in the packed layout, any other graph in the split float layout.
-template <int TPB, typename T>
+template <int TPB, bool PULL, typename T>
 __device__ __forceinline__ void hub_accumulate(const SweepView &a, const HubArgs &h, int hh, int64_t c, const T &tab,
                                                int32_t *s_list, uint32_t &s_cnt, uint32_t &s_base,
                                                unsigned long long *s_best)
@@ -843,12 +887,17 @@ __device__ __forceinline__ void hub_accumulate(const SweepView &a, const HubArgs
     const int64_t e0 = h.chunk_e0[c], e1 = h.chunk_e1[c];
     unsigned fb = 0;
     unsigned long long best = 0;
-    scan_row<32, true, true, 2>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab, p1, b, best, fb,
-                                &s_cnt, s_list, TPB * 2);
+    uint32_t seen = 0;
+    scan_row<32, true, true, 2, PULL>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab, p1, b, best,
+                                      fb, seen, &s_cnt, s_list, TPB * 2);
     if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
     best = group_max<32>(best);
     if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-    __syncthreads();
+    if (PULL) {
+        if (__syncthreads_or((seen & kMovedBit) != 0) && threadIdx.x == 0) h.hub_seen[hh] = 1;
+    } else {
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         for (int w = 1; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
         if (best) atomicMax(h.hub_best + hh, best);
@@ -859,7 +908,7 @@ __device__ __forceinline__ void hub_accumulate(const SweepView &a, const HubArgs
     for (uint32_t q = threadIdx.x; q < s_cnt; q += TPB) ulist[q] = s_list[q];
 }
 
-template <int TPB>
+template <int TPB, bool PULL>
 __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
 {
     if (*k.active == 0) return;
@@ -869,7 +918,7 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
     __shared__ uint32_t s_cnt, s_base;
     const WorkItem item = k.items[blockIdx.x];
     const SweepView a = view_of(k.gd, item.g);
-    if (a.done) return;
+    if (a.done || (a.pull != 0) != PULL) return;      // the other launch takes it
     const HubArgs &h = k.gd[item.g].hub;
     const int64_t c = item.start;
     const int hh = h.chunk_h[c];
@@ -878,10 +927,10 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
     __syncthreads();
     if (k.gd[item.g].int_weights) {
         PackedTable tab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1};
-        hub_accumulate<TPB>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
+        hub_accumulate<TPB, PULL>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
     } else {
         SplitTable<float> tab{h.tab_k + h.hub_tab[hh], h.tab_v + h.hub_tab[hh], 1};
-        hub_accumulate<TPB>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
+        hub_accumulate<TPB, PULL>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
     }
 }
 
@@ -934,8 +983,9 @@ __global__ void k_hub_move(HArgs k)
     unsigned long long n_act = 0, n_edges = 0, n_moved = 0, n_marks = 0;
     for (int64_t hh = item.start + threadIdx.x; hh < item.start + item.count; hh += blockDim.x) {
         if (!h.hub_act[hh]) continue;
+        if (a.pull && !h.hub_seen[hh]) continue;      // no neighbour moved: not active
         const int32_t v = h.hub_v[hh];
-        const int32_t cur = a.C[v];
+        const int32_t cur = (int32_t)((uint32_t)a.C[v] & kLabelMask);
         int32_t cstar = -1;
         const bool moved = decide(h.hub_best[hh], cur, a.pl, cstar);
         const unsigned long long D = (unsigned long long)(a.off[v + 1] - a.off[v]);
@@ -950,9 +1000,9 @@ __global__ void k_hub_move(HArgs k)
                 a.mover_v[pos] = v;
                 a.mover_c[pos] = cstar;
             }
-            h.hub_act[hh] = 2;
+            if (a.mark) h.hub_act[hh] = 2;          // k_hub_mark marks its neighbours
             n_moved += 1;
-            n_marks += D;
+            if (a.mark) n_marks += D;
         }
     }
     unsigned long long *c = a.ctr + LPA_K_HUB_ACC * kCtrFields;
@@ -976,8 +1026,28 @@ __global__ void __launch_bounds__(TPB) k_hub_mark(HArgs k)
     for (int64_t e = e0 + threadIdx.x; e < e1; e += TPB) a.flag_next[a.idx[e]] = 1;
 }
 
+// Synchronous mode, after a pull sweep: clear the moved bits of the previous sweep's movers
+// (blockIdx.y: graph, blockIdx.x: stride over the list).  Runs before k_apply, which may set
+// the bit again on a vertex that moved in both sweeps.
+__global__ void k_apply_unmark(HArgs k)
+{
+    if (*k.active == 0) return;
+    const WorkItem item = k.items[blockIdx.y];
+    const SweepView a = view_of(k.gd, item.g);
+    if (a.done || a.async_mode || !a.pull) return;
+    const GraphDev &G = k.gd[item.g];
+    const int l = G.rs->l;
+    const int32_t *prev = ((l - 1) & 1) ? G.mover_v1 : G.mover_v;
+    const unsigned long long n = G.mover_count[(l - 1) & 1];
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t v = prev[i];
+        a.C[v] = (int32_t)((uint32_t)a.C[v] & kLabelMask);
+    }
+}
+
 // Synchronous mode: publish the labels recorded during the sweep (blockIdx.y: graph,
-// blockIdx.x: stride over its movers).
+// blockIdx.x: stride over its movers), with the moved bit when this sweep wrote no marks.
 __global__ void k_apply(HArgs k)
 {
     if (*k.active == 0) return;
@@ -985,19 +1055,28 @@ __global__ void k_apply(HArgs k)
     const SweepView a = view_of(k.gd, item.g);
     if (a.done || a.async_mode) return;
     const unsigned long long n = *a.mover_count;
+    const uint32_t bit = a.mark ? 0u : kMovedBit;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x)
-        a.C[a.mover_v[i]] = a.mover_c[i];
+        a.C[a.mover_v[i]] = (int32_t)((uint32_t)a.mover_c[i] | bit);
 }
 
 // After each sweep, per graph: the stop test of Algorithm 1 (after a sweep without Pick-Less,
 // stop when dN / n < tolerance; stop at max_iters), then advance to the next sweep.
+// Synchronous mode: the next sweep pulls its active vertices from moved bits when this sweep
+// wrote no marks.  Only the first sweep of a fresh run skips its marks (it moves most vertices
+// and its marks are the costliest); every later sweep marks, which measured cheaper than
+// processing every vertex in the sweep after it.
+
 __global__ void k_decide(const GraphDev *gd, int n_graphs, int32_t *active)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_graphs) return;
     RunState *rs = gd[g].rs;
-    if (rs->done) return;
+    if (rs->done) {
+        rs->fin = 0;                                  // k_finalize has run once for this graph
+        return;
+    }
     const SweepView a = view_of(gd, g);
     long long dn = 0;
     for (int q = 0; q < LPA_NUM_KERNELS; ++q) dn += (long long)a.ctr[q * kCtrFields + CTR_MOVED];
@@ -1009,12 +1088,42 @@ __global__ void k_decide(const GraphDev *gd, int n_graphs, int32_t *active)
     } else if (l + 1 >= rs->max_iters) {
         done = 1;
     }
+    if (!rs->async_mode) {
+        if (done) {
+            rs->fin = rs->mark ? 0 : 1;               // this sweep's moved bits still stand
+        } else {
+            rs->pull = rs->mark ? 0 : 1;
+            rs->mark = 1;
+        }
+    }
     rs->l = l + 1;
     rs->last_dn = dn;
     rs->done = done;
     rs->converged = conv;
-    *gd[g].mover_count = 0ull;
+    gd[g].mover_count[(l + 1) & 1] = 0ull;           // the next sweep's list; this one stays for k_apply_unmark
     if (!done) atomicAdd(active, 1);
+}
+
+// After the last sweep of a synchronous run that set moved bits: turn them into the marks of
+// the next sweep's processed flags (so the state is that of the marking sweep) and clear them.
+// blockIdx.y: graph; a warp per mover of the last sweep.
+__global__ void k_finalize(const GraphDev *gd)
+{
+    const GraphDev &G = gd[blockIdx.y];
+    const RunState *rs = G.rs;
+    if (!rs->fin) return;
+    const int last = rs->l - 1;
+    const int32_t *mv = (last & 1) ? G.mover_v1 : G.mover_v;
+    const unsigned long long n = G.mover_count[last & 1];
+    uint8_t *flags = (rs->l & 1) ? G.flags1 : G.flags0;      // processed flags of sweep rs->l
+    const int lane = threadIdx.x & 31;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+         i += warps) {
+        const int32_t v = mv[i];
+        if (lane == 0) G.C[v] = (int32_t)((uint32_t)G.C[v] & kLabelMask);
+        for (int64_t e = G.off[v] + lane; e < G.off[v + 1]; e += 32) flags[G.idx[e]] = 1;
+    }
 }
 
 // Initial clear of all hub tables of a graph: `n` slots in the packed or the split layout.
@@ -1078,47 +1187,51 @@ static int64_t persistent_grid(K kernel, int threads, size_t smem, int64_t work_
     return work_blocks < cap ? work_blocks : cap;
 }
 
-template <int G, int TPB, typename V>
+template <int G, int TPB, typename V, bool PULL>
 static cudaError_t launch_gv(const KArgs &k, cudaStream_t s)
 {
     constexpr int NG = TPB / G;
     const size_t smem = (size_t)NG * k.slots * (sizeof(int32_t) + sizeof(V));
-    cudaError_t e = set_smem(k_group<G, TPB, V>, smem);
+    cudaError_t e = set_smem(k_group<G, TPB, V, PULL>, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = persistent_grid(k_group<G, TPB, V>, TPB, smem, ((int64_t)k.n_items + 7) / 8 * 8);
-    k_group<G, TPB, V><<<(unsigned)(blocks < 1 ? 1 : blocks), TPB, smem, s>>>(k);
+    const int64_t blocks = persistent_grid(k_group<G, TPB, V, PULL>, TPB, smem, ((int64_t)k.n_items + 7) / 8 * 8);
+    k_group<G, TPB, V, PULL><<<(unsigned)(blocks < 1 ? 1 : blocks), TPB, smem, s>>>(k);
     return cudaGetLastError();
 }
 
-template <int G, int TPB>
+template <int G, int TPB, bool PULL>
 static cudaError_t launch_g(const KArgs &k, bool int_w, cudaStream_t s)
 {
-    return int_w ? launch_gv<G, TPB, uint32_t>(k, s) : launch_gv<G, TPB, float>(k, s);
+    return int_w ? launch_gv<G, TPB, uint32_t, PULL>(k, s) : launch_gv<G, TPB, float, PULL>(k, s);
 }
 
-template <int TPB, typename V>
+template <int TPB, typename V, bool PULL>
 static cudaError_t launch_cv(const KArgs &k, cudaStream_t s)
 {
     const size_t smem = (size_t)k.slots * (sizeof(int32_t) + sizeof(V));
-    cudaError_t e = set_smem(k_cta<TPB, V>, smem);
+    cudaError_t e = set_smem(k_cta<TPB, V, PULL>, smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = persistent_grid(k_cta<TPB, V>, TPB, smem, k.n_items);
-    k_cta<TPB, V><<<(unsigned)(blocks < 1 ? 1 : blocks), TPB, smem, s>>>(k);
+    const int64_t blocks = persistent_grid(k_cta<TPB, V, PULL>, TPB, smem, k.n_items);
+    k_cta<TPB, V, PULL><<<(unsigned)(blocks < 1 ? 1 : blocks), TPB, smem, s>>>(k);
     return cudaGetLastError();
 }
 
+template <bool PULL>
 static cudaError_t launch_cta(const KArgs &k, int threads, bool int_w, cudaStream_t s)
 {
     switch (threads) {
-    case 64: return int_w ? launch_cv<64, uint32_t>(k, s) : launch_cv<64, float>(k, s);
-    case 128: return int_w ? launch_cv<128, uint32_t>(k, s) : launch_cv<128, float>(k, s);
-    case 256: return int_w ? launch_cv<256, uint32_t>(k, s) : launch_cv<256, float>(k, s);
-    case 512: return int_w ? launch_cv<512, uint32_t>(k, s) : launch_cv<512, float>(k, s);
-    case 1024: return int_w ? launch_cv<1024, uint32_t>(k, s) : launch_cv<1024, float>(k, s);
+    case 64: return int_w ? launch_cv<64, uint32_t, PULL>(k, s) : launch_cv<64, float, PULL>(k, s);
+    case 128: return int_w ? launch_cv<128, uint32_t, PULL>(k, s) : launch_cv<128, float, PULL>(k, s);
+    case 256: return int_w ? launch_cv<256, uint32_t, PULL>(k, s) : launch_cv<256, float, PULL>(k, s);
+    case 512: return int_w ? launch_cv<512, uint32_t, PULL>(k, s) : launch_cv<512, float, PULL>(k, s);
+    case 1024: return int_w ? launch_cv<1024, uint32_t, PULL>(k, s) : launch_cv<1024, float, PULL>(k, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
+// The kernel of bucket b for the push (PULL = false) or pull sweeps of the plan's graphs;
+// each instantiation has its own work-queue counter.
+template <bool PULL>
 static cudaError_t launch_vertex(const SweepPlan &p, int b, cudaStream_t s)
 {
     KArgs k{};
@@ -1126,32 +1239,33 @@ static cudaError_t launch_vertex(const SweepPlan &p, int b, cudaStream_t s)
     k.items = p.items[b];
     k.n_items = p.n_items[b];
     k.slots = p.slots[b];
-    k.queue = p.queues + b;
+    k.queue = p.queues + b + (PULL ? B_COUNT : 0);
     k.active = p.active_count;
     k.kslot = b;                                       // bucket index == kernel slot
     const bool iw = p.int_weights != 0;
     switch (b) {
-    case B_THREAD: return launch_g<1, 128>(k, iw, s);
+    case B_THREAD: return launch_g<1, 128, PULL>(k, iw, s);
     case B_GROUP:
         switch (p.group_lanes) {
-        case 2: return launch_g<2, 256>(k, iw, s);
-        case 4: return launch_g<4, 256>(k, iw, s);
-        case 8: return launch_g<8, 256>(k, iw, s);
-        case 16: return launch_g<16, 256>(k, iw, s);
+        case 2: return launch_g<2, 256, PULL>(k, iw, s);
+        case 4: return launch_g<4, 256, PULL>(k, iw, s);
+        case 8: return launch_g<8, 256, PULL>(k, iw, s);
+        case 16: return launch_g<16, 256, PULL>(k, iw, s);
         default: return cudaErrorInvalidValue;
         }
-    case B_WARP: return launch_g<32, 256>(k, iw, s);
-    case B_CTA: return launch_cta(k, p.cta_threads, iw, s);
-    case B_CTA_LARGE: return launch_cta(k, p.cta_large_threads, iw, s);
-    case B_CTA_XL: return launch_cta(k, p.cta_xl_threads, iw, s);
+    case B_WARP: return launch_g<32, 256, PULL>(k, iw, s);
+    case B_CTA: return launch_cta<PULL>(k, p.cta_threads, iw, s);
+    case B_CTA_LARGE: return launch_cta<PULL>(k, p.cta_large_threads, iw, s);
+    case B_CTA_XL: return launch_cta<PULL>(k, p.cta_xl_threads, iw, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, int *launches)
 {
-    cudaError_t e = cudaMemsetAsync(p.queues, 0, sizeof(unsigned) * B_COUNT, s);
+    cudaError_t e = cudaMemsetAsync(p.queues, 0, sizeof(unsigned) * 2 * B_COUNT, s);
     if (e != cudaSuccess) return e;
+    const bool push = p.pull_mode != 1, pull = p.pull_mode != 0;
     auto timed = [&](int slot, auto &&fn) -> cudaError_t {
         if (hook) hook->before(slot);
         cudaError_t r = fn();
@@ -1161,8 +1275,13 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
     };
     for (int b = B_THREAD; b <= B_CTA_XL; ++b) {
         if (p.n_items[b] <= 0) continue;
-        e = timed(b, [&] { return launch_vertex(p, b, s); });
+        e = timed(b, [&] {
+            cudaError_t r = push ? launch_vertex<false>(p, b, s) : cudaSuccess;
+            if (r == cudaSuccess && pull) r = launch_vertex<true>(p, b, s);
+            return r;
+        });
         if (e != cudaSuccess) return e;
+        if (launches && push && pull) ++*launches;
     }
     HArgs h{};
     h.gd = p.gd;
@@ -1178,12 +1297,21 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
         h.items = p.hub_chunks;
         e = timed(LPA_K_HUB_ACC, [&] {
             const size_t smem = (size_t)p.hub_chunk * sizeof(int32_t);
-            cudaError_t r = set_smem(k_hub_acc<1024>, smem);
-            if (r != cudaSuccess) return r;
-            k_hub_acc<1024><<<p.n_hub_chunks, 1024, smem, s>>>(h);
+            cudaError_t r = cudaSuccess;
+            if (push) {
+                r = set_smem(k_hub_acc<1024, false>, smem);
+                if (r != cudaSuccess) return r;
+                k_hub_acc<1024, false><<<p.n_hub_chunks, 1024, smem, s>>>(h);
+            }
+            if (pull) {
+                r = set_smem(k_hub_acc<1024, true>, smem);
+                if (r != cudaSuccess) return r;
+                k_hub_acc<1024, true><<<p.n_hub_chunks, 1024, smem, s>>>(h);
+            }
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
+        if (launches && push && pull) ++*launches;
         h.items = p.hub_slices;
         e = timed(LPA_K_HUB_CLEAR, [&] {
             k_hub_clear<256><<<p.n_hub_slices, 256, 0, s>>>(h);
@@ -1204,16 +1332,19 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
         if (e != cudaSuccess) return e;
     }
     h.items = p.per_graph;
+    const unsigned bx = p.n_graphs == 1 ? (unsigned)(num_sms() * 4) : 8u;
     e = timed(LPA_K_APPLY, [&] {
-        const unsigned bx = p.n_graphs == 1 ? (unsigned)(num_sms() * 4) : 8u;
+        k_apply_unmark<<<dim3(bx, (unsigned)p.n_graphs), 256, 0, s>>>(h);
         k_apply<<<dim3(bx, (unsigned)p.n_graphs), 256, 0, s>>>(h);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
+    if (launches) ++*launches;                         // k_apply_unmark
     e = cudaMemsetAsync(p.active_count, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     k_decide<<<(p.n_graphs + 127) / 128, 128, 0, s>>>(p.gd, p.n_graphs, p.active_count);
-    if (launches) ++*launches;
+    k_finalize<<<dim3(bx, (unsigned)p.n_graphs), 256, 0, s>>>(p.gd);
+    if (launches) *launches += 2;
     return cudaGetLastError();
 }
 

@@ -177,6 +177,60 @@ def test_sync_is_deterministic(lpa):
 
 
 # ---------------------------------------------------------------------------------------
+# processed vertices per sweep (pruning, Algorithm 1)
+
+def expected_active(csr, og, iterations, tol, pl):
+    """Vertices processed at each synchronous sweep by the definition: every vertex with an
+    edge at sweep 0, then exactly the vertices with a neighbour (self-loops included) that
+    moved in the previous sweep.  Movers come from the oracle's labels after t sweeps."""
+    off, idx = csr.offsets.numpy(), csr.indices.numpy()
+    deg = off[1:] - off[:-1]
+    src = np.repeat(np.arange(og.n), deg)
+    labels = [np.arange(og.n, dtype=np.int32)]
+    labels += [np.asarray(oracle.lpa_sync(og, tol, t, pl).labels) for t in range(1, iterations + 1)]
+    out = [int((deg > 0).sum())]
+    for t in range(iterations - 1):
+        moved = labels[t + 1] != labels[t]
+        hit = np.zeros(og.n, dtype=bool)
+        hit[idx[moved[src]]] = True
+        out.append(int(hit.sum()))
+    return out
+
+
+@pytest.mark.parametrize("which", ["random0", "random1", "random-loops", "sbm", "rmat-small-buckets"])
+def test_sync_active_sets_match_definition(lpa, which):
+    """The per-sweep active counts equal the definition whether a sweep learnt its active
+    vertices from marks or from the moved bits of the sweep before (sweeps that move many
+    vertices skip the marks), and the run ends with clean labels and materialised flags."""
+    tuning = None
+    if which.startswith("random"):
+        seed = {"random0": 0, "random1": 1, "random-loops": 2}[which]
+        csr = gg.random_small(600, 0.02, 3000 + seed, wmax=4, self_loops=(which == "random-loops"))
+    elif which == "sbm":
+        csr = gg.sbm(3000, 50, 10.0, 2.0, seed=3, weights="int8")
+    else:
+        csr, tuning = gg.rmat(12, weights="int8"), SMALL_BUCKETS
+    og = oracle_graph(csr)
+    ref = oracle.lpa_sync(og, 0.0, 12, 4)
+    g = make(lpa, csr, True, tuning)
+    st = g.run(0.0, 12, 4, lpa.SYNC).to_dict()
+    assert st["changed"] == ref.dN
+    assert st["active"] == expected_active(csr, og, ref.iterations, 0.0, 4)
+    C, A, it = g.get_state()                        # labels and the next sweep's processed flags
+    assert C.numpy().tolist() == ref.labels.tolist()
+    assert A.numpy().tolist() == np.asarray(ref.active).tolist() and it == ref.iterations
+    for t in (1, 2, 5):                             # runs cut short: state after t sweeps
+        rt = oracle.lpa_sync(og, 0.0, t, 4)
+        g.run(0.0, t, 4, lpa.SYNC)
+        C, A, it = g.get_state()
+        assert C.numpy().tolist() == rt.labels.tolist(), t
+        assert A.numpy().tolist() == np.asarray(rt.active).tolist(), t
+    # resuming from the saved state continues exactly like an uninterrupted run
+    g.run(0.0, 12, 4, lpa.SYNC, resume=True)
+    assert g.labels().cpu().numpy().tolist() == ref.labels.tolist()
+
+
+# ---------------------------------------------------------------------------------------
 # asynchronous mode: acceptance bounds
 
 @pytest.mark.parametrize("which", ["sbm", "rmat14", "rmat14-small"])
