@@ -110,8 +110,10 @@ typedef struct lpa_stats {
  * Shared-memory tables have capacity nextPow2(D << smem_table_shift) - 1 (shift 0 is the
  * paper's nextPow2(D) - 1, shift 1 keeps the load factor at or below one half); each
  * bucket's table, sized for its largest degree, must fit in shared memory, else
- * lpa_set_tuning returns LPA_EINVAL.  Hub tables live in HBM with capacity
- * nextPow2(D << hub_table_shift) - 1. */
+ * lpa_set_tuning returns LPA_EINVAL.  Hub tables have capacity
+ * nextPow2(D << hub_table_shift) - 1 and live in HBM, or, with hub_cluster = 1 and integer
+ * sums, in the distributed shared memory of a 2..16-block thread-block cluster when they
+ * fit there (up to 2^18 slots; larger ones stay in HBM). */
 typedef struct lpa_tuning {
     int32_t thread_max;       /* thread per vertex for 1 <= D <= thread_max               */
     int32_t group_max;        /* group of group_lanes lanes per vertex                   */
@@ -128,7 +130,7 @@ typedef struct lpa_tuning {
     int32_t cta_xl_threads;
     int32_t item_vertices;    /* vertices per work item of the thread/group/warp kernels (0 = default) */
     int32_t float_values;     /* 1: float32 label sums even when integer sums would do   */
-    int32_t reserved[1];
+    int32_t hub_cluster;      /* 1: hub tables in cluster shared memory where they fit   */
 } lpa_tuning;
 
 typedef struct lpa_graph lpa_graph;
@@ -305,7 +307,8 @@ void lpa_server_destroy(lpa_server *s);
 /* Picks the handle's degree-bucket configuration by timing: a coordinate descent over fixed
  * candidates for each lpa_tuning field (hub chunk, block sizes and thresholds of the three
  * block tiers, warp and group thresholds, lanes per group, thread threshold), starting from
- * the current configuration.  Every candidate is applied (lpa_set_tuning) and timed on the
+ * the current configuration; hub tables in HBM or in cluster shared memory (hub_cluster) are
+ * one more axis.  Every candidate is applied (lpa_set_tuning) and timed on the
  * run given by tolerance / max_iters / pl_period / mode (as lpa_run, from fresh labels; best
  * of reps CUDA-event timings); a candidate is kept when it is at least 2% faster.  Section 4.3
  * chooses its one switch degree (thread vs block per vertex) by timing a range of thresholds

@@ -24,6 +24,7 @@ const std::vector<Axis> &axes()
 {
     static const std::vector<Axis> a = {
         {[](lpa_tuning &t, int v) { t.hub_chunk = v; }, {4096, 8192, 16384, 32768}},
+        {[](lpa_tuning &t, int v) { t.hub_cluster = v; }, {0, 1}},
         {[](lpa_tuning &t, int v) { t.cta_xl_threads = v; }, {512, 1024}},
         {[](lpa_tuning &t, int v) { t.cta_xl_max = v; }, {4095, 8191}},
         {[](lpa_tuning &t, int v) { t.cta_large_threads = v; }, {256, 512}},

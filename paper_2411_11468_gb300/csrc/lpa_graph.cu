@@ -630,6 +630,7 @@ int check_tuning(const lpa_tuning &t)
     if (t.hub_chunk < 256 || t.hub_chunk > 32768) return LPA_EINVAL;
     if (t.item_vertices < 0 || t.item_vertices > (1 << 20)) return LPA_EINVAL;
     if (t.float_values != 0 && t.float_values != 1) return LPA_EINVAL;
+    if (t.hub_cluster != 0 && t.hub_cluster != 1) return LPA_EINVAL;
     const int64_t smem = (int64_t)max_dynamic_smem();
     const int64_t bytes_group = (256 / t.group_lanes) * slots_for(t.group_max, sh) * 8;
     const int64_t bytes_warp = 8 * slots_for(t.warp_max, sh) * 8;
@@ -665,9 +666,7 @@ void free_buckets(lpa_graph *g)
     g->gdh.hub = HubArgs{};
     g->table_slots = 0;
     for (auto &v : g->items_h) v.clear();
-    g->hub_hubs_h.clear();
-    g->hub_chunks_h.clear();
-    g->hub_slices_h.clear();
+    for (auto &v : g->hub_items_h) v.clear();
 }
 
 int build_buckets(lpa_graph *g)
@@ -760,18 +759,33 @@ int build_buckets(lpa_graph *g)
         std::vector<int32_t> ch, sh, sj;
         std::vector<int64_t> ce0, ce1;
         int64_t slots = 0, used_total = 0;
+        // With hub_cluster, tables of at most 2^kDsmMaxBits slots (integer sums) live in the
+        // shared memory of a cluster of 2..16 blocks; the others live in HBM with accumulate
+        // chunks and clear slices.
+        const int dsm_bits = (g->tuning.hub_cluster && plan_int_weights(g)) ? dsm_max_class_bits() : 0;
+        const bool dsm_ok = dsm_bits > 0;
+        std::vector<int64_t> acc_chunks;
         for (int64_t h = 0; h < H; ++h) {
             const int64_t D = o1[h] - o0[h];
             const int64_t want = std::min<int64_t>(D << g->tuning.hub_table_shift, (int64_t)1 << 31);
             bb[h] = capacity_bits(want);
             p1[h] = (uint32_t)(((int64_t)1 << bb[h]) - 1);
-            tab[h] = slots;
-            ubase[h] = used_total;
+            const bool dsm = dsm_ok && (int)bb[h] <= kDsmSliceBits + dsm_bits;
             for (int64_t e0 = o0[h]; e0 < o1[h]; e0 += chunk) {
+                if (!dsm) acc_chunks.push_back((int64_t)ch.size());
                 ch.push_back((int32_t)h);
                 ce0.push_back(e0);
                 ce1.push_back(std::min(o1[h], e0 + chunk));
             }
+            if (dsm) {
+                const int cs_bits = std::min(4, std::max(1, (int)bb[h] - kDsmSliceBits));
+                g->hub_items_h[HL_DSM2 + cs_bits - 1].push_back(WorkItem{0, 0, h, 1});
+                tab[h] = -1;
+                ubase[h] = -1;
+                continue;
+            }
+            tab[h] = slots;
+            ubase[h] = used_total;
             for (int64_t j = 0; j * kHubSlice < (int64_t)p1[h]; ++j) {   // clear slices cover the table
                 sh.push_back((int32_t)h);
                 sj.push_back((int32_t)j);
@@ -820,9 +834,9 @@ int build_buckets(lpa_graph *g)
         LPA_CUDA(cudaMemsetAsync(d_best, 0, H * 8, g->stream));
         LPA_CUDA(cudaMemsetAsync(d_used, 0, H * 4, g->stream));
         // 8 bytes per slot in one block: split keys then values, or packed 64-bit slots
-        LPA_CHECK(dalloc(g, &g->tab_k, (size_t)slots * 2));
-        g->tab_v = reinterpret_cast<float *>(g->tab_k + slots);
-        LPA_CHECK(dalloc(g, &g->used_list, (size_t)used_total));
+        LPA_CHECK(dalloc(g, &g->tab_k, (size_t)std::max<int64_t>(slots, 2) * 2));     // (none when every hub
+        g->tab_v = reinterpret_cast<float *>(g->tab_k + slots);                       //  is in a cluster)
+        LPA_CHECK(dalloc(g, &g->used_list, (size_t)std::max<int64_t>(used_total, 1)));
         LPA_CUDA(launch_hub_table_clear(g->tab_k, g->tab_v, slots, plan_int_weights(g), g->stream));
         ha.hub_v = d_hv;
         ha.hub_p1 = d_p1;
@@ -844,36 +858,35 @@ int build_buckets(lpa_graph *g)
         ha.n_hubs = (int32_t)H;
         ha.n_chunks = (int32_t)n_chunks;
         ha.n_slices = (int32_t)n_slices;
-        for (int64_t h0 = 0; h0 < H; h0 += 256) g->hub_hubs_h.push_back(WorkItem{0, 0, h0, std::min<int64_t>(256, H - h0)});
-        for (int64_t c = 0; c < n_chunks; ++c) g->hub_chunks_h.push_back(WorkItem{0, 0, c, 1});
-        for (int64_t j = 0; j < n_slices; ++j) g->hub_slices_h.push_back(WorkItem{0, 0, j, 1});
+        for (int64_t h0 = 0; h0 < H; h0 += 256)
+            g->hub_items_h[HL_HUBS].push_back(WorkItem{0, 0, h0, std::min<int64_t>(256, H - h0)});
+        for (int64_t c : acc_chunks) g->hub_items_h[HL_ACC].push_back(WorkItem{0, 0, c, 1});
+        for (int64_t c = 0; c < n_chunks; ++c) g->hub_items_h[HL_MARK].push_back(WorkItem{0, 0, c, 1});
+        for (int64_t j = 0; j < n_slices; ++j) g->hub_items_h[HL_SLICES].push_back(WorkItem{0, 0, j, 1});
     }
 
     // every item of this graph in one device block: vertex items, hub items, one per-graph item
-    size_t total_items = 1 + g->hub_hubs_h.size() + g->hub_chunks_h.size() + g->hub_slices_h.size();
+    size_t total_items = 1;
     for (int b = B_THREAD; b <= B_CTA_XL; ++b) total_items += g->items_h[b].size();
+    for (int q = 0; q < HL_COUNT; ++q) total_items += g->hub_items_h[q].size();
     std::vector<WorkItem> all;
     all.reserve(total_items);
-    size_t at[B_COUNT] = {}, at_hh = 0, at_hc = 0, at_hs = 0, at_pg = 0;
+    size_t at[B_COUNT] = {}, at_h[HL_COUNT] = {}, at_pg = 0;
     for (int b = B_THREAD; b <= B_CTA_XL; ++b) {
         at[b] = all.size();
         all.insert(all.end(), g->items_h[b].begin(), g->items_h[b].end());
     }
-    at_hh = all.size();
-    all.insert(all.end(), g->hub_hubs_h.begin(), g->hub_hubs_h.end());
-    at_hc = all.size();
-    all.insert(all.end(), g->hub_chunks_h.begin(), g->hub_chunks_h.end());
-    at_hs = all.size();
-    all.insert(all.end(), g->hub_slices_h.begin(), g->hub_slices_h.end());
+    for (int q = 0; q < HL_COUNT; ++q) {
+        at_h[q] = all.size();
+        all.insert(all.end(), g->hub_items_h[q].begin(), g->hub_items_h[q].end());
+    }
     at_pg = all.size();
     all.push_back(WorkItem{0, 0, 0, 0});
     LPA_CHECK(dalloc(g, &g->items_d, all.size()));
     LPA_CUDA(cudaMemcpyAsync(g->items_d, all.data(), all.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
                              g->stream));
     for (int b = B_THREAD; b <= B_CTA_XL; ++b) g->items_at[b] = g->items_d + at[b];
-    g->hub_hubs_d = g->items_d + at_hh;
-    g->hub_chunks_d = g->items_d + at_hc;
-    g->hub_slices_d = g->items_d + at_hs;
+    for (int q = 0; q < HL_COUNT; ++q) g->hub_items_d[q] = g->items_d + at_h[q];
     g->per_graph_d = g->items_d + at_pg;
     LPA_CHECK(upload_descriptor(g));
     LPA_CUDA(cudaStreamSynchronize(g->stream));
@@ -1071,7 +1084,7 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
     if ((st = dalloc(g, &g->macc, 4)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->gdd, 1)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->rs_d, 1)) != LPA_OK) return fail(st);
-    if ((st = dalloc(g, &g->queues, 2 * B_COUNT)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->queues, kQueueCount)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->active, 1)) != LPA_OK) return fail(st);
     if ((st = ensure_counters(g, 1, false)) != LPA_OK) return fail(st);
 
@@ -1451,12 +1464,10 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
         p.n_vertices[b] = g->bucket_start[b + 1] - g->bucket_start[b];
     }
     plan_slots(g->tuning, p.slots);
-    p.hub_hubs = g->hub_hubs_d;
-    p.n_hub_hubs = (int32_t)g->hub_hubs_h.size();
-    p.hub_chunks = g->hub_chunks_d;
-    p.n_hub_chunks = (int32_t)g->hub_chunks_h.size();
-    p.hub_slices = g->hub_slices_d;
-    p.n_hub_slices = (int32_t)g->hub_slices_h.size();
+    for (int q = 0; q < HL_COUNT; ++q) {
+        p.hub_items[q] = g->hub_items_d[q];
+        p.n_hub_items[q] = (int32_t)g->hub_items_h[q].size();
+    }
     p.per_graph = g->per_graph_d;
     p.queues = g->queues;
     p.active_count = g->active;

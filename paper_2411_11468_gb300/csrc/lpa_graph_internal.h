@@ -39,10 +39,11 @@ struct lpa_graph {
     int64_t table_slots = 0;
     // work items of this graph (graph index 0); batches re-index copies of the host vectors
     std::vector<lpa::WorkItem> items_h[lpa::B_COUNT];
-    std::vector<lpa::WorkItem> hub_hubs_h, hub_chunks_h, hub_slices_h;
+    std::vector<lpa::WorkItem> hub_items_h[lpa::HL_COUNT];
     lpa::WorkItem *items_d = nullptr;                // every item of this graph in one block
     lpa::WorkItem *items_at[lpa::B_COUNT] = {};
-    lpa::WorkItem *hub_hubs_d = nullptr, *hub_chunks_d = nullptr, *hub_slices_d = nullptr, *per_graph_d = nullptr;
+    lpa::WorkItem *hub_items_d[lpa::HL_COUNT] = {};
+    lpa::WorkItem *per_graph_d = nullptr;
     // descriptor and run state of this graph alone (lpa_run)
     lpa::GraphDev gdh{};
     lpa::GraphDev *gdd = nullptr;

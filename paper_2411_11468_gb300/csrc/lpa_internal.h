@@ -16,6 +16,14 @@ constexpr int kMaxRetries = 32;    // hybrid probes before the linear fallback (
 constexpr int kCtrFields = 4;      // per kernel slot: active, edges, moved, marks
 enum { CTR_ACTIVE = 0, CTR_EDGES = 1, CTR_MOVED = 2, CTR_MARKS = 3 };
 enum Bucket { B_THREAD = 0, B_GROUP, B_WARP, B_CTA, B_CTA_LARGE, B_CTA_XL, B_HUB, B_COUNT };
+// Work-item lists of the hub bucket: hubs (begin, move), accumulate chunks of hubs whose table
+// is in HBM, mark chunks of every hub, clear slices of HBM tables, and the hubs whose table
+// lives in the distributed shared memory of a 2-, 4-, 8- or 16-block cluster.
+enum HubList { HL_HUBS = 0, HL_ACC, HL_MARK, HL_SLICES, HL_DSM2, HL_DSM4, HL_DSM8, HL_DSM16, HL_COUNT };
+constexpr int kDsmSliceBits = 14;  // table slots per cluster block (2^14 x 8 bytes = 128 KB)
+constexpr int kDsmMaxBits = 18;    // largest table in cluster shared memory: 2^18 slots over 16 blocks
+// Work-queue counters: vertex buckets for push and pull launches, then the cluster classes.
+constexpr int kQueueCount = 2 * B_COUNT + 2 * 4;
 constexpr int kHubSlice = 4096;    // table slots / used-list entries per hub clear block
 constexpr int kPerSweep = LPA_NUM_KERNELS * kCtrFields;   // counter words per sweep
 
@@ -109,14 +117,10 @@ struct SweepPlan {
     int32_t n_items[B_COUNT];
     int64_t n_vertices[B_COUNT];       // vertices covered by the items of each bucket
     int32_t slots[B_COUNT];    // smem slots per table for each vertex kernel
-    const WorkItem *hub_hubs;  // items over hubs (begin, move)
-    int32_t n_hub_hubs;
-    const WorkItem *hub_chunks;        // one item per hub chunk (acc, mark)
-    int32_t n_hub_chunks;
-    const WorkItem *hub_slices;        // one item per hub clear slice
-    int32_t n_hub_slices;
+    const WorkItem *hub_items[HL_COUNT];       // hub work items (HubList)
+    int32_t n_hub_items[HL_COUNT];
     const WorkItem *per_graph;         // one item per graph (apply, decide)
-    unsigned *queues;          // [2 * B_COUNT] work-queue counters (push, pull launches), zeroed per sweep
+    unsigned *queues;          // [kQueueCount] work-queue counters, zeroed per sweep
     int32_t *active_count;     // device counter written by k_decide (graphs still running)
     int32_t group_lanes, cta_threads, cta_large_threads, cta_xl_threads, hub_chunk;
     int32_t pull_mode;         // kernels launched for this sweep: 0 push only, 1 pull only, 2 both
@@ -137,6 +141,9 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
 // Clears `slots` hub-table slots: packed (one 64-bit word per slot over k) or split (k, v).
 cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, bool packed, cudaStream_t s);
 size_t max_dynamic_smem();
+// Largest cluster class (log2 of the blocks per cluster, 0 = none) that the device can run
+// with a hub table slice of 2^kDsmSliceBits slots per block.
+int dsm_max_class_bits();
 int num_sms();
 
 // Device memory arena: reservations carved into 256-byte aligned blocks (first fit with a

@@ -120,7 +120,7 @@ struct MultiPlan {
         LPA_CHECK(grow(&gd, &gd_cap, n));
         LPA_CHECK(grow(&rs, &rs_cap, n));
         LPA_CHECK(ensure_host(n));
-        if (!queues && cudaMalloc((void **)&queues, sizeof(unsigned) * 2 * B_COUNT) != cudaSuccess) {
+        if (!queues && cudaMalloc((void **)&queues, sizeof(unsigned) * kQueueCount) != cudaSuccess) {
             cudaGetLastError();
             set_error("cudaMalloc failed");
             return LPA_ENOMEM;
@@ -138,7 +138,7 @@ struct MultiPlan {
             all_int = all_int && plan_int_weights(gs[i]);
         }
         std::vector<WorkItem> all;
-        size_t at[B_COUNT] = {}, at_hh, at_hc, at_hs, at_pg;
+        size_t at[B_COUNT] = {}, at_h[HL_COUNT] = {}, at_pg;
         SweepPlan p{};
         for (int b = B_THREAD; b <= B_CTA_XL; ++b) {
             at[b] = all.size();
@@ -151,21 +151,15 @@ struct MultiPlan {
             }
             p.n_items[b] = (int32_t)(all.size() - at[b]);
         }
-        auto append = [&](std::vector<WorkItem> lpa_graph::*field) {
-            const size_t start = all.size();
+        for (int q = 0; q < HL_COUNT; ++q) {
+            at_h[q] = all.size();
             for (size_t i = 0; i < n; ++i)
-                for (WorkItem it : gs[i]->*field) {
+                for (WorkItem it : gs[i]->hub_items_h[q]) {
                     it.g = (int32_t)i;
                     all.push_back(it);
                 }
-            return start;
-        };
-        at_hh = append(&lpa_graph::hub_hubs_h);
-        p.n_hub_hubs = (int32_t)(all.size() - at_hh);
-        at_hc = append(&lpa_graph::hub_chunks_h);
-        p.n_hub_chunks = (int32_t)(all.size() - at_hc);
-        at_hs = append(&lpa_graph::hub_slices_h);
-        p.n_hub_slices = (int32_t)(all.size() - at_hs);
+            p.n_hub_items[q] = (int32_t)(all.size() - at_h[q]);
+        }
         at_pg = all.size();
         for (size_t i = 0; i < n; ++i) all.push_back(WorkItem{(int32_t)i, 0, 0, 0});
         LPA_CHECK(grow(&items, &items_cap, all.size()));
@@ -176,9 +170,7 @@ struct MultiPlan {
         p.n_graphs = (int32_t)n;
         for (int b = B_THREAD; b <= B_CTA_XL; ++b) p.items[b] = items + at[b];
         plan_slots(t, p.slots);
-        p.hub_hubs = items + at_hh;
-        p.hub_chunks = items + at_hc;
-        p.hub_slices = items + at_hs;
+        for (int q = 0; q < HL_COUNT; ++q) p.hub_items[q] = items + at_h[q];
         p.per_graph = items + at_pg;
         p.queues = queues;
         p.active_count = active;

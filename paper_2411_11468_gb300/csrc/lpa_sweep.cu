@@ -18,10 +18,13 @@
 // lane that made its last add and no observed sum exceeds a final sum (weights are >= 0),
 // so the reduction equals the maximum over the table: the largest weight and, among equal
 // weights, the smallest label (Section 4 item 5).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "lpa_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace lpa {
 
@@ -135,27 +138,15 @@ __device__ __forceinline__ bool try_slot(const SplitTable<V> &T, size_t s, int32
     return false;
 }
 
-template <bool SHARED, bool TRACK>
-__device__ __forceinline__ bool try_slot(const PackedTable &T, size_t s, int32_t k, uint32_t v,
-                                         unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
+// Shared (atomic) update of one packed slot at p (slot index s for the used list).
+template <bool TRACK>
+__device__ __forceinline__ bool packed_update(unsigned long long *p, size_t s, int32_t k, uint32_t v,
+                                              unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
 {
-    unsigned long long *p = T.h + s;
     const uint32_t uk = (uint32_t)k;
-    const unsigned long long mine = ((unsigned long long)uk << 32) | v;
-    if (!SHARED) {
-        const unsigned long long cur = *p;
-        const uint32_t ck = (uint32_t)(cur >> 32);
-        if (ck == uk || ck == 0xFFFFFFFFu) {
-            const uint32_t nv = (uint32_t)cur + v;       // an empty slot holds sum 0
-            *p = ((unsigned long long)uk << 32) | nv;
-            best = umax64(best, pack_kv(nv, k));
-            return true;
-        }
-        return false;
-    }
     uint32_t ck = (uint32_t)(*((volatile unsigned long long *)p) >> 32);
     if (ck == 0xFFFFFFFFu) {
-        const unsigned long long old = atomicCAS(p, kEmptySlot, mine);
+        const unsigned long long old = atomicCAS(p, kEmptySlot, ((unsigned long long)uk << 32) | v);
         if (old == kEmptySlot) {
             if (TRACK) ulist[atomicAdd(ucnt, 1u)] = (int32_t)s;
             best = umax64(best, pack_kv(v, k));
@@ -172,6 +163,45 @@ __device__ __forceinline__ bool try_slot(const PackedTable &T, size_t s, int32_t
         return true;
     }
     return false;
+}
+
+template <bool SHARED, bool TRACK>
+__device__ __forceinline__ bool try_slot(const PackedTable &T, size_t s, int32_t k, uint32_t v,
+                                         unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
+{
+    unsigned long long *p = T.h + s;
+    if (!SHARED) {
+        const uint32_t uk = (uint32_t)k;
+        const unsigned long long cur = *p;
+        const uint32_t ck = (uint32_t)(cur >> 32);
+        if (ck == uk || ck == 0xFFFFFFFFu) {
+            const uint32_t nv = (uint32_t)cur + v;       // an empty slot holds sum 0
+            *p = ((unsigned long long)uk << 32) | nv;
+            best = umax64(best, pack_kv(nv, k));
+            return true;
+        }
+        return false;
+    }
+    return packed_update<TRACK>(p, s, k, v, best, ucnt, ulist);
+}
+
+// A hub table spread over the shared memory of the blocks of a thread-block cluster (packed
+// layout): slot s lives in block s >> lb at index s & (2^lb - 1) of that block's slice, and
+// is reached through the cluster's distributed shared memory.
+struct ClusterTable {
+    using Val = uint32_t;
+    unsigned long long *base;  // this block's slice
+    uint32_t lb;               // log2 of the slots per block
+    int stride;                // 1
+};
+
+template <bool SHARED, bool TRACK>
+__device__ __forceinline__ bool try_slot(const ClusterTable &T, size_t s, int32_t k, uint32_t v,
+                                         unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
+{
+    unsigned long long *p = cg::this_cluster().map_shared_rank(T.base, (unsigned)(s >> T.lb)) +
+                            (s & (((size_t)1 << T.lb) - 1));
+    return packed_update<TRACK>(p, s, k, v, best, ucnt, ulist);
 }
 
 // hashtableAccumulate (Algorithm 2) with i and delta kept reduced mod p1 (same slots),
@@ -934,6 +964,73 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
     }
 }
 
+// Hubs whose table fits in the shared memory of a cluster of CS blocks (1024 threads each).
+// Persistent: rank 0 takes a hub from the queue and broadcasts it; every block clears its
+// slice of the hub's table, the cluster synchronises, every block scans 1/CS of the row and
+// inserts into the distributed table (Algorithm 2's probe sequence over the whole table),
+// folds its running maximum into hub_best, and the cluster synchronises again before the
+// next hub.  Integer sums only (packed slots).
+constexpr int kDsmThreads = 1024;
+
+template <int CS, bool PULL>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kDsmThreads) k_hub_dsm(HArgs k, int32_t n_items,
+                                                                                   unsigned *queue)
+{
+    if (*k.active == 0) return;                        // the same value in every block of the cluster
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    constexpr int csb = CS == 2 ? 1 : (CS == 4 ? 2 : (CS == 8 ? 3 : 4));
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *slice = (unsigned long long *)smem;
+    __shared__ int s_it;
+    __shared__ unsigned long long s_best[kDsmThreads / 32];
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int it = (int)atomicAdd(queue, 1u);
+            for (unsigned r = 0; r < (unsigned)CS; ++r) *cluster.map_shared_rank(&s_it, r) = it;
+        }
+        cluster.sync();                                // the hub is known in every block
+        const int it = s_it;
+        if (it >= n_items) break;
+        const WorkItem item = k.items[it];
+        const SweepView a = view_of(k.gd, item.g);
+        const HubArgs &h = k.gd[item.g].hub;
+        const int hh = (int)item.start;
+        if (a.done || (a.pull != 0) != PULL || !h.hub_act[hh]) {
+            cluster.sync();                            // s_it is read before rank 0 writes the next
+            continue;
+        }
+        const uint32_t b = h.hub_b[hh], p1 = h.hub_p1[hh];
+        const uint32_t lb = b - csb;                   // 2^lb slots per block
+        clear_table_vec(PackedTable{slice, 1}, (1u << lb) - 1u, threadIdx.x, kDsmThreads);
+        cluster.sync();                                // every slice is clear
+        const ClusterTable tab{slice, lb, 1};
+        const int32_t v = h.hub_v[hh];
+        const int64_t o0 = a.off[v], o1 = a.off[v + 1];
+        const int64_t per = (o1 - o0 + CS - 1) / CS;
+        const int64_t e0 = o0 + (int64_t)rank * per;
+        const int64_t e1 = e0 + per < o1 ? e0 + per : o1;
+        unsigned fb = 0;
+        unsigned long long best = 0;
+        uint32_t seen = 0;
+        if (e0 < e1)
+            scan_row<32, true, false, 2, PULL>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab,
+                                               p1, b, best, fb, seen, nullptr, nullptr, kDsmThreads * 2);
+        if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
+        best = group_max<32>(best);
+        if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+        bool any_seen = false;
+        if (PULL) any_seen = __syncthreads_or((seen & kMovedBit) != 0) != 0;
+        else __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < kDsmThreads / 32; ++w) best = umax64(best, s_best[w]);
+            if (best) atomicMax(h.hub_best + hh, best);
+            if (PULL && any_seen) h.hub_seen[hh] = 1;
+        }
+        cluster.sync();                                // every insert is done before the next clear
+    }
+}
+
 // Clears the table slots a hub used in this sweep: slot by slot from the used list when
 // few were used, or the whole table with coalesced stores when more than an eighth were.
 template <int TPB>
@@ -1261,9 +1358,81 @@ static cudaError_t launch_vertex(const SweepPlan &p, int b, cudaStream_t s)
     }
 }
 
+constexpr size_t kDsmSmem = ((size_t)1 << kDsmSliceBits) * sizeof(unsigned long long);
+
+template <int CS, bool PULL>
+static cudaError_t launch_dsm_cs(const HArgs &h, int32_t n_items, unsigned *queue, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_hub_dsm<CS, PULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDsmSmem);
+    if (e == cudaSuccess && CS > 8)
+        e = cudaFuncSetAttribute(k_hub_dsm<CS, PULL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    query_device();
+    int64_t clusters = g_num_sms / CS;
+    if (clusters > n_items) clusters = n_items;
+    if (clusters < 1) clusters = 1;
+    k_hub_dsm<CS, PULL><<<(unsigned)(clusters * CS), kDsmThreads, kDsmSmem, s>>>(h, n_items, queue);
+    return cudaGetLastError();
+}
+
+// Cluster class c (cluster of 2 << c blocks).
+template <bool PULL>
+static cudaError_t launch_dsm(int c, const HArgs &h, int32_t n_items, unsigned *queue, cudaStream_t s)
+{
+    switch (c) {
+    case 0: return launch_dsm_cs<2, PULL>(h, n_items, queue, s);
+    case 1: return launch_dsm_cs<4, PULL>(h, n_items, queue, s);
+    case 2: return launch_dsm_cs<8, PULL>(h, n_items, queue, s);
+    case 3: return launch_dsm_cs<16, PULL>(h, n_items, queue, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int CS>
+static int active_clusters()
+{
+    if (cudaFuncSetAttribute(k_hub_dsm<CS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDsmSmem) !=
+            cudaSuccess ||
+        (CS > 8 && cudaFuncSetAttribute(k_hub_dsm<CS, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                       cudaSuccess)) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS * 8, 1, 1);
+    cfg.blockDim = dim3(kDsmThreads, 1, 1);
+    cfg.dynamicSmemBytes = kDsmSmem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = CS;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_hub_dsm<CS, false>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+int dsm_max_class_bits()
+{
+    static int cached = -1;                            // per process (one device type)
+    if (cached >= 0) return cached;
+    int bits = 0;
+    if (active_clusters<2>() > 0) bits = 1;
+    if (bits == 1 && active_clusters<4>() > 0) bits = 2;
+    if (bits == 2 && active_clusters<8>() > 0) bits = 3;
+    if (bits == 3 && active_clusters<16>() > 0) bits = 4;
+    cached = bits;
+    return bits;
+}
+
 cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, int *launches)
 {
-    cudaError_t e = cudaMemsetAsync(p.queues, 0, sizeof(unsigned) * 2 * B_COUNT, s);
+    cudaError_t e = cudaMemsetAsync(p.queues, 0, sizeof(unsigned) * kQueueCount, s);
     if (e != cudaSuccess) return e;
     const bool push = p.pull_mode != 1, pull = p.pull_mode != 0;
     auto timed = [&](int slot, auto &&fn) -> cudaError_t {
@@ -1287,46 +1456,64 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
     h.gd = p.gd;
     h.active = p.active_count;
     h.chunk = p.hub_chunk;
-    if (p.n_hub_hubs > 0) {
-        h.items = p.hub_hubs;
+    if (p.n_hub_items[HL_HUBS] > 0) {
+        h.items = p.hub_items[HL_HUBS];
         e = timed(LPA_K_HUB_BEGIN, [&] {
-            k_hub_begin<<<p.n_hub_hubs, 256, 0, s>>>(h);
+            k_hub_begin<<<p.n_hub_items[HL_HUBS], 256, 0, s>>>(h);
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
-        h.items = p.hub_chunks;
         e = timed(LPA_K_HUB_ACC, [&] {
-            const size_t smem = (size_t)p.hub_chunk * sizeof(int32_t);
             cudaError_t r = cudaSuccess;
-            if (push) {
-                r = set_smem(k_hub_acc<1024, false>, smem);
-                if (r != cudaSuccess) return r;
-                k_hub_acc<1024, false><<<p.n_hub_chunks, 1024, smem, s>>>(h);
+            if (p.n_hub_items[HL_ACC] > 0) {          // hubs with tables in HBM
+                HArgs ha = h;
+                ha.items = p.hub_items[HL_ACC];
+                const size_t smem = (size_t)p.hub_chunk * sizeof(int32_t);
+                if (push) {
+                    r = set_smem(k_hub_acc<1024, false>, smem);
+                    if (r != cudaSuccess) return r;
+                    k_hub_acc<1024, false><<<p.n_hub_items[HL_ACC], 1024, smem, s>>>(ha);
+                }
+                if (pull) {
+                    r = set_smem(k_hub_acc<1024, true>, smem);
+                    if (r != cudaSuccess) return r;
+                    k_hub_acc<1024, true><<<p.n_hub_items[HL_ACC], 1024, smem, s>>>(ha);
+                }
+                if (launches) *launches += (push && pull) ? 1 : 0;
             }
-            if (pull) {
-                r = set_smem(k_hub_acc<1024, true>, smem);
-                if (r != cudaSuccess) return r;
-                k_hub_acc<1024, true><<<p.n_hub_chunks, 1024, smem, s>>>(h);
+            for (int c = 0; c < 4 && r == cudaSuccess; ++c) {    // hubs with tables in cluster memory
+                if (p.n_hub_items[HL_DSM2 + c] <= 0) continue;
+                HArgs ha = h;
+                ha.items = p.hub_items[HL_DSM2 + c];
+                if (push) {
+                    r = launch_dsm<false>(c, ha, p.n_hub_items[HL_DSM2 + c], p.queues + 2 * B_COUNT + c, s);
+                    if (launches) ++*launches;
+                }
+                if (pull && r == cudaSuccess) {
+                    r = launch_dsm<true>(c, ha, p.n_hub_items[HL_DSM2 + c], p.queues + 2 * B_COUNT + 4 + c, s);
+                    if (launches) ++*launches;
+                }
             }
-            return cudaGetLastError();
+            return r != cudaSuccess ? r : cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
-        if (launches && push && pull) ++*launches;
-        h.items = p.hub_slices;
-        e = timed(LPA_K_HUB_CLEAR, [&] {
-            k_hub_clear<256><<<p.n_hub_slices, 256, 0, s>>>(h);
-            return cudaGetLastError();
-        });
-        if (e != cudaSuccess) return e;
-        h.items = p.hub_hubs;
+        if (p.n_hub_items[HL_SLICES] > 0) {
+            h.items = p.hub_items[HL_SLICES];
+            e = timed(LPA_K_HUB_CLEAR, [&] {
+                k_hub_clear<256><<<p.n_hub_items[HL_SLICES], 256, 0, s>>>(h);
+                return cudaGetLastError();
+            });
+            if (e != cudaSuccess) return e;
+        }
+        h.items = p.hub_items[HL_HUBS];
         e = timed(LPA_K_HUB_MOVE, [&] {
-            k_hub_move<<<p.n_hub_hubs, 128, 0, s>>>(h);
+            k_hub_move<<<p.n_hub_items[HL_HUBS], 128, 0, s>>>(h);
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
-        h.items = p.hub_chunks;
+        h.items = p.hub_items[HL_MARK];
         e = timed(LPA_K_HUB_MARK, [&] {
-            k_hub_mark<512><<<p.n_hub_chunks, 512, 0, s>>>(h);
+            k_hub_mark<512><<<p.n_hub_items[HL_MARK], 512, 0, s>>>(h);
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;

@@ -75,6 +75,20 @@ def test_batch_sync_equals_oracle_and_single_runs(lpa):
     assert all(torch.equal(labels0[i], b.labels(i).cpu()) for i in range(len(graphs)))
 
 
+def test_batch_cluster_hub_tables(lpa):
+    """Graphs with hubs of several sizes whose tables live in cluster shared memory, beside
+    graphs without hubs, in one batch."""
+    graphs = [gg.star(20_000), gg.star(70_000), gg.rmat(13, weights="int8")] + mixed_graphs(7, count=6,
+                                                                                             with_hub=False)
+    b = lpa.Batch([as_tuple(g) for g in graphs])
+    b.set_tuning(hub_cluster=1, cta_xl_max=1023, cta_large_max=1023)
+    results, _ = b.run(0.05, 20, 4, lpa.SYNC)
+    for i, g in enumerate(graphs):
+        ref = oracle.lpa_sync(oracle.Graph.of(g), 0.05, 20, 4)
+        assert b.labels(i).cpu().numpy().tolist() == ref.labels.tolist(), f"graph {i}"
+        assert results[i]["iterations"] == ref.iterations
+
+
 def test_batch_modularity_and_other_parameters(lpa):
     graphs = mixed_graphs(2, count=12, with_hub=False)
     b = lpa.Batch([as_tuple(g) for g in graphs])

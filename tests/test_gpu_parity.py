@@ -24,6 +24,8 @@ SMALL_BUCKETS = dict(thread_max=3, group_max=7, group_lanes=4, warp_max=31, cta_
                      hub_table_shift=0)
 # the paper's table capacity nextPow2(D) - 1 everywhere (load factor up to 1, probe fallbacks)
 PAPER_TABLES = dict(SMALL_BUCKETS, smem_table_shift=0, hub_table_shift=0)
+# hub tables in thread-block cluster shared memory (integer sums)
+CLUSTER_HUBS = dict(SMALL_BUCKETS, hub_cluster=1)
 
 
 @pytest.fixture(scope="module")
@@ -77,7 +79,7 @@ def test_closed_form_cases_sync(lpa, case):
         "star": (gg.star(9), 4),
     }
     csr, pl = fixtures[case]
-    for tuning in (None, SMALL_BUCKETS):
+    for tuning in (None, SMALL_BUCKETS, CLUSTER_HUBS):
         check_sync_every_iteration(lpa, csr, 0.05, 20, pl, tuning)
 
 
@@ -99,10 +101,15 @@ def test_sync_rmat_default_buckets(lpa, scale, weights):
     check_sync_every_iteration(lpa, csr, 0.05, 20, 4)
 
 
-@pytest.mark.parametrize("scale,tables", [(13, "half"), (15, "half"), (14, "paper")])
+@pytest.mark.parametrize("scale,tables", [(13, "half"), (15, "half"), (14, "paper"), (13, "cluster"),
+                                          (15, "cluster"), (14, "cluster-paper")])
 def test_sync_rmat_small_buckets_with_hubs(lpa, scale, tables):
+    """Hubs above every shared-memory bucket, with tables in HBM or in cluster shared memory
+    (the R-MAT 15 hubs span several cluster sizes)."""
     csr = gg.rmat(scale, weights="int8")
-    check_sync_every_iteration(lpa, csr, 0.05, 20, 4, SMALL_BUCKETS if tables == "half" else PAPER_TABLES)
+    tuning = {"half": SMALL_BUCKETS, "paper": PAPER_TABLES, "cluster": CLUSTER_HUBS,
+              "cluster-paper": dict(PAPER_TABLES, hub_cluster=1)}[tables]
+    check_sync_every_iteration(lpa, csr, 0.05, 20, 4, tuning)
 
 
 @pytest.mark.parametrize("scale,tuning", [(13, "float"), (14, "float-small")])
@@ -197,7 +204,7 @@ def expected_active(csr, og, iterations, tol, pl):
     return out
 
 
-@pytest.mark.parametrize("which", ["random0", "random1", "random-loops", "sbm", "rmat-small-buckets"])
+@pytest.mark.parametrize("which", ["random0", "random1", "random-loops", "sbm", "rmat-cluster-hubs"])
 def test_sync_active_sets_match_definition(lpa, which):
     """The per-sweep active counts equal the definition whether a sweep learnt its active
     vertices from marks or from the moved bits of the sweep before (sweeps that move many
@@ -209,7 +216,7 @@ def test_sync_active_sets_match_definition(lpa, which):
     elif which == "sbm":
         csr = gg.sbm(3000, 50, 10.0, 2.0, seed=3, weights="int8")
     else:
-        csr, tuning = gg.rmat(12, weights="int8"), SMALL_BUCKETS
+        csr, tuning = gg.rmat(12, weights="int8"), CLUSTER_HUBS
     og = oracle_graph(csr)
     ref = oracle.lpa_sync(og, 0.0, 12, 4)
     g = make(lpa, csr, True, tuning)
