@@ -226,6 +226,30 @@ template <> __device__ __forceinline__ double acc_weight<double>(const float *w,
     return w ? (double)w[e] : 1.0;
 }
 
+// Sums over entries e = start, start + STEP, ... < end of one row: k += w_e, and in += w_e
+// where the neighbour's label equals ci.  Four entries per round so that four label gathers
+// are in flight per thread.
+template <int STEP, typename ACC>
+__device__ __forceinline__ void mod_row(const int32_t *idx, const float *w, const int32_t *C, int64_t start,
+                                        int64_t end, int32_t ci, ACC &k, ACC &in)
+{
+    for (int64_t e = start; e < end; e += 4 * (int64_t)STEP) {
+        int32_t j[4];
+        ACC we[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t eu = e + (int64_t)u * STEP;
+            j[u] = eu < end ? idx[eu] : -1;
+            we[u] = eu < end ? acc_weight<ACC>(w, eu) : ACC(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            k += we[u];
+            if (j[u] >= 0 && C[j[u]] == ci) in += we[u];
+        }
+    }
+}
+
 template <int G, typename ACC>
 __global__ void __launch_bounds__(256) k_mod_list(const int64_t *off, const int32_t *idx, const float *w,
                                                   const int32_t *C, const int32_t *list, int64_t count, ACC *Sig,
@@ -249,11 +273,7 @@ __global__ void __launch_bounds__(256) k_mod_list(const int64_t *off, const int3
         const int64_t o0 = off[i], o1 = off[i + 1];
         const int32_t ci = C[i];
         ACC k = ACC(0), in = ACC(0);
-        for (int64_t e = o0 + lane; e < o1; e += G) {
-            const ACC we = acc_weight<ACC>(w, e);
-            k += we;
-            if (C[idx[e]] == ci) in += we;
-        }
+        mod_row<G, ACC>(idx, w, C, o0 + lane, o1, ci, k, in);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
             k += __shfl_xor_sync(gm, k, o);
@@ -299,11 +319,7 @@ __global__ void __launch_bounds__(256) k_mod_hub_chunks(const int32_t *idx, cons
     const int32_t v = hub_v[chunk_h[blockIdx.x]];
     const int32_t ci = C[v];
     ACC k = ACC(0), in = ACC(0);
-    for (int64_t e = chunk_e0[blockIdx.x] + threadIdx.x; e < chunk_e1[blockIdx.x]; e += 256) {
-        const ACC we = acc_weight<ACC>(w, e);
-        k += we;
-        if (C[idx[e]] == ci) in += we;
-    }
+    mod_row<256, ACC>(idx, w, C, chunk_e0[blockIdx.x] + threadIdx.x, chunk_e1[blockIdx.x], ci, k, in);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         k += __shfl_xor_sync(0xFFFFFFFFu, k, o);
@@ -349,6 +365,43 @@ __global__ void __launch_bounds__(256) k_weight_props(const int64_t *off, const 
     }
     if (!integral) atomicAnd(flags, ~2u);
     if (lane == 0 && mx) atomicMax(max_k, mx);
+}
+
+// Flat pass over all weights: bit 1 of *flags is cleared when a weight is not an integer in
+// [0, 2^24); *wmax_bits receives the bits of the largest weight (non-negative floats order
+// like their bit patterns).  Row sums are needed only when max weight x max degree can
+// reach 2^24 (then k_weight_props computes them).
+__global__ void __launch_bounds__(256) k_weight_flat(const float *w, int64_t m, unsigned *flags, unsigned *wmax_bits)
+{
+    bool integral = true;
+    float mx = 0.0f;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const float x = w[e];
+        if (!(x >= 0.0f && x < 16777216.0f && truncf(x) == x)) integral = false;
+        mx = fmaxf(mx, x);
+    }
+    integral = __all_sync(0xFFFFFFFFu, integral);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    if ((threadIdx.x & 31) == 0) {
+        if (!integral) atomicAnd(flags, ~2u);
+        atomicMax(wmax_bits, __float_as_uint(mx));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_degree_max(const int64_t *off, int64_t n, unsigned long long *dmax)
+{
+    unsigned long long mx = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long d = (unsigned long long)(off[i + 1] - off[i]);
+        mx = d > mx ? d : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(dmax, mx);
 }
 
 // Integer-weight modularity: every sum is an exact integer (int64 for sigma, Sigma_c and 2m,
@@ -1134,21 +1187,47 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
         return fail(LPA_EINVAL);
     }
     {
+        // integer sums are exact when every weight is an integer and every row sum is below
+        // 2^24: max weight x max degree below 2^24 settles it, else the exact row sums do
         unsigned long long *mk = nullptr;
-        if ((st = dalloc(g, &mk, 1)) != LPA_OK) return fail(st);
+        if ((st = dalloc(g, &mk, 2)) != LPA_OK) return fail(st);
         unsigned *fl = reinterpret_cast<unsigned *>(g->d_err);
-        cudaMemsetAsync(mk, 0, sizeof(unsigned long long), s);
-        const unsigned two = 2u;
-        cudaMemcpyAsync(fl, &two, sizeof(unsigned), cudaMemcpyHostToDevice, s);
-        k_weight_props<<<grid_for(n * 32, 256, 16), 256, 0, s>>>(g->off, g->w, n, fl, mk);
-        unsigned hf = 0;
-        unsigned long long hk = 0;
-        cudaMemcpyAsync(&hf, fl, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&hk, mk, sizeof(hk), cudaMemcpyDeviceToHost, s);
+        cudaMemsetAsync(mk, 0, 2 * sizeof(unsigned long long), s);
+        const unsigned init[2] = {2u, 0u};            // flags, largest weight bits
+        cudaMemcpyAsync(fl, init, sizeof(init), cudaMemcpyHostToDevice, s);
+        if (g->w && m > 0)
+            k_weight_flat<<<grid_for(m, 256, 16), 256, 0, s>>>(g->w, m, fl, fl + 1);
+        k_degree_max<<<grid_for(n, 256, 16), 256, 0, s>>>(g->off, n, mk + 1);
+        unsigned hf[2] = {0u, 0u};
+        unsigned long long hd = 0;
+        cudaMemcpyAsync(hf, fl, sizeof(hf), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&hd, mk + 1, sizeof(hd), cudaMemcpyDeviceToHost, s);
         e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            dfree(g, mk);
+            return cuda_fail(e, "weight properties");
+        }
+        float wmax = 1.0f;
+        if (g->w) memcpy(&wmax, &hf[1], sizeof(float));
+        const bool integral = (hf[0] & 2u) != 0;
+        if (integral && (double)wmax * (double)hd < 16777216.0) {
+            g->int_weights = true;
+        } else if (integral) {
+            const unsigned two = 2u;
+            cudaMemcpyAsync(fl, &two, sizeof(unsigned), cudaMemcpyHostToDevice, s);
+            k_weight_props<<<grid_for(n * 32, 256, 16), 256, 0, s>>>(g->off, g->w, n, fl, mk);
+            unsigned long long hk = 0;
+            cudaMemcpyAsync(&hk, mk, sizeof(hk), cudaMemcpyDeviceToHost, s);
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                dfree(g, mk);
+                return cuda_fail(e, "weight properties");
+            }
+            g->int_weights = hk < (1ull << 24);
+        } else {
+            g->int_weights = false;
+        }
         dfree(g, mk);
-        if (e != cudaSuccess) return cuda_fail(e, "weight properties");
-        g->int_weights = (hf & 2u) && hk < (1ull << 24);
     }
     if (flags & LPA_CHECK_SYMMETRIC) {
         unsigned long long *acc = nullptr;
