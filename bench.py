@@ -194,6 +194,24 @@ def cpu_baseline(csr_dev, n_windows=16, target_s=12.0):
                 host=dict(machine=platform.machine(), nproc=os.cpu_count(), cpu=_cpu_model()))
 
 
+def cpu_multicore(csr_dev, h_off=None, h_idx=None, h_w=None):
+    """The multicore CPU baseline (OpenMP restatement of the synchronous sweep, all host
+    cores) on the first, all-active synchronous sweep of the whole graph, in entries/s."""
+    import oracle
+    if h_off is None:
+        h_off, h_idx = csr_dev.offsets.cpu(), csr_dev.indices.cpu()
+        h_w = None if csr_dev.weights is None else csr_dev.weights.cpu()
+    og = oracle.Graph(h_off, h_idx, h_w)
+    threads = oracle.multicore_threads()
+    t0 = time.perf_counter()
+    r = oracle.multicore_lpa_sync(og, ALG["tolerance"], 1, ALG["pl_period"])
+    t = time.perf_counter() - t0
+    return dict(value=og.m / t, unit="edges/s", cores=threads, kind="multicore", seconds=round(t, 3),
+                moved=r.dN[0] if r.dN else 0,
+                sample=f"first synchronous sweep (Pick-Less, all vertices active) over the whole graph: {og.n} "
+                       f"vertices, {og.m} CSR entries; OpenMP over {threads} threads, per-thread hash tables")
+
+
 def _cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -385,6 +403,20 @@ def run_ours(args):
                                     for k in range(lpa.NUM_KERNELS) if first["kernel_ms"][i][k] > 0}}
                        for i in range(len(first["iter_ms"]))]}
 
+    # probe-scheme comparison (Section 4.2): the same run with each scheme of the tables
+    if not args.no_ablation and ws == 1:
+        ab = {}
+        names = {0: "quadratic-double", 1: "linear", 2: "quadratic", 3: "double"}
+        for pr in (1, 2, 3, 0):
+            g.set_tuning(probe=pr)
+            best = None
+            for _ in range(2):
+                st = g.run(ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode).to_dict()
+                if best is None or st["total_ms"] < best["total_ms"]:
+                    best = st
+            ab[names[pr]] = {"run_ms": round(best["total_ms"], 2), "probe_fallbacks": best["probe_fallbacks"],
+                             "iterations": best["iterations"]}
+        line["probe_ablation"] = ab
     # end to end through the public API with host buffers
     h_off = h_idx = h_w = h_lab = None
     if not args.no_e2e:
@@ -420,6 +452,7 @@ def run_ours(args):
                                    "lpa_labels to pinned host, lpa_modularity, lpa_destroy"}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(csr, target_s=args.ref_seconds)
+        line["cpu_multicore"] = cpu_multicore(csr, h_off, h_idx, h_w)
     # the batched and served workloads, summarised in the same line (one GPU only)
     if ws == 1 and not args.no_extras:
         h_off = h_idx = h_w = h_lab = None
@@ -682,6 +715,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served summaries")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the default buckets")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the probe-scheme comparison")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=20_000)

@@ -131,6 +131,10 @@ typedef struct lpa_tuning {
     int32_t item_vertices;    /* vertices per work item of the thread/group/warp kernels (0 = default) */
     int32_t float_values;     /* 1: float32 label sums even when integer sums would do   */
     int32_t hub_cluster;      /* 1: hub tables in cluster shared memory where they fit   */
+    int32_t probe;            /* table probe scheme (Section 4.2): 0 quadratic-double
+                                 (Algorithm 2), 1 linear, 2 quadratic, 3 double hashing;
+                                 the table contents, hence the labels, do not depend on it */
+    int32_t reserved[3];      /* zero                                                    */
 } lpa_tuning;
 
 typedef struct lpa_graph lpa_graph;

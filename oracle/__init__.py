@@ -12,6 +12,8 @@ Functions and the passages they follow:
   modularity / modularity_exact          -- Eq. 1 (community form)
   violations            -- vertices whose label is not a max-weight neighbour label
   sweep_range           -- one all-active synchronous sweep over a vertex range
+  multicore_lpa_sync    -- the synchronous run on all host cores (OpenMP, lpa_multicore.c):
+                           a timing baseline that must give lpa_sync's result
 """
 from __future__ import annotations
 
@@ -31,12 +33,18 @@ _LIB = os.path.join(_HERE, f"liblpa_oracle.{platform.machine()}.so")   # per hos
 MAX_RETRIES = 32      # hashtable probe budget before the linear fallback (reading of Algorithm 2)
 
 
+_MC_SRC = os.path.join(_HERE, "lpa_multicore.c")
+_MC_LIB = os.path.join(_HERE, f"liblpa_multicore.{platform.machine()}.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, C11).  Returns the library path."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
+    """Compile the oracle with gcc (-O2, C11), and the multicore baseline with -fopenmp.
+    Returns the oracle library path."""
+    for src, out, extra in ((_SRC, _LIB, []), (_MC_SRC, _MC_LIB, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+            tmp = out + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", *extra, "-o", tmp, src])
+            os.replace(tmp, out)
     return _LIB
 
 
@@ -138,6 +146,35 @@ def lpa_sync(g: Graph, tol=0.05, max_iters=20, pl_period=4, labels=None, active=
 def lpa_async(g: Graph, tol=0.05, max_iters=20, pl_period=4, labels=None, active=None, start_iter=0):
     """Asynchronous in-place LPA, vertices visited in order 0..n-1 (Section 4 item 1)."""
     return _run(lib().orc_lpa_async, g, tol, max_iters, pl_period, labels, active, start_iter)
+
+
+_mc = None
+
+
+def _mc_lib():
+    global _mc
+    if _mc is None:
+        build()
+        L = ct.CDLL(_MC_LIB)
+        P = ct.c_void_p
+        L.mc_lpa_sync.argtypes = [ct.c_int64, P, P, P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P,
+                                  ct.c_int]
+        L.mc_lpa_sync.restype = ct.c_int
+        L.mc_threads.restype = ct.c_int
+        _mc = L
+    return _mc
+
+
+def multicore_threads() -> int:
+    return int(_mc_lib().mc_threads())
+
+
+def multicore_lpa_sync(g: Graph, tol=0.05, max_iters=20, pl_period=4, labels=None, active=None, start_iter=0,
+                       threads=0):
+    """The synchronous run of lpa_sync on all host cores (OpenMP); threads <= 0: all."""
+    L = _mc_lib()
+    return _run(lambda *a: L.mc_lpa_sync(*a, int(threads)), g, tol, max_iters, pl_period, labels, active,
+                start_iter)
 
 
 def sweep_range(g: Graph, labels, v0: int, v1: int, pl: bool = False):

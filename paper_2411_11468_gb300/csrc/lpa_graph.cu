@@ -684,6 +684,9 @@ int check_tuning(const lpa_tuning &t)
     if (t.item_vertices < 0 || t.item_vertices > (1 << 20)) return LPA_EINVAL;
     if (t.float_values != 0 && t.float_values != 1) return LPA_EINVAL;
     if (t.hub_cluster != 0 && t.hub_cluster != 1) return LPA_EINVAL;
+    if (t.probe < 0 || t.probe > 3) return LPA_EINVAL;
+    for (int r : t.reserved)
+        if (r != 0) return LPA_EINVAL;
     const int64_t smem = (int64_t)max_dynamic_smem();
     const int64_t bytes_group = (256 / t.group_lanes) * slots_for(t.group_max, sh) * 8;
     const int64_t bytes_warp = 8 * slots_for(t.warp_max, sh) * 8;
@@ -1063,6 +1066,7 @@ int upload_descriptor(lpa_graph *g)
     d.lists = g->lists;
     d.rs = g->rs_d;
     d.tshift = g->tuning.smem_table_shift;
+    d.probe = g->tuning.probe;
     d.int_weights = plan_int_weights(g) ? 1 : 0;
     LPA_CUDA(cudaMemcpyAsync(g->gdd, &g->gdh, sizeof(GraphDev), cudaMemcpyHostToDevice, g->stream));
     return LPA_OK;

@@ -95,7 +95,7 @@ struct GraphDev {
     int32_t ctr_iters;
     int32_t tshift;            // smem table capacity = nextPow2(D << tshift) - 1
     int32_t int_weights;       // integer weights with weighted degrees < 2^24 (uint32 sums)
-    int32_t pad;
+    int32_t probe;             // table probe scheme (lpa_tuning.probe)
     HubArgs hub;
 };
 

@@ -84,18 +84,24 @@ __device__ __forceinline__ uint32_t cap_of_bits(uint32_t b) { return b >= 32 ? 0
 // the low half, so taking an empty slot is one compare-and-swap that also stores the first
 // weight, and adding to a present key is one add (sums stay below 2^24, so the low half
 // never carries into the key).  Both hold the same (key, sum) pairs at the same slots.
+// Probe schemes of Section 4.2 (lpa_tuning.probe): the quadratic-double hybrid of Algorithm 2
+// (the default), and for comparison linear probing, quadratic probing and double hashing.
+enum { kProbeQuadDouble = 0, kProbeLinear = 1, kProbeQuadratic = 2, kProbeDouble = 3 };
+
 template <typename V>
 struct SplitTable {
     using Val = V;
     int32_t *k;
     V *v;
     int stride;
+    int probe = kProbeQuadDouble;
 };
 
 struct PackedTable {
     using Val = uint32_t;
     unsigned long long *h;
     int stride;
+    int probe = kProbeQuadDouble;
 };
 
 constexpr unsigned long long kEmptySlot = 0xFFFFFFFF00000000ull;   // key -1, sum 0
@@ -193,6 +199,7 @@ struct ClusterTable {
     unsigned long long *base;  // this block's slice
     uint32_t lb;               // log2 of the slots per block
     int stride;                // 1
+    int probe = kProbeQuadDouble;
 };
 
 template <bool SHARED, bool TRACK>
@@ -205,33 +212,48 @@ __device__ __forceinline__ bool try_slot(const ClusterTable &T, size_t s, int32_
 }
 
 // hashtableAccumulate (Algorithm 2) with i and delta kept reduced mod p1 (same slots),
-// then a linear scan from the last probed slot once the probe budget is spent.
+// then a linear scan from the last probed slot once the probe budget is spent.  The probe
+// step follows the table's scheme: Algorithm 2's delta <- 2 delta + (k mod p2) from delta = 1;
+// linear: delta = 1; quadratic: delta <- 2 delta from 1; double hashing: delta = k mod p2.
+__device__ __forceinline__ uint32_t second_step(uint32_t uk, uint32_t b, uint32_t p1)
+{
+    uint32_t q = mod_mersenne(uk, b + 1, 2u * p1 + 1u);          // (k mod p2) mod p1
+    if (q >= p1) q -= p1;
+    if (q >= p1) q -= p1;
+    return q;
+}
+
 template <bool SHARED, bool TRACK, typename T>
 __device__ __forceinline__ void ht_accumulate(const T &tab, uint32_t p1, uint32_t b, int32_t k, typename T::Val v,
                                               unsigned long long &best, unsigned &fallbacks,
                                               uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
 {
     const uint32_t uk = (uint32_t)k;
+    const int mode = tab.probe;
     uint32_t i = mod_mersenne(uk, b, p1);
     uint32_t delta = (p1 > 1u) ? 1u : 0u;
-    uint32_t step = 0xFFFFFFFFu;                      // (k mod p2) mod p1, on first collision
+    uint32_t step = 0xFFFFFFFFu;                      // (k mod p2) mod p1, on first need
+    if (mode == kProbeDouble) {
+        step = second_step(uk, b, p1);
+        delta = step;
+    }
     uint32_t s = i;
 #pragma unroll 1
     for (int t = 0; t < kMaxRetries; ++t) {
         s = i;
         if (try_slot<SHARED, TRACK>(tab, (size_t)s * tab.stride, k, v, best, ucnt, ulist)) return;
-        if (step == 0xFFFFFFFFu) {
-            uint32_t q = mod_mersenne(uk, b + 1, 2u * p1 + 1u);
-            if (q >= p1) q -= p1;
-            if (q >= p1) q -= p1;
-            step = q;
-        }
         i += delta;
         if (i >= p1) i -= p1;
-        unsigned long long d2 = 2ull * delta + step;    // < 3 p1
-        if (d2 >= p1) d2 -= p1;
-        if (d2 >= p1) d2 -= p1;
-        delta = (uint32_t)d2;
+        if (mode == kProbeQuadDouble) {
+            if (step == 0xFFFFFFFFu) step = second_step(uk, b, p1);
+            unsigned long long d2 = 2ull * delta + step;    // < 3 p1
+            if (d2 >= p1) d2 -= p1;
+            if (d2 >= p1) d2 -= p1;
+            delta = (uint32_t)d2;
+        } else if (mode == kProbeQuadratic) {
+            delta <<= 1;
+            if (delta >= p1) delta -= p1;
+        }
     }
     ++fallbacks;
 #pragma unroll 1
@@ -353,6 +375,7 @@ struct SweepView {
     const int32_t *lists;
     int32_t pl, async_mode, tshift, done;
     int32_t mark, pull;        // marks written this sweep; activity from moved bits (sync)
+    int32_t probe;             // probe scheme of the tables
 };
 
 __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
@@ -380,6 +403,7 @@ __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
     v.mover_count = G.mover_count + (l & 1);
     v.mark = rs->mark;
     v.pull = rs->pull;
+    v.probe = G.probe;
     const int slot = (l - rs->first) % (G.ctr_iters > 0 ? G.ctr_iters : 1);
     v.ctr = G.ctr + (size_t)(slot < 0 ? 0 : slot) * kPerSweep;
     v.fallbacks = G.fallbacks;
@@ -608,6 +632,7 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
             }
             cur_g = item.g;
             a = view_of(k.gd, item.g);
+            tab.probe = a.probe;
         }
         if (a.done || (a.pull != 0) != PULL) continue;                // the other launch takes it
         for (int64_t base = 0; base < item.count; base += 32) {       // uniform per warp
@@ -778,6 +803,7 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
             if (cur_g >= 0) flush_counts();
             cur_g = item.g;
             a = view_of(k.gd, item.g);
+            tab.probe = a.probe;
         }
         if (a.done || (a.pull != 0) != PULL) continue;        // the other launch takes it
         for (int64_t base = 0; base < item.count; base += 32) {
@@ -956,10 +982,10 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     if (k.gd[item.g].int_weights) {
-        PackedTable tab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1};
+        PackedTable tab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
         hub_accumulate<TPB, PULL>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
     } else {
-        SplitTable<float> tab{h.tab_k + h.hub_tab[hh], h.tab_v + h.hub_tab[hh], 1};
+        SplitTable<float> tab{h.tab_k + h.hub_tab[hh], h.tab_v + h.hub_tab[hh], 1, a.probe};
         hub_accumulate<TPB, PULL>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
     }
 }
@@ -1004,7 +1030,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kDsmThreads) k_hub_
         const uint32_t lb = b - csb;                   // 2^lb slots per block
         clear_table_vec(PackedTable{slice, 1}, (1u << lb) - 1u, threadIdx.x, kDsmThreads);
         cluster.sync();                                // every slice is clear
-        const ClusterTable tab{slice, lb, 1};
+        const ClusterTable tab{slice, lb, 1, a.probe};
         const int32_t v = h.hub_v[hh];
         const int64_t o0 = a.off[v], o1 = a.off[v + 1];
         const int64_t per = (o1 - o0 + CS - 1) / CS;

@@ -112,6 +112,16 @@ def test_sync_rmat_small_buckets_with_hubs(lpa, scale, tables):
     check_sync_every_iteration(lpa, csr, 0.05, 20, 4, tuning)
 
 
+@pytest.mark.parametrize("probe", [1, 2, 3])
+def test_sync_probe_schemes(lpa, probe):
+    """Linear probing, quadratic probing and double hashing (the alternatives Section 4.2
+    compares) place keys differently but hold the same (label, sum) pairs, so labels and dN
+    equal Algorithm 2's at every sweep, in shared-memory and in hub tables."""
+    csr = gg.rmat(13, weights="int8")
+    for tuning in (dict(probe=probe), dict(SMALL_BUCKETS, probe=probe), dict(CLUSTER_HUBS, probe=probe)):
+        check_sync_every_iteration(lpa, csr, 0.05, 20, 4, tuning)
+
+
 @pytest.mark.parametrize("scale,tuning", [(13, "float"), (14, "float-small")])
 def test_sync_float_label_sums(lpa, scale, tuning):
     """Integer-weight graphs forced onto the float32 label-sum kernels."""

@@ -444,3 +444,30 @@ def test_sweep_window_equals_first_sync_sweep():
         assert e == g.off[v1] - g.off[v0]
         out2, _ = oracle.sweep_range(g, labels0, v0, v1, pl=True)
         assert out2.tolist() == out.tolist()
+
+
+# ---------------------------------------------------------------------------------------
+# the multicore CPU baseline gives the oracle's synchronous result
+
+@pytest.mark.parametrize("seed", range(4))
+def test_multicore_baseline_equals_oracle(seed):
+    import random
+    rnd = random.Random(seed)
+    csr = gg.random_small(rnd.choice([60, 200, 400]), rnd.choice([0.02, 0.1]), 500 + seed, wmax=rnd.choice([1, 5]),
+                          self_loops=seed % 2 == 1)
+    og = oracle.Graph.of(csr)
+    for pl in (0, 4):
+        ref = oracle.lpa_sync(og, 0.05, 20, pl)
+        for threads in (1, 3):
+            got = oracle.multicore_lpa_sync(og, 0.05, 20, pl, threads=threads)
+            assert got.labels.tolist() == ref.labels.tolist()
+            assert got.dN == ref.dN and got.iterations == ref.iterations
+            assert got.active.tolist() == ref.active.tolist()
+
+
+def test_multicore_baseline_rmat_and_closed_forms():
+    for csr in (gg.rmat(11, weights="int8"), gg.complete_bipartite(6), gg.two_cliques_bridge(7), gg.star(12)):
+        og = oracle.Graph.of(csr)
+        ref = oracle.lpa_sync(og, 0.05, 20, 4)
+        got = oracle.multicore_lpa_sync(og, 0.05, 20, 4, threads=4)
+        assert got.labels.tolist() == ref.labels.tolist() and got.dN == ref.dN
