@@ -1560,6 +1560,7 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
     p.cta_xl_threads = g->tuning.cta_xl_threads;
     p.hub_chunk = g->tuning.hub_chunk;
     p.int_weights = plan_int_weights(g) ? 1 : 0;
+    p.probe = g->tuning.probe;
 
     size_t evn = 0;
     cudaEvent_t run0 = event_at(g, evn++), run1 = event_at(g, evn++);

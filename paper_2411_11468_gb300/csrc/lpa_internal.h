@@ -125,6 +125,7 @@ struct SweepPlan {
     int32_t group_lanes, cta_threads, cta_large_threads, cta_xl_threads, hub_chunk;
     int32_t pull_mode;         // kernels launched for this sweep: 0 push only, 1 pull only, 2 both
     int32_t int_weights;       // 1: every graph of the plan uses uint32 sums (else float32)
+    int32_t probe;             // table probe scheme of every graph of the plan (lpa_tuning.probe)
 };
 
 // Optional hook around each kernel launch (CUDA-event timing per kernel slot).

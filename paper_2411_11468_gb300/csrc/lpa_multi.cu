@@ -180,6 +180,7 @@ struct MultiPlan {
         p.cta_xl_threads = t.cta_xl_threads;
         p.hub_chunk = t.hub_chunk;
         p.int_weights = all_int ? 1 : 0;
+        p.probe = t.probe;
         plan = p;
         return LPA_OK;
     }

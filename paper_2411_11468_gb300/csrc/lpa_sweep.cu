@@ -18,896 +18,27 @@
 // lane that made its last add and no observed sum exceeds a final sum (weights are >= 0),
 // so the reduction equals the maximum over the table: the largest weight and, among equal
 // weights, the smallest label (Section 4 item 5).
-#include <cooperative_groups.h>
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-#include "lpa_internal.h"
-
-namespace cg = cooperative_groups;
+#include "sweep_kernels.cuh"
 
 namespace lpa {
 
-// Multipliers for remainders by Mersenne numbers: c_magic[b] = ceil(2^64 / (2^b - 1))
-// (0 for b = 1, where every remainder is 0).  a mod d = mulhi64(M * a, d) for 32-bit a
-// and d (Lemire, Kaser and Kurz, "Faster remainder by direct computation", 2019).
-__constant__ unsigned long long c_magic[33];
-
 cudaError_t sweep_init_constants()
 {
-    unsigned long long h[33];
-    h[0] = 0;
-    for (int b = 1; b <= 32; ++b) {
-        unsigned long long p = (b == 32) ? 0xFFFFFFFFull : ((1ull << b) - 1);
-        h[b] = (p == 1) ? 0ull : (0xFFFFFFFFFFFFFFFFull / p + 1);
-    }
-    return cudaMemcpyToSymbol(c_magic, h, sizeof(h));
+    const cudaError_t e = init_magic();
+    return e != cudaSuccess ? e : sweep_init_constants_alt();
 }
 
-__device__ __forceinline__ uint32_t mod_mersenne(uint32_t a, uint32_t b, uint32_t p)
+size_t max_dynamic_smem()
 {
-    unsigned long long low = c_magic[b] * (unsigned long long)a;
-    return (uint32_t)__umul64hi(low, (unsigned long long)p);
+    query_device();
+    return g_max_smem;
 }
 
-// Label-weight values are float32, or uint32 when every weight is an integer and every
-// weighted degree is below 2^24 (then each float32 sum is exact and equals the integer sum,
-// and both compare the same way).  vbits gives bits that order like the value (values >= 0).
-__device__ __forceinline__ uint32_t vbits(float w) { return __float_as_uint(w); }
-__device__ __forceinline__ uint32_t vbits(uint32_t w) { return w; }
-template <typename V> __device__ __forceinline__ V to_value(float w);
-template <> __device__ __forceinline__ float to_value<float>(float w) { return w; }
-template <> __device__ __forceinline__ uint32_t to_value<uint32_t>(float w) { return (uint32_t)w; }
-
-template <typename V>
-__device__ __forceinline__ unsigned long long pack_kv(V w, int32_t k)
+int num_sms()
 {
-    return ((unsigned long long)vbits(w) << 32) | (unsigned long long)(~(uint32_t)k);
+    query_device();
+    return g_num_sms;
 }
-
-__device__ __forceinline__ int32_t unpack_key(unsigned long long p)
-{
-    return (int32_t)(~(uint32_t)(p & 0xFFFFFFFFull));
-}
-
-__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b)
-{
-    return a > b ? a : b;
-}
-
-// capacity 2^b - 1 >= x (x >= 1)
-__device__ __forceinline__ uint32_t cap_bits(uint32_t x) { return 32u - __clz(x); }
-__device__ __forceinline__ uint32_t cap_of_bits(uint32_t b) { return b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u); }
-
-// Table layouts.  Split: keys and values in two arrays (slot s at index s * stride).  Packed
-// (integer sums only): one 64-bit word per slot, key in the high half and the uint32 sum in
-// the low half, so taking an empty slot is one compare-and-swap that also stores the first
-// weight, and adding to a present key is one add (sums stay below 2^24, so the low half
-// never carries into the key).  Both hold the same (key, sum) pairs at the same slots.
-// Probe schemes of Section 4.2 (lpa_tuning.probe): the quadratic-double hybrid of Algorithm 2
-// (the default), and for comparison linear probing, quadratic probing and double hashing.
-enum { kProbeQuadDouble = 0, kProbeLinear = 1, kProbeQuadratic = 2, kProbeDouble = 3 };
-
-template <typename V>
-struct SplitTable {
-    using Val = V;
-    int32_t *k;
-    V *v;
-    int stride;
-    int probe = kProbeQuadDouble;
-};
-
-struct PackedTable {
-    using Val = uint32_t;
-    unsigned long long *h;
-    int stride;
-    int probe = kProbeQuadDouble;
-};
-
-constexpr unsigned long long kEmptySlot = 0xFFFFFFFF00000000ull;   // key -1, sum 0
-
-// One slot attempt of Algorithm 2: take slot s if it is empty or already holds k, add v
-// and fold the new sum into `best`.  With TRACK a slot taken from empty is appended to the
-// table's used list.
-template <bool SHARED, bool TRACK, typename V>
-__device__ __forceinline__ bool try_slot(const SplitTable<V> &T, size_t s, int32_t k, V v, unsigned long long &best,
-                                         uint32_t *ucnt, int32_t *ulist)
-{
-    int32_t *Hk = T.k;
-    V *Hv = T.v;
-    if (!SHARED) {                                    // single owner: plain accesses
-        const int32_t kk = Hk[s];
-        if (kk == k || kk == kEmpty) {
-            Hk[s] = k;
-            const V nv = Hv[s] + v;
-            Hv[s] = nv;
-            best = umax64(best, pack_kv(nv, k));
-            return true;
-        }
-        return false;
-    }
-    int32_t kk = *((volatile int32_t *)(Hk + s));
-    if (kk == kEmpty) {
-        const int32_t old = atomicCAS(Hk + s, kEmpty, k);
-        if (old == kEmpty) {
-            kk = k;
-            if (TRACK) ulist[atomicAdd(ucnt, 1u)] = (int32_t)s;
-        } else {
-            kk = old;
-        }
-    }
-    if (kk == k) {
-        const V nv = atomicAdd(Hv + s, v) + v;
-        best = umax64(best, pack_kv(nv, k));
-        return true;
-    }
-    return false;
-}
-
-// Shared (atomic) update of one packed slot at p (slot index s for the used list).
-template <bool TRACK>
-__device__ __forceinline__ bool packed_update(unsigned long long *p, size_t s, int32_t k, uint32_t v,
-                                              unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
-{
-    const uint32_t uk = (uint32_t)k;
-    uint32_t ck = (uint32_t)(*((volatile unsigned long long *)p) >> 32);
-    if (ck == 0xFFFFFFFFu) {
-        const unsigned long long old = atomicCAS(p, kEmptySlot, ((unsigned long long)uk << 32) | v);
-        if (old == kEmptySlot) {
-            if (TRACK) ulist[atomicAdd(ucnt, 1u)] = (int32_t)s;
-            best = umax64(best, pack_kv(v, k));
-            return true;
-        }
-        ck = (uint32_t)(old >> 32);
-    }
-    if (ck == uk) {
-        // 32-bit add on the sum half (the low word, at the lower address): native in shared
-        // memory, unlike a 64-bit add.  The key half never changes once the slot is taken, so
-        // a concurrent compare-and-swap on the slot fails on the key whatever the sum.
-        const uint32_t nv = atomicAdd(reinterpret_cast<uint32_t *>(p), v) + v;
-        best = umax64(best, pack_kv(nv, k));
-        return true;
-    }
-    return false;
-}
-
-template <bool SHARED, bool TRACK>
-__device__ __forceinline__ bool try_slot(const PackedTable &T, size_t s, int32_t k, uint32_t v,
-                                         unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
-{
-    unsigned long long *p = T.h + s;
-    if (!SHARED) {
-        const uint32_t uk = (uint32_t)k;
-        const unsigned long long cur = *p;
-        const uint32_t ck = (uint32_t)(cur >> 32);
-        if (ck == uk || ck == 0xFFFFFFFFu) {
-            const uint32_t nv = (uint32_t)cur + v;       // an empty slot holds sum 0
-            *p = ((unsigned long long)uk << 32) | nv;
-            best = umax64(best, pack_kv(nv, k));
-            return true;
-        }
-        return false;
-    }
-    return packed_update<TRACK>(p, s, k, v, best, ucnt, ulist);
-}
-
-// A hub table spread over the shared memory of the blocks of a thread-block cluster (packed
-// layout): slot s lives in block s >> lb at index s & (2^lb - 1) of that block's slice, and
-// is reached through the cluster's distributed shared memory.
-struct ClusterTable {
-    using Val = uint32_t;
-    unsigned long long *base;  // this block's slice
-    uint32_t lb;               // log2 of the slots per block
-    int stride;                // 1
-    int probe = kProbeQuadDouble;
-};
-
-template <bool SHARED, bool TRACK>
-__device__ __forceinline__ bool try_slot(const ClusterTable &T, size_t s, int32_t k, uint32_t v,
-                                         unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
-{
-    unsigned long long *p = cg::this_cluster().map_shared_rank(T.base, (unsigned)(s >> T.lb)) +
-                            (s & (((size_t)1 << T.lb) - 1));
-    return packed_update<TRACK>(p, s, k, v, best, ucnt, ulist);
-}
-
-// hashtableAccumulate (Algorithm 2) with i and delta kept reduced mod p1 (same slots),
-// then a linear scan from the last probed slot once the probe budget is spent.  The probe
-// step follows the table's scheme: Algorithm 2's delta <- 2 delta + (k mod p2) from delta = 1;
-// linear: delta = 1; quadratic: delta <- 2 delta from 1; double hashing: delta = k mod p2.
-__device__ __forceinline__ uint32_t second_step(uint32_t uk, uint32_t b, uint32_t p1)
-{
-    uint32_t q = mod_mersenne(uk, b + 1, 2u * p1 + 1u);          // (k mod p2) mod p1
-    if (q >= p1) q -= p1;
-    if (q >= p1) q -= p1;
-    return q;
-}
-
-template <bool SHARED, bool TRACK, typename T>
-__device__ __forceinline__ void ht_accumulate(const T &tab, uint32_t p1, uint32_t b, int32_t k, typename T::Val v,
-                                              unsigned long long &best, unsigned &fallbacks,
-                                              uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
-{
-    const uint32_t uk = (uint32_t)k;
-    const int mode = tab.probe;
-    uint32_t i = mod_mersenne(uk, b, p1);
-    uint32_t delta = (p1 > 1u) ? 1u : 0u;
-    uint32_t step = 0xFFFFFFFFu;                      // (k mod p2) mod p1, on first need
-    if (mode == kProbeDouble) {
-        step = second_step(uk, b, p1);
-        delta = step;
-    }
-    uint32_t s = i;
-#pragma unroll 1
-    for (int t = 0; t < kMaxRetries; ++t) {
-        s = i;
-        if (try_slot<SHARED, TRACK>(tab, (size_t)s * tab.stride, k, v, best, ucnt, ulist)) return;
-        i += delta;
-        if (i >= p1) i -= p1;
-        if (mode == kProbeQuadDouble) {
-            if (step == 0xFFFFFFFFu) step = second_step(uk, b, p1);
-            unsigned long long d2 = 2ull * delta + step;    // < 3 p1
-            if (d2 >= p1) d2 -= p1;
-            if (d2 >= p1) d2 -= p1;
-            delta = (uint32_t)d2;
-        } else if (mode == kProbeQuadratic) {
-            delta <<= 1;
-            if (delta >= p1) delta -= p1;
-        }
-    }
-    ++fallbacks;
-#pragma unroll 1
-    for (uint32_t u = 1; u <= p1; ++u) {
-        uint32_t q = s + u;
-        if (q >= p1) q -= p1;
-        if (try_slot<SHARED, TRACK>(tab, (size_t)q * tab.stride, k, v, best, ucnt, ulist)) return;
-    }
-}
-
-template <int G>
-__device__ __forceinline__ unsigned group_mask()
-{
-    if (G >= 32) return 0xFFFFFFFFu;
-    const unsigned lane = threadIdx.x & 31u;
-    return ((1u << (G & 31)) - 1u) << (lane & ~(unsigned)(G - 1));
-}
-
-template <int G>
-__device__ __forceinline__ void group_sync()
-{
-    if (G > 1) __syncwarp(group_mask<G>());
-}
-
-template <int G>
-__device__ __forceinline__ unsigned long long group_max(unsigned long long x)
-{
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) x = umax64(x, __shfl_xor_sync(group_mask<G>(), x, o, G));
-    return x;
-}
-
-// Lanes of one group (G lanes, aligned inside the warp) insert their (key, weight) pairs
-// into the group's shared table.  Before the per-lane inserts, up to kPeel rounds take the
-// key of the lowest pending lane, sum the weights of every lane holding that key with a
-// shuffle reduction and insert the sum once: after a few sweeps most neighbours of a vertex
-// share a handful of labels, and same-slot atomics would otherwise serialise.  Integer
-// weights keep every partial sum exact, so the table contents do not depend on the order.
-constexpr int kPeel = 3;
-
-template <int G, bool SHARED, bool TRACK, typename T>
-__device__ __forceinline__ void group_insert(const T &tab, uint32_t p1, uint32_t b, bool has, int32_t k,
-                                             typename T::Val w, unsigned long long &best, unsigned &fb,
-                                             uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
-{
-    using V = typename T::Val;
-    if (G >= 2) {
-        const unsigned gm = group_mask<G>();
-        const int lane = threadIdx.x & 31;
-        unsigned pend = __ballot_sync(gm, has);
-#pragma unroll 1
-        for (int r = 0; r < kPeel && pend; ++r) {
-            const int leader = __ffs(pend) - 1;
-            const int32_t kl = __shfl_sync(gm, k, leader);
-            const bool mine = has && k == kl;
-            const unsigned same = __ballot_sync(gm, mine);
-            if (__popc(same) < 2) break;
-            V sum = mine ? w : V(0);
-#pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(gm, sum, o);
-            if (lane == leader) ht_accumulate<SHARED, TRACK>(tab, p1, b, kl, sum, best, fb, ucnt, ulist);
-            if (mine) has = false;
-            pend &= ~same;
-        }
-    }
-    if (has) ht_accumulate<SHARED, TRACK>(tab, p1, b, k, w, best, fb, ucnt, ulist);
-}
-
-// hashtableClear of slots [0, p1] of a contiguous, 16-byte aligned table with 16-byte stores
-// (p1 + 1 is a power of two, at least 4 slots are allocated).
-// (Values are cleared to all-zero bits, which is 0 for both value types.)
-template <typename V>
-__device__ __forceinline__ void clear_table_vec(const SplitTable<V> &T, uint32_t p1, int first, int step)
-{
-    const uint32_t chunks = (p1 + 4u) >> 2;
-    int4 *K4 = reinterpret_cast<int4 *>(T.k);
-    int4 *V4 = reinterpret_cast<int4 *>(T.v);
-    for (uint32_t q = first; q < chunks; q += step) {
-        K4[q] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
-        V4[q] = make_int4(0, 0, 0, 0);
-    }
-}
-
-__device__ __forceinline__ void clear_table_vec(const PackedTable &T, uint32_t p1, int first, int step)
-{
-    const uint32_t chunks = (p1 + 2u) >> 1;          // two slots per 16 bytes
-    int4 *H4 = reinterpret_cast<int4 *>(T.h);
-    for (uint32_t q = first; q < chunks; q += step) H4[q] = make_int4(0, kEmpty, 0, kEmpty);
-}
-
-// Clear of a thread's private interleaved table (slot s at s * stride).
-template <typename V>
-__device__ __forceinline__ void clear_table_private(const SplitTable<V> &T, uint32_t p1)
-{
-    for (uint32_t s = 0; s < p1; ++s) {
-        T.k[(size_t)s * T.stride] = kEmpty;
-        T.v[(size_t)s * T.stride] = V(0);
-    }
-}
-
-__device__ __forceinline__ void clear_table_private(const PackedTable &T, uint32_t p1)
-{
-    for (uint32_t s = 0; s < p1; ++s) T.h[(size_t)s * T.stride] = kEmptySlot;
-}
-
-// The per-sweep view of one graph: what the sweep kernels read and write for an item of
-// graph g, derived from its descriptor and run state.
-struct SweepView {
-    const int64_t *off;
-    const int32_t *idx;
-    const float *w;
-    int32_t *C;
-    uint8_t *flag_cur;         // unprocessed flags read (and cleared) by this sweep
-    uint8_t *flag_next;        // flags set for the next sweep (== flag_cur in ASYNC mode)
-    int32_t *mover_v, *mover_c;
-    unsigned long long *mover_count;
-    unsigned long long *ctr;   // this sweep's counters [LPA_NUM_KERNELS][kCtrFields]
-    unsigned long long *fallbacks;
-    const int32_t *lists;
-    int32_t pl, async_mode, tshift, done;
-    int32_t mark, pull;        // marks written this sweep; activity from moved bits (sync)
-    int32_t probe;             // probe scheme of the tables
-};
-
-__device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
-{
-    const GraphDev &G = gd[g];
-    const RunState *rs = G.rs;
-    SweepView v;
-    const int l = rs->l;
-    v.done = rs->done;
-    v.pl = (rs->pl_period > 0) && (l % rs->pl_period == 0);
-    v.async_mode = rs->async_mode;
-    v.off = G.off;
-    v.idx = G.idx;
-    v.w = G.w;
-    v.C = G.C;
-    if (v.async_mode) {
-        v.flag_cur = G.flags0;
-        v.flag_next = G.flags0;
-    } else {
-        v.flag_cur = (l & 1) ? G.flags1 : G.flags0;
-        v.flag_next = (l & 1) ? G.flags0 : G.flags1;
-    }
-    v.mover_v = (l & 1) ? G.mover_v1 : G.mover_v;
-    v.mover_c = G.mover_c;
-    v.mover_count = G.mover_count + (l & 1);
-    v.mark = rs->mark;
-    v.pull = rs->pull;
-    v.probe = G.probe;
-    const int slot = (l - rs->first) % (G.ctr_iters > 0 ? G.ctr_iters : 1);
-    v.ctr = G.ctr + (size_t)(slot < 0 ? 0 : slot) * kPerSweep;
-    v.fallbacks = G.fallbacks;
-    v.lists = G.lists;
-    v.tshift = G.tshift;
-    return v;
-}
-
-// Synchronous movers are staged per warp in shared memory (32 (v, c) pairs) and appended to
-// the graph's mover list with one atomic per 32 movers: a per-vertex atomic on the single
-// list counter would serialise in L2.  Every lane of the warp calls these; n is uniform.
-__device__ __forceinline__ void movers_flush(unsigned long long *count, int32_t *mv, int32_t *mc, int2 *sbuf, int &n)
-{
-    if (n == 0) return;
-    __syncwarp();
-    const int lane = threadIdx.x & 31;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(count, (unsigned long long)n);
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (lane < n) {
-        const int2 m = sbuf[lane];
-        mv[base + lane] = m.x;
-        mc[base + lane] = m.y;
-    }
-    __syncwarp();
-    n = 0;
-}
-
-__device__ __forceinline__ void movers_push(const SweepView &a, int2 *sbuf, int &n, bool pred, int32_t v, int32_t c)
-{
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
-    if (!bal) return;
-    const int cnt = __popc(bal);
-    if (n + cnt > 32) movers_flush(a.mover_count, a.mover_v, a.mover_c, sbuf, n);
-    const int lane = threadIdx.x & 31;
-    if (pred) sbuf[n + __popc(bal & ((1u << lane) - 1u))] = make_int2(v, c);
-    n += cnt;
-}
-
-// Loads entry e of the row of v: (label of the neighbour, weight); has = false for e past
-// the row end and for self-loops (Algorithm 1 skips j = i).  With SEEN (pull sweeps) the raw
-// label words are or-ed into `seen` (bit 31: the neighbour moved in the previous sweep),
-// self-loops included; push sweeps never see the bit and skip that work.
-template <bool SEEN, typename V>
-__device__ __forceinline__ void load_entry(const SweepView &a, int32_t v, int64_t e, int64_t end, bool &has,
-                                           int32_t &k, V &wv, uint32_t &seen)
-{
-    has = e < end;
-    k = 0;
-    wv = V(0);
-    if (has) {
-        const int32_t j = a.idx[e];
-        if (SEEN) {
-            const uint32_t cj = (uint32_t)a.C[j];
-            seen |= cj;
-            has = (j != v);
-            k = (int32_t)(cj & kLabelMask);
-            if (has) wv = a.w ? to_value<V>(a.w[e]) : V(1);
-        } else {
-            has = (j != v);
-            if (has) {
-                k = a.C[j];
-                wv = a.w ? to_value<V>(a.w[e]) : V(1);
-            }
-        }
-    }
-}
-
-// Scans entries [start, end) of the row of v in rounds: each round covers U * step entries,
-// lane offset `lane` inside each step.  All U entries of a round are loaded (index, weight,
-// gathered label) before any of them is inserted, so U gathers per thread are in flight.
-template <int G, bool SHARED, bool TRACK, int U, bool SEEN, typename T>
-__device__ __forceinline__ void scan_row(const SweepView &a, int32_t v, int64_t start, int64_t end, int step,
-                                         int lane, const T &tab, uint32_t p1, uint32_t b,
-                                         unsigned long long &best, unsigned &fb, uint32_t &seen,
-                                         uint32_t *ucnt = nullptr, int32_t *ulist = nullptr, int round = 0)
-{
-    using V = typename T::Val;
-    const int64_t adv = round ? round : (int64_t)step * U;   // a block-wide round for the CTA kernels
-    for (int64_t eb = start; eb < end; eb += adv) {
-        bool has[U];
-        int32_t k[U];
-        V wv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) load_entry<SEEN>(a, v, eb + (int64_t)u * step + lane, end, has[u], k[u], wv[u], seen);
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            group_insert<G, SHARED, TRACK>(tab, p1, b, has[u], k[u], wv[u], best, fb, ucnt, ulist);
-    }
-}
-
-// Move rule of Algorithm 1: c* != C[i] and, on Pick-Less sweeps, c* < C[i].
-__device__ __forceinline__ bool decide(unsigned long long best, int32_t cur, int pl, int32_t &cstar)
-{
-    if (best == 0) return false;                   // no neighbour label (isolated / self-loops only)
-    cstar = unpack_key(best);
-    return (cstar != cur) && (!pl || cstar < cur);
-}
-
-// Shared-memory tables use the packed layout when the sums are integers.
-constexpr bool kPackShared = true;
-template <typename V, bool PACK> struct TableFor {
-    using type = SplitTable<V>;
-};
-template <> struct TableFor<uint32_t, true> {
-    using type = PackedTable;
-};
-
-// Table t of n_tables tables of `slots` slots at `base` (8 bytes per slot in both layouts):
-// interleaved (slot s of table t at s * n_tables + t) or one table after another.
-template <typename V>
-__device__ __forceinline__ void table_at(SplitTable<V> &T, unsigned char *base, int n_tables, int slots, int t,
-                                         bool interleaved)
-{
-    V *vbase = (V *)(base + (size_t)n_tables * slots * sizeof(int32_t));
-    if (interleaved) {
-        T.k = (int32_t *)base + t;
-        T.v = vbase + t;
-        T.stride = n_tables;
-    } else {
-        T.k = (int32_t *)base + (size_t)t * slots;
-        T.v = vbase + (size_t)t * slots;
-        T.stride = 1;
-    }
-}
-
-__device__ __forceinline__ void table_at(PackedTable &T, unsigned char *base, int n_tables, int slots, int t,
-                                         bool interleaved)
-{
-    if (interleaved) {
-        T.h = (unsigned long long *)base + t;
-        T.stride = n_tables;
-    } else {
-        T.h = (unsigned long long *)base + (size_t)t * slots;
-        T.stride = 1;
-    }
-}
-
-// ---------------------------------------------------------------------------------
-// Kernel arguments common to the vertex kernels: the plan's graphs, this kernel's work items
-// and work-queue counter, and the number of graphs still running (0: return at once).
-struct KArgs {
-    const GraphDev *gd;
-    const WorkItem *items;
-    int32_t n_items;
-    int32_t slots;
-    unsigned *queue;
-    const int32_t *active;
-    int32_t kslot;
-    int32_t pad;
-};
-
-// Adds a warp's four counters and its fallback count to graph counters (every lane calls).
-__device__ __forceinline__ void warp_flush(const SweepView &a, int kslot, unsigned act, unsigned edges,
-                                           unsigned moved, unsigned marks, unsigned fb)
-{
-    act = __reduce_add_sync(0xFFFFFFFFu, act);
-    edges = __reduce_add_sync(0xFFFFFFFFu, edges);
-    moved = __reduce_add_sync(0xFFFFFFFFu, moved);
-    marks = __reduce_add_sync(0xFFFFFFFFu, marks);
-    fb = __reduce_add_sync(0xFFFFFFFFu, fb);
-    if ((threadIdx.x & 31) == 0) {
-        unsigned long long *c = a.ctr + kslot * kCtrFields;
-        if (act) atomicAdd(c + CTR_ACTIVE, (unsigned long long)act);
-        if (edges) atomicAdd(c + CTR_EDGES, (unsigned long long)edges);
-        if (moved) atomicAdd(c + CTR_MOVED, (unsigned long long)moved);
-        if (marks) atomicAdd(c + CTR_MARKS, (unsigned long long)marks);
-        if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
-    }
-}
-
-// Entries loaded per lane and round by the G-lane kernels: enough that one round covers the
-// default degree range of each bucket (G = 1: D <= 8, G = 8: D <= 32, G = 32: D <= 256), so
-// a row's index, weight and label loads are all in flight together.
-constexpr int kUnrollThread = 2;      // G = 1
-constexpr int kUnrollSmall = 4;       // G = 2, 4
-constexpr int kUnrollGroup = 2;       // G = 8, 16
-constexpr int kUnrollWarp = 4;        // G = 32
-constexpr int kMinBlocksThread = 6;   // resident blocks per SM asked of the register allocator (128 threads)
-constexpr int kMinBlocks = 3;         // (256 threads)
-template <int G> struct GroupUnroll {
-    static constexpr int U = G == 1 ? kUnrollThread : (G <= 4 ? kUnrollSmall : (G <= 16 ? kUnrollGroup : kUnrollWarp));
-    static constexpr int kMinBlocks = G == 1 ? ::lpa::kMinBlocksThread : ::lpa::kMinBlocks;
-};
-
-// G lanes per vertex (G = 1: thread per vertex with a private table; G = 32: warp per
-// vertex).  Persistent: each warp takes work items (a range of one graph's bucket list) from
-// the queue.  The warp fetches the list entry, processed flag and row bounds of 32 vertices
-// at once (one per lane), then its groups take them 32/G at a time: the per-vertex chain of
-// dependent loads (list, flag, offsets) is paid once per 32 vertices.  Neighbour ids of a
-// row that fits one round stay in registers for the marks.
-template <int G, int TPB, typename V, bool PULL>
-__global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs k)
-{
-    if (*k.active == 0) return;                        // every graph has stopped
-    extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int NG = TPB / G;
-    constexpr int GPW = 32 / G;                        // groups per warp
-    constexpr int U = GroupUnroll<G>::U;
-    const int lane_w = threadIdx.x & 31;
-    const int lane = (G == 1) ? 0 : (threadIdx.x & (G - 1));
-    const int grp = threadIdx.x / G;
-    const int gw = lane_w / G;                         // group within the warp
-    using Tab = typename TableFor<V, kPackShared>::type;
-    Tab tab;
-    if (G == 1) table_at(tab, smem, TPB, k.slots, threadIdx.x, true);      // private, interleaved
-    else table_at(tab, smem, NG, k.slots, grp, false);
-    __shared__ int2 s_mov[TPB / 32][32];
-    int2 *mbuf = s_mov[threadIdx.x >> 5];
-    int nmov = 0;
-    // counters and movers are kept per warp while consecutive items belong to one graph
-    int cur_g = -1;
-    SweepView a{};
-    unsigned fb = 0, c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
-    for (;;) {
-        int it = 0;
-        if (lane_w == 0) it = (int)atomicAdd(k.queue, 1u);
-        it = __shfl_sync(0xFFFFFFFFu, it, 0);
-        if (it >= k.n_items) break;
-        const WorkItem item = k.items[it];
-        if (item.g != cur_g) {
-            if (cur_g >= 0) {
-                movers_flush(a.mover_count, a.mover_v, a.mover_c, mbuf, nmov);
-                warp_flush(a, k.kslot, c_act, c_edges, c_moved, c_marks, fb);
-                fb = c_act = c_edges = c_moved = c_marks = 0;
-            }
-            cur_g = item.g;
-            a = view_of(k.gd, item.g);
-            tab.probe = a.probe;
-        }
-        if (a.done || (a.pull != 0) != PULL) continue;                // the other launch takes it
-        for (int64_t base = 0; base < item.count; base += 32) {       // uniform per warp
-            // lane L: vertex base + L of the item (its flag is taken here: mark processed; in a
-            // pull sweep every vertex is a candidate and its activity is known after the scan)
-            int32_t mv = -1;
-            int64_t mo0 = 0, mo1 = 0;
-            if (base + lane_w < item.count) {
-                mv = __ldg(a.lists + item.start + base + lane_w);
-                bool cand = PULL;
-                if (!PULL && a.flag_cur[mv] != 0) {
-                    a.flag_cur[mv] = 0;
-                    cand = true;
-                }
-                if (cand) {
-                    mo0 = a.off[mv];
-                    mo1 = a.off[mv + 1];
-                } else {
-                    mv = -1;                                   // not active in this sweep
-                }
-            }
-#pragma unroll 1
-            for (int st = 0; st < 32 && base + st < item.count; st += GPW) {    // uniform per warp
-                const int src = st + gw;
-                const int32_t v = __shfl_sync(0xFFFFFFFFu, mv, src);
-                const int64_t o0 = __shfl_sync(0xFFFFFFFFu, mo0, src);
-                const int64_t o1 = __shfl_sync(0xFFFFFFFFu, mo1, src);
-                const bool cand = v >= 0 && o1 > o0;
-                int32_t cstar = -1;
-                bool moved = false;
-                if (cand) {
-                    const uint32_t D = (uint32_t)(o1 - o0);
-                    const uint32_t b = cap_bits(D << a.tshift);    // capacity >= D << tshift
-                    const uint32_t p1 = cap_of_bits(b);
-                    const int32_t cur = PULL ? (int32_t)((uint32_t)a.C[v] & kLabelMask) : a.C[v];
-                    uint32_t seen = 0;
-                    if (G == 1) {
-                        clear_table_private(tab, p1);              // hashtableClear
-                    } else {
-                        group_sync<G>();                           // previous vertex's inserts are done
-                        clear_table_vec(tab, p1, lane, G);
-                        group_sync<G>();
-                    }
-                    unsigned long long best = 0;
-                    int32_t jr[U];                                 // neighbour ids of the first round
-#pragma unroll
-                    for (int u = 0; u < U; ++u) jr[u] = -1;
-                    for (int64_t eb = o0; eb < o1; eb += (int64_t)U * G) {
-                        bool has[U];
-                        int32_t kk[U];
-                        V wv[U];
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {              // indices and weights
-                            const int64_t e = eb + (int64_t)u * G + lane;
-                            has[u] = e < o1;
-                            jr[u] = has[u] ? a.idx[e] : -1;
-                            wv[u] = (has[u] && a.w) ? to_value<V>(a.w[e]) : V(1);
-                        }
-#pragma unroll
-                        for (int u = 0; u < U; ++u) {              // labels (self-loops not inserted)
-                            if (PULL) {
-                                const uint32_t cj = has[u] ? (uint32_t)a.C[jr[u]] : 0u;
-                                seen |= cj;
-                                has[u] = has[u] && jr[u] != v;
-                                kk[u] = (int32_t)(cj & kLabelMask);
-                            } else {
-                                has[u] = has[u] && jr[u] != v;
-                                kk[u] = has[u] ? a.C[jr[u]] : 0;
-                            }
-                        }
-                        // inserts one slot at a time (rolled loop, entries shifted down in
-                        // registers) so that the probe loop is not replicated U times
-#pragma unroll 1
-                        for (int u = 0; u < U; ++u) {
-                            if (!__any_sync(group_mask<G>(), has[0])) break;     // lanes of this group only
-                            group_insert<G, (G > 1), false>(tab, p1, b, has[0], kk[0], wv[0], best, fb);
-#pragma unroll
-                            for (int q = 0; q + 1 < U; ++q) {
-                                has[q] = has[q + 1];
-                                kk[q] = kk[q + 1];
-                                wv[q] = wv[q + 1];
-                            }
-                            has[U - 1] = false;
-                        }
-                    }
-                    best = group_max<G>(best);                     // hashtableMaxKey
-                    bool act = true;
-                    if (PULL) {                                    // a neighbour moved in the last sweep
-                        if (G > 1) seen = __reduce_or_sync(group_mask<G>(), seen);
-                        act = (seen & kMovedBit) != 0;
-                    }
-                    moved = act && decide(best, cur, a.pl, cstar);
-                    if (moved) {
-                        if (a.async_mode && lane == 0) {
-                            a.C[v] = cstar;
-                            __threadfence();
-                        }
-                        if (!a.mark) {
-                        } else if (D <= (uint32_t)(U * G)) {       // mark neighbours (ids in registers)
-#pragma unroll
-                            for (int u = 0; u < U; ++u)
-                                if (jr[u] >= 0) a.flag_next[jr[u]] = 1;
-                        } else {
-                            for (int64_t e = o0 + lane; e < o1; e += G) a.flag_next[a.idx[e]] = 1;
-                        }
-                    }
-                    if (lane == 0 && act) {
-                        c_act += 1;
-                        c_edges += D;
-                        if (moved) {
-                            c_moved += 1;
-                            if (a.mark) c_marks += D;
-                        }
-                    }
-                }
-                if (!a.async_mode) movers_push(a, mbuf, nmov, moved && lane == 0, v, cstar);
-            }
-        }
-    }
-    if (cur_g >= 0) {
-        movers_flush(a.mover_count, a.mover_v, a.mover_c, mbuf, nmov);
-        warp_flush(a, k.kslot, c_act, c_edges, c_moved, c_marks, fb);
-    }
-}
-
-// One thread block per vertex; the table (up to k.slots entries) lives in dynamic smem.
-// Persistent: each block takes work items from the queue; the list entries, processed flags
-// and row bounds of up to 32 vertices of the item are fetched at once into shared memory.
-template <int TPB, typename V, bool PULL>
-__global__ void __launch_bounds__(TPB) k_cta(KArgs k)
-{
-    if (*k.active == 0) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    using Tab = typename TableFor<V, kPackShared>::type;
-    Tab tab;
-    table_at(tab, smem, 1, k.slots, 0, false);
-    __shared__ int s_item, s_nmov;
-    __shared__ int32_t s_mv[32];
-    __shared__ int64_t s_mo0[32], s_mo1[32];
-    __shared__ int2 s_mov[32];
-    __shared__ unsigned long long s_best[TPB / 32], s_mbase;
-    if (threadIdx.x == 0) s_nmov = 0;
-    // counters (thread 0) are kept while consecutive items belong to one graph
-    int cur_g = -1;
-    SweepView a{};
-    unsigned fb = 0;
-    unsigned long long c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
-    auto flush_counts = [&]() {
-        if (threadIdx.x == 0) {
-            unsigned long long *c = a.ctr + k.kslot * kCtrFields;
-            if (c_act) atomicAdd(c + CTR_ACTIVE, c_act);
-            if (c_edges) atomicAdd(c + CTR_EDGES, c_edges);
-            if (c_moved) atomicAdd(c + CTR_MOVED, c_moved);
-            if (c_marks) atomicAdd(c + CTR_MARKS, c_marks);
-        }
-        if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
-        fb = 0;
-        c_act = c_edges = c_moved = c_marks = 0;
-    };
-    for (;;) {
-        __syncthreads();                               // s_item and s_best of the last round are consumed
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(k.queue, 1u);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= k.n_items) break;
-        const WorkItem item = k.items[it];
-        if (item.g != cur_g) {
-            if (cur_g >= 0) flush_counts();
-            cur_g = item.g;
-            a = view_of(k.gd, item.g);
-            tab.probe = a.probe;
-        }
-        if (a.done || (a.pull != 0) != PULL) continue;        // the other launch takes it
-        for (int64_t base = 0; base < item.count; base += 32) {
-            __syncthreads();                           // the previous batch is finished
-            if (threadIdx.x < 32 && base + threadIdx.x < item.count) {
-                int32_t v0 = __ldg(a.lists + item.start + base + threadIdx.x);
-                int64_t m0 = 0, m1 = 0;
-                bool cand = PULL;                      // pull sweep: activity known after the scan
-                if (!PULL && a.flag_cur[v0] != 0) {
-                    a.flag_cur[v0] = 0;                // mark processed
-                    cand = true;
-                }
-                if (cand) {
-                    m0 = a.off[v0];
-                    m1 = a.off[v0 + 1];
-                } else {
-                    v0 = -1;
-                }
-                s_mv[threadIdx.x] = v0;
-                s_mo0[threadIdx.x] = m0;
-                s_mo1[threadIdx.x] = m1;
-            }
-            __syncthreads();
-            const int nb = (int)(item.count - base < 32 ? item.count - base : 32);
-            for (int q = 0; q < nb; ++q) {
-                const int32_t v = s_mv[q];
-                if (v < 0) continue;                   // uniform for the block
-                const int64_t o0 = s_mo0[q], o1 = s_mo1[q];
-                const uint32_t D = (uint32_t)(o1 - o0);
-                const uint32_t b = cap_bits(D << a.tshift);
-                const uint32_t p1 = cap_of_bits(b);
-                const int32_t cur = PULL ? (int32_t)((uint32_t)a.C[v] & kLabelMask) : a.C[v];
-                __syncthreads();                       // the previous vertex is finished
-                clear_table_vec(tab, p1, threadIdx.x, TPB);
-                __syncthreads();
-                unsigned long long best = 0;
-                uint32_t seen = 0;
-                constexpr int U = TPB >= 1024 ? 2 : 1;     // loads in flight per thread
-                scan_row<32, true, false, U, PULL>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, tab,
-                                                   p1, b, best, fb, seen, nullptr, nullptr, TPB * U);
-                best = group_max<32>(best);
-                if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-                bool act = true;
-                if (PULL) act = __syncthreads_or((seen & kMovedBit) != 0) != 0;   // a neighbour moved
-                else __syncthreads();
-                best = 0;
-#pragma unroll
-                for (int w = 0; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
-                int32_t cstar = -1;
-                const bool moved = act && decide(best, cur, a.pl, cstar);
-                if (moved) {
-                    if (threadIdx.x == 0) {
-                        if (a.async_mode) {
-                            a.C[v] = cstar;
-                            __threadfence();
-                        } else {
-                            s_mov[s_nmov++] = make_int2(v, cstar);     // at most 32 per batch
-                        }
-                    }
-                    if (a.async_mode) __syncthreads();
-                    if (a.mark)
-                        for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
-                }
-                if (threadIdx.x == 0 && act) {
-                    c_act += 1;
-                    c_edges += D;
-                    if (moved) {
-                        c_moved += 1;
-                        if (a.mark) c_marks += D;
-                    }
-                }
-            }
-            // append the batch's synchronous movers with one atomic
-            __syncthreads();
-            const int nm = s_nmov;
-            if (nm > 0) {
-                if (threadIdx.x == 0) s_mbase = atomicAdd(a.mover_count, (unsigned long long)nm);
-                __syncthreads();
-                if (threadIdx.x < nm) {
-                    const int2 m = s_mov[threadIdx.x];
-                    a.mover_v[s_mbase + threadIdx.x] = m.x;
-                    a.mover_c[s_mbase + threadIdx.x] = m.y;
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) s_nmov = 0;
-            }
-        }
-    }
-    if (cur_g >= 0) flush_counts();
-}
-
-// ---------------------------------------------------------------------------------
-// Hubs: tables in HBM shared by several blocks.  Per sweep: begin (take the processed
-// flag), accumulate (a block per CSR chunk; each block folds its running maximum into
-// hub_best), clear (a block per slice of the used-slot list or of the table), move (the
-// decision), mark (a block per CSR chunk of the hubs that moved).  Items: begin and move take
-// a graph's hubs [start, start + count); accumulate, clear and mark take one chunk / slice.
-struct HArgs {
-    const GraphDev *gd;
-    const WorkItem *items;
-    const int32_t *active;
-    int32_t chunk;
-    int32_t pad;
-};
 
 __global__ void k_hub_begin(HArgs k)
 {
@@ -927,133 +58,6 @@ __global__ void k_hub_begin(HArgs k)
         h.hub_seen[t] = 0;
         h.hub_best[t] = 0ull;
         h.hub_used[t] = 0u;
-    }
-}
-
-// Slots taken from empty are collected in a block-local list in shared memory and copied to
-// the hub's used list with one global atomic per block.  A graph with integer sums keeps its
-// hub tables in the packed layout, any other graph in the split float layout.
-template <int TPB, bool PULL, typename T>
-__device__ __forceinline__ void hub_accumulate(const SweepView &a, const HubArgs &h, int hh, int64_t c, const T &tab,
-                                               int32_t *s_list, uint32_t &s_cnt, uint32_t &s_base,
-                                               unsigned long long *s_best)
-{
-    const int32_t v = h.hub_v[hh];
-    const uint32_t p1 = h.hub_p1[hh], b = h.hub_b[hh];
-    const int64_t e0 = h.chunk_e0[c], e1 = h.chunk_e1[c];
-    unsigned fb = 0;
-    unsigned long long best = 0;
-    uint32_t seen = 0;
-    scan_row<32, true, true, 2, PULL>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab, p1, b, best,
-                                      fb, seen, &s_cnt, s_list, TPB * 2);
-    if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
-    best = group_max<32>(best);
-    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-    if (PULL) {
-        if (__syncthreads_or((seen & kMovedBit) != 0) && threadIdx.x == 0) h.hub_seen[hh] = 1;
-    } else {
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
-        if (best) atomicMax(h.hub_best + hh, best);
-        s_base = s_cnt ? atomicAdd(h.hub_used + hh, s_cnt) : 0u;
-    }
-    __syncthreads();
-    int32_t *ulist = h.used_list + h.used_base[hh] + s_base;
-    for (uint32_t q = threadIdx.x; q < s_cnt; q += TPB) ulist[q] = s_list[q];
-}
-
-template <int TPB, bool PULL>
-__global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
-{
-    if (*k.active == 0) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    int32_t *s_list = (int32_t *)smem;                 // [chunk]
-    __shared__ unsigned long long s_best[TPB / 32];
-    __shared__ uint32_t s_cnt, s_base;
-    const WorkItem item = k.items[blockIdx.x];
-    const SweepView a = view_of(k.gd, item.g);
-    if (a.done || (a.pull != 0) != PULL) return;      // the other launch takes it
-    const HubArgs &h = k.gd[item.g].hub;
-    const int64_t c = item.start;
-    const int hh = h.chunk_h[c];
-    if (!h.hub_act[hh]) return;
-    if (threadIdx.x == 0) s_cnt = 0;
-    __syncthreads();
-    if (k.gd[item.g].int_weights) {
-        PackedTable tab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
-        hub_accumulate<TPB, PULL>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
-    } else {
-        SplitTable<float> tab{h.tab_k + h.hub_tab[hh], h.tab_v + h.hub_tab[hh], 1, a.probe};
-        hub_accumulate<TPB, PULL>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
-    }
-}
-
-// Hubs whose table fits in the shared memory of a cluster of CS blocks (1024 threads each).
-// Persistent: rank 0 takes a hub from the queue and broadcasts it; every block clears its
-// slice of the hub's table, the cluster synchronises, every block scans 1/CS of the row and
-// inserts into the distributed table (Algorithm 2's probe sequence over the whole table),
-// folds its running maximum into hub_best, and the cluster synchronises again before the
-// next hub.  Integer sums only (packed slots).
-constexpr int kDsmThreads = 1024;
-
-template <int CS, bool PULL>
-__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kDsmThreads) k_hub_dsm(HArgs k, int32_t n_items,
-                                                                                   unsigned *queue)
-{
-    if (*k.active == 0) return;                        // the same value in every block of the cluster
-    cg::cluster_group cluster = cg::this_cluster();
-    const unsigned rank = cluster.block_rank();
-    constexpr int csb = CS == 2 ? 1 : (CS == 4 ? 2 : (CS == 8 ? 3 : 4));
-    extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long *slice = (unsigned long long *)smem;
-    __shared__ int s_it;
-    __shared__ unsigned long long s_best[kDsmThreads / 32];
-    for (;;) {
-        if (rank == 0 && threadIdx.x == 0) {
-            const int it = (int)atomicAdd(queue, 1u);
-            for (unsigned r = 0; r < (unsigned)CS; ++r) *cluster.map_shared_rank(&s_it, r) = it;
-        }
-        cluster.sync();                                // the hub is known in every block
-        const int it = s_it;
-        if (it >= n_items) break;
-        const WorkItem item = k.items[it];
-        const SweepView a = view_of(k.gd, item.g);
-        const HubArgs &h = k.gd[item.g].hub;
-        const int hh = (int)item.start;
-        if (a.done || (a.pull != 0) != PULL || !h.hub_act[hh]) {
-            cluster.sync();                            // s_it is read before rank 0 writes the next
-            continue;
-        }
-        const uint32_t b = h.hub_b[hh], p1 = h.hub_p1[hh];
-        const uint32_t lb = b - csb;                   // 2^lb slots per block
-        clear_table_vec(PackedTable{slice, 1}, (1u << lb) - 1u, threadIdx.x, kDsmThreads);
-        cluster.sync();                                // every slice is clear
-        const ClusterTable tab{slice, lb, 1, a.probe};
-        const int32_t v = h.hub_v[hh];
-        const int64_t o0 = a.off[v], o1 = a.off[v + 1];
-        const int64_t per = (o1 - o0 + CS - 1) / CS;
-        const int64_t e0 = o0 + (int64_t)rank * per;
-        const int64_t e1 = e0 + per < o1 ? e0 + per : o1;
-        unsigned fb = 0;
-        unsigned long long best = 0;
-        uint32_t seen = 0;
-        if (e0 < e1)
-            scan_row<32, true, false, 2, PULL>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab,
-                                               p1, b, best, fb, seen, nullptr, nullptr, kDsmThreads * 2);
-        if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
-        best = group_max<32>(best);
-        if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-        bool any_seen = false;
-        if (PULL) any_seen = __syncthreads_or((seen & kMovedBit) != 0) != 0;
-        else __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < kDsmThreads / 32; ++w) best = umax64(best, s_best[w]);
-            if (best) atomicMax(h.hub_best + hh, best);
-            if (PULL && any_seen) h.hub_seen[hh] = 1;
-        }
-        cluster.sync();                                // every insert is done before the next clear
     }
 }
 
@@ -1263,163 +267,12 @@ __global__ void k_table_clear(int32_t *k, float *v, int64_t n, int packed)
     }
 }
 
-// ---------------------------------------------------------------------------------
-// launchers
-
-static int g_num_sms = 0;
-static size_t g_max_smem = 0;
-
-static void query_device()
-{
-    if (g_num_sms) return;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    int smem = 0;
-    cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    g_max_smem = (size_t)smem;
-}
-
-size_t max_dynamic_smem()
-{
-    query_device();
-    return g_max_smem;
-}
-
-int num_sms()
-{
-    query_device();
-    return g_num_sms;
-}
-
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes)
-{
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <typename K>
-static int64_t persistent_grid(K kernel, int threads, size_t smem, int64_t work_blocks)
-{
-    query_device();
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    const int64_t cap = (int64_t)g_num_sms * per_sm;
-    return work_blocks < cap ? work_blocks : cap;
-}
-
-template <int G, int TPB, typename V, bool PULL>
-static cudaError_t launch_gv(const KArgs &k, cudaStream_t s)
-{
-    constexpr int NG = TPB / G;
-    const size_t smem = (size_t)NG * k.slots * (sizeof(int32_t) + sizeof(V));
-    cudaError_t e = set_smem(k_group<G, TPB, V, PULL>, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = persistent_grid(k_group<G, TPB, V, PULL>, TPB, smem, ((int64_t)k.n_items + 7) / 8 * 8);
-    k_group<G, TPB, V, PULL><<<(unsigned)(blocks < 1 ? 1 : blocks), TPB, smem, s>>>(k);
-    return cudaGetLastError();
-}
-
-template <int G, int TPB, bool PULL>
-static cudaError_t launch_g(const KArgs &k, bool int_w, cudaStream_t s)
-{
-    return int_w ? launch_gv<G, TPB, uint32_t, PULL>(k, s) : launch_gv<G, TPB, float, PULL>(k, s);
-}
-
-template <int TPB, typename V, bool PULL>
-static cudaError_t launch_cv(const KArgs &k, cudaStream_t s)
-{
-    const size_t smem = (size_t)k.slots * (sizeof(int32_t) + sizeof(V));
-    cudaError_t e = set_smem(k_cta<TPB, V, PULL>, smem);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = persistent_grid(k_cta<TPB, V, PULL>, TPB, smem, k.n_items);
-    k_cta<TPB, V, PULL><<<(unsigned)(blocks < 1 ? 1 : blocks), TPB, smem, s>>>(k);
-    return cudaGetLastError();
-}
-
-template <bool PULL>
-static cudaError_t launch_cta(const KArgs &k, int threads, bool int_w, cudaStream_t s)
-{
-    switch (threads) {
-    case 64: return int_w ? launch_cv<64, uint32_t, PULL>(k, s) : launch_cv<64, float, PULL>(k, s);
-    case 128: return int_w ? launch_cv<128, uint32_t, PULL>(k, s) : launch_cv<128, float, PULL>(k, s);
-    case 256: return int_w ? launch_cv<256, uint32_t, PULL>(k, s) : launch_cv<256, float, PULL>(k, s);
-    case 512: return int_w ? launch_cv<512, uint32_t, PULL>(k, s) : launch_cv<512, float, PULL>(k, s);
-    case 1024: return int_w ? launch_cv<1024, uint32_t, PULL>(k, s) : launch_cv<1024, float, PULL>(k, s);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-// The kernel of bucket b for the push (PULL = false) or pull sweeps of the plan's graphs;
-// each instantiation has its own work-queue counter.
-template <bool PULL>
-static cudaError_t launch_vertex(const SweepPlan &p, int b, cudaStream_t s)
-{
-    KArgs k{};
-    k.gd = p.gd;
-    k.items = p.items[b];
-    k.n_items = p.n_items[b];
-    k.slots = p.slots[b];
-    k.queue = p.queues + b + (PULL ? B_COUNT : 0);
-    k.active = p.active_count;
-    k.kslot = b;                                       // bucket index == kernel slot
-    const bool iw = p.int_weights != 0;
-    switch (b) {
-    case B_THREAD: return launch_g<1, 128, PULL>(k, iw, s);
-    case B_GROUP:
-        switch (p.group_lanes) {
-        case 2: return launch_g<2, 256, PULL>(k, iw, s);
-        case 4: return launch_g<4, 256, PULL>(k, iw, s);
-        case 8: return launch_g<8, 256, PULL>(k, iw, s);
-        case 16: return launch_g<16, 256, PULL>(k, iw, s);
-        default: return cudaErrorInvalidValue;
-        }
-    case B_WARP: return launch_g<32, 256, PULL>(k, iw, s);
-    case B_CTA: return launch_cta<PULL>(k, p.cta_threads, iw, s);
-    case B_CTA_LARGE: return launch_cta<PULL>(k, p.cta_large_threads, iw, s);
-    case B_CTA_XL: return launch_cta<PULL>(k, p.cta_xl_threads, iw, s);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-constexpr size_t kDsmSmem = ((size_t)1 << kDsmSliceBits) * sizeof(unsigned long long);
-
-template <int CS, bool PULL>
-static cudaError_t launch_dsm_cs(const HArgs &h, int32_t n_items, unsigned *queue, cudaStream_t s)
-{
-    cudaError_t e = cudaFuncSetAttribute(k_hub_dsm<CS, PULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDsmSmem);
-    if (e == cudaSuccess && CS > 8)
-        e = cudaFuncSetAttribute(k_hub_dsm<CS, PULL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-    query_device();
-    int64_t clusters = g_num_sms / CS;
-    if (clusters > n_items) clusters = n_items;
-    if (clusters < 1) clusters = 1;
-    k_hub_dsm<CS, PULL><<<(unsigned)(clusters * CS), kDsmThreads, kDsmSmem, s>>>(h, n_items, queue);
-    return cudaGetLastError();
-}
-
-// Cluster class c (cluster of 2 << c blocks).
-template <bool PULL>
-static cudaError_t launch_dsm(int c, const HArgs &h, int32_t n_items, unsigned *queue, cudaStream_t s)
-{
-    switch (c) {
-    case 0: return launch_dsm_cs<2, PULL>(h, n_items, queue, s);
-    case 1: return launch_dsm_cs<4, PULL>(h, n_items, queue, s);
-    case 2: return launch_dsm_cs<8, PULL>(h, n_items, queue, s);
-    case 3: return launch_dsm_cs<16, PULL>(h, n_items, queue, s);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
 template <int CS>
 static int active_clusters()
 {
-    if (cudaFuncSetAttribute(k_hub_dsm<CS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDsmSmem) !=
+    if (cudaFuncSetAttribute(k_hub_dsm<CS, false, kProbeQuadDouble>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDsmSmem) !=
             cudaSuccess ||
-        (CS > 8 && cudaFuncSetAttribute(k_hub_dsm<CS, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        (CS > 8 && cudaFuncSetAttribute(k_hub_dsm<CS, false, kProbeQuadDouble>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                        cudaSuccess)) {
         cudaGetLastError();
         return 0;
@@ -1436,7 +289,7 @@ static int active_clusters()
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_hub_dsm<CS, false>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_hub_dsm<CS, false, kProbeQuadDouble>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -1460,7 +313,6 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
 {
     cudaError_t e = cudaMemsetAsync(p.queues, 0, sizeof(unsigned) * kQueueCount, s);
     if (e != cudaSuccess) return e;
-    const bool push = p.pull_mode != 1, pull = p.pull_mode != 0;
     auto timed = [&](int slot, auto &&fn) -> cudaError_t {
         if (hook) hook->before(slot);
         cudaError_t r = fn();
@@ -1468,16 +320,9 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
         if (launches) ++*launches;
         return r;
     };
-    for (int b = B_THREAD; b <= B_CTA_XL; ++b) {
-        if (p.n_items[b] <= 0) continue;
-        e = timed(b, [&] {
-            cudaError_t r = push ? launch_vertex<false>(p, b, s) : cudaSuccess;
-            if (r == cudaSuccess && pull) r = launch_vertex<true>(p, b, s);
-            return r;
-        });
-        if (e != cudaSuccess) return e;
-        if (launches && push && pull) ++*launches;
-    }
+    e = p.probe == kProbeQuadDouble ? launch_vertex_phase<kProbeQuadDouble>(p, s, hook, launches)
+                                    : launch_vertex_phase_alt(p, s, hook, launches);
+    if (e != cudaSuccess) return e;
     HArgs h{};
     h.gd = p.gd;
     h.active = p.active_count;
@@ -1489,39 +334,8 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
-        e = timed(LPA_K_HUB_ACC, [&] {
-            cudaError_t r = cudaSuccess;
-            if (p.n_hub_items[HL_ACC] > 0) {          // hubs with tables in HBM
-                HArgs ha = h;
-                ha.items = p.hub_items[HL_ACC];
-                const size_t smem = (size_t)p.hub_chunk * sizeof(int32_t);
-                if (push) {
-                    r = set_smem(k_hub_acc<1024, false>, smem);
-                    if (r != cudaSuccess) return r;
-                    k_hub_acc<1024, false><<<p.n_hub_items[HL_ACC], 1024, smem, s>>>(ha);
-                }
-                if (pull) {
-                    r = set_smem(k_hub_acc<1024, true>, smem);
-                    if (r != cudaSuccess) return r;
-                    k_hub_acc<1024, true><<<p.n_hub_items[HL_ACC], 1024, smem, s>>>(ha);
-                }
-                if (launches) *launches += (push && pull) ? 1 : 0;
-            }
-            for (int c = 0; c < 4 && r == cudaSuccess; ++c) {    // hubs with tables in cluster memory
-                if (p.n_hub_items[HL_DSM2 + c] <= 0) continue;
-                HArgs ha = h;
-                ha.items = p.hub_items[HL_DSM2 + c];
-                if (push) {
-                    r = launch_dsm<false>(c, ha, p.n_hub_items[HL_DSM2 + c], p.queues + 2 * B_COUNT + c, s);
-                    if (launches) ++*launches;
-                }
-                if (pull && r == cudaSuccess) {
-                    r = launch_dsm<true>(c, ha, p.n_hub_items[HL_DSM2 + c], p.queues + 2 * B_COUNT + 4 + c, s);
-                    if (launches) ++*launches;
-                }
-            }
-            return r != cudaSuccess ? r : cudaGetLastError();
-        });
+        e = p.probe == kProbeQuadDouble ? launch_hub_acc_phase<kProbeQuadDouble>(p, h, s, hook, launches)
+                                        : launch_hub_acc_phase_alt(p, h, s, hook, launches);
         if (e != cudaSuccess) return e;
         if (p.n_hub_items[HL_SLICES] > 0) {
             h.items = p.hub_items[HL_SLICES];
