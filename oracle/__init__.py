@@ -7,6 +7,7 @@ C11, built with gcc by `build()`); this module only marshals numpy arrays.
 
 Functions and the passages they follow:
   lpa_sync / lpa_async  -- Algorithm 1 (lpa, lpaMove), Eq. 3, Section 4 items (1)-(5)
+  cross_check           -- Section 4.1's Cross-Check (reverts of bad moves), in id order
   label_weights         -- Preliminaries, K_{i->c}, by sort-and-count
   ht_build / ht_probe_slot / ht_capacity -- Section 4.2 per-vertex hashtable, Algorithm 2
   modularity / modularity_exact          -- Eq. 1 (community form)
@@ -60,6 +61,10 @@ def lib():
         i64, i32, u32, dbl = ct.c_int64, ct.c_int32, ct.c_uint32, ct.c_double
         L.orc_lpa_sync.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P]
         L.orc_lpa_sync.restype = ct.c_int
+        L.orc_lpa_sync_cc.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P]
+        L.orc_lpa_sync_cc.restype = ct.c_int
+        L.orc_cross_check.argtypes = [i64, P, P]
+        L.orc_cross_check.restype = i64
         L.orc_lpa_async.argtypes = L.orc_lpa_sync.argtypes
         L.orc_lpa_async.restype = ct.c_int
         L.orc_sweep_range.argtypes = [i64, P, P, P, ct.c_int, i64, i64, P, P]
@@ -138,9 +143,24 @@ def _run(fn, g: Graph, tol, max_iters, pl_period, labels=None, active=None, star
     return RunResult(C, A, [int(x) for x in dN[start_iter:iters]], iters, bool(cv[0]))
 
 
-def lpa_sync(g: Graph, tol=0.05, max_iters=20, pl_period=4, labels=None, active=None, start_iter=0):
-    """Synchronous (double-buffered) LPA: Algorithm 1 applied to frozen labels."""
+def lpa_sync(g: Graph, tol=0.05, max_iters=20, pl_period=4, labels=None, active=None, start_iter=0, cc_period=0):
+    """Synchronous (double-buffered) LPA: Algorithm 1 applied to frozen labels; with
+    cc_period > 0 the Cross-Check of Section 4.1 after every cc_period-th sweep."""
+    if cc_period:
+        L = lib()
+        return _run(lambda n, o, i, w, t, m, p, s, *rest: L.orc_lpa_sync_cc(n, o, i, w, t, m, p, int(cc_period), s,
+                                                                              *rest),
+                    g, tol, max_iters, pl_period, labels, active, start_iter)
     return _run(lib().orc_lpa_sync, g, tol, max_iters, pl_period, labels, active, start_iter)
+
+
+def cross_check(labels, prev):
+    """The Cross-Check of one sweep (Section 4.1) on host arrays: returns (labels after the
+    reverts, number reverted)."""
+    C = _np(labels, np.int32).copy()
+    P = _np(prev, np.int32)
+    k = lib().orc_cross_check(C.size, _p(C), _p(P))
+    return C, int(k)
 
 
 def lpa_async(g: Graph, tol=0.05, max_iters=20, pl_period=4, labels=None, active=None, start_iter=0):

@@ -135,9 +135,33 @@ static void orc_work_free(orc_work *wk)
  * *converged out: 1 when the tolerance test stopped the loop.
  * Returns 0, or -1 on allocation failure.
  */
-int orc_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
-                 double tol, int max_iters, int pl_period, int start_iter,
-                 int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged)
+/* Cross-Check (Section 4.1), after the sweep that moved some vertices from Cprev to C:
+ * a move of i to c* = C[i] is good when vertex c* is in community c* (C[c*] = c*); a bad
+ * move reverts i to Cprev[i].  The paper reverts atomically, so that the two vertices of a
+ * swap do not both revert; this reading checks the moved vertices in increasing id order
+ * against the labels as they stand, earlier reverts included.  Returns the number of
+ * reverted moves.  Marks made during the sweep stay. */
+int64_t orc_cross_check(int64_t n, int32_t *C, const int32_t *Cprev)
+{
+    int64_t reverted = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (C[i] == Cprev[i]) continue;
+        const int32_t c = C[i];
+        if (C[c] != c) {
+            C[i] = Cprev[i];
+            ++reverted;
+        }
+    }
+    return reverted;
+}
+
+/* Synchronous LPA with Pick-Less every pl_period sweeps (Section 4.1; 0: never) and
+ * Cross-Check after every cc_period-th sweep (0: never): both on sweeps l with
+ * l mod period = 0, so pl_period = cc_period > 0 is the paper's Hybrid.  dN counts the moves
+ * that remain after the Cross-Check. */
+int orc_lpa_sync_cc(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                    double tol, int max_iters, int pl_period, int cc_period, int start_iter,
+                    int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged)
 {
     *converged = 0;
     *iters = start_iter;
@@ -166,6 +190,7 @@ int orc_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float 
                 for (int64_t e = off[i]; e < off[i + 1]; ++e) an[idx[e]] = 1;
             }
         }
+        if (cc_period > 0 && l % cc_period == 0) changed -= orc_cross_check(n, Cn, C);
         memcpy(C, Cn, (size_t)n * sizeof(int32_t));
         memcpy(active, an, (size_t)n);   /* processed vertices are cleared, marks set */
         dN[l] = changed;
@@ -179,6 +204,14 @@ int orc_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float 
     free(an);
     orc_work_free(&wk);
     return 0;
+}
+
+int orc_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                 double tol, int max_iters, int pl_period, int start_iter,
+                 int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged)
+{
+    return orc_lpa_sync_cc(n, off, idx, w, tol, max_iters, pl_period, 0, start_iter, C, active, dN, iters,
+                           converged);
 }
 
 /* Asynchronous LPA in the paper's sense (Section 4, item 1): one label vector and one

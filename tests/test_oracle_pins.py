@@ -471,3 +471,89 @@ def test_multicore_baseline_rmat_and_closed_forms():
         ref = oracle.lpa_sync(og, 0.05, 20, 4)
         got = oracle.multicore_lpa_sync(og, 0.05, 20, 4, threads=4)
         assert got.labels.tolist() == ref.labels.tolist() and got.dN == ref.dN
+
+
+# ---------------------------------------------------------------------------------------
+# Cross-Check (Section 4.1): closed forms, order of the checks, dense restatement
+
+def _dense_sync_cc(W, tol, max_iters, pl_period, cc_period):
+    """_dense_sync with the Cross-Check after every cc_period-th sweep: moved vertices are
+    checked in increasing id order; a move of i to c is kept when vertex c holds label c at
+    that moment (earlier reverts included), else i goes back to its label before the sweep."""
+    n = W.shape[0]
+    C = list(range(n))
+    act = [True] * n
+    dns, per_iter = [], []
+    for l in range(max_iters):
+        pl = pl_period > 0 and l % pl_period == 0
+        Cn, an, ch = list(C), [False] * n, 0
+        for i in range(n):
+            if not act[i]:
+                continue
+            c = _best_dense(W, C, i)
+            if c is not None and c != C[i] and (not pl or c < C[i]):
+                Cn[i] = c
+                ch += 1
+                for j in np.nonzero(W[i])[0]:
+                    an[j] = True
+        if cc_period > 0 and l % cc_period == 0:
+            for i in range(n):
+                if Cn[i] != C[i] and Cn[Cn[i]] != Cn[i]:
+                    Cn[i] = C[i]
+                    ch -= 1
+        C, act = Cn, an
+        dns.append(ch)
+        per_iter.append(list(C))
+        if not pl and ch / n < tol:
+            break
+    return dns, per_iter
+
+
+def test_cross_check_breaks_the_bipartite_swap():
+    """K_{n,n} without Pick-Less, Cross-Check after every sweep.  Sweep 0: every A vertex
+    (ids 0..n-1) picks label n, every B vertex label 0.  In id order A checks first: vertex n
+    still holds 0, not n, so every A move is reverted; then each B vertex finds vertex 0 back
+    in community 0 and keeps its move (n moves remain).  Sweep 1: A vertices 1..n-1 join 0
+    (vertex 0 keeps it, B already holds 0; n-1 moves, all good).  Sweep 2: no move, the run
+    converges after 3 sweeps with one community.  Without the check the swap repeats to the
+    cap."""
+    for n in (2, 3, 6):
+        g = G(gg.complete_bipartite(n))
+        r = oracle.lpa_sync(g, 0.05, 20, 0, cc_period=1)
+        assert r.dN == [n, n - 1, 0] and r.iterations == 3 and r.converged
+        assert set(r.labels.tolist()) == {0}
+        swap = oracle.lpa_sync(g, 0.05, 20, 0)
+        assert swap.iterations == 20 and not swap.converged
+
+
+def test_cross_check_order_on_a_path():
+    """Path 0-1-...-(k-1), Pick-Less and Cross-Check after sweep 0.  Every vertex but 0
+    picks its left neighbour's label (a tie broken by the smaller label).  Checked in id
+    order: 1 keeps 0 (vertex 0 holds 0); 2 reverts (vertex 1 now holds 0, not 1); 3 keeps 2
+    (vertex 2 is back at 2); 4 reverts; ...: odd vertices keep, even ones revert.  (Checking
+    all moves against the labels after the sweep at once would revert every vertex but 1.)"""
+    for k in (2, 5, 8, 11):
+        g = G(gg.from_edges(k, [(i, i + 1) for i in range(k - 1)]))
+        r = oracle.lpa_sync(g, 0.0, 1, 1, cc_period=1)
+        assert r.labels.tolist() == [i - (i % 2) for i in range(k)]
+        assert r.dN == [k // 2]
+
+
+def test_cross_check_function_by_hand():
+    C, k = oracle.cross_check([1, 0, 2, 2], [0, 1, 2, 3])     # a swap 0 <-> 1 and 3 joining 2
+    assert C.tolist() == [0, 0, 2, 2] and k == 1                # 0 reverts, then 1 keeps 0
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_sync_cross_check_matches_dense_restatement(seed):
+    rnd = random.Random(300 + seed)
+    n = rnd.randint(5, 64)
+    g = G(gg.random_small(n, rnd.choice([0.05, 0.1, 0.3]), 900 + seed, wmax=rnd.choice([1, 4]),
+                          self_loops=(seed % 3 == 0)))
+    W = _dense(g)
+    pl, cc = rnd.choice([(0, 1), (0, 2), (4, 1), (2, 2), (3, 4)])
+    dns, per_iter = _dense_sync_cc(W, 0.05, 20, pl, cc)
+    r = oracle.lpa_sync(g, 0.05, 20, pl, cc_period=cc)
+    assert r.dN == dns and r.labels.tolist() == per_iter[-1]
+    for t in range(1, len(per_iter) + 1):
+        assert oracle.lpa_sync(g, 0.05, t, pl, cc_period=cc).labels.tolist() == per_iter[t - 1]
