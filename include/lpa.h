@@ -170,6 +170,19 @@ int lpa_create(const void *offsets, const int32_t *indices, const float *weights
 int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mode,
             lpa_stats *stats);
 
+/* lpa_run with the Cross-Check of Section 4.1 after every cc_period-th sweep (sweeps l with
+ * l % cc_period == 0; 0 = never, which is lpa_run): each vertex that moved in that sweep keeps
+ * its new label c* only when vertex c* is in community c*, else it returns to its label
+ * before the sweep.  The paper reverts atomically so that both vertices of a swap do not
+ * revert; here the moved vertices are checked in increasing id order against the labels as
+ * they stand, earlier reverts included (resolved on the device by pointer jumping over the
+ * forest of moves that depend on an earlier mover).  dN counts the moves that remain; marks
+ * made during the sweep stay.  pl_period = cc_period > 0 is the paper's Hybrid.  Synchronous
+ * mode only (LPA_EINVAL for LPA_ASYNC); the first call with cc_period > 0 allocates 20 bytes per
+ * vertex for the check.  LPA_ESTATE if the resolution did not finish (not expected). */
+int lpa_run_cc(lpa_graph *g, double tolerance, int max_iters, int pl_period, int cc_period, int mode,
+               lpa_stats *stats);
+
 /* Copies the n = n_vertices labels to `out` (host or device per out_on_device). */
 int lpa_labels(const lpa_graph *g, int32_t *out, int64_t n, int out_on_device);
 

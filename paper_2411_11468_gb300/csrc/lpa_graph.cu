@@ -1058,6 +1058,10 @@ int upload_descriptor(lpa_graph *g)
     d.flags1 = g->flags[1];
     d.mover_v = g->mover_v;
     d.mover_v1 = g->mover_v1;
+    d.cc_prev = g->cc_prev;
+    d.cc_midx = g->cc_midx;
+    d.cc_par0 = g->cc_par0;
+    d.cc_word = g->cc_word;
     d.mover_c = g->mover_c;
     d.mover_count = g->mover_count;
     d.ctr = g->ctr;
@@ -1478,13 +1482,32 @@ int lpa_modularity(const lpa_graph *gc, double *q)
 
 int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mode, lpa_stats *stats)
 {
-    if (!g || max_iters < 0 || pl_period < 0 || !std::isfinite(tolerance) ||
+    return lpa_run_cc(g, tolerance, max_iters, pl_period, 0, mode, stats);
+}
+
+int lpa_run_cc(lpa_graph *g, double tolerance, int max_iters, int pl_period, int cc_period, int mode,
+               lpa_stats *stats)
+{
+    if (!g || max_iters < 0 || pl_period < 0 || cc_period < 0 || !std::isfinite(tolerance) ||
         ((mode & ~LPA_RESUME) != LPA_SYNC && (mode & ~LPA_RESUME) != LPA_ASYNC)) {
         set_error("lpa_run: bad arguments");
         return LPA_EINVAL;
     }
+    if (cc_period > 0 && (mode & ~LPA_RESUME) != LPA_SYNC) {
+        set_error("lpa_run_cc: the Cross-Check is available in the synchronous mode only");
+        return LPA_EINVAL;
+    }
     DeviceGuard dg(g->device);
     const bool async_mode = (mode & ~LPA_RESUME) == LPA_ASYNC;
+    if (cc_period > 0 && !g->cc_word) {               // Cross-Check arrays, on first use
+        LPA_CHECK(dalloc(g, &g->cc_prev, (size_t)std::max<int64_t>(g->n, 1)));
+        LPA_CHECK(dalloc(g, &g->cc_midx, (size_t)std::max<int64_t>(g->n, 1)));
+        LPA_CHECK(dalloc(g, &g->cc_par0, (size_t)std::max<int64_t>(g->n, 1)));
+        LPA_CHECK(dalloc(g, &g->cc_word, (size_t)std::max<int64_t>(g->n, 1)));
+        LPA_CHECK(dalloc(g, &g->cc_ctr, (size_t)(kCcPasses + 1)));
+        LPA_CUDA(cudaMemsetAsync(g->cc_midx, 0xFF, (size_t)std::max<int64_t>(g->n, 1) * sizeof(int32_t), g->stream));
+        LPA_CHECK(upload_descriptor(g));
+    }
     cudaStream_t s = g->stream;
     const bool timing = stats && stats->time_kernels;
     if (stats) {
@@ -1530,8 +1553,9 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
     rs.pl_period = pl_period;
     rs.async_mode = async_mode ? 1 : 0;
     // a fresh synchronous run starts without marks (the first sweep moves most vertices); a
-    // resumed run starts from its processed flags
-    rs.mark = (async_mode || (mode & LPA_RESUME)) ? 1 : 0;
+    // resumed run starts from its processed flags; Cross-Check runs always mark
+    rs.mark = (async_mode || (mode & LPA_RESUME) || cc_period > 0) ? 1 : 0;
+    rs.cc_period = cc_period;
     rs.tol = tolerance;
     rs.n = g->n;
     g->hm->active = 1;
@@ -1561,6 +1585,8 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
     p.hub_chunk = g->tuning.hub_chunk;
     p.int_weights = plan_int_weights(g) ? 1 : 0;
     p.probe = g->tuning.probe;
+    p.cc_any = cc_period > 0 ? 1 : 0;
+    p.cc_ctr = g->cc_ctr;
 
     size_t evn = 0;
     cudaEvent_t run0 = event_at(g, evn++), run1 = event_at(g, evn++);
@@ -1585,6 +1611,10 @@ int lpa_run(lpa_graph *g, double tolerance, int max_iters, int pl_period, int mo
         iter_ev.push_back({ie0, ie1});
         LPA_CUDA(cudaMemcpyAsync(&g->hm->rs, g->rs_d, sizeof(RunState), cudaMemcpyDeviceToHost, s));
         LPA_CUDA(cudaStreamSynchronize(s));
+        if (g->hm->rs.cc_unresolved) {
+            set_error("lpa_run_cc: the Cross-Check resolution did not finish");
+            return LPA_ESTATE;
+        }
         if (g->hm->rs.done) {
             ++ran;
             break;

@@ -20,6 +20,9 @@ struct lpa_graph {
     uint8_t *flags[2] = {nullptr, nullptr};
     int active_buf = 0;                              // flags[active_buf]: unprocessed flags of the next sweep
     int32_t *mover_v = nullptr, *mover_v1 = nullptr, *mover_c = nullptr;
+    int32_t *cc_prev = nullptr, *cc_midx = nullptr, *cc_par0 = nullptr;   // Cross-Check (on demand)
+    long long *cc_word = nullptr;
+    unsigned *cc_ctr = nullptr;
     unsigned long long *mover_count = nullptr;       // [2]
     unsigned long long *fallbacks = nullptr;
     unsigned long long *ctr = nullptr;               // [ctr_iters][kPerSweep]

@@ -43,6 +43,8 @@ struct RunState {
     int64_t last_dn;
     int32_t pull;         // this sweep takes activity from the previous sweep's moved bits
     int32_t fin;          // stopped after a sweep that set moved bits: k_finalize turns them into marks
+    int32_t cc_period;    // Cross-Check after sweeps l with l mod cc_period = 0 (0: never; sync only)
+    int32_t cc_unresolved;  // set when the Cross-Check resolution did not finish (not expected)
 };
 
 // Synchronous mode, sweeps that move many vertices: instead of marking the neighbours of each
@@ -96,6 +98,13 @@ struct GraphDev {
     int32_t tshift;            // smem table capacity = nextPow2(D << tshift) - 1
     int32_t int_weights;       // integer weights with weighted degrees < 2^24 (uint32 sums)
     int32_t probe;             // table probe scheme (lpa_tuning.probe)
+    // Cross-Check (allocated when a run asks for it): labels before the sweep of each mover,
+    // vertex -> position in the mover list (-1 otherwise), per position the parent position
+    // (or -1 / -2 for a move found good / bad directly) and the resolution word
+    int32_t *cc_prev;
+    int32_t *cc_midx;
+    int32_t *cc_par0;
+    long long *cc_word;
     HubArgs hub;
 };
 
@@ -126,7 +135,11 @@ struct SweepPlan {
     int32_t pull_mode;         // kernels launched for this sweep: 0 push only, 1 pull only, 2 both
     int32_t int_weights;       // 1: every graph of the plan uses uint32 sums (else float32)
     int32_t probe;             // table probe scheme of every graph of the plan (lpa_tuning.probe)
+    int32_t cc_any;            // some graph of the plan may run a Cross-Check (launch its kernels)
+    unsigned *cc_ctr;          // [kCcPasses + 1] pending counts of the resolution passes
 };
+
+constexpr int kCcPasses = 40;      // pointer-jumping passes of the Cross-Check resolution (>= 32)
 
 // Optional hook around each kernel launch (CUDA-event timing per kernel slot).
 struct LaunchHook {

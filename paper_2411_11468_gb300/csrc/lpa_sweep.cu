@@ -183,10 +183,132 @@ __global__ void k_apply(HArgs k)
     if (a.done || a.async_mode) return;
     const unsigned long long n = *a.mover_count;
     const uint32_t bit = a.mark ? 0u : kMovedBit;
+    const GraphDev &G = k.gd[item.g];
+    const RunState *rs = G.rs;
+    const bool cc = rs->cc_period > 0 && rs->l % rs->cc_period == 0;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        a.C[a.mover_v[i]] = (int32_t)((uint32_t)a.mover_c[i] | bit);
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t v = a.mover_v[i];
+        if (cc) {                                      // the Cross-Check needs the label before the sweep
+            G.cc_prev[v] = a.C[v];
+            G.cc_midx[v] = (int32_t)i;
+        }
+        a.C[v] = (int32_t)((uint32_t)a.mover_c[i] | bit);
+    }
 }
+
+// ---------------------------------------------------------------------------------
+// Cross-Check (Section 4.1) after a synchronous sweep l with l mod cc_period = 0.  The reading
+// checks the movers in increasing id order: the move of x to p = C[x] is good iff vertex p
+// holds label p at that moment.  For p = x, for p > x (not checked yet) and for p not a mover
+// that is read directly from the labels after the sweep.  For a mover p < x it is K(p), where
+// K(y) = [final label of y == y]; since y moved, K(y) = good(y) ? [p_y == y] : [prev_y == y],
+// and for a dependent y (p_y < y, so p_y != y) that is [prev_y == y] AND NOT good(y).  So each
+// dependent mover's K is a constant or the negation of its parent's K: a forest over smaller
+// ids, resolved by pointer jumping.  Word of position j: negative = resolved, K in bit 0;
+// otherwise parent position << 1 | parity (K_j = parity XOR K_parent).  Any snapshot of a
+// parent's word keeps that relation, so the passes update in place.
+__device__ __forceinline__ bool cc_sweep(const GraphDev &G)
+{
+    const RunState *rs = G.rs;
+    return !rs->done && !rs->async_mode && rs->cc_period > 0 && rs->l % rs->cc_period == 0;
+}
+
+constexpr long long kCcResolved = (long long)0x8000000000000000ull;
+
+__global__ void k_cc_init(HArgs k, unsigned *ctr)
+{
+    if (*k.active == 0) return;
+    const GraphDev &G = k.gd[k.items[blockIdx.y].g];
+    if (!cc_sweep(G)) return;
+    const int l = G.rs->l;
+    const int32_t *mv = (l & 1) ? G.mover_v1 : G.mover_v;
+    const unsigned long long n = G.mover_count[l & 1];
+    unsigned pending = 0;
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t x = mv[j];
+        const int32_t p = (int32_t)((uint32_t)G.C[x] & kLabelMask);
+        const int32_t prev = G.cc_prev[x];
+        const int32_t q = (p < x) ? G.cc_midx[p] : -1;
+        long long word;
+        if (p == x) {                                  // joined its own id: good, K = 1
+            G.cc_par0[j] = -1;
+            word = kCcResolved | 1;
+        } else if (q >= 0) {                           // depends on the earlier mover p
+            G.cc_par0[j] = q;
+            if (prev == x) {
+                word = ((long long)q << 1) | 1;        // K = NOT K(p)
+                ++pending;
+            } else {
+                word = kCcResolved;                    // K = 0 whatever good is
+            }
+        } else {                                       // p not yet checked, or not a mover
+            const bool good = (int32_t)((uint32_t)G.C[p] & kLabelMask) == p;
+            G.cc_par0[j] = good ? -1 : -2;
+            word = kCcResolved | (good ? 0 : (prev == x ? 1 : 0));
+        }
+        G.cc_word[j] = word;
+    }
+    if (pending) atomicAdd(ctr, pending);
+}
+
+// One pointer-jumping pass; skipped once a pass left nothing pending.
+__global__ void k_cc_jump(HArgs k, unsigned *ctr, int pass)
+{
+    if (*k.active == 0 || ctr[pass] == 0) return;     // ctr[pass]: pending before this pass
+    const GraphDev &G = k.gd[k.items[blockIdx.y].g];
+    if (!cc_sweep(G)) return;
+    const int l = G.rs->l;
+    const unsigned long long n = G.mover_count[l & 1];
+    unsigned pending = 0;
+    volatile long long *W = G.cc_word;
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const long long w = W[j];
+        if (w < 0) continue;
+        const long long wq = W[w >> 1];
+        long long nw;
+        if (wq < 0) {
+            nw = kCcResolved | ((w ^ wq) & 1);
+        } else {
+            nw = (wq & ~1ll) | ((w ^ wq) & 1);
+            ++pending;
+        }
+        W[j] = nw;
+    }
+    if (pending) atomicAdd(ctr + pass + 1, pending);
+}
+
+// Reverts the bad moves (back to the label before the sweep) and takes them off this sweep's
+// move count (the apply slot's moved counter holds minus the reverted moves); clears the
+// vertex -> position map.
+__global__ void k_cc_revert(HArgs k, const unsigned *ctr)
+{
+    if (*k.active == 0) return;
+    const GraphDev &G = k.gd[k.items[blockIdx.y].g];
+    if (!cc_sweep(G)) return;
+    const SweepView a = view_of(k.gd, k.items[blockIdx.y].g);
+    const int l = G.rs->l;
+    const int32_t *mv = (l & 1) ? G.mover_v1 : G.mover_v;
+    const unsigned long long n = G.mover_count[l & 1];
+    const bool resolved = ctr[kCcPasses] == 0;
+    if (!resolved && blockIdx.x == 0 && threadIdx.x == 0) G.rs->cc_unresolved = 1;
+    unsigned long long reverted = 0;
+    for (unsigned long long j = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t x = mv[j];
+        const int32_t q = G.cc_par0[j];
+        const bool good = q >= 0 ? (G.cc_word[q] & 1) != 0 : q == -1;
+        if (resolved && !good) {
+            G.C[x] = G.cc_prev[x];
+            ++reverted;
+        }
+        G.cc_midx[x] = -1;
+    }
+    if (reverted) atomicAdd(a.ctr + LPA_K_APPLY * kCtrFields + CTR_MOVED, (unsigned long long)(0 - reverted));
+}
+
 
 // After each sweep, per graph: the stop test of Algorithm 1 (after a sweep without Pick-Less,
 // stop when dN / n < tolerance; stop at max_iters), then advance to the next sweep.
@@ -367,6 +489,17 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
     });
     if (e != cudaSuccess) return e;
     if (launches) ++*launches;                         // k_apply_unmark
+    if (p.cc_any) {                                    // Cross-Check of the graphs that ask for it
+        e = cudaMemsetAsync(p.cc_ctr, 0, sizeof(unsigned) * (kCcPasses + 1), s);
+        if (e != cudaSuccess) return e;
+        k_cc_init<<<dim3(bx, (unsigned)p.n_graphs), 256, 0, s>>>(h, p.cc_ctr);
+        for (int pass = 0; pass < kCcPasses; ++pass)
+            k_cc_jump<<<dim3(bx, (unsigned)p.n_graphs), 256, 0, s>>>(h, p.cc_ctr, pass);
+        k_cc_revert<<<dim3(bx, (unsigned)p.n_graphs), 256, 0, s>>>(h, p.cc_ctr);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (launches) *launches += kCcPasses + 2;
+    }
     e = cudaMemsetAsync(p.active_count, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     k_decide<<<(p.n_graphs + 127) / 128, 128, 0, s>>>(p.gd, p.n_graphs, p.active_count);

@@ -37,7 +37,7 @@ SYMBOLS = ["lpa_create", "lpa_run", "lpa_labels", "lpa_modularity", "lpa_set_lab
            "lpa_batch_modularity", "lpa_batch_graph", "lpa_batch_size", "lpa_batch_device_bytes", "lpa_batch_destroy",
            "lpa_server_create", "lpa_server_submit", "lpa_server_step", "lpa_server_poll", "lpa_server_result",
            "lpa_server_clock", "lpa_server_device_bytes", "lpa_server_destroy", "lpa_batch_get_tuning",
-           "lpa_batch_set_tuning", "lpa_autotune", "lpa_batch_autotune", "lpa_modularity_noalloc"]
+           "lpa_batch_set_tuning", "lpa_autotune", "lpa_batch_autotune", "lpa_modularity_noalloc", "lpa_run_cc"]
 
 
 class LpaError(RuntimeError):
@@ -110,6 +110,7 @@ def load() -> ct.CDLL:
     P, i64, i32 = ct.c_void_p, ct.c_int64, ct.c_int
     L.lpa_create.argtypes = [P, P, P, i64, i64, i32, P, ct.POINTER(P)]
     L.lpa_run.argtypes = [P, ct.c_double, i32, i32, i32, ct.POINTER(Stats)]
+    L.lpa_run_cc.argtypes = [P, ct.c_double, i32, i32, i32, i32, ct.POINTER(Stats)]
     L.lpa_labels.argtypes = [P, P, i64, i32]
     L.lpa_modularity.argtypes = [P, ct.POINTER(ct.c_double)]
     L.lpa_set_labels.argtypes = [P, P, i64, i32]
@@ -220,11 +221,17 @@ class Graph:
 
     # -- algorithm ------------------------------------------------------------------
     def run(self, tolerance: float = 0.05, max_iters: int = 20, pl_period: int = 4, mode: int = SYNC,
-            resume: bool = False, time_kernels: bool = False) -> Stats:
+            resume: bool = False, time_kernels: bool = False, cc_period: int = 0) -> Stats:
+        """lpa_run, or lpa_run_cc when cc_period > 0 (Cross-Check every cc_period sweeps)."""
         st = Stats()
         st.time_kernels = 1 if time_kernels else 0
-        _check(load().lpa_run(self._h, float(tolerance), int(max_iters), int(pl_period),
-                              int(mode) | (RESUME if resume else 0), ct.byref(st)), "lpa_run")
+        m = int(mode) | (RESUME if resume else 0)
+        if cc_period:
+            _check(load().lpa_run_cc(self._h, float(tolerance), int(max_iters), int(pl_period), int(cc_period), m,
+                                     ct.byref(st)), "lpa_run_cc")
+        else:
+            _check(load().lpa_run(self._h, float(tolerance), int(max_iters), int(pl_period), m, ct.byref(st)),
+                   "lpa_run")
         return st
 
     def labels(self, out: torch.Tensor | None = None) -> torch.Tensor:

@@ -194,6 +194,74 @@ def test_sync_is_deterministic(lpa):
 
 
 # ---------------------------------------------------------------------------------------
+# Cross-Check (Section 4.1) and the Hybrid with Pick-Less
+
+def check_cc_every_iteration(lpa, csr, tol, max_iters, pl, cc, tuning=None):
+    og = oracle_graph(csr)
+    ref = oracle.lpa_sync(og, tol, max_iters, pl, cc_period=cc)
+    g = make(lpa, csr, True, tuning)
+    st = g.run(tol, max_iters, pl, lpa.SYNC, cc_period=cc)
+    assert st.dN() == ref.dN and st.iterations == ref.iterations and bool(st.converged) == ref.converged
+    assert g.labels().cpu().numpy().tolist() == ref.labels.tolist()
+    C, A, it = g.get_state()
+    assert A.numpy().tolist() == np.asarray(ref.active).tolist()
+    for t in range(1, ref.iterations):
+        rt = oracle.lpa_sync(og, tol, t, pl, cc_period=cc)
+        g.run(tol, t, pl, lpa.SYNC, cc_period=cc)
+        assert g.labels().cpu().numpy().tolist() == rt.labels.tolist(), f"iteration {t}"
+    return g, ref
+
+
+def test_cross_check_closed_forms(lpa):
+    """The bipartite swap is broken in three sweeps; on a path the moves are checked in id
+    order (odd vertices keep, even ones revert after sweep 0), a chain of dependent moves as
+    long as the path (about 17 pointer-jumping passes for 100,000 vertices)."""
+    for n in (3, 7):
+        g, ref = check_cc_every_iteration(lpa, gg.complete_bipartite(n), 0.05, 20, 0, 1)
+        assert ref.dN == [n, n - 1, 0]
+    for k in (9, 100_000):
+        path = gg.from_edges(k, [(i, i + 1) for i in range(k - 1)]) if k < 1000 else path_graph(k)
+        check_cc_every_iteration(lpa, path, 0.0, 6, 1, 1)
+
+
+def path_graph(k):
+    idx = np.empty(2 * (k - 1), dtype=np.int32)
+    off = np.zeros(k + 1, dtype=np.int64)
+    deg = np.full(k, 2, dtype=np.int64)
+    deg[0] = deg[-1] = 1
+    off[1:] = np.cumsum(deg)
+    i = np.arange(k)
+    left, right = off[:-1], off[:-1] + (deg - 1)
+    idx[left[1:]] = (i[1:] - 1).astype(np.int32)
+    idx[right[:-1]] = (i[:-1] + 1).astype(np.int32)
+    return gg.CSRGraph(torch.from_numpy(off), torch.from_numpy(idx), None, name="path")
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_cross_check_random_graphs(lpa, seed):
+    rnd = random.Random(40 + seed)
+    csr = gg.random_small(rnd.choice([80, 300, 700]), rnd.choice([0.02, 0.08]), 7000 + seed, wmax=rnd.choice([1, 4]),
+                          self_loops=seed % 2 == 0)
+    pl, cc = [(0, 1), (0, 2), (4, 1), (2, 2), (3, 4), (1, 1)][seed]
+    check_cc_every_iteration(lpa, csr, 0.05, 20, pl, cc, SMALL_BUCKETS if seed % 2 else None)
+
+
+@pytest.mark.parametrize("which", ["rmat-default", "rmat-hubs", "sbm"])
+def test_cross_check_larger(lpa, which):
+    if which == "sbm":
+        csr, tuning = gg.sbm(5000, 50, 12.0, 2.0, seed=2, weights="int8"), None
+    else:
+        csr, tuning = gg.rmat(13, weights="int8"), (SMALL_BUCKETS if which == "rmat-hubs" else None)
+    check_cc_every_iteration(lpa, csr, 0.05, 20, 4, 2, tuning)
+
+
+def test_cross_check_rejected_in_async_mode(lpa):
+    g = make(lpa, gg.cliques(3, 4))
+    with pytest.raises(lpa.LpaError):
+        g.run(0.05, 20, 4, lpa.ASYNC, cc_period=1)
+
+
+# ---------------------------------------------------------------------------------------
 # processed vertices per sweep (pruning, Algorithm 1)
 
 def expected_active(csr, og, iterations, tol, pl):
