@@ -417,6 +417,15 @@ def run_ours(args):
             ab[names[pr]] = {"run_ms": round(best["total_ms"], 2), "probe_fallbacks": best["probe_fallbacks"],
                              "iterations": best["iterations"]}
         line["probe_ablation"] = ab
+        # swap mitigation (Section 4.1): Pick-Less and Cross-Check periods on the same graph
+        sw = {}
+        if mode == lpa.SYNC:
+            for name, pl, cc in (("none", 0, 0), ("PL4", 4, 0), ("CC1", 0, 1), ("CC2", 0, 2), ("PL4+CC4", 4, 4),
+                                 ("PL2+CC2", 2, 2)):
+                st = g.run(ALG["tolerance"], ALG["max_iters"], pl, mode, cc_period=cc).to_dict()
+                sw[name] = {"run_ms": round(st["total_ms"], 2), "iterations": st["iterations"],
+                            "converged": st["converged"], "modularity": g.modularity()}
+            line["swap_mitigation"] = sw
     # end to end through the public API with host buffers
     h_off = h_idx = h_w = h_lab = None
     if not args.no_e2e:
