@@ -53,6 +53,34 @@ BYTES_PER_EDGE_U = 8       # unit weights passed as NULL: index 4 + label 4
 BYTES_PER_VERTEX = 17      # offsets 2x4 (amortised) + own label 4 + label write 4 + flag 1
 
 
+# DRAM bytes per launch of the dominant kernel, from one ncu capture of this bench's own command
+# on the default workload (profiles/hub_acc_rmat26_dram.md: mean of the four hub-accumulate
+# launches of one run).  Reported while the sweep sources hash as they did at capture time.
+TRAFFIC = {
+    "kernel": "hub_acc", "workload": "rmat26", "bytes_per_launch": 14.307e9,
+    "sources": {
+        "sweep_kernels.cuh": "99d0f465351c0c421f8f7b6f4e606c324294cfd773d4909a412555ba02e017d7",
+        "lpa_sweep.cu": "b258eb6309abbb1ebfbb02c09f0abae54229d2143dc67bebe116b5c38daee45d",
+        "lpa_internal.h": "996792bd64dcb4cd653bc40a8a9eef0646c85b4f425476f3da89136918969fd8",
+    },
+}
+
+
+def traffic_for(kernel: str, workload: str):
+    import hashlib
+    if kernel != TRAFFIC["kernel"] or workload != TRAFFIC["workload"]:
+        return None
+    csrc = os.path.join(ROOT, "paper_2411_11468_gb300", "csrc")
+    for name, digest in TRAFFIC["sources"].items():
+        try:
+            with open(os.path.join(csrc, name), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return TRAFFIC["bytes_per_launch"]
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -398,7 +426,8 @@ def run_ours(args):
                                               gbs=round(kbytes[k] / (kms[k] / 1000.0) / 1e9, 1) if kms[k] > 0 else None)
                     for k in range(lpa.NUM_KERNELS) if kms[k] > 0}
     roofline = {"bound": "hbm", "kernel": lpa.KERNEL_NAMES[dom], "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic_for(lpa.KERNEL_NAMES[dom], args.workload), "peak_source": peak_src,
                 "bytes_model": f"{BYTES_PER_EDGE_W if weighted else BYTES_PER_EDGE_U} B per scanned entry + "
                                f"{BYTES_PER_VERTEX} B per processed vertex",
                 "first_sweep": {"ms": round(sweep0_ms, 3), "edges": first["edges"][0],
