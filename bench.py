@@ -85,6 +85,17 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def over_ranks(x: float, op: str, device=None) -> float:
+    """x reduced over the ranks of the default process group ("max" or "sum"); x itself
+    without a group.  The replicas' step time is the maximum over ranks, their work the sum."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -392,14 +403,12 @@ def run_ours(args):
         stats.append(st.to_dict())
     e1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    edges_per_step = statistics.median(sum(s["edges"]) for s in stats)
-    value = ws * edges_per_step / (ms / 1000.0)
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = over_ranks(e0.elapsed_time(e1) / args.steps, "max", dev)
+    edges_per_step = over_ranks(statistics.median(sum(s["edges"]) for s in stats), "sum", dev)
+    value = edges_per_step / (ms / 1000.0)
 
     # roofline of the dominant kernel over the timed steps
     peak, peak_src = measured_peaks()
@@ -498,13 +507,10 @@ def run_ours(args):
             if rep > 0:
                 times.append(time.perf_counter() - t0)
                 edges.append(sum(st2.to_dict()["edges"]))
-        e2e_s = statistics.median(times)
-        if ws > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = over_ranks(statistics.median(times), "max", dev)
         h2d = h_off.numel() * h_off.element_size() + h_idx.numel() * 4 + (0 if h_w is None else h_w.numel() * 4)
-        line["e2e"] = {"value": ws * statistics.median(edges) / e2e_s, "unit": "edges/s", "ms_per_step": e2e_s * 1000,
+        line["e2e"] = {"value": over_ranks(statistics.median(edges), "sum", dev) / e2e_s, "unit": "edges/s",
+                       "ms_per_step": e2e_s * 1000,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": csr.n * 4 + 8,
                        "includes": "lpa_create from pinned host CSR (copy, validation, buckets), lpa_run, "
                                    "lpa_labels to pinned host, lpa_modularity, lpa_destroy"}
