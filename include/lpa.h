@@ -51,6 +51,7 @@ extern "C" {
 #define LPA_ECUDA    (-3)   /* a CUDA runtime call or kernel launch failed            */
 #define LPA_ETIMEOUT (-4)   /* a bounded device wait gave up (status word set)        */
 #define LPA_ESTATE   (-5)   /* call not valid in the handle's current state           */
+#define LPA_ECANCELED (-6)  /* server request cancelled (lpa_server_cancel)           */
 
 /* ---- lpa_run modes (Section 4 item 1 is the asynchronous mode) -------------------- */
 #define LPA_SYNC    0       /* deterministic: every sweep reads the previous sweep's labels */
@@ -221,6 +222,12 @@ void lpa_destroy(lpa_graph *g);
 
 const char *lpa_strerror(int status);
 const char *lpa_last_error(void);
+
+/* Fault injection for tests (host side only, process-wide): after `after` further device
+ * allocations by the library succeed, every later one fails with LPA_ENOMEM as if the device
+ * were full; a negative value turns it off.  Every entry point must then fail cleanly
+ * (no partial handle, nothing leaked).  The paper has no counterpart. */
+void lpa_debug_fail_allocations(long long after);
 const char *lpa_kernel_name(int slot);
 
 /* ---- batches: many independent graphs solved together -------------------------------- */
@@ -302,6 +309,11 @@ int lpa_server_submit(lpa_server *s, const lpa_graph_desc *graph, int flags, dou
  * *n_running and *n_queued (optional) report the state after the step; *n_completed (optional)
  * the requests that finished in this step. */
 int lpa_server_step(lpa_server *s, int *n_completed, int *n_running, int *n_queued);
+
+/* Cancels a request: a queued one leaves the queue, a running one is retired (its memory goes
+ * back to the arena); either is then listed by lpa_server_poll with status LPA_ECANCELED.
+ * LPA_ESTATE when it has already finished, LPA_EINVAL for an unknown id. */
+int lpa_server_cancel(lpa_server *s, int64_t request_id);
 
 /* Ids of finished requests not yet collected (at most max_ids); *n receives how many. */
 int lpa_server_poll(lpa_server *s, int64_t *ids, int max_ids, int *n);

@@ -4,6 +4,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <climits>
 #include <type_traits>
@@ -605,12 +607,30 @@ size_t Arena::largest_free() const
 // ---------------------------------------------------------------------------------------
 namespace {
 
+// Host-side fault injection (lpa_debug_fail_allocations): the number of further device
+// allocations that succeed before every later one fails; negative = off.
+std::atomic<long long> g_alloc_budget{-1};
+
+bool injected_alloc_failure()
+{
+    long long b = g_alloc_budget.load();
+    while (b >= 0) {
+        if (b == 0) return true;
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) return false;
+    }
+    return false;
+}
+
 template <typename T>
 int dalloc(lpa_graph *g, T **p, size_t count)
 {
     *p = nullptr;
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
     void *q = nullptr;
+    if (injected_alloc_failure()) {
+        set_error("device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
+        return LPA_ENOMEM;
+    }
     if (g->arena) {
         q = g->arena->alloc(bytes);
     } else if (cudaMalloc(&q, bytes) != cudaSuccess) {
@@ -1323,11 +1343,14 @@ const char *lpa_strerror(int status)
     case LPA_ECUDA: return "CUDA error";
     case LPA_ETIMEOUT: return "device wait timed out";
     case LPA_ESTATE: return "invalid state";
+    case LPA_ECANCELED: return "request cancelled";
     default: return "unknown status";
     }
 }
 
 const char *lpa_last_error(void) { return t_error.c_str(); }
+
+void lpa_debug_fail_allocations(long long after) { g_alloc_budget.store(after < 0 ? -1 : after); }
 
 const char *lpa_kernel_name(int slot)
 {

@@ -742,6 +742,35 @@ int lpa_server_step(lpa_server *s, int *n_completed, int *n_running, int *n_queu
     return LPA_OK;
 }
 
+int lpa_server_cancel(lpa_server *s, int64_t request_id)
+{
+    if (!s) return LPA_EINVAL;
+    DeviceGuard dg(s->device);
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        if ((*it)->id != request_id) continue;
+        Request *r = *it;
+        s->queue.erase(it);
+        finish_request(s, r, LPA_ECANCELED);
+        return LPA_OK;
+    }
+    // between steps no work of the server is in flight (a step ends by synchronising)
+    for (size_t i = 0; i < s->running.size(); ++i) {
+        if (s->running[i]->id != request_id) continue;
+        Request *r = s->running[i];
+        s->running.erase(s->running.begin() + (long)i);
+        finish_request(s, r, LPA_ECANCELED);
+        s->dirty = true;
+        return LPA_OK;
+    }
+    if (s->finished.count(request_id)) {
+        set_error("lpa_server_cancel: the request has finished");
+        return LPA_ESTATE;
+    }
+    set_error("lpa_server_cancel: unknown request");
+    return LPA_EINVAL;
+}
+
 int lpa_server_poll(lpa_server *s, int64_t *ids, int max_ids, int *n)
 {
     if (!s || !n || (max_ids > 0 && !ids)) return LPA_EINVAL;

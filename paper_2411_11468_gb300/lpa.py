@@ -21,7 +21,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblpa.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ECANCELED = 0, -1, -2, -3, -4, -5, -6
 SYNC, ASYNC, RESUME = 0, 1, 16
 OFFSETS_I32, OFFSETS_I64, HOST_PTRS, DEVICE_PTRS, CHECK_SYMMETRIC = 0, 1, 0, 2, 4
 BORROW_INPUTS = 8
@@ -37,7 +37,8 @@ SYMBOLS = ["lpa_create", "lpa_run", "lpa_labels", "lpa_modularity", "lpa_set_lab
            "lpa_batch_modularity", "lpa_batch_graph", "lpa_batch_size", "lpa_batch_device_bytes", "lpa_batch_destroy",
            "lpa_server_create", "lpa_server_submit", "lpa_server_step", "lpa_server_poll", "lpa_server_result",
            "lpa_server_clock", "lpa_server_device_bytes", "lpa_server_destroy", "lpa_batch_get_tuning",
-           "lpa_batch_set_tuning", "lpa_autotune", "lpa_batch_autotune", "lpa_modularity_noalloc", "lpa_run_cc"]
+           "lpa_batch_set_tuning", "lpa_autotune", "lpa_batch_autotune", "lpa_modularity_noalloc", "lpa_run_cc", "lpa_server_cancel",
+           "lpa_debug_fail_allocations"]
 
 
 class LpaError(RuntimeError):
@@ -313,6 +314,14 @@ class Result(ct.Structure):
 _multi_ready = False
 
 
+def debug_fail_allocations(after: int):
+    """lpa_debug_fail_allocations: device allocations fail after `after` more (< 0: off)."""
+    L = load()
+    L.lpa_debug_fail_allocations.argtypes = [ct.c_longlong]
+    L.lpa_debug_fail_allocations.restype = None
+    L.lpa_debug_fail_allocations(int(after))
+
+
 def _load_multi():
     global _multi_ready
     L = load()
@@ -339,6 +348,7 @@ def _load_multi():
     L.lpa_server_submit.argtypes = [P, ct.POINTER(GraphDesc), i32, ct.c_double, i32, i32, i32, ct.POINTER(ct.c_int64)]
     L.lpa_server_step.argtypes = [P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
     L.lpa_server_poll.argtypes = [P, ct.POINTER(ct.c_int64), i32, ct.POINTER(ct.c_int)]
+    L.lpa_server_cancel.argtypes = [P, i64]
     L.lpa_server_result.argtypes = [P, i64, P, i64, ct.POINTER(Result), ct.POINTER(ct.c_double),
                                     ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
     L.lpa_server_clock.argtypes = [P]
@@ -490,6 +500,9 @@ class Server:
         _check(_load_multi().lpa_server_step(self._h, ct.byref(c), ct.byref(r), ct.byref(q)), "lpa_server_step")
         return c.value, r.value, q.value
 
+    def cancel(self, rid):
+        _check(_load_multi().lpa_server_cancel(self._h, int(rid)), "lpa_server_cancel")
+
     def poll(self, max_ids=4096):
         ids = (ct.c_int64 * max_ids)()
         n = ct.c_int()
@@ -498,6 +511,7 @@ class Server:
 
     def result(self, rid):
         n = self._sizes.pop(rid)
+        self._borrowed.pop(rid, None)
         lab = torch.empty(n, dtype=torch.int32)
         res = Result()
         ts, ta, tf = ct.c_double(), ct.c_double(), ct.c_double()

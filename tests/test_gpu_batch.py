@@ -260,3 +260,95 @@ def test_batch_set_tuning_rejects_invalid(lpa):
 
 SMALL = dict(thread_max=3, group_max=7, group_lanes=4, warp_max=31, cta_max=63, cta_threads=64, cta_large_max=95,
              cta_large_threads=128, cta_xl_max=127, cta_xl_threads=256, hub_chunk=256, hub_table_shift=0)
+
+
+# ---------------------------------------------------------------------------------------
+# faults made on the host: invalid requests, cancellation, failed allocations
+
+def test_server_invalid_and_cancelled_requests(lpa):
+    """An invalid graph fails alone at admission (LPA_EINVAL); a queued and a running request
+    are cancelled (LPA_ECANCELED); every other request still equals the oracle."""
+    good = [gg.rmat(11, weights="int8"), gg.sbm(2000, 40, 10.0, 2.0, seed=5, weights="int8"), gg.cliques(4, 6)]
+    bad = gg.rmat(10, weights="int8")
+    bad_idx = bad.indices.clone()
+    bad_idx[7] = bad.n + 3                               # neighbour id out of range
+    srv = lpa.Server(1 << 28, max_resident=1)
+    ids = [srv.submit(g.offsets, g.indices, g.weights) for g in good]
+    bad_id = srv.submit(bad.offsets, bad_idx, bad.weights)
+    running = srv.submit(good[0].offsets, good[0].indices, good[0].weights)
+    queued = srv.submit(good[1].offsets, good[1].indices, good[1].weights)
+    srv.cancel(queued)                                   # still queued (one resident at a time)
+    seen, finished = {}, set()
+    for _ in range(10_000):
+        c, r, q = srv.step()
+        for rid in srv.poll():
+            finished.add(rid)
+            if rid in (bad_id, queued, running):
+                with pytest.raises(lpa.LpaError) as ei:
+                    srv.result(rid)
+                seen[rid] = ei.value.status
+            else:
+                seen[rid] = srv.result(rid)
+        if running not in finished and ids[-1] in finished:
+            srv.cancel(running)                          # admitted after the others: cancel it mid-run
+        if r == 0 and q == 0:
+            break
+    assert seen[bad_id] == lpa.EINVAL and seen[queued] == lpa.ECANCELED and seen[running] == lpa.ECANCELED
+    for rid, g in zip(ids, good):
+        ref = oracle.lpa_sync(oracle.Graph.of(g))
+        assert seen[rid][0].numpy().tolist() == ref.labels.tolist()
+    with pytest.raises(lpa.LpaError):
+        srv.cancel(ids[0])                               # already finished and collected
+    srv.close()
+
+
+def test_allocation_failures_fail_cleanly(lpa):
+    """Every device allocation of lpa_create, of a batch and of server admission made to fail in
+    turn: the call reports LPA_ENOMEM, leaves no handle and leaks no device memory, and the next
+    call with allocations allowed works."""
+    csr = gg.rmat(10, weights="int8")
+    ref = oracle.lpa_sync(oracle.Graph.of(csr))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failures = 0
+    try:
+        for n in range(0, 60):
+            lpa.debug_fail_allocations(n)
+            try:
+                g = lpa.Graph(csr.offsets, csr.indices, csr.weights)
+            except lpa.LpaError as e:
+                assert e.status == lpa.ENOMEM
+                failures += 1
+                continue
+            lpa.debug_fail_allocations(-1)
+            g.run()
+            assert g.labels().cpu().numpy().tolist() == ref.labels.tolist()
+            g.close()
+            break
+        for n in (0, 3, 10):
+            lpa.debug_fail_allocations(n)
+            with pytest.raises(lpa.LpaError):
+                lpa.Batch([as_tuple(csr), as_tuple(gg.cliques(3, 5))])
+    finally:
+        lpa.debug_fail_allocations(-1)
+    assert failures >= 10
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)      # nothing leaked beyond allocator slack
+    srv = lpa.Server(1 << 26, max_resident=2)
+    lpa.debug_fail_allocations(2)
+    try:
+        rid = srv.submit(csr.offsets, csr.indices, csr.weights)
+        srv.step()
+    finally:
+        lpa.debug_fail_allocations(-1)
+    with pytest.raises(lpa.LpaError) as ei:
+        srv.result(srv.poll()[0])
+    assert ei.value.status == lpa.ENOMEM
+    rid = srv.submit(csr.offsets, csr.indices, csr.weights)
+    for _ in range(100):
+        srv.step()
+        done = srv.poll()
+        if done:
+            break
+    assert srv.result(done[0])[0].numpy().tolist() == ref.labels.tolist()
+    srv.close()
