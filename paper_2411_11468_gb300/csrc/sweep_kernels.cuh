@@ -298,6 +298,12 @@ __device__ __forceinline__ void group_sync()
 template <int G>
 __device__ __forceinline__ unsigned long long group_max(unsigned long long x)
 {
+    if (G == 32) {                  // whole warp: two 32-bit reductions (weight word, then label word)
+        const unsigned hi = (unsigned)(x >> 32);
+        const unsigned mh = __reduce_max_sync(0xFFFFFFFFu, hi);
+        const unsigned ml = __reduce_max_sync(0xFFFFFFFFu, hi == mh ? (unsigned)x : 0u);
+        return ((unsigned long long)mh << 32) | ml;
+    }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) x = umax64(x, __shfl_xor_sync(group_mask<G>(), x, o, G));
     return x;
@@ -790,7 +796,7 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
     Tab tab;
     table_at(tab, smem, 1, k.slots, 0, false);
     __shared__ int s_item, s_nmov;
-    __shared__ int32_t s_mv[32];
+    __shared__ int32_t s_mv[32], s_dec;
     __shared__ int64_t s_mo0[32], s_mo1[32];
     __shared__ int2 s_mov[32];
     __shared__ unsigned long long s_best[TPB / 32], s_mbase;
@@ -869,11 +875,17 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
                 bool act = true;
                 if (PULL) act = __syncthreads_or((seen & kMovedBit) != 0) != 0;   // a neighbour moved
                 else __syncthreads();
-                best = 0;
-#pragma unroll
-                for (int w = 0; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
-                int32_t cstar = -1;
-                const bool moved = act && decide(best, cur, a.pl, cstar);
+                if (threadIdx.x < 32) {                // warp 0 combines the warps and decides
+                    unsigned long long x = threadIdx.x < TPB / 32 ? s_best[threadIdx.x] : 0ull;
+                    x = group_max<32>(x);
+                    if (threadIdx.x == 0) {
+                        int32_t c = -1;
+                        s_dec = (act && decide(x, cur, a.pl, c)) ? c : -1;
+                    }
+                }
+                __syncthreads();
+                const int32_t cstar = s_dec;
+                const bool moved = cstar >= 0;
                 if (moved) {
                     if (threadIdx.x == 0) {
                         if (a.async_mode) {
