@@ -57,9 +57,9 @@ BYTES_PER_VERTEX = 17      # offsets 2x4 (amortised) + own label 4 + label write
 # on the default workload (profiles/hub_acc_rmat26_dram.md: mean of the four hub-accumulate
 # launches of one run).  Reported while the sweep sources hash as they did at capture time.
 TRAFFIC = {
-    "kernel": "hub_acc", "workload": "rmat26", "bytes_per_launch": 14.307e9,
+    "kernel": "hub_acc", "workload": "rmat26", "bytes_per_launch": 14.310e9,
     "sources": {
-        "sweep_kernels.cuh": "99d0f465351c0c421f8f7b6f4e606c324294cfd773d4909a412555ba02e017d7",
+        "sweep_kernels.cuh": "370553a2339b1f9520042fc823017f9b117b9ca380c909e73bfcd3dee0fb1e64",
         "lpa_sweep.cu": "b258eb6309abbb1ebfbb02c09f0abae54229d2143dc67bebe116b5c38daee45d",
         "lpa_internal.h": "996792bd64dcb4cd653bc40a8a9eef0646c85b4f425476f3da89136918969fd8",
     },
