@@ -49,7 +49,7 @@ WORKLOADS = {
 }
 ALG = dict(tolerance=0.05, max_iters=20, pl_period=4)
 BYTES_PER_EDGE_W = 12      # neighbour index 4 + weight 4 + gathered label 4
-BYTES_PER_EDGE_U = 8       # unit weights passed as NULL: index 4 + label 4
+BYTES_PER_EDGE_U = 8       # unit weights (NULL, or all exactly 1: not read): index 4 + label 4
 BYTES_PER_VERTEX = 17      # offsets 2x4 (amortised) + own label 4 + label write 4 + flag 1
 
 
@@ -57,11 +57,12 @@ BYTES_PER_VERTEX = 17      # offsets 2x4 (amortised) + own label 4 + label write
 # on the default workload (profiles/hub_acc_rmat26_dram.md: mean of the four hub-accumulate
 # launches of one run).  Reported while the sweep sources hash as they did at capture time.
 TRAFFIC = {
-    "kernel": "hub_acc", "workload": "rmat26", "bytes_per_launch": 14.310e9,
+    "kernel": "hub_acc", "workload": "rmat26", "bytes_per_launch": 11.888e9,
     "sources": {
         "sweep_kernels.cuh": "370553a2339b1f9520042fc823017f9b117b9ca380c909e73bfcd3dee0fb1e64",
         "lpa_sweep.cu": "b258eb6309abbb1ebfbb02c09f0abae54229d2143dc67bebe116b5c38daee45d",
         "lpa_internal.h": "996792bd64dcb4cd653bc40a8a9eef0646c85b4f425476f3da89136918969fd8",
+        "lpa_graph.cu": "5051321e543232447e868b05d78cdf04177b7de703077ab18074a1f48f8cdbc0",
     },
 }
 
@@ -376,7 +377,7 @@ def run_ours(args):
     csr = make_graph(args.workload, dev)
     torch.cuda.synchronize()
     log(f"[bench] graph {args.workload}: n={csr.n} m={csr.m} generated in {time.time() - t0:.1f}s")
-    weighted = csr.weights is not None
+    weighted = csr.weights is not None and not bool(torch.all(csr.weights == 1))   # all-one weights are not read
     stream = torch.cuda.current_stream(dev)
     g = lpa.Graph(csr.offsets, csr.indices, csr.weights)
     log(f"[bench] lpa_create done; device bytes {g.device_bytes() / 1e9:.2f} GB")

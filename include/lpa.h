@@ -146,6 +146,8 @@ typedef struct lpa_graph lpa_graph;
  *  indices   host or device; int32_t [n_entries], each in [0, n_vertices).  Self-loops are
  *            allowed and skipped by the sweep (Algorithm 1 skips j = i).
  *  weights   host or device; float [n_entries], finite and >= 0; NULL = unit weights.
+ *            Weights that are all exactly 1 are taken as unit weights (the same sums; the
+ *            kernels skip the weight reads and the device copy is released).
  *  n_vertices in [0, 2^31 - 1); n_entries >= 0.
  *  flags     LPA_OFFSETS_I32 / LPA_OFFSETS_I64, LPA_HOST_PTRS / LPA_DEVICE_PTRS,
  *            optionally LPA_CHECK_SYMMETRIC.

@@ -370,23 +370,26 @@ __global__ void __launch_bounds__(256) k_weight_props(const int64_t *off, const 
 }
 
 // Flat pass over all weights: bit 1 of *flags is cleared when a weight is not an integer in
-// [0, 2^24); *wmax_bits receives the bits of the largest weight (non-negative floats order
-// like their bit patterns).  Row sums are needed only when max weight x max degree can
-// reach 2^24 (then k_weight_props computes them).
+// [0, 2^24), bit 2 when a weight is not exactly 1; *wmax_bits receives the bits of the
+// largest weight (non-negative floats order like their bit patterns).  Row sums are needed
+// only when max weight x max degree can reach 2^24 (then k_weight_props computes them).
 __global__ void __launch_bounds__(256) k_weight_flat(const float *w, int64_t m, unsigned *flags, unsigned *wmax_bits)
 {
-    bool integral = true;
+    bool integral = true, ones = true;
     float mx = 0.0f;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         const float x = w[e];
         if (!(x >= 0.0f && x < 16777216.0f && truncf(x) == x)) integral = false;
+        if (x != 1.0f) ones = false;
         mx = fmaxf(mx, x);
     }
     integral = __all_sync(0xFFFFFFFFu, integral);
+    ones = __all_sync(0xFFFFFFFFu, ones);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
     if ((threadIdx.x & 31) == 0) {
         if (!integral) atomicAnd(flags, ~2u);
+        if (!ones) atomicAnd(flags, ~4u);
         atomicMax(wmax_bits, __float_as_uint(mx));
     }
 }
@@ -1214,6 +1217,7 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
         set_error(msg);
         return fail(LPA_EINVAL);
     }
+    bool unit_weights = false;
     {
         // integer sums are exact when every weight is an integer and every row sum is below
         // 2^24: max weight x max degree below 2^24 settles it, else the exact row sums do
@@ -1221,7 +1225,7 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
         if ((st = dalloc(g, &mk, 2)) != LPA_OK) return fail(st);
         unsigned *fl = reinterpret_cast<unsigned *>(g->d_err);
         cudaMemsetAsync(mk, 0, 2 * sizeof(unsigned long long), s);
-        const unsigned init[2] = {2u, 0u};            // flags, largest weight bits
+        const unsigned init[2] = {6u, 0u};            // flags, largest weight bits
         cudaMemcpyAsync(fl, init, sizeof(init), cudaMemcpyHostToDevice, s);
         if (g->w && m > 0)
             k_weight_flat<<<grid_for(m, 256, 16), 256, 0, s>>>(g->w, m, fl, fl + 1);
@@ -1238,6 +1242,7 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
         float wmax = 1.0f;
         if (g->w) memcpy(&wmax, &hf[1], sizeof(float));
         const bool integral = (hf[0] & 2u) != 0;
+        unit_weights = (hf[0] & 4u) != 0;
         if (integral && (double)wmax * (double)hd < 16777216.0) {
             g->int_weights = true;
         } else if (integral) {
@@ -1271,6 +1276,14 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
             set_error("lpa_create: graph is not undirected (entry (i,j,w) without (j,i,w))");
             return fail(LPA_EINVAL);
         }
+    }
+    if (unit_weights && g->w) {
+        // every weight is exactly 1: the kernels take the unit-weight path (same sums, no
+        // weight reads) and the device copy is released
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "weights");
+        dfree(g, g->w);
+        g->w = nullptr;
     }
     if ((st = build_buckets(g)) != LPA_OK) return fail(st);
     if ((st = init_state(g)) != LPA_OK) return fail(st);

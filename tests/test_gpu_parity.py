@@ -184,6 +184,38 @@ def test_unit_weights_null_pointer(lpa):
     assert st.dN() == ref.dN and g.labels().cpu().numpy().tolist() == ref.labels.tolist()
 
 
+def test_all_one_weights_take_the_unit_path(lpa):
+    # weights that are all exactly 1 are released at creation: same labels, sweeps and
+    # modularity as no weights, and the same device footprint
+    csr = gg.rmat(13, weights="unit")
+    ones = lpa.Graph(csr.offsets.cuda(), csr.indices.cuda(), torch.ones(csr.m, dtype=torch.float32, device="cuda"))
+    none = lpa.Graph(csr.offsets.cuda(), csr.indices.cuda(), None)
+    assert ones.device_bytes() == none.device_bytes()
+    s1, s2 = ones.run(), none.run()
+    assert s1.dN() == s2.dN() and torch.equal(ones.labels(), none.labels())
+    assert ones.modularity() == none.modularity()
+    ref = oracle.lpa_sync(oracle.Graph(csr.offsets, csr.indices, None))
+    assert s1.dN() == ref.dN and ones.labels().cpu().numpy().tolist() == ref.labels.tolist()
+
+
+def test_one_weight_not_one_keeps_the_weights(lpa):
+    # a single symmetric pair of weight 2 among ones: the weights stay and count
+    csr = gg.rmat(12, weights="unit")
+    w = torch.ones(csr.m, dtype=torch.float32)
+    off, idx = csr.offsets, csr.indices
+    i = int(torch.argmax(off[1:] - off[:-1]))                 # the largest hub and its first neighbour
+    j = int(idx[off[i]])
+    w[off[i]] = 2.0
+    row_j = idx[off[j]:off[j + 1]]
+    w[off[j] + int((row_j == i).nonzero()[0])] = 2.0
+    g = lpa.Graph(off.cuda(), idx.cuda(), w.cuda())
+    none = lpa.Graph(off.cuda(), idx.cuda(), None)
+    assert g.device_bytes() == none.device_bytes() + 4 * csr.m
+    ref = oracle.lpa_sync(oracle.Graph(off, idx, w))
+    st = g.run()
+    assert st.dN() == ref.dN and g.labels().cpu().numpy().tolist() == ref.labels.tolist()
+
+
 def test_sync_is_deterministic(lpa):
     csr = gg.rmat(14, weights="int8").to("cuda")
     g = lpa.Graph(csr.offsets, csr.indices, csr.weights)
