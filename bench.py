@@ -476,6 +476,19 @@ def run_ours(args):
             ab[names[pr]] = {"run_ms": round(best["total_ms"], 2), "probe_fallbacks": best["probe_fallbacks"],
                              "iterations": best["iterations"]}
         line["probe_ablation"] = ab
+        # hashtable value type (Section 4.4): uint32 sums (the default for integer weights),
+        # float32 and float64 values on the same graph
+        va = {}
+        for name, fv in (("float64", 2), ("float32", 1), ("uint32", 0)):
+            g.set_tuning(float_values=fv)
+            best = None
+            for _ in range(2):
+                st = g.run(ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode).to_dict()
+                if best is None or st["total_ms"] < best["total_ms"]:
+                    best = st
+            va[name] = {"run_ms": round(best["total_ms"], 2), "iterations": best["iterations"],
+                        "modularity": g.modularity(), "device_gb": round(g.device_bytes() / 1e9, 2)}
+        line["value_ablation"] = va
         # swap mitigation (Section 4.1): Pick-Less and Cross-Check periods on the same graph
         sw = {}
         if mode == lpa.SYNC:
@@ -780,7 +793,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and served summaries")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: keep the default buckets")
-    ap.add_argument("--no-ablation", action="store_true", help="skip the probe-scheme comparison")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the probe-scheme and value-type comparisons")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=20_000)

@@ -130,7 +130,8 @@ typedef struct lpa_tuning {
     int32_t cta_xl_max;       /* block of cta_xl_threads per vertex; above: hubs         */
     int32_t cta_xl_threads;
     int32_t item_vertices;    /* vertices per work item of the thread/group/warp kernels (0 = default) */
-    int32_t float_values;     /* 1: float32 label sums even when integer sums would do   */
+    int32_t float_values;     /* label sums: 0 uint32 when exact, else float32; 1 float32;
+                                 2 float64 (Section 4.4's 64-bit hashtable values)       */
     int32_t hub_cluster;      /* 1: hub tables in cluster shared memory where they fit   */
     int32_t probe;            /* table probe scheme (Section 4.2): 0 quadratic-double
                                  (Algorithm 2), 1 linear, 2 quadratic, 3 double hashing;

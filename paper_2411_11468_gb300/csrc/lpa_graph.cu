@@ -705,17 +705,18 @@ int check_tuning(const lpa_tuning &t)
         if (!pow2(th) || th < 64 || th > 1024) return LPA_EINVAL;
     if (t.hub_chunk < 256 || t.hub_chunk > 32768) return LPA_EINVAL;
     if (t.item_vertices < 0 || t.item_vertices > (1 << 20)) return LPA_EINVAL;
-    if (t.float_values != 0 && t.float_values != 1) return LPA_EINVAL;
+    if (t.float_values < 0 || t.float_values > 2) return LPA_EINVAL;
     if (t.hub_cluster != 0 && t.hub_cluster != 1) return LPA_EINVAL;
     if (t.probe < 0 || t.probe > 3) return LPA_EINVAL;
     for (int r : t.reserved)
         if (r != 0) return LPA_EINVAL;
     const int64_t smem = (int64_t)max_dynamic_smem();
-    const int64_t bytes_group = (256 / t.group_lanes) * slots_for(t.group_max, sh) * 8;
-    const int64_t bytes_warp = 8 * slots_for(t.warp_max, sh) * 8;
-    const int64_t bytes_cta = slots_for(t.cta_max, sh) * 8;
-    const int64_t bytes_large = slots_for(t.cta_large_max, sh) * 8;
-    const int64_t bytes_xl = slots_for(t.cta_xl_max, sh) * 8;
+    const int64_t sb = t.float_values == 2 ? 12 : 8;  // bytes per slot: key + value
+    const int64_t bytes_group = (256 / t.group_lanes) * slots_for(t.group_max, sh) * sb;
+    const int64_t bytes_warp = 8 * slots_for(t.warp_max, sh) * sb;
+    const int64_t bytes_cta = slots_for(t.cta_max, sh) * sb;
+    const int64_t bytes_large = slots_for(t.cta_large_max, sh) * sb;
+    const int64_t bytes_xl = slots_for(t.cta_xl_max, sh) * sb;
     if (bytes_group > smem || bytes_warp > smem || bytes_cta > smem || bytes_large > smem || bytes_xl > smem)
         return LPA_EINVAL;
     return LPA_OK;
@@ -874,8 +875,9 @@ int build_buckets(lpa_graph *g)
         }
         const int64_t n_chunks = (int64_t)ch.size(), n_slices = (int64_t)sh.size();
         g->table_slots = slots;
-        const size_t n8 = (size_t)(3 * H + 2 * n_chunks);
-        const size_t n4 = (size_t)(4 * H + n_chunks + 2 * n_slices);
+        const bool f64 = g->tuning.float_values == 2;   // float64 values: per-chunk arg-max pairs
+        const size_t n8 = (size_t)(3 * H + 2 * n_chunks + (f64 ? n_chunks : 0));
+        const size_t n4 = (size_t)(4 * H + n_chunks + 2 * n_slices + (f64 ? n_chunks + H + 1 : 0));
         unsigned char *mem = nullptr;
         LPA_CHECK(dalloc(g, &mem, n8 * 8 + n4 * 4 + 2 * (size_t)H));
         g->hub_mem = mem;
@@ -890,6 +892,7 @@ int build_buckets(lpa_graph *g)
         int64_t *d_ubase = (int64_t *)take(H * 8);
         int64_t *d_ce0 = (int64_t *)take(n_chunks * 8);
         int64_t *d_ce1 = (int64_t *)take(n_chunks * 8);
+        double *d_cbv = f64 ? (double *)take(n_chunks * 8) : nullptr;
         int32_t *d_hv = (int32_t *)take(H * 4);
         uint32_t *d_p1 = (uint32_t *)take(H * 4);
         uint32_t *d_b = (uint32_t *)take(H * 4);
@@ -897,6 +900,8 @@ int build_buckets(lpa_graph *g)
         int32_t *d_ch = (int32_t *)take(n_chunks * 4);
         int32_t *d_sh = (int32_t *)take(n_slices * 4);
         int32_t *d_sj = (int32_t *)take(n_slices * 4);
+        int32_t *d_cbk = f64 ? (int32_t *)take(n_chunks * 4) : nullptr;
+        int32_t *d_hc0 = f64 ? (int32_t *)take((H + 1) * 4) : nullptr;
         uint8_t *d_act = (uint8_t *)take(H);
         uint8_t *d_seen = (uint8_t *)take(H);
         LPA_CUDA(cudaMemcpyAsync(d_tab, tab.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
@@ -912,11 +917,20 @@ int build_buckets(lpa_graph *g)
         LPA_CUDA(cudaMemsetAsync(d_act, 0, 2 * H, g->stream));     // hub_act and hub_seen
         LPA_CUDA(cudaMemsetAsync(d_best, 0, H * 8, g->stream));
         LPA_CUDA(cudaMemsetAsync(d_used, 0, H * 4, g->stream));
-        // 8 bytes per slot in one block: split keys then values, or packed 64-bit slots
-        LPA_CHECK(dalloc(g, &g->tab_k, (size_t)std::max<int64_t>(slots, 2) * 2));     // (none when every hub
-        g->tab_v = reinterpret_cast<float *>(g->tab_k + slots);                       //  is in a cluster)
+        if (f64) {
+            std::vector<int32_t> hc0((size_t)H + 1, (int32_t)n_chunks);
+            for (int64_t c = n_chunks - 1; c >= 0; --c) hc0[(size_t)ch[(size_t)c]] = (int32_t)c;
+            LPA_CUDA(cudaMemcpyAsync(d_hc0, hc0.data(), (H + 1) * 4, cudaMemcpyHostToDevice, g->stream));
+            LPA_CUDA(cudaStreamSynchronize(g->stream));
+        }
+        // 8 bytes per slot in one block: split keys then values, or packed 64-bit slots; with
+        // float64 values 12 bytes: keys, then the values from an 8-byte boundary
+        const int64_t keys_even = (std::max<int64_t>(slots, 2) + 1) & ~(int64_t)1;
+        LPA_CHECK(dalloc(g, &g->tab_k, (size_t)(f64 ? 3 * keys_even : std::max<int64_t>(slots, 2) * 2)));
+        g->tab_v = reinterpret_cast<float *>(g->tab_k + slots);                       // (none when every hub
+        double *tab_vd = f64 ? reinterpret_cast<double *>(g->tab_k + keys_even) : nullptr;   //  is in a cluster)
         LPA_CHECK(dalloc(g, &g->used_list, (size_t)std::max<int64_t>(used_total, 1)));
-        LPA_CUDA(launch_hub_table_clear(g->tab_k, g->tab_v, slots, plan_int_weights(g), g->stream));
+        LPA_CUDA(launch_hub_table_clear(g->tab_k, g->tab_v, slots, plan_int_weights(g), g->stream, tab_vd));
         ha.hub_v = d_hv;
         ha.hub_p1 = d_p1;
         ha.hub_b = d_b;
@@ -934,6 +948,10 @@ int build_buckets(lpa_graph *g)
         ha.slice_j = d_sj;
         ha.tab_k = g->tab_k;
         ha.tab_v = g->tab_v;
+        ha.tab_vd = tab_vd;
+        ha.chunk_bv = d_cbv;
+        ha.chunk_bk = d_cbk;
+        ha.hub_c0 = d_hc0;
         ha.n_hubs = (int32_t)H;
         ha.n_chunks = (int32_t)n_chunks;
         ha.n_slices = (int32_t)n_slices;
@@ -1623,6 +1641,7 @@ int lpa_run_cc(lpa_graph *g, double tolerance, int max_iters, int pl_period, int
     p.probe = g->tuning.probe;
     p.cc_any = cc_period > 0 ? 1 : 0;
     p.cc_ctr = g->cc_ctr;
+    p.f64 = g->tuning.float_values == 2 ? 1 : 0;
 
     size_t evn = 0;
     cudaEvent_t run0 = event_at(g, evn++), run1 = event_at(g, evn++);

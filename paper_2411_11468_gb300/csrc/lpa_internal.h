@@ -73,6 +73,10 @@ struct HubArgs {
     const int32_t *slice_j;    // [n_slices] slice index within the hub's table / used list
     int32_t *tab_k;            // hub tables: keys (split layout) or 64-bit slots over tab_k and tab_v (packed)
     float *tab_v;              // hub table values (split layout; directly after tab_k)
+    double *tab_vd;            // float64 table values (lpa_tuning.float_values = 2), else null
+    double *chunk_bv;          // float64 values: [n_chunks] arg-max pair of each accumulate
+    int32_t *chunk_bk;         //   block (label < 0: none), reduced per hub by k_hub_move
+    const int32_t *hub_c0;     // float64 values: [H + 1] first accumulate chunk of each hub
     int32_t n_hubs;
     int32_t n_chunks;
     int32_t n_slices;
@@ -136,6 +140,7 @@ struct SweepPlan {
     int32_t int_weights;       // 1: every graph of the plan uses uint32 sums (else float32)
     int32_t probe;             // table probe scheme of every graph of the plan (lpa_tuning.probe)
     int32_t cc_any;            // some graph of the plan may run a Cross-Check (launch its kernels)
+    int32_t f64;               // every graph of the plan keeps float64 table values
     unsigned *cc_ctr;          // [kCcPasses + 1] pending counts of the resolution passes
 };
 
@@ -152,8 +157,10 @@ cudaError_t sweep_init_constants();
 // Enqueues one sweep of every graph of the plan (graphs whose run has stopped do no work),
 // the synchronous label publication and k_decide.  *launches counts kernel launches.
 cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, int *launches);
-// Clears `slots` hub-table slots: packed (one 64-bit word per slot over k) or split (k, v).
-cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, bool packed, cudaStream_t s);
+// Clears `slots` hub-table slots: packed (one 64-bit word per slot over k), split (k, v) or
+// split with float64 values (k, vd; v unused).
+cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, bool packed, cudaStream_t s,
+                                   double *vd = nullptr);
 size_t max_dynamic_smem();
 // Largest cluster class (log2 of the blocks per cluster, 0 = none) that the device can run
 // with a hub table slice of 2^kDsmSliceBits slots per block.

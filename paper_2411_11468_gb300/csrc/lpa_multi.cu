@@ -181,6 +181,7 @@ struct MultiPlan {
         p.hub_chunk = t.hub_chunk;
         p.int_weights = all_int ? 1 : 0;
         p.probe = t.probe;
+        p.f64 = t.float_values == 2 ? 1 : 0;
         plan = p;
         return LPA_OK;
     }

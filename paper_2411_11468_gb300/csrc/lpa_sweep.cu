@@ -24,8 +24,9 @@ namespace lpa {
 
 cudaError_t sweep_init_constants()
 {
-    const cudaError_t e = init_magic();
-    return e != cudaSuccess ? e : sweep_init_constants_alt();
+    cudaError_t e = init_magic();
+    if (e == cudaSuccess) e = sweep_init_constants_alt();
+    return e != cudaSuccess ? e : sweep_init_constants_f64();
 }
 
 size_t max_dynamic_smem()
@@ -79,13 +80,15 @@ __global__ void __launch_bounds__(TPB) k_hub_clear(HArgs k)
     const int64_t p1 = h.hub_p1[hh];
     int32_t *Hk = h.tab_k + h.hub_tab[hh];
     float *Hv = h.tab_v + h.hub_tab[hh];
+    double *Hd = h.tab_vd ? h.tab_vd + h.hub_tab[hh] : nullptr;
     unsigned long long *H = (unsigned long long *)h.tab_k + h.hub_tab[hh];
     auto clear = [&](int64_t q) {
         if (packed) {
             H[q] = kEmptySlot;
         } else {
             Hk[q] = kEmpty;
-            Hv[q] = 0.0f;
+            if (Hd) Hd[q] = 0.0;
+            else Hv[q] = 0.0f;
         }
     };
     if (cnt * 8 > p1) {
@@ -114,7 +117,15 @@ __global__ void k_hub_move(HArgs k)
         const int32_t v = h.hub_v[hh];
         const int32_t cur = (int32_t)((uint32_t)a.C[v] & kLabelMask);
         int32_t cstar = -1;
-        const bool moved = decide(h.hub_best[hh], cur, a.pl, cstar);
+        bool moved;
+        if (h.chunk_bv) {                             // float64 values: reduce the chunks' pairs
+            BestD best;
+            best_init(best);
+            for (int32_t c = h.hub_c0[hh]; c < h.hub_c0[hh + 1]; ++c) best_merge(best, BestD{h.chunk_bv[c], h.chunk_bk[c]});
+            moved = decide(best, cur, a.pl, cstar);
+        } else {
+            moved = decide(h.hub_best[hh], cur, a.pl, cstar);
+        }
         const unsigned long long D = (unsigned long long)(a.off[v + 1] - a.off[v]);
         n_act += 1;
         n_edges += D;
@@ -376,7 +387,7 @@ __global__ void k_finalize(const GraphDev *gd)
 }
 
 // Initial clear of all hub tables of a graph: `n` slots in the packed or the split layout.
-__global__ void k_table_clear(int32_t *k, float *v, int64_t n, int packed)
+__global__ void k_table_clear(int32_t *k, float *v, double *vd, int64_t n, int packed)
 {
     unsigned long long *h = (unsigned long long *)k;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -384,7 +395,8 @@ __global__ void k_table_clear(int32_t *k, float *v, int64_t n, int packed)
             h[i] = kEmptySlot;
         } else {
             k[i] = kEmpty;
-            v[i] = 0.0f;
+            if (vd) vd[i] = 0.0;
+            else v[i] = 0.0f;
         }
     }
 }
@@ -442,8 +454,9 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
         if (launches) ++*launches;
         return r;
     };
-    e = p.probe == kProbeQuadDouble ? launch_vertex_phase<kProbeQuadDouble>(p, s, hook, launches)
-                                    : launch_vertex_phase_alt(p, s, hook, launches);
+    e = p.f64 ? launch_vertex_phase_f64(p, s, hook, launches)
+              : (p.probe == kProbeQuadDouble ? launch_vertex_phase<kProbeQuadDouble>(p, s, hook, launches)
+                                             : launch_vertex_phase_alt(p, s, hook, launches));
     if (e != cudaSuccess) return e;
     HArgs h{};
     h.gd = p.gd;
@@ -456,8 +469,9 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
-        e = p.probe == kProbeQuadDouble ? launch_hub_acc_phase<kProbeQuadDouble>(p, h, s, hook, launches)
-                                        : launch_hub_acc_phase_alt(p, h, s, hook, launches);
+        e = p.f64 ? launch_hub_acc_phase_f64(p, h, s, hook, launches)
+                  : (p.probe == kProbeQuadDouble ? launch_hub_acc_phase<kProbeQuadDouble>(p, h, s, hook, launches)
+                                                 : launch_hub_acc_phase_alt(p, h, s, hook, launches));
         if (e != cudaSuccess) return e;
         if (p.n_hub_items[HL_SLICES] > 0) {
             h.items = p.hub_items[HL_SLICES];
@@ -508,14 +522,14 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, bool packed, cudaStream_t s)
+cudaError_t launch_hub_table_clear(int32_t *k, float *v, int64_t slots, bool packed, cudaStream_t s, double *vd)
 {
     if (slots <= 0) return cudaSuccess;
     query_device();
     int64_t blocks = (slots + 255) / 256;
     const int64_t cap = (int64_t)g_num_sms * 16;
     if (blocks > cap) blocks = cap;
-    k_table_clear<<<(unsigned)blocks, 256, 0, s>>>(k, v, slots, packed ? 1 : 0);
+    k_table_clear<<<(unsigned)blocks, 256, 0, s>>>(k, v, vd, slots, packed ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,7 @@ __device__ __forceinline__ uint32_t vbits(uint32_t w) { return w; }
 template <typename V> __device__ __forceinline__ V to_value(float w);
 template <> __device__ __forceinline__ float to_value<float>(float w) { return w; }
 template <> __device__ __forceinline__ uint32_t to_value<uint32_t>(float w) { return (uint32_t)w; }
+template <> __device__ __forceinline__ double to_value<double>(float w) { return (double)w; }
 
 template <typename V>
 __device__ __forceinline__ unsigned long long pack_kv(V w, int32_t k)
@@ -83,6 +84,42 @@ __device__ __forceinline__ int32_t unpack_key(unsigned long long p)
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b)
 {
     return a > b ? a : b;
+}
+
+// Running arg-max of a lane (largest sum, smallest label among equal sums).  uint32 and
+// float32 sums: one 64-bit word, pack_kv(sum, label), whose unsigned maximum is the arg-max
+// (0 = none).  float64 sums (lpa_tuning.float_values = 2) do not fit beside a label in 64
+// bits: the pair itself (k < 0 = none).
+struct BestD {
+    double v;
+    int32_t k;
+};
+template <typename V> struct BestOf {
+    using type = unsigned long long;
+};
+template <> struct BestOf<double> {
+    using type = BestD;
+};
+
+__device__ __forceinline__ void best_init(unsigned long long &b) { b = 0ull; }
+__device__ __forceinline__ void best_init(BestD &b)
+{
+    b.v = -1.0;
+    b.k = -1;
+}
+template <typename V>
+__device__ __forceinline__ void best_add(unsigned long long &b, V w, int32_t k) { b = umax64(b, pack_kv(w, k)); }
+__device__ __forceinline__ void best_add(BestD &b, double w, int32_t k)
+{
+    if (w > b.v || (w == b.v && k < b.k)) {
+        b.v = w;
+        b.k = k;
+    }
+}
+__device__ __forceinline__ void best_merge(unsigned long long &b, unsigned long long o) { b = umax64(b, o); }
+__device__ __forceinline__ void best_merge(BestD &b, const BestD &o)
+{
+    if (o.k >= 0) best_add(b, o.v, o.k);
 }
 
 // capacity 2^b - 1 >= x (x >= 1)
@@ -125,8 +162,8 @@ constexpr unsigned long long kEmptySlot = 0xFFFFFFFF00000000ull;   // key -1, su
 // and fold the new sum into `best`.  With TRACK a slot taken from empty is appended to the
 // table's used list.
 template <bool SHARED, bool TRACK, typename V, int PROBE>
-__device__ __forceinline__ bool try_slot(const SplitTable<V, PROBE> &T, size_t s, int32_t k, V v, unsigned long long &best,
-                                         uint32_t *ucnt, int32_t *ulist)
+__device__ __forceinline__ bool try_slot(const SplitTable<V, PROBE> &T, size_t s, int32_t k, V v,
+                                         typename BestOf<V>::type &best, uint32_t *ucnt, int32_t *ulist)
 {
     int32_t *Hk = T.k;
     V *Hv = T.v;
@@ -136,7 +173,7 @@ __device__ __forceinline__ bool try_slot(const SplitTable<V, PROBE> &T, size_t s
             Hk[s] = k;
             const V nv = Hv[s] + v;
             Hv[s] = nv;
-            best = umax64(best, pack_kv(nv, k));
+            best_add(best, nv, k);
             return true;
         }
         return false;
@@ -153,7 +190,7 @@ __device__ __forceinline__ bool try_slot(const SplitTable<V, PROBE> &T, size_t s
     }
     if (kk == k) {
         const V nv = atomicAdd(Hv + s, v) + v;
-        best = umax64(best, pack_kv(nv, k));
+        best_add(best, nv, k);
         return true;
     }
     return false;
@@ -242,7 +279,7 @@ __device__ __forceinline__ uint32_t second_step(uint32_t uk, uint32_t b, uint32_
 
 template <bool SHARED, bool TRACK, typename T>
 __device__ __forceinline__ void ht_accumulate(const T &tab, uint32_t p1, uint32_t b, int32_t k, typename T::Val v,
-                                              unsigned long long &best, unsigned &fallbacks,
+                                              typename BestOf<typename T::Val>::type &best, unsigned &fallbacks,
                                               uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
 {
     const uint32_t uk = (uint32_t)k;
@@ -298,14 +335,28 @@ __device__ __forceinline__ void group_sync()
 template <int G>
 __device__ __forceinline__ unsigned long long group_max(unsigned long long x)
 {
-    if (G == 32) {                  // whole warp: two 32-bit reductions (weight word, then label word)
+    if constexpr (G == 32) {        // whole warp: two 32-bit reductions (weight word, then label word)
         const unsigned hi = (unsigned)(x >> 32);
         const unsigned mh = __reduce_max_sync(0xFFFFFFFFu, hi);
         const unsigned ml = __reduce_max_sync(0xFFFFFFFFu, hi == mh ? (unsigned)x : 0u);
         return ((unsigned long long)mh << 32) | ml;
-    }
+    } else {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) x = umax64(x, __shfl_xor_sync(group_mask<G>(), x, o, G));
+        for (int o = G / 2; o > 0; o >>= 1) x = umax64(x, __shfl_xor_sync(group_mask<G>(), x, o, G));
+        return x;
+    }
+}
+
+template <int G>
+__device__ __forceinline__ BestD group_max(BestD x)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        BestD y;
+        y.v = __shfl_xor_sync(group_mask<G>(), x.v, o, G);
+        y.k = __shfl_xor_sync(group_mask<G>(), x.k, o, G);
+        best_merge(x, y);
+    }
     return x;
 }
 
@@ -319,8 +370,8 @@ constexpr int kPeel = 3;
 
 template <int G, bool SHARED, bool TRACK, typename T>
 __device__ __forceinline__ void group_insert(const T &tab, uint32_t p1, uint32_t b, bool has, int32_t k,
-                                             typename T::Val w, unsigned long long &best, unsigned &fb,
-                                             uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
+                                             typename T::Val w, typename BestOf<typename T::Val>::type &best,
+                                             unsigned &fb, uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
 {
     using V = typename T::Val;
     if (G >= 2) {
@@ -351,12 +402,14 @@ __device__ __forceinline__ void group_insert(const T &tab, uint32_t p1, uint32_t
 template <typename V, int PROBE>
 __device__ __forceinline__ void clear_table_vec(const SplitTable<V, PROBE> &T, uint32_t p1, int first, int step)
 {
-    const uint32_t chunks = (p1 + 4u) >> 2;
+    const uint32_t chunks = (p1 + 4u) >> 2;            // 16-byte chunks of keys (4 slots each)
+    constexpr uint32_t per = sizeof(V) / sizeof(int32_t);   // value chunks per key chunk
     int4 *K4 = reinterpret_cast<int4 *>(T.k);
     int4 *V4 = reinterpret_cast<int4 *>(T.v);
     for (uint32_t q = first; q < chunks; q += step) {
         K4[q] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
-        V4[q] = make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (uint32_t r = 0; r < per; ++r) V4[q * per + r] = make_int4(0, 0, 0, 0);
     }
 }
 
@@ -503,8 +556,9 @@ __device__ __forceinline__ void load_entry(const SweepView &a, int32_t v, int64_
 template <int G, bool SHARED, bool TRACK, int U, bool SEEN, typename T>
 __device__ __forceinline__ void scan_row(const SweepView &a, int32_t v, int64_t start, int64_t end, int step,
                                          int lane, const T &tab, uint32_t p1, uint32_t b,
-                                         unsigned long long &best, unsigned &fb, uint32_t &seen,
-                                         uint32_t *ucnt = nullptr, int32_t *ulist = nullptr, int round = 0)
+                                         typename BestOf<typename T::Val>::type &best, unsigned &fb,
+                                         uint32_t &seen, uint32_t *ucnt = nullptr, int32_t *ulist = nullptr,
+                                         int round = 0)
 {
     using V = typename T::Val;
     const int64_t adv = round ? round : (int64_t)step * U;   // a block-wide round for the CTA kernels
@@ -525,6 +579,13 @@ __device__ __forceinline__ bool decide(unsigned long long best, int32_t cur, int
 {
     if (best == 0) return false;                   // no neighbour label (isolated / self-loops only)
     cstar = unpack_key(best);
+    return (cstar != cur) && (!pl || cstar < cur);
+}
+
+__device__ __forceinline__ bool decide(const BestD &best, int32_t cur, int pl, int32_t &cstar)
+{
+    if (best.k < 0) return false;
+    cstar = best.k;
     return (cstar != cur) && (!pl || cstar < cur);
 }
 
@@ -702,7 +763,8 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                         clear_table_vec(tab, p1, lane, G);
                         group_sync<G>();
                     }
-                    unsigned long long best = 0;
+                    typename BestOf<V>::type best;
+                    best_init(best);
                     int32_t jr[U];                                 // neighbour ids of the first round
 #pragma unroll
                     for (int u = 0; u < U; ++u) jr[u] = -1;
@@ -799,7 +861,9 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
     __shared__ int32_t s_mv[32], s_dec;
     __shared__ int64_t s_mo0[32], s_mo1[32];
     __shared__ int2 s_mov[32];
-    __shared__ unsigned long long s_best[TPB / 32], s_mbase;
+    using Best = typename BestOf<V>::type;
+    __shared__ Best s_best[TPB / 32];
+    __shared__ unsigned long long s_mbase;
     if (threadIdx.x == 0) s_nmov = 0;
     // counters (thread 0) are kept while consecutive items belong to one graph
     int cur_g = -1;
@@ -865,7 +929,8 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
                 __syncthreads();                       // the previous vertex is finished
                 clear_table_vec(tab, p1, threadIdx.x, TPB);
                 __syncthreads();
-                unsigned long long best = 0;
+                Best best;
+                best_init(best);
                 uint32_t seen = 0;
                 constexpr int U = TPB >= 1024 ? 2 : 1;     // loads in flight per thread
                 scan_row<32, true, false, U, PULL>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, tab,
@@ -876,7 +941,9 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
                 if (PULL) act = __syncthreads_or((seen & kMovedBit) != 0) != 0;   // a neighbour moved
                 else __syncthreads();
                 if (threadIdx.x < 32) {                // warp 0 combines the warps and decides
-                    unsigned long long x = threadIdx.x < TPB / 32 ? s_best[threadIdx.x] : 0ull;
+                    Best x;
+                    best_init(x);
+                    if (threadIdx.x < TPB / 32) x = s_best[threadIdx.x];
                     x = group_max<32>(x);
                     if (threadIdx.x == 0) {
                         int32_t c = -1;
@@ -944,16 +1011,19 @@ struct HArgs {
 // Slots taken from empty are collected in a block-local list in shared memory and copied to
 // the hub's used list with one global atomic per block.  A graph with integer sums keeps its
 // hub tables in the packed layout, any other graph in the split float layout.
+// The block's arg-max is folded into hub_best with one atomic maximum (packed word), or, for
+// float64 sums, stored as the chunk's pair and reduced over the hub's chunks by k_hub_move.
 template <int TPB, bool PULL, typename T>
 __device__ __forceinline__ void hub_accumulate(const SweepView &a, const HubArgs &h, int hh, int64_t c, const T &tab,
                                                int32_t *s_list, uint32_t &s_cnt, uint32_t &s_base,
-                                               unsigned long long *s_best)
+                                               typename BestOf<typename T::Val>::type *s_best)
 {
     const int32_t v = h.hub_v[hh];
     const uint32_t p1 = h.hub_p1[hh], b = h.hub_b[hh];
     const int64_t e0 = h.chunk_e0[c], e1 = h.chunk_e1[c];
     unsigned fb = 0;
-    unsigned long long best = 0;
+    typename BestOf<typename T::Val>::type best;
+    best_init(best);
     uint32_t seen = 0;
     scan_row<32, true, true, 2, PULL>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab, p1, b, best,
                                       fb, seen, &s_cnt, s_list, TPB * 2);
@@ -966,8 +1036,13 @@ __device__ __forceinline__ void hub_accumulate(const SweepView &a, const HubArgs
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        for (int w = 1; w < TPB / 32; ++w) best = umax64(best, s_best[w]);
-        if (best) atomicMax(h.hub_best + hh, best);
+        for (int w = 1; w < TPB / 32; ++w) best_merge(best, s_best[w]);
+        if constexpr (std::is_same<typename T::Val, double>::value) {
+            h.chunk_bv[c] = best.v;
+            h.chunk_bk[c] = best.k;
+        } else {
+            if (best) atomicMax(h.hub_best + hh, best);
+        }
         s_base = s_cnt ? atomicAdd(h.hub_used + hh, s_cnt) : 0u;
     }
     __syncthreads();
@@ -975,13 +1050,13 @@ __device__ __forceinline__ void hub_accumulate(const SweepView &a, const HubArgs
     for (uint32_t q = threadIdx.x; q < s_cnt; q += TPB) ulist[q] = s_list[q];
 }
 
-template <int TPB, bool PULL, int PROBE>
+template <int TPB, bool PULL, int PROBE, bool F64>
 __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
 {
     if (*k.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
     int32_t *s_list = (int32_t *)smem;                 // [chunk]
-    __shared__ unsigned long long s_best[TPB / 32];
+    __shared__ typename BestOf<typename std::conditional<F64, double, float>::type>::type s_best[TPB / 32];
     __shared__ uint32_t s_cnt, s_base;
     const WorkItem item = k.items[blockIdx.x];
     const SweepView a = view_of(k.gd, item.g);
@@ -992,7 +1067,10 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
     if (!h.hub_act[hh]) return;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    if (k.gd[item.g].int_weights) {
+    if constexpr (F64) {
+        SplitTable<double, PROBE> tab{h.tab_k + h.hub_tab[hh], h.tab_vd + h.hub_tab[hh], 1, a.probe};
+        hub_accumulate<TPB, PULL>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
+    } else if (k.gd[item.g].int_weights) {
         PackedTable<PROBE> tab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
         hub_accumulate<TPB, PULL>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
     } else {
@@ -1086,10 +1164,12 @@ static void query_device()
 }
 
 
+// Dynamic shared memory beyond the default allowance: the kernels' own static shared memory
+// (at most a few KB) counts against the same 48 KB, hence the margin.
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (bytes <= 40 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -1116,10 +1196,13 @@ static cudaError_t launch_gv(const KArgs &k, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <int G, int TPB, bool PULL, int PROBE>
+// Value type of the tables: double with F64 (lpa_tuning.float_values = 2), else uint32 for
+// integer sums and float for the rest.
+template <int G, int TPB, bool PULL, int PROBE, bool F64>
 static cudaError_t launch_g(const KArgs &k, bool int_w, cudaStream_t s)
 {
-    return int_w ? launch_gv<G, TPB, uint32_t, PULL, PROBE>(k, s) : launch_gv<G, TPB, float, PULL, PROBE>(k, s);
+    if constexpr (F64) return launch_gv<G, TPB, double, PULL, PROBE>(k, s);
+    else return int_w ? launch_gv<G, TPB, uint32_t, PULL, PROBE>(k, s) : launch_gv<G, TPB, float, PULL, PROBE>(k, s);
 }
 
 template <int TPB, typename V, bool PULL, int PROBE>
@@ -1133,22 +1216,29 @@ static cudaError_t launch_cv(const KArgs &k, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <bool PULL, int PROBE>
+template <int TPB, bool PULL, int PROBE, bool F64>
+static cudaError_t launch_cvt(const KArgs &k, bool int_w, cudaStream_t s)
+{
+    if constexpr (F64) return launch_cv<TPB, double, PULL, PROBE>(k, s);
+    else return int_w ? launch_cv<TPB, uint32_t, PULL, PROBE>(k, s) : launch_cv<TPB, float, PULL, PROBE>(k, s);
+}
+
+template <bool PULL, int PROBE, bool F64>
 static cudaError_t launch_cta(const KArgs &k, int threads, bool int_w, cudaStream_t s)
 {
     switch (threads) {
-    case 64: return int_w ? launch_cv<64, uint32_t, PULL, PROBE>(k, s) : launch_cv<64, float, PULL, PROBE>(k, s);
-    case 128: return int_w ? launch_cv<128, uint32_t, PULL, PROBE>(k, s) : launch_cv<128, float, PULL, PROBE>(k, s);
-    case 256: return int_w ? launch_cv<256, uint32_t, PULL, PROBE>(k, s) : launch_cv<256, float, PULL, PROBE>(k, s);
-    case 512: return int_w ? launch_cv<512, uint32_t, PULL, PROBE>(k, s) : launch_cv<512, float, PULL, PROBE>(k, s);
-    case 1024: return int_w ? launch_cv<1024, uint32_t, PULL, PROBE>(k, s) : launch_cv<1024, float, PULL, PROBE>(k, s);
+    case 64: return launch_cvt<64, PULL, PROBE, F64>(k, int_w, s);
+    case 128: return launch_cvt<128, PULL, PROBE, F64>(k, int_w, s);
+    case 256: return launch_cvt<256, PULL, PROBE, F64>(k, int_w, s);
+    case 512: return launch_cvt<512, PULL, PROBE, F64>(k, int_w, s);
+    case 1024: return launch_cvt<1024, PULL, PROBE, F64>(k, int_w, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // The kernel of bucket b for the push (PULL = false) or pull sweeps of the plan's graphs;
 // each instantiation has its own work-queue counter.
-template <bool PULL, int PROBE>
+template <bool PULL, int PROBE, bool F64>
 static cudaError_t launch_vertex(const SweepPlan &p, int b, cudaStream_t s)
 {
     KArgs k{};
@@ -1161,19 +1251,19 @@ static cudaError_t launch_vertex(const SweepPlan &p, int b, cudaStream_t s)
     k.kslot = b;                                       // bucket index == kernel slot
     const bool iw = p.int_weights != 0;
     switch (b) {
-    case B_THREAD: return launch_g<1, 128, PULL, PROBE>(k, iw, s);
+    case B_THREAD: return launch_g<1, 128, PULL, PROBE, F64>(k, iw, s);
     case B_GROUP:
         switch (p.group_lanes) {
-        case 2: return launch_g<2, 256, PULL, PROBE>(k, iw, s);
-        case 4: return launch_g<4, 256, PULL, PROBE>(k, iw, s);
-        case 8: return launch_g<8, 256, PULL, PROBE>(k, iw, s);
-        case 16: return launch_g<16, 256, PULL, PROBE>(k, iw, s);
+        case 2: return launch_g<2, 256, PULL, PROBE, F64>(k, iw, s);
+        case 4: return launch_g<4, 256, PULL, PROBE, F64>(k, iw, s);
+        case 8: return launch_g<8, 256, PULL, PROBE, F64>(k, iw, s);
+        case 16: return launch_g<16, 256, PULL, PROBE, F64>(k, iw, s);
         default: return cudaErrorInvalidValue;
         }
-    case B_WARP: return launch_g<32, 256, PULL, PROBE>(k, iw, s);
-    case B_CTA: return launch_cta<PULL, PROBE>(k, p.cta_threads, iw, s);
-    case B_CTA_LARGE: return launch_cta<PULL, PROBE>(k, p.cta_large_threads, iw, s);
-    case B_CTA_XL: return launch_cta<PULL, PROBE>(k, p.cta_xl_threads, iw, s);
+    case B_WARP: return launch_g<32, 256, PULL, PROBE, F64>(k, iw, s);
+    case B_CTA: return launch_cta<PULL, PROBE, F64>(k, p.cta_threads, iw, s);
+    case B_CTA_LARGE: return launch_cta<PULL, PROBE, F64>(k, p.cta_large_threads, iw, s);
+    case B_CTA_XL: return launch_cta<PULL, PROBE, F64>(k, p.cta_xl_threads, iw, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1211,15 +1301,15 @@ static cudaError_t launch_dsm(int c, const HArgs &h, int32_t n_items, unsigned *
 // The table kernels of one sweep for probe scheme PROBE: every vertex bucket, then (after
 // k_hub_begin, which the caller launches) the hub accumulation in HBM or cluster tables.
 // Push and pull variants as the plan asks; CUDA-event hooks per kernel slot.
-template <int PROBE>
+template <int PROBE, bool F64 = false>
 static cudaError_t launch_vertex_phase(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, int *launches)
 {
     const bool push = p.pull_mode != 1, pull = p.pull_mode != 0;
     for (int b = B_THREAD; b <= B_CTA_XL; ++b) {
         if (p.n_items[b] <= 0) continue;
         if (hook) hook->before(b);
-        cudaError_t r = push ? launch_vertex<false, PROBE>(p, b, s) : cudaSuccess;
-        if (r == cudaSuccess && pull) r = launch_vertex<true, PROBE>(p, b, s);
+        cudaError_t r = push ? launch_vertex<false, PROBE, F64>(p, b, s) : cudaSuccess;
+        if (r == cudaSuccess && pull) r = launch_vertex<true, PROBE, F64>(p, b, s);
         if (hook) hook->after(b);
         if (r != cudaSuccess) return r;
         if (launches) *launches += (push ? 1 : 0) + (pull ? 1 : 0);
@@ -1227,7 +1317,7 @@ static cudaError_t launch_vertex_phase(const SweepPlan &p, cudaStream_t s, Launc
     return cudaSuccess;
 }
 
-template <int PROBE>
+template <int PROBE, bool F64 = false>
 static cudaError_t launch_hub_acc_phase(const SweepPlan &p, const HArgs &h, cudaStream_t s, LaunchHook *hook,
                                         int *launches)
 {
@@ -1239,13 +1329,13 @@ static cudaError_t launch_hub_acc_phase(const SweepPlan &p, const HArgs &h, cuda
         ha.items = p.hub_items[HL_ACC];
         const size_t smem = (size_t)p.hub_chunk * sizeof(int32_t);
         if (push && r == cudaSuccess) {
-            r = set_smem(k_hub_acc<1024, false, PROBE>, smem);
-            if (r == cudaSuccess) k_hub_acc<1024, false, PROBE><<<p.n_hub_items[HL_ACC], 1024, smem, s>>>(ha);
+            r = set_smem(k_hub_acc<1024, false, PROBE, F64>, smem);
+            if (r == cudaSuccess) k_hub_acc<1024, false, PROBE, F64><<<p.n_hub_items[HL_ACC], 1024, smem, s>>>(ha);
             if (launches) ++*launches;
         }
         if (pull && r == cudaSuccess) {
-            r = set_smem(k_hub_acc<1024, true, PROBE>, smem);
-            if (r == cudaSuccess) k_hub_acc<1024, true, PROBE><<<p.n_hub_items[HL_ACC], 1024, smem, s>>>(ha);
+            r = set_smem(k_hub_acc<1024, true, PROBE, F64>, smem);
+            if (r == cudaSuccess) k_hub_acc<1024, true, PROBE, F64><<<p.n_hub_items[HL_ACC], 1024, smem, s>>>(ha);
             if (launches) ++*launches;
         }
     }
@@ -1271,6 +1361,11 @@ static cudaError_t launch_hub_acc_phase(const SweepPlan &p, const HArgs &h, cuda
 cudaError_t sweep_init_constants_alt();
 cudaError_t launch_vertex_phase_alt(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, int *launches);
 cudaError_t launch_hub_acc_phase_alt(const SweepPlan &p, const HArgs &h, cudaStream_t s, LaunchHook *hook,
+                                     int *launches);
+// Defined in lpa_sweep_f64.cu (float64 table values, both probe instantiations).
+cudaError_t sweep_init_constants_f64();
+cudaError_t launch_vertex_phase_f64(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, int *launches);
+cudaError_t launch_hub_acc_phase_f64(const SweepPlan &p, const HArgs &h, cudaStream_t s, LaunchHook *hook,
                                      int *launches);
 
 }  // namespace lpa

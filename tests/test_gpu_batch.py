@@ -89,6 +89,18 @@ def test_batch_cluster_hub_tables(lpa):
         assert results[i]["iterations"] == ref.iterations
 
 
+def test_batch_float64_values(lpa):
+    """Float64 table values in a batch: hubs with HBM tables beside graphs without hubs."""
+    graphs = [gg.star(20_000), gg.rmat(13, weights="int8")] + mixed_graphs(8, count=5, with_hub=False)
+    b = lpa.Batch([as_tuple(g) for g in graphs])
+    b.set_tuning(float_values=2, cta_xl_max=1023, cta_large_max=1023)
+    results, _ = b.run(0.05, 20, 4, lpa.SYNC)
+    for i, g in enumerate(graphs):
+        ref = oracle.lpa_sync(oracle.Graph.of(g), 0.05, 20, 4)
+        assert b.labels(i).cpu().numpy().tolist() == ref.labels.tolist(), f"graph {i}"
+        assert results[i]["iterations"] == ref.iterations
+
+
 def test_batch_modularity_and_other_parameters(lpa):
     graphs = mixed_graphs(2, count=12, with_hub=False)
     b = lpa.Batch([as_tuple(g) for g in graphs])

@@ -122,12 +122,17 @@ def test_sync_probe_schemes(lpa, probe):
         check_sync_every_iteration(lpa, csr, 0.05, 20, 4, tuning)
 
 
-@pytest.mark.parametrize("scale,tuning", [(13, "float"), (14, "float-small")])
+@pytest.mark.parametrize("scale,tuning", [(13, "float"), (14, "float-small"), (13, "double"), (14, "double-small"),
+                                          (12, "double-paper"), (13, "double-linear")])
 def test_sync_float_label_sums(lpa, scale, tuning):
-    """Integer-weight graphs forced onto the float32 label-sum kernels."""
+    """Integer-weight graphs forced onto the float32 or float64 label-sum kernels (Section
+    4.4's value types); with small buckets the rows above 127 entries are hubs with HBM tables
+    (float64 values: per-chunk arg-max pairs)."""
     csr = gg.rmat(scale, weights="int8")
-    t = dict(float_values=1) if tuning == "float" else dict(SMALL_BUCKETS, float_values=1)
-    check_sync_every_iteration(lpa, csr, 0.05, 20, 4, t)
+    fv = 1 if tuning.startswith("float") else 2
+    t = {"float": {}, "float-small": SMALL_BUCKETS, "double": {}, "double-small": SMALL_BUCKETS,
+         "double-paper": PAPER_TABLES, "double-linear": dict(SMALL_BUCKETS, probe=1)}[tuning]
+    check_sync_every_iteration(lpa, csr, 0.05, 20, 4, dict(t, float_values=fv))
 
 
 def dyadic(csr, seed):
@@ -148,6 +153,13 @@ def test_sync_non_integer_weights(lpa, seed):
     g, ref = check_sync_every_iteration(lpa, csr, 0.05, 20, 4, SMALL_BUCKETS if seed == 1 else None)
     q = g.modularity()                                  # float64 path (weights not integers)
     assert abs(q - oracle.modularity(oracle_graph(csr), ref.labels)) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_sync_non_integer_weights_float64_values(lpa, seed):
+    csr = dyadic(gg.rmat(12 + seed, weights="unit"), seed)
+    t = dict(SMALL_BUCKETS, float_values=2) if seed == 1 else dict(float_values=2)
+    check_sync_every_iteration(lpa, csr, 0.05, 20, 4, t)
 
 
 def test_sync_sbm_config(lpa):
