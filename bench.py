@@ -57,12 +57,12 @@ BYTES_PER_VERTEX = 17      # offsets 2x4 (amortised) + own label 4 + label write
 # on the default workload (profiles/hub_acc_rmat26_dram.md: mean of the four hub-accumulate
 # launches of one run).  Reported while the sweep sources hash as they did at capture time.
 TRAFFIC = {
-    "kernel": "hub_acc", "workload": "rmat26", "bytes_per_launch": 11.888e9,
+    "kernel": "hub_acc", "workload": "rmat26", "bytes_per_launch": 11.889e9,
     "sources": {
-        "sweep_kernels.cuh": "370553a2339b1f9520042fc823017f9b117b9ca380c909e73bfcd3dee0fb1e64",
-        "lpa_sweep.cu": "b258eb6309abbb1ebfbb02c09f0abae54229d2143dc67bebe116b5c38daee45d",
-        "lpa_internal.h": "996792bd64dcb4cd653bc40a8a9eef0646c85b4f425476f3da89136918969fd8",
-        "lpa_graph.cu": "5051321e543232447e868b05d78cdf04177b7de703077ab18074a1f48f8cdbc0",
+        "sweep_kernels.cuh": "bb1e3a4f17ca7a0d7563b7dc45cdea595ae675b600c392283451a9ff6d07baf7",
+        "lpa_sweep.cu": "c56f7b1dab01bfda7178475a2ef3e657b6b22c1064b6c79bd059a0cbdd94f710",
+        "lpa_internal.h": "9d205a69fd4a3e0c95545856e8d398b9e0d6e078554f05c87780059ad362406e",
+        "lpa_graph.cu": "fe05abc931c4e147f686a4faf0d2927afeb1b1c4b79b8b2db1d4b563ef06391e",
     },
 }
 

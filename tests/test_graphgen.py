@@ -1,4 +1,6 @@
-"""Input generators: counter-based hashing, CSR validity, symmetry, shapes (no GPU)."""
+"""Input generators: counter-based hashing, CSR validity, symmetry, shapes; the GPU-marked
+tests check that CPU and GPU generation agree."""
+import pytest
 import torch
 
 from paper_2411_11468_gb300 import graphgen as gg
@@ -76,3 +78,21 @@ def test_fixtures():
     assert g.m == 18
     s = gg.star(4)
     assert s.degrees().tolist() == [4, 1, 1, 1, 1]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("scale,weights", [(12, "int8"), (14, "unit"), (16, "int8")])
+def test_rmat_cpu_and_gpu_generation_agree(scale, weights):
+    """The large R-MAT workloads are generated on the GPU; the CPU generator (which the oracle
+    tests use) gives the same CSR at small scales."""
+    a = gg.rmat(scale, weights=weights, device="cpu")
+    b = gg.rmat(scale, weights=weights, device="cuda").to("cpu")
+    assert torch.equal(a.offsets, b.offsets) and torch.equal(a.indices, b.indices)
+    assert torch.equal(a.weights, b.weights)
+
+
+@pytest.mark.gpu
+def test_sbm_cpu_and_gpu_generation_agree():
+    a = gg.sbm(10_000, 100, 16.0, 2.0, seed=0, device="cpu")
+    b = gg.sbm(10_000, 100, 16.0, 2.0, seed=0, device="cuda").to("cpu")
+    assert torch.equal(a.offsets, b.offsets) and torch.equal(a.indices, b.indices)
