@@ -662,15 +662,16 @@ __device__ __forceinline__ void warp_flush(const SweepView &a, int kslot, unsign
     }
 }
 
-// Entries loaded per lane and round by the G-lane kernels: enough that one round covers the
-// default degree range of each bucket (G = 1: D <= 8, G = 8: D <= 32, G = 32: D <= 256), so
-// a row's index, weight and label loads are all in flight together.
+// Entries loaded per lane and round by the G-lane kernels: for G = 1 and G = 8 enough that one
+// round covers the default degree range of the bucket (D <= 8, D <= 32), so a row's index,
+// weight and label loads are all in flight together; for G = 32 two (64 entries a round),
+// which with four resident blocks per SM measured faster than four entries with three blocks.
 constexpr int kUnrollThread = 2;      // G = 1
 constexpr int kUnrollSmall = 4;       // G = 2, 4
 constexpr int kUnrollGroup = 2;       // G = 8, 16
-constexpr int kUnrollWarp = 4;        // G = 32
-constexpr int kMinBlocksThread = 6;   // resident blocks per SM asked of the register allocator (128 threads)
-constexpr int kMinBlocks = 3;         // (256 threads)
+constexpr int kUnrollWarp = 2;        // G = 32
+constexpr int kMinBlocksThread = 8;   // resident blocks per SM asked of the register allocator (128 threads)
+constexpr int kMinBlocks = 4;         // (256 threads)
 template <int G> struct GroupUnroll {
     static constexpr int U = G == 1 ? kUnrollThread : (G <= 4 ? kUnrollSmall : (G <= 16 ? kUnrollGroup : kUnrollWarp));
     static constexpr int kMinBlocks = G == 1 ? ::lpa::kMinBlocksThread : ::lpa::kMinBlocks;
