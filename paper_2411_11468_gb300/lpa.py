@@ -96,6 +96,15 @@ class Tuning(ct.Structure):
     def to_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
+    def update(self, **kw) -> "Tuning":
+        """Sets the named fields (an unknown name raises KeyError instead of being ignored)."""
+        names = {f for f, _ in self._fields_ if f != "reserved"}
+        for k, v in kw.items():
+            if k not in names:
+                raise KeyError(f"lpa_tuning has no field {k!r}")
+            setattr(self, k, int(v))
+        return self
+
 
 _lib = None
 
@@ -276,8 +285,7 @@ class Graph:
     def set_tuning(self, t: Tuning | None = None, **kw):
         if t is None:
             t = self.tuning()
-        for k, v in kw.items():
-            setattr(t, k, int(v))
+        t.update(**kw)
         _check(load().lpa_set_tuning(self._h, ct.byref(t)), "lpa_set_tuning")
 
     def autotune(self, tolerance=0.05, max_iters=20, pl_period=4, mode=SYNC, reps=2):
@@ -441,8 +449,7 @@ class Batch:
     def set_tuning(self, t: Tuning | None = None, **kw):
         if t is None:
             t = self.tuning()
-        for k, v in kw.items():
-            setattr(t, k, int(v))
+        t.update(**kw)
         _check(_load_multi().lpa_batch_set_tuning(self._h, ct.byref(t)), "lpa_batch_set_tuning")
 
     def autotune(self, tolerance=0.05, max_iters=20, pl_period=4, mode=SYNC, reps=2):

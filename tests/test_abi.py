@@ -52,3 +52,13 @@ def test_strerror_without_gpu(lib):
     assert lib.lpa_strerror(-1) == b"invalid argument"
     lib.lpa_kernel_name.restype = ct.c_char_p
     assert lib.lpa_kernel_name(2) == b"warp"
+
+
+def test_tuning_fields_are_checked_by_name():
+    from paper_2411_11468_gb300 import lpa
+    t = lpa.Tuning().update(float_values=2, hub_chunk=4096)
+    assert t.float_values == 2 and t.hub_chunk == 4096
+    with pytest.raises(KeyError):
+        t.update(float_value=2)          # a misspelt field is an error, not a no-op
+    with pytest.raises(KeyError):
+        t.update(reserved=1)
