@@ -59,7 +59,7 @@ BYTES_PER_VERTEX = 17      # offsets 2x4 (amortised) + own label 4 + label write
 TRAFFIC = {
     "kernel": "hub_acc", "workload": "rmat26", "bytes_per_launch": 11.889e9,
     "sources": {
-        "sweep_kernels.cuh": "e07dc7657e68f4589be015b976f5cc3299a8b085e31460ba346014a3b5df67b7",
+        "sweep_kernels.cuh": "00243f705dafa377d69aacb39e4ecffbc1c40fc0bc3d19ac08111c802fd8be6b",
         "lpa_sweep.cu": "c56f7b1dab01bfda7178475a2ef3e657b6b22c1064b6c79bd059a0cbdd94f710",
         "lpa_internal.h": "9d205a69fd4a3e0c95545856e8d398b9e0d6e078554f05c87780059ad362406e",
         "lpa_graph.cu": "fe05abc931c4e147f686a4faf0d2927afeb1b1c4b79b8b2db1d4b563ef06391e",

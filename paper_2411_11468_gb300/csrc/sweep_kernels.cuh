@@ -147,7 +147,11 @@ struct SplitTable {
     int probe = kProbeQuadDouble;
 };
 
-template <int PROBE>
+// READ_FIRST: a slot is read before it is updated (HBM hub tables: after the first sweep most
+// labels are present, and a read plus an add is cheaper than a compare-and-swap that fails on
+// a contended line); otherwise (shared memory) the compare-and-swap comes first and the read
+// is saved when the slot is empty.
+template <int PROBE, bool READ_FIRST = false>
 struct PackedTable {
     using Val = uint32_t;
     static constexpr int kProbe = PROBE;
@@ -197,12 +201,12 @@ __device__ __forceinline__ bool try_slot(const SplitTable<V, PROBE> &T, size_t s
 }
 
 // Shared (atomic) update of one packed slot at p (slot index s for the used list).
-template <bool TRACK>
+template <bool TRACK, bool READ_FIRST>
 __device__ __forceinline__ bool packed_update(unsigned long long *p, size_t s, int32_t k, uint32_t v,
                                               unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
 {
     const uint32_t uk = (uint32_t)k;
-    uint32_t ck = (uint32_t)(*((volatile unsigned long long *)p) >> 32);
+    uint32_t ck = READ_FIRST ? (uint32_t)(*((volatile unsigned long long *)p) >> 32) : 0xFFFFFFFFu;
     if (ck == 0xFFFFFFFFu) {
         const unsigned long long old = atomicCAS(p, kEmptySlot, ((unsigned long long)uk << 32) | v);
         if (old == kEmptySlot) {
@@ -223,8 +227,8 @@ __device__ __forceinline__ bool packed_update(unsigned long long *p, size_t s, i
     return false;
 }
 
-template <bool SHARED, bool TRACK, int PROBE>
-__device__ __forceinline__ bool try_slot(const PackedTable<PROBE> &T, size_t s, int32_t k, uint32_t v,
+template <bool SHARED, bool TRACK, int PROBE, bool READ_FIRST>
+__device__ __forceinline__ bool try_slot(const PackedTable<PROBE, READ_FIRST> &T, size_t s, int32_t k, uint32_t v,
                                          unsigned long long &best, uint32_t *ucnt, int32_t *ulist)
 {
     unsigned long long *p = T.h + s;
@@ -240,7 +244,7 @@ __device__ __forceinline__ bool try_slot(const PackedTable<PROBE> &T, size_t s, 
         }
         return false;
     }
-    return packed_update<TRACK>(p, s, k, v, best, ucnt, ulist);
+    return packed_update<TRACK, READ_FIRST>(p, s, k, v, best, ucnt, ulist);
 }
 
 // A hub table spread over the shared memory of the blocks of a thread-block cluster (packed
@@ -262,7 +266,7 @@ __device__ __forceinline__ bool try_slot(const ClusterTable<PROBE> &T, size_t s,
 {
     unsigned long long *p = cg::this_cluster().map_shared_rank(T.base, (unsigned)(s >> T.lb)) +
                             (s & (((size_t)1 << T.lb) - 1));
-    return packed_update<TRACK>(p, s, k, v, best, ucnt, ulist);
+    return packed_update<TRACK, true>(p, s, k, v, best, ucnt, ulist);
 }
 
 // hashtableAccumulate (Algorithm 2) with i and delta kept reduced mod p1 (same slots),
@@ -1072,7 +1076,7 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
         SplitTable<double, PROBE> tab{h.tab_k + h.hub_tab[hh], h.tab_vd + h.hub_tab[hh], 1, a.probe};
         hub_accumulate<TPB, PULL>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
     } else if (k.gd[item.g].int_weights) {
-        PackedTable<PROBE> tab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
+        PackedTable<PROBE, true> tab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
         hub_accumulate<TPB, PULL>(a, h, hh, c, tab, s_list, s_cnt, s_base, s_best);
     } else {
         SplitTable<float, PROBE> tab{h.tab_k + h.hub_tab[hh], h.tab_v + h.hub_tab[hh], 1, a.probe};
