@@ -36,7 +36,7 @@ def _rank(rank, world, port, out):
 def test_replicas_reduce_time_by_max_and_work_by_sum():
     world = 2
     port = _free_port()
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
     for rank in range(world):
         ms, work, ws, r = out[rank]
