@@ -507,3 +507,22 @@ def test_resume_from_checkpoint(lpa):
     # the oracle agrees with the resumed state as well
     ref = oracle.lpa_sync(oracle_graph(csr), 0.0, 15, 4, labels=C, active=A, start_iter=it)
     assert fresh.labels().cpu().numpy().tolist() == ref.labels.tolist()
+
+
+def test_tolerance_boundary_matches_oracle(lpa):
+    """The device-side stop test (k_decide) is strict and in double like the oracle's: at a
+    tolerance equal to a non-Pick-Less sweep's dN / N the run goes on, at the next double it
+    stops there; a Pick-Less sweep never stops it."""
+    csr = gg.rmat(11, weights="int8")
+    og = oracle_graph(csr)
+    n, pl = og.n, 4
+    base = oracle.lpa_sync(og, 0.0, 20, pl)
+    ratios = [(l, base.dN[l] / n) for l in range(base.iterations) if l % pl != 0]
+    k = next(l for i, (l, r) in enumerate(ratios) if i > 0 and 0 < r < min(x for _, x in ratios[:i]))
+    tau = base.dN[k] / n
+    g = make(lpa, csr)
+    for tol in (tau, float(np.nextafter(tau, 1.0)), 1.0):
+        ref = oracle.lpa_sync(og, tol, 20, pl)
+        st = g.run(tol, 20, pl, lpa.SYNC)
+        assert st.iterations == ref.iterations and st.dN() == ref.dN and bool(st.converged) == ref.converged
+        assert g.labels().cpu().numpy().tolist() == ref.labels.tolist()

@@ -557,3 +557,25 @@ def test_sync_cross_check_matches_dense_restatement(seed):
     assert r.dN == dns and r.labels.tolist() == per_iter[-1]
     for t in range(1, len(per_iter) + 1):
         assert oracle.lpa_sync(g, 0.05, t, pl, cc_period=cc).labels.tolist() == per_iter[t - 1]
+
+
+def test_tolerance_test_is_strict_and_skips_pick_less_sweeps():
+    """Algorithm 1 stops after a non-Pick-Less sweep l with dN_l / N < tolerance (strictly, in
+    double): a tolerance equal to a sweep's ratio does not stop at that sweep, the next double
+    above it does, and a Pick-Less sweep never stops the loop."""
+    g = G(gg.rmat(11, weights="int8"))
+    n, pl = g.n, 4
+    base = oracle.lpa_sync(g, 0.0, 20, pl)             # tolerance 0: only the cap stops it
+    ratios = [(l, base.dN[l] / n) for l in range(base.iterations) if l % pl != 0]
+    k = next(l for i, (l, r) in enumerate(ratios) if i > 0 and 0 < r < min(x for _, x in ratios[:i]))
+    tau = base.dN[k] / n
+    eq = oracle.lpa_sync(g, tau, 20, pl)
+    up = oracle.lpa_sync(g, float(np.nextafter(tau, 1.0)), 20, pl)
+    assert eq.converged and eq.iterations > k + 1 and eq.dN == base.dN[:eq.iterations]
+    assert up.converged and up.iterations == k + 1 and up.dN == base.dN[:k + 1]
+    big = oracle.lpa_sync(g, 1.0, 20, pl)              # sweep 0 is Pick-Less: only sweep 1 stops
+    assert big.converged and big.iterations == 2
+    assert oracle.lpa_sync(g, 1.0, 20, 0).iterations == 1
+    for tol, its in ((tau, eq.iterations), (float(np.nextafter(tau, 1.0)), k + 1)):
+        mc = oracle.multicore_lpa_sync(g, tol, 20, pl)
+        assert mc.iterations == its and mc.dN == base.dN[:its]
