@@ -17,7 +17,9 @@
  * Vertex ids and labels are int32; weights and label sums are float32 (the
  * paper's Configuration paragraph); when every weight is an integer and every weighted
  * degree is below 2^24 the label sums are kept as uint32, which gives the same sums and
- * the same winners.  Modularity (Eq. 1) is exact for integer weights, else float64.
+ * the same winners (lpa_tuning.float_values selects float32 or float64 sums instead;
+ * weights that are all exactly 1 are taken as unit weights).  Modularity (Eq. 1) is exact
+ * for integer weights, else float64.
  *
  * Conventions for every call:
  *  - Status: every call returns LPA_OK (0) or a negative LPA_E* code; lpa_strerror()
@@ -49,7 +51,8 @@ extern "C" {
 #define LPA_EINVAL   (-1)   /* invalid argument or invalid graph                      */
 #define LPA_ENOMEM   (-2)   /* device or pinned host allocation failed                */
 #define LPA_ECUDA    (-3)   /* a CUDA runtime call or kernel launch failed            */
-#define LPA_ETIMEOUT (-4)   /* a bounded device wait gave up (status word set)        */
+#define LPA_ETIMEOUT (-4)   /* a bounded device wait gave up (reserved: no kernel of
+                               this version waits on another, so no call returns it)   */
 #define LPA_ESTATE   (-5)   /* call not valid in the handle's current state           */
 #define LPA_ECANCELED (-6)  /* server request cancelled (lpa_server_cancel)           */
 
