@@ -7,6 +7,8 @@ C11, built with gcc by `build()`); this module only marshals numpy arrays.
 
 Functions and the passages they follow:
   lpa_sync / lpa_async  -- Algorithm 1 (lpa, lpaMove), Eq. 3, Section 4 items (1)-(5)
+  lpa_async_waves       -- the asynchronous mode under a schedule of parallel waves (a
+                           reading of Section 4 item 1): between lpa_async and lpa_sync
   cross_check           -- Section 4.1's Cross-Check (reverts of bad moves), in id order
   label_weights         -- Preliminaries, K_{i->c}, by sort-and-count
   ht_build / ht_probe_slot / ht_capacity -- Section 4.2 per-vertex hashtable, Algorithm 2
@@ -67,6 +69,8 @@ def lib():
         L.orc_cross_check.restype = i64
         L.orc_lpa_async.argtypes = L.orc_lpa_sync.argtypes
         L.orc_lpa_async.restype = ct.c_int
+        L.orc_lpa_async_waves.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, P, i32, P, P, P, P, P]
+        L.orc_lpa_async_waves.restype = ct.c_int
         L.orc_sweep_range.argtypes = [i64, P, P, P, ct.c_int, i64, i64, P, P]
         L.orc_sweep_range.restype = i64
         L.orc_sweep_window.argtypes = [i64, i64, P, P, P, P, ct.c_int, P]
@@ -166,6 +170,29 @@ def cross_check(labels, prev):
 def lpa_async(g: Graph, tol=0.05, max_iters=20, pl_period=4, labels=None, active=None, start_iter=0):
     """Asynchronous in-place LPA, vertices visited in order 0..n-1 (Section 4 item 1)."""
     return _run(lib().orc_lpa_async, g, tol, max_iters, pl_period, labels, active, start_iter)
+
+
+def lpa_async_waves(g: Graph, wave_of, tol=0.05, max_iters=20, pl_period=4, labels=None, active=None,
+                    start_iter=0):
+    """Asynchronous LPA under a wave schedule: each sweep runs the waves 0, 1, ... in turn
+    (vertex i in wave wave_of[i]); a wave reads the labels and flags as they stand at its
+    start and its moves and marks land at its end.  One vertex per wave in id order is
+    lpa_async; a single wave is lpa_sync."""
+    W = _np(wave_of, np.int32)
+    if W.size != g.n:
+        raise ValueError("wave_of needs one entry per vertex")
+    n_waves = int(W.max()) + 1 if W.size else 1
+    L = lib()
+    out = _run(lambda n, o, i, w, t, m, p, s, *rest: _waves_rc(L.orc_lpa_async_waves(n, o, i, w, t, m, p, s, _p(W),
+                                                                                       n_waves, *rest)),
+               g, tol, max_iters, pl_period, labels, active, start_iter)
+    return out
+
+
+def _waves_rc(rc):
+    if rc == -2:
+        raise ValueError("wave index outside [0, n_waves)")
+    return rc
 
 
 _mc = None

@@ -252,6 +252,91 @@ int orc_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, const float
     return 0;
 }
 
+/* Asynchronous LPA under a wave schedule: a reading of Section 4 item 1 for a sweep that
+ * many threads run at once.  Each sweep visits the waves 0, 1, ..., n_waves - 1 in turn;
+ * vertex i belongs to wave wave_of[i].  Within a wave every flagged vertex is marked
+ * processed and computes c* from the labels as they stand when the wave starts (no
+ * vertex of the wave sees another's move); the moves of the wave and the neighbour marks
+ * of its movers take effect when the wave ends, before the next wave starts.  So a
+ * schedule of one vertex per wave in id order is orc_lpa_async, and one wave holding every
+ * vertex is orc_lpa_sync; a parallel sweep sits between the two.  Pick-Less and the stop
+ * rule are those of Algorithm 1.  Returns 0, -1 on allocation failure, -2 for a wave
+ * index outside [0, n_waves). */
+int orc_lpa_async_waves(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                        double tol, int max_iters, int pl_period, int start_iter,
+                        const int32_t *wave_of, int32_t n_waves,
+                        int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged)
+{
+    *converged = 0;
+    *iters = start_iter;
+    if (n <= 0) return 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (wave_of[i] < 0 || wave_of[i] >= n_waves) return -2;
+    /* members of each wave, ascending ids (counting sort by wave) */
+    int64_t *first = (int64_t *)calloc((size_t)n_waves + 1, sizeof(int64_t));
+    int64_t *member = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int32_t *newc = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    orc_work wk;
+    if (!first || !member || !newc || orc_work_alloc(&wk, orc_max_degree(n, off)) != 0) {
+        free(first);
+        free(member);
+        free(newc);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i) ++first[wave_of[i] + 1];
+    for (int32_t q = 0; q < n_waves; ++q) first[q + 1] += first[q];
+    {
+        int64_t *fill = (int64_t *)malloc((size_t)n_waves * sizeof(int64_t));
+        if (!fill) {
+            free(first);
+            free(member);
+            free(newc);
+            orc_work_free(&wk);
+            return -1;
+        }
+        memcpy(fill, first, (size_t)n_waves * sizeof(int64_t));
+        for (int64_t i = 0; i < n; ++i) member[fill[wave_of[i]]++] = i;
+        free(fill);
+    }
+    for (int l = start_iter; l < max_iters; ++l) {
+        int pl = (pl_period > 0) && (l % pl_period == 0);
+        int64_t changed = 0;
+        for (int32_t q = 0; q < n_waves; ++q) {
+            /* the wave reads: flags taken and c* computed on the labels at its start */
+            for (int64_t r = first[q]; r < first[q + 1]; ++r) {
+                const int64_t i = member[r];
+                newc[i] = -1;
+                if (!active[i]) continue;
+                active[i] = 0;                              /* mark processed */
+                newc[i] = orc_best_label(i, off, idx, w, C, wk.lab, wk.sum, wk.scratch);
+            }
+            /* the wave writes: moves and neighbour marks */
+            for (int64_t r = first[q]; r < first[q + 1]; ++r) {
+                const int64_t i = member[r];
+                const int32_t c = newc[i];
+                if (c < 0) continue;
+                const int32_t cur = C[i];
+                if (c != cur && (!pl || c < cur)) {
+                    C[i] = c;
+                    ++changed;
+                    for (int64_t e = off[i]; e < off[i + 1]; ++e) active[idx[e]] = 1;
+                }
+            }
+        }
+        dN[l] = changed;
+        *iters = l + 1;
+        if (!pl && (double)changed / (double)n < tol) {
+            *converged = 1;
+            break;
+        }
+    }
+    free(first);
+    free(member);
+    free(newc);
+    orc_work_free(&wk);
+    return 0;
+}
+
 /* One synchronous sweep over vertices [v0, v1) only, with all of them active and the
  * given frozen labels C (all n labels): the per-vertex step of Algorithm 1 (lpaMove) on a
  * bounded sample.  The rows come as a window: off_w[k] - off_w[0] is where row v0+k starts

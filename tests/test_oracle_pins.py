@@ -579,3 +579,101 @@ def test_tolerance_test_is_strict_and_skips_pick_less_sweeps():
     for tol, its in ((tau, eq.iterations), (float(np.nextafter(tau, 1.0)), k + 1)):
         mc = oracle.multicore_lpa_sync(g, tol, 20, pl)
         assert mc.iterations == its and mc.dN == base.dN[:its]
+
+
+# --------------------------------------------------------------------------------------
+# the asynchronous mode under a wave schedule (a reading of Section 4 item 1 for a parallel
+# sweep: each wave reads the state at its start, its moves and marks land at its end)
+
+def _dense_waves(W, wave_of, tol, max_iters, pl_period):
+    """Dense restatement: per sweep, per wave in increasing index, take the flagged members,
+    clear their flags, decide each on the labels frozen at the wave's start, then apply."""
+    n = W.shape[0]
+    C = list(range(n))
+    act = [True] * n
+    dns = []
+    waves = sorted(set(wave_of))
+    for l in range(max_iters):
+        pl = pl_period > 0 and l % pl_period == 0
+        ch = 0
+        for q in waves:
+            frozen = list(C)
+            members = [i for i in range(n) if wave_of[i] == q and act[i]]
+            for i in members:
+                act[i] = False
+            moves = []
+            for i in members:
+                c = _best_dense(W, frozen, i)
+                if c is not None and c != frozen[i] and (not pl or c < frozen[i]):
+                    moves.append((i, c))
+            for i, c in moves:
+                C[i] = c
+                ch += 1
+                for j in np.nonzero(W[i])[0]:
+                    act[j] = True
+        dns.append(ch)
+        if not pl and ch / n < tol:
+            break
+    return dns, C, act
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_async_waves_match_dense_restatement(seed):
+    rnd = random.Random(700 + seed)
+    n = rnd.randint(5, 64)
+    g = G(gg.random_small(n, rnd.choice([0.05, 0.15, 0.3]), 900 + seed, wmax=rnd.choice([1, 8]),
+                          self_loops=(seed % 3 == 0)))
+    W = _dense(g)
+    n_waves = rnd.choice([1, 2, 3, 7, n])
+    wave_of = [rnd.randrange(n_waves) for _ in range(n)]
+    wave_of[0] = n_waves - 1                      # every index below the largest is allowed to stay empty
+    tol, mi, pl = rnd.choice([0.0, 0.05]), rnd.choice([5, 20]), rnd.choice([0, 2, 4])
+    dns, C, act = _dense_waves(W, wave_of, tol, mi, pl)
+    r = oracle.lpa_async_waves(g, wave_of, tol, mi, pl)
+    assert r.dN == dns
+    assert r.labels.tolist() == C
+    assert r.active.astype(bool).tolist() == act
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_async_waves_endpoints(seed):
+    """One vertex per wave in id order is the sequential asynchronous run; one wave holding
+    every vertex is the synchronous run (labels, dN, flags, stop)."""
+    rnd = random.Random(800 + seed)
+    csr = [gg.sbm(500, 25, 8, 2, seed=seed, weights="int8"), gg.rmat(9, weights="int8"),
+           gg.two_cliques_bridge(6), gg.complete_bipartite(5), gg.star(9),
+           gg.random_small(200, 0.05, seed, self_loops=True)][seed]
+    g = G(csr)
+    pl = rnd.choice([0, 4])
+    a = oracle.lpa_async(g, 0.05, 20, pl)
+    w1 = oracle.lpa_async_waves(g, np.arange(g.n), 0.05, 20, pl)
+    assert (a.dN, a.labels.tolist(), a.active.tolist(), a.iterations, a.converged) == \
+        (w1.dN, w1.labels.tolist(), w1.active.tolist(), w1.iterations, w1.converged)
+    s = oracle.lpa_sync(g, 0.05, 20, pl)
+    w0 = oracle.lpa_async_waves(g, np.zeros(g.n, np.int32), 0.05, 20, pl)
+    assert (s.dN, s.labels.tolist(), s.active.tolist(), s.iterations, s.converged) == \
+        (w0.dN, w0.labels.tolist(), w0.active.tolist(), w0.iterations, w0.converged)
+
+
+def test_async_waves_bipartite_by_hand():
+    """K_{n,n}, A = 0..n-1 in wave 0 and B = n..2n-1 in wave 1, no Pick-Less.  Sweep 0:
+    wave A sees only B labels, each once, and takes the smallest, n (all n move); wave B then
+    sees label n on all of A and takes it, except vertex n, which holds n already: dN =
+    2n - 1.  Sweep 1 (every vertex marked by a mover of the other side): every vertex sees
+    only label n, its own: dN = 0 < tolerance, stop.  All labels n, Q = 0.  (The synchronous
+    run swaps A and B at every sweep.)"""
+    n = 5
+    g = G(gg.complete_bipartite(n))
+    r = oracle.lpa_async_waves(g, [0] * n + [1] * n, 0.05, 20, 0)
+    assert r.dN == [2 * n - 1, 0]
+    assert r.labels.tolist() == [n] * (2 * n)
+    assert r.converged
+    assert oracle.modularity(g, r.labels) == 0.0
+    s = oracle.lpa_sync(g, 0.05, 20, 0)
+    assert s.dN == [2 * n] * 20
+
+
+def test_async_waves_rejects_bad_wave_index():
+    g = G(gg.star(4))
+    with pytest.raises(ValueError):
+        oracle.lpa_async_waves(g, [0, 1, -1, 0, 0])
