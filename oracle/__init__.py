@@ -61,15 +61,15 @@ def lib():
         L = ct.CDLL(_LIB)
         P = ct.c_void_p
         i64, i32, u32, dbl = ct.c_int64, ct.c_int32, ct.c_uint32, ct.c_double
-        L.orc_lpa_sync.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P]
+        L.orc_lpa_sync.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P]
         L.orc_lpa_sync.restype = ct.c_int
-        L.orc_lpa_sync_cc.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P]
+        L.orc_lpa_sync_cc.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P]
         L.orc_lpa_sync_cc.restype = ct.c_int
         L.orc_cross_check.argtypes = [i64, P, P]
         L.orc_cross_check.restype = i64
         L.orc_lpa_async.argtypes = L.orc_lpa_sync.argtypes
         L.orc_lpa_async.restype = ct.c_int
-        L.orc_lpa_async_waves.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, P, i32, P, P, P, P, P]
+        L.orc_lpa_async_waves.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, P, i32, P, P, P, P, P, P]
         L.orc_lpa_async_waves.restype = ct.c_int
         L.orc_sweep_range.argtypes = [i64, P, P, P, ct.c_int, i64, i64, P, P]
         L.orc_sweep_range.restype = i64
@@ -130,6 +130,7 @@ class RunResult:
     dN: list
     iterations: int
     converged: bool
+    edges: list = None       # CSR entries of the vertices each sweep processed
 
 
 def _run(fn, g: Graph, tol, max_iters, pl_period, labels=None, active=None, start_iter=0):
@@ -139,12 +140,14 @@ def _run(fn, g: Graph, tol, max_iters, pl_period, labels=None, active=None, star
     dN = np.zeros(max(max_iters, 1), dtype=np.int64)
     it = np.zeros(1, np.int32)
     cv = np.zeros(1, np.int32)
+    E = np.zeros(max(max_iters, 1), dtype=np.int64)
     rc = fn(n, _p(g.off), _p(g.idx), _p(g.w), float(tol), int(max_iters), int(pl_period),
-            int(start_iter), _p(C), _p(A), _p(dN), _p(it), _p(cv))
+            int(start_iter), _p(C), _p(A), _p(dN), _p(it), _p(cv), _p(E))
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     iters = int(it[0])
-    return RunResult(C, A, [int(x) for x in dN[start_iter:iters]], iters, bool(cv[0]))
+    return RunResult(C, A, [int(x) for x in dN[start_iter:iters]], iters, bool(cv[0]),
+                     [int(x) for x in E[start_iter:iters]])
 
 
 def lpa_sync(g: Graph, tol=0.05, max_iters=20, pl_period=4, labels=None, active=None, start_iter=0, cc_period=0):
@@ -204,7 +207,7 @@ def _mc_lib():
         build()
         L = ct.CDLL(_MC_LIB)
         P = ct.c_void_p
-        L.mc_lpa_sync.argtypes = [ct.c_int64, P, P, P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P,
+        L.mc_lpa_sync.argtypes = [ct.c_int64, P, P, P, ct.c_double, ct.c_int, ct.c_int, ct.c_int, P, P, P, P, P, P,
                                   ct.c_int]
         L.mc_lpa_sync.restype = ct.c_int
         L.mc_threads.restype = ct.c_int

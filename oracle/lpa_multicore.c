@@ -78,10 +78,11 @@ static int32_t mc_best(int64_t i, const int64_t *off, const int32_t *idx, const 
 int mc_threads(void) { return omp_get_max_threads(); }
 
 /* Same arguments and meaning as orc_lpa_sync (synchronous, double-buffered labels and
- * processed flags; dN indexed by absolute iteration), plus the thread count (<= 0: all). */
+ * processed flags; dN and edges indexed by absolute iteration), plus the thread count
+ * (<= 0: all). */
 int mc_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float *w, double tol, int max_iters,
                 int pl_period, int start_iter, int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters,
-                int32_t *converged, int threads)
+                int32_t *converged, int64_t *edges, int threads)
 {
     *converged = 0;
     *iters = start_iter;
@@ -108,10 +109,11 @@ int mc_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float *
         const int pl = (pl_period > 0) && (l % pl_period == 0);
         memcpy(Cn, C, (size_t)n * sizeof(int32_t));
         memset(an, 0, (size_t)n);
-        int64_t changed = 0;
-#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : changed)
+        int64_t changed = 0, scanned = 0;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : changed, scanned)
         for (int64_t i = 0; i < n; ++i) {
             if (!active[i]) continue;
+            scanned += off[i + 1] - off[i];
             mc_table *t = &tabs[omp_get_thread_num()];
             const int32_t c = mc_best(i, off, idx, w, C, t);
             if (c < 0) continue;
@@ -125,6 +127,7 @@ int mc_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float *
         memcpy(C, Cn, (size_t)n * sizeof(int32_t));
         memcpy(active, an, (size_t)n);
         dN[l] = changed;
+        if (edges) edges[l] = scanned;
         *iters = l + 1;
         if (!pl && (double)changed / (double)n < tol) {
             *converged = 1;

@@ -131,6 +131,7 @@ static void orc_work_free(orc_work *wk)
  * active [n]  in: active set at start_iter (1 = unprocessed); out: the set for the
  *             next iteration.
  * dN [max_iters] out: changed-vertex counts, indexed by absolute iteration.
+ * edges [max_iters] out (nullable): CSR entries of the vertices each iteration processed.
  * *iters out: index of the next iteration (= last iteration run + 1).
  * *converged out: 1 when the tolerance test stopped the loop.
  * Returns 0, or -1 on allocation failure.
@@ -161,7 +162,8 @@ int64_t orc_cross_check(int64_t n, int32_t *C, const int32_t *Cprev)
  * that remain after the Cross-Check. */
 int orc_lpa_sync_cc(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                     double tol, int max_iters, int pl_period, int cc_period, int start_iter,
-                    int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged)
+                    int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged,
+                    int64_t *edges)
 {
     *converged = 0;
     *iters = start_iter;
@@ -178,9 +180,10 @@ int orc_lpa_sync_cc(int64_t n, const int64_t *off, const int32_t *idx, const flo
         int pl = (pl_period > 0) && (l % pl_period == 0);
         memcpy(Cn, C, (size_t)n * sizeof(int32_t));
         memset(an, 0, (size_t)n);
-        int64_t changed = 0;
+        int64_t changed = 0, scanned = 0;
         for (int64_t i = 0; i < n; ++i) {
             if (!active[i]) continue;
+            scanned += off[i + 1] - off[i];
             int32_t c = orc_best_label(i, off, idx, w, C, wk.lab, wk.sum, wk.scratch);
             if (c < 0) continue;
             int32_t cur = C[i];
@@ -194,6 +197,7 @@ int orc_lpa_sync_cc(int64_t n, const int64_t *off, const int32_t *idx, const flo
         memcpy(C, Cn, (size_t)n * sizeof(int32_t));
         memcpy(active, an, (size_t)n);   /* processed vertices are cleared, marks set */
         dN[l] = changed;
+        if (edges) edges[l] = scanned;
         *iters = l + 1;
         if (!pl && (double)changed / (double)n < tol) {
             *converged = 1;
@@ -208,10 +212,11 @@ int orc_lpa_sync_cc(int64_t n, const int64_t *off, const int32_t *idx, const flo
 
 int orc_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                  double tol, int max_iters, int pl_period, int start_iter,
-                 int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged)
+                 int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged,
+                 int64_t *edges)
 {
     return orc_lpa_sync_cc(n, off, idx, w, tol, max_iters, pl_period, 0, start_iter, C, active, dN, iters,
-                           converged);
+                           converged, edges);
 }
 
 /* Asynchronous LPA in the paper's sense (Section 4, item 1): one label vector and one
@@ -219,7 +224,8 @@ int orc_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float 
  * 0..n-1, so the result is one particular schedule of the paper's racy sweep. */
 int orc_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                   double tol, int max_iters, int pl_period, int start_iter,
-                  int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged)
+                  int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged,
+                  int64_t *edges)
 {
     *converged = 0;
     *iters = start_iter;
@@ -228,10 +234,11 @@ int orc_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, const float
     if (orc_work_alloc(&wk, orc_max_degree(n, off)) != 0) return -1;
     for (int l = start_iter; l < max_iters; ++l) {
         int pl = (pl_period > 0) && (l % pl_period == 0);
-        int64_t changed = 0;
+        int64_t changed = 0, scanned = 0;
         for (int64_t i = 0; i < n; ++i) {
             if (!active[i]) continue;
             active[i] = 0;                                  /* mark processed */
+            scanned += off[i + 1] - off[i];
             int32_t c = orc_best_label(i, off, idx, w, C, wk.lab, wk.sum, wk.scratch);
             if (c < 0) continue;
             int32_t cur = C[i];
@@ -242,6 +249,7 @@ int orc_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, const float
             }
         }
         dN[l] = changed;
+        if (edges) edges[l] = scanned;
         *iters = l + 1;
         if (!pl && (double)changed / (double)n < tol) {
             *converged = 1;
@@ -265,7 +273,8 @@ int orc_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, const float
 int orc_lpa_async_waves(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                         double tol, int max_iters, int pl_period, int start_iter,
                         const int32_t *wave_of, int32_t n_waves,
-                        int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged)
+                        int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged,
+                        int64_t *edges)
 {
     *converged = 0;
     *iters = start_iter;
@@ -300,7 +309,7 @@ int orc_lpa_async_waves(int64_t n, const int64_t *off, const int32_t *idx, const
     }
     for (int l = start_iter; l < max_iters; ++l) {
         int pl = (pl_period > 0) && (l % pl_period == 0);
-        int64_t changed = 0;
+        int64_t changed = 0, scanned = 0;
         for (int32_t q = 0; q < n_waves; ++q) {
             /* the wave reads: flags taken and c* computed on the labels at its start */
             for (int64_t r = first[q]; r < first[q + 1]; ++r) {
@@ -308,6 +317,7 @@ int orc_lpa_async_waves(int64_t n, const int64_t *off, const int32_t *idx, const
                 newc[i] = -1;
                 if (!active[i]) continue;
                 active[i] = 0;                              /* mark processed */
+                scanned += off[i + 1] - off[i];
                 newc[i] = orc_best_label(i, off, idx, w, C, wk.lab, wk.sum, wk.scratch);
             }
             /* the wave writes: moves and neighbour marks */
@@ -324,6 +334,7 @@ int orc_lpa_async_waves(int64_t n, const int64_t *off, const int32_t *idx, const
             }
         }
         dN[l] = changed;
+        if (edges) edges[l] = scanned;
         *iters = l + 1;
         if (!pl && (double)changed / (double)n < tol) {
             *converged = 1;

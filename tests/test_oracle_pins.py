@@ -463,6 +463,7 @@ def test_multicore_baseline_equals_oracle(seed):
             assert got.labels.tolist() == ref.labels.tolist()
             assert got.dN == ref.dN and got.iterations == ref.iterations
             assert got.active.tolist() == ref.active.tolist()
+            assert got.edges == ref.edges
 
 
 def test_multicore_baseline_rmat_and_closed_forms():
@@ -677,3 +678,35 @@ def test_async_waves_rejects_bad_wave_index():
     g = G(gg.star(4))
     with pytest.raises(ValueError):
         oracle.lpa_async_waves(g, [0, 1, -1, 0, 0])
+
+
+# --------------------------------------------------------------------------------------
+# scanned-entry counts reported per sweep (the CPU baselines' unit of work)
+
+@pytest.mark.parametrize("seed", range(4))
+def test_sync_edges_are_the_rows_of_the_active_vertices(seed):
+    """Synchronous sweep l scans the rows of exactly the vertices unprocessed at its start:
+    stepping one sweep at a time from the saved state, sum(D_i over active i) is edges[l]."""
+    g = G(gg.random_small(300, 0.03, 40 + seed, wmax=4, self_loops=seed % 2 == 0))
+    deg = np.diff(g.off)
+    full = oracle.lpa_sync(g, 0.02, 20, 4)
+    C, A = None, None
+    for t in range(1, full.iterations + 1):
+        act = np.ones(g.n, bool) if A is None else A.astype(bool)
+        r = oracle.lpa_sync(g, 0.02, t, 4, labels=C, active=A, start_iter=t - 1)
+        assert r.edges == [int(deg[act].sum())]
+        C, A = r.labels, r.active
+    assert len(full.edges) == full.iterations
+
+
+def test_async_edges_by_hand():
+    """Five disjoint K_6 (ids contiguous), sequential asynchronous mode, Pick-Less at sweep 0.
+    Sweep 0 processes all 30 vertices (150 entries): in each clique the minimum m sees larger
+    labels only and is blocked; m+1..m+5 move to m in turn, each marking its clique, so every
+    vertex but m+5 ends flagged.  Sweep 1 processes 5 vertices per clique (125 entries),
+    none moves, and the run stops.  The synchronous run re-processes all 30 (150)."""
+    g = G(gg.cliques(5, 6))
+    a = oracle.lpa_async(g, 0.05, 20, 4)
+    assert a.dN == [25, 0] and a.edges == [150, 125]
+    assert oracle.lpa_sync(g, 0.05, 20, 4).edges == [150, 150]
+    assert oracle.lpa_async_waves(g, np.arange(g.n), 0.05, 20, 4).edges == [150, 125]
