@@ -31,6 +31,8 @@ import tempfile
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -254,9 +256,10 @@ def swap_sbm(lpa, dev):
     return out
 
 
-def cpu_multicore(csr_dev, h_off=None, h_idx=None, h_w=None):
-    """The multicore CPU baseline (OpenMP restatement of the synchronous sweep, all host
-    cores) on the first, all-active synchronous sweep of the whole graph, in entries/s."""
+def cpu_multicore(csr_dev, h_off=None, h_idx=None, h_w=None, full=False):
+    """The multicore CPU baseline (OpenMP restatement of the synchronous run, all host cores):
+    the first, all-active sweep of the whole graph in entries/s, and with full=True the whole
+    run too (returned with its result, for the parity check)."""
     import oracle
     if h_off is None:
         h_off, h_idx = csr_dev.offsets.cpu(), csr_dev.indices.cpu()
@@ -266,10 +269,18 @@ def cpu_multicore(csr_dev, h_off=None, h_idx=None, h_w=None):
     t0 = time.perf_counter()
     r = oracle.multicore_lpa_sync(og, ALG["tolerance"], 1, ALG["pl_period"])
     t = time.perf_counter() - t0
-    return dict(value=og.m / t, unit="edges/s", cores=threads, kind="multicore", seconds=round(t, 3),
-                moved=r.dN[0] if r.dN else 0,
-                sample=f"first synchronous sweep (Pick-Less, all vertices active) over the whole graph: {og.n} "
-                       f"vertices, {og.m} CSR entries; OpenMP over {threads} threads, per-thread hash tables")
+    out = dict(value=r.edges[0] / t, unit="edges/s", cores=threads, kind="multicore", seconds=round(t, 3),
+               moved=r.dN[0] if r.dN else 0,
+               sample=f"first synchronous sweep (Pick-Less, all vertices active) over the whole graph: {og.n} "
+                      f"vertices, {og.m} CSR entries; OpenMP over {threads} threads, per-thread hash tables")
+    if not full:
+        return out
+    t0 = time.perf_counter()
+    rf = oracle.multicore_lpa_sync(og, ALG["tolerance"], ALG["max_iters"], ALG["pl_period"])
+    tf = time.perf_counter() - t0
+    out["full_run"] = dict(seconds=round(tf, 3), sweeps=rf.iterations, edges=sum(rf.edges),
+                           value=sum(rf.edges) / tf, unit="edges/s")
+    return out, rf
 
 
 def _cpu_model():
@@ -360,59 +371,10 @@ def metric_name(workload):
     return f"LPA CSR entries scanned per second, full run to convergence ({workload})"
 
 
-def run_ours(args):
-    from paper_2411_11468_gb300 import build, lpa
-    ws, rank, local = dist_env()
-    if not torch.cuda.is_available():
-        raise RuntimeError("bench needs a CUDA device")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    build.build()
-    lpa.load()
-    mode = lpa.SYNC if args.mode == "sync" else lpa.ASYNC
-    t0 = time.time()
-    csr = make_graph(args.workload, dev)
-    torch.cuda.synchronize()
-    log(f"[bench] graph {args.workload}: n={csr.n} m={csr.m} generated in {time.time() - t0:.1f}s")
-    weighted = csr.weights is not None and not bool(torch.all(csr.weights == 1))   # all-one weights are not read
-    stream = torch.cuda.current_stream(dev)
-    g = lpa.Graph(csr.offsets, csr.indices, csr.weights)
-    log(f"[bench] lpa_create done; device bytes {g.device_bytes() / 1e9:.2f} GB")
-
-    def step(time_kernels=False):
-        st = g.run(ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode, time_kernels=time_kernels)
-        q = g.modularity()
-        return st, q
-
-    for _ in range(args.warmup):
-        st, q = step()
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    clocks = Clocks(local)
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    stats = []
-    for _ in range(args.steps):
-        st, q = step(time_kernels=True)
-        stats.append(st.to_dict())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    ms = over_ranks(e0.elapsed_time(e1) / args.steps, "max", dev)
-    edges_per_step = over_ranks(statistics.median(sum(s["edges"]) for s in stats), "sum", dev)
-    value = edges_per_step / (ms / 1000.0)
-
-    # roofline of the dominant kernel over the timed steps
-    peak, peak_src = measured_peaks()
+def roofline_of(stats, weighted, peak, peak_src, workload, steps):
+    """Dominant kernel (largest CUDA-event time over the instrumented steps) with its
+    algorithmic bytes / time, and the same for the first, all-active sweep."""
+    from paper_2411_11468_gb300 import lpa
     kms = [0.0] * lpa.NUM_KERNELS
     kbytes = [0.0] * lpa.NUM_KERNELS
     klaunch = [0] * lpa.NUM_KERNELS
@@ -425,118 +387,272 @@ def run_ours(args):
                     klaunch[k] += 1
         for k in range(lpa.NUM_KERNELS):
             kbytes[k] += kb[k]
-    # hub accumulate owns the hub edges; its bytes are the scanned-entry bytes
     dom = max(range(lpa.NUM_KERNELS), key=lambda k: kms[k])
     achieved = kbytes[dom] / (kms[dom] / 1000.0) / 1e9 if kms[dom] > 0 else 0.0
-    first = stats[-1]
-    sweep0_ms = first["iter_ms"][0]
-    sweep0_bytes = (BYTES_PER_EDGE_W if weighted else BYTES_PER_EDGE_U) * first["edges"][0] + \
-        BYTES_PER_VERTEX * first["active"][0]
-    kernel_table = {lpa.KERNEL_NAMES[k]: dict(ms_per_step=round(kms[k] / args.steps, 4), launches_per_step=klaunch[k] / args.steps,
+    last = stats[-1]
+    per_edge = BYTES_PER_EDGE_W if weighted else BYTES_PER_EDGE_U
+    sweep0_ms = last["iter_ms"][0] if last["iter_ms"] else 0.0
+    sweep0_bytes = per_edge * last["edges"][0] + BYTES_PER_VERTEX * last["active"][0] if last["edges"] else 0
+    kernel_table = {lpa.KERNEL_NAMES[k]: dict(ms_per_step=round(kms[k] / steps, 4), launches_per_step=klaunch[k] / steps,
                                               gbs=round(kbytes[k] / (kms[k] / 1000.0) / 1e9, 1) if kms[k] > 0 else None)
                     for k in range(lpa.NUM_KERNELS) if kms[k] > 0}
-    roofline = {"bound": "hbm", "kernel": lpa.KERNEL_NAMES[dom], "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic_for(lpa.KERNEL_NAMES[dom], args.workload), "peak_source": peak_src,
-                "bytes_model": f"{BYTES_PER_EDGE_W if weighted else BYTES_PER_EDGE_U} B per scanned entry + "
-                               f"{BYTES_PER_VERTEX} B per processed vertex",
-                "first_sweep": {"ms": round(sweep0_ms, 3), "edges": first["edges"][0],
-                                "edges_per_s": first["edges"][0] / (sweep0_ms / 1000.0),
-                                "gbs": round(sweep0_bytes / (sweep0_ms / 1000.0) / 1e9, 1),
-                                "frac": round(sweep0_bytes / (sweep0_ms / 1000.0) / 1e9 / peak, 4)},
-                "kernels": kernel_table}
+    first = None
+    if sweep0_ms > 0:
+        first = {"ms": round(sweep0_ms, 3), "edges": last["edges"][0],
+                 "edges_per_s": last["edges"][0] / (sweep0_ms / 1000.0),
+                 "gbs": round(sweep0_bytes / (sweep0_ms / 1000.0) / 1e9, 1),
+                 "frac": round(sweep0_bytes / (sweep0_ms / 1000.0) / 1e9 / peak, 4)}
+    return {"bound": "hbm", "kernel": lpa.KERNEL_NAMES[dom], "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": traffic_for(lpa.KERNEL_NAMES[dom], workload), "peak_source": peak_src,
+            "bytes_model": f"{per_edge} B per scanned entry + {BYTES_PER_VERTEX} B per processed vertex",
+            "first_sweep": first, "kernels": kernel_table}
 
-    line = {"metric": metric_name(args.workload), "value": value, "unit": "edges/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "graph": WORKLOADS[args.workload]["desc"], "n": csr.n, "m": csr.m,
-                       "mode": args.mode, **ALG, "l2": "inputs larger than L2 (CSR resident in HBM)"},
-            "iterations": first["iterations"], "dN": first["changed"], "edges_per_sweep": first["edges"],
-            "modularity": q, "processing_rate": ws * csr.m / (ms / 1000.0),
-            "roofline": roofline, "gpu_launches": int(statistics.median(s["launches"] for s in stats)) + 2,
-            "clocks": clk, "probe_fallbacks": first["probe_fallbacks"],
-            "sweeps": [{"ms": round(first["iter_ms"][i], 3), "edges": first["edges"][i], "active": first["active"][i],
-                        "changed": first["changed"][i],
-                        "kernels": {lpa.KERNEL_NAMES[k]: [round(first["kernel_ms"][i][k], 3), first["kernel_active"][i][k],
-                                                          first["kernel_edges"][i][k]]
-                                    for k in range(lpa.NUM_KERNELS) if first["kernel_ms"][i][k] > 0}}
-                       for i in range(len(first["iter_ms"]))]}
 
-    # probe-scheme comparison (Section 4.2): the same run with each scheme of the tables
-    if not args.no_ablation and ws == 1:
-        ab = {}
-        names = {0: "quadratic-double", 1: "linear", 2: "quadratic", 3: "double"}
-        for pr in (1, 2, 3, 0):
-            g.set_tuning(probe=pr)
-            best = None
-            for _ in range(2):
-                st = g.run(ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode).to_dict()
-                if best is None or st["total_ms"] < best["total_ms"]:
-                    best = st
-            ab[names[pr]] = {"run_ms": round(best["total_ms"], 2), "probe_fallbacks": best["probe_fallbacks"],
-                             "iterations": best["iterations"]}
-        line["probe_ablation"] = ab
-        # hashtable value type (Section 4.4): uint32 sums (the default for integer weights),
-        # float32 and float64 values on the same graph
-        va = {}
-        for name, fv in (("float64", 2), ("float32", 1), ("uint32", 0)):
-            g.set_tuning(float_values=fv)
-            best = None
-            for _ in range(2):
-                st = g.run(ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode).to_dict()
-                if best is None or st["total_ms"] < best["total_ms"]:
-                    best = st
-            va[name] = {"run_ms": round(best["total_ms"], 2), "iterations": best["iterations"],
-                        "modularity": g.modularity(), "device_gb": round(g.device_bytes() / 1e9, 2)}
-        line["value_ablation"] = va
-        # swap mitigation (Section 4.1): Pick-Less and Cross-Check periods on the same graph
-        sw = {}
-        if mode == lpa.SYNC:
-            for name, pl, cc in (("none", 0, 0), ("PL4", 4, 0), ("CC1", 0, 1), ("CC2", 0, 2), ("PL4+CC4", 4, 4),
-                                 ("PL2+CC2", 2, 2)):
-                st = g.run(ALG["tolerance"], ALG["max_iters"], pl, mode, cc_period=cc).to_dict()
-                sw[name] = {"run_ms": round(st["total_ms"], 2), "iterations": st["iterations"],
-                            "converged": st["converged"], "modularity": g.modularity()}
-            line["swap_mitigation"] = {"rmat26": sw, "sbm": swap_sbm(lpa, dev)}
+def oracle_full_run(csr_dev, mode, waves_tuning=None):
+    """The single-threaded oracle's whole run (tolerance 0.05, cap 20, Pick-Less every 4th):
+    synchronous, or asynchronous in sequential id order; with waves_tuning also the
+    asynchronous run under the wave model of the GPU's schedule.  Returns the results and
+    the timed seconds of the first run."""
+    import oracle
+    og = oracle.Graph.of(csr_dev)
+    fn = oracle.lpa_sync if mode == "sync" else oracle.lpa_async
+    t0 = time.perf_counter()
+    r = fn(og, ALG["tolerance"], ALG["max_iters"], ALG["pl_period"])
+    secs = time.perf_counter() - t0
+    rw = None
+    if waves_tuning is not None:
+        from oracle.schedule import gpu_waves
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        rw = oracle.lpa_async_waves(og, gpu_waves(og.off, waves_tuning, sms), ALG["tolerance"], ALG["max_iters"],
+                                    ALG["pl_period"])
+    return og, r, secs, rw
+
+
+_CPU_SAMPLE = {}     # the oracle's sampled first-sweep rate, taken once per workload
+
+
+def measure_single(args, lpa, dev, workload, mode_name, steps, warmup, e2e_steps, extras=False):
+    """One workload and mode: the timed steps (uninstrumented), an instrumented pass of the same
+    steps for the per-kernel breakdown, parity against the oracle (or the pinned multicore
+    baseline), the CPU baseline, end to end from pinned host buffers.  Returns the JSON object."""
+    import oracle
+    mode = lpa.SYNC if mode_name == "sync" else lpa.ASYNC
+    ws, rank, local = dist_env()
+    t0 = time.time()
+    csr = make_graph(workload, dev)
+    torch.cuda.synchronize()
+    log(f"[bench] {workload}/{mode_name}: n={csr.n} m={csr.m} generated in {time.time() - t0:.1f}s")
+    weighted = csr.weights is not None and not bool(torch.all(csr.weights == 1))   # all-one weights are not read
+    stream = torch.cuda.current_stream(dev)
+    g = lpa.Graph(csr.offsets, csr.indices, csr.weights)
+
+    def step(time_kernels=False):
+        st = g.run(ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode, time_kernels=time_kernels)
+        q = g.modularity()
+        return st, q
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plain = []
+    for _ in range(steps):
+        st, q = step()
+        plain.append(st.to_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = over_ranks(e0.elapsed_time(e1) / steps, "max", dev)
+    edges_per_step = over_ranks(statistics.median(sum(s["edges"]) for s in plain), "sum", dev)
+    value = edges_per_step / (ms / 1000.0)
+    # the same steps with every kernel timed by CUDA events: the per-kernel breakdown
+    inst = []
+    e0.record(stream)
+    for _ in range(steps):
+        st_i, q_i = step(time_kernels=True)
+        inst.append(st_i.to_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    inst_ms = e0.elapsed_time(e1) / steps
+    peak, peak_src = measured_peaks()
+    last = plain[-1]
+    labels_gpu = g.labels().cpu()
+    out = {"metric": metric_name(workload), "value": value, "unit": "edges/s", "n_gpus": ws, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": workload, "graph": WORKLOADS[workload]["desc"], "n": csr.n, "m": csr.m,
+                      "mode": mode_name, **ALG,
+                      "l2": "inputs larger than L2 (CSR resident in HBM)" if csr.m * 4 > 256e6 else
+                            "graph smaller than L2: repeated runs read it from L2 (no flush)"},
+           "iterations": last["iterations"], "dN": last["changed"], "edges_per_sweep": last["edges"],
+           "modularity": q, "processing_rate": ws * csr.m / (ms / 1000.0),
+           "roofline": roofline_of(inst, weighted, peak, peak_src, workload, steps),
+           "instrumented_ms_per_step": inst_ms,
+           "gpu_launches": int(statistics.median(s["launches"] for s in plain)) + 2,
+           "clocks": clk, "probe_fallbacks": last["probe_fallbacks"],
+           "sweeps": [{"ms": round(inst[-1]["iter_ms"][i], 3), "edges": inst[-1]["edges"][i],
+                       "active": inst[-1]["active"][i], "changed": inst[-1]["changed"][i],
+                       "kernels": {lpa.KERNEL_NAMES[k]: [round(inst[-1]["kernel_ms"][i][k], 3),
+                                                         inst[-1]["kernel_active"][i][k], inst[-1]["kernel_edges"][i][k]]
+                                   for k in range(lpa.NUM_KERNELS) if inst[-1]["kernel_ms"][i][k] > 0}}
+                      for i in range(len(inst[-1]["iter_ms"]))]}
+
+    if extras and not args.no_ablation and ws == 1:
+        out.update(ablations(args, lpa, dev, g, mode))
+        g.set_tuning(probe=0, float_values=0)
+
     # end to end through the public API with host buffers
-    h_off = h_idx = h_w = h_lab = None
+    h_off = csr.offsets.cpu().pin_memory()
+    h_idx = csr.indices.cpu().pin_memory()
+    h_w = None if csr.weights is None else csr.weights.cpu().pin_memory()
     if not args.no_e2e:
-        h_off = csr.offsets.cpu().pin_memory()
-        h_idx = csr.indices.cpu().pin_memory()
-        h_w = None if csr.weights is None else csr.weights.cpu().pin_memory()
         h_lab = torch.empty(csr.n, dtype=torch.int32).pin_memory()
-        g = None
         torch.cuda.synchronize()
-        times = []
-        edges = []
-        for rep in range(args.e2e_steps + 1):
+        times, edges = [], []
+        for rep in range(e2e_steps + 1):
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
+            t1 = time.perf_counter()
             g2 = lpa.Graph(h_off, h_idx, h_w)
             st2 = g2.run(ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode)
             g2.labels(h_lab)
-            q2 = g2.modularity()
+            g2.modularity()
             g2.close()
             torch.cuda.synchronize()
             if rep > 0:
-                times.append(time.perf_counter() - t0)
+                times.append(time.perf_counter() - t1)
                 edges.append(sum(st2.to_dict()["edges"]))
         e2e_s = over_ranks(statistics.median(times), "max", dev)
         h2d = h_off.numel() * h_off.element_size() + h_idx.numel() * 4 + (0 if h_w is None else h_w.numel() * 4)
-        line["e2e"] = {"value": over_ranks(statistics.median(edges), "sum", dev) / e2e_s, "unit": "edges/s",
-                       "ms_per_step": e2e_s * 1000,
-                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": csr.n * 4 + 8,
-                       "includes": "lpa_create from pinned host CSR (copy, validation, buckets), lpa_run, "
-                                   "lpa_labels to pinned host, lpa_modularity, lpa_destroy"}
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_baseline(csr, target_s=args.ref_seconds)
-        line["cpu_multicore"] = cpu_multicore(csr, h_off, h_idx, h_w)
+        out["e2e"] = {"value": over_ranks(statistics.median(edges), "sum", dev) / e2e_s, "unit": "edges/s",
+                      "ms_per_step": e2e_s * 1000, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": csr.n * 4 + 8,
+                      "includes": "lpa_create from pinned host CSR (copy, validation, buckets), lpa_run, "
+                                  "lpa_labels to pinned host, lpa_modularity, lpa_destroy"}
+    tuning = g.tuning().to_dict()
+    g.close()
+
+    # parity and the CPU baseline (rank 0, one GPU)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        host = dict(machine=platform.machine(), nproc=os.cpu_count(), cpu=_cpu_model())
+        if workload == "rmat26":
+            # the oracle on a bounded sample of the first sweep; the whole run extrapolated from its rate
+            if "rmat26" not in _CPU_SAMPLE:
+                _CPU_SAMPLE["rmat26"] = cpu_baseline(csr, target_s=args.ref_seconds)
+            cb = dict(_CPU_SAMPLE["rmat26"])
+            total_edges = sum(last["edges"])
+            cb["full_run_seconds_extrapolated"] = round(total_edges / cb["value"], 1)
+            cb["full_run_note"] = ("extrapolated: the GPU run's scanned entries over the sampled single-thread rate "
+                                   "(the whole single-thread run would take about that long)")
+            out["cpu_baseline"] = cb
+            if mode_name == "sync":
+                mc, r = cpu_multicore(csr, h_off, h_idx, h_w, full=True)
+                out["cpu_multicore"] = mc
+                out["parity"] = {"against": "multicore baseline (pinned equal to the oracle's synchronous run), "
+                                            "whole graph, whole run",
+                                 "labels_equal": bool(torch.equal(labels_gpu, torch.from_numpy(r.labels))),
+                                 "dN_equal": r.dN == last["changed"], "edges_equal": r.edges == last["edges"],
+                                 "sweeps": r.iterations, "dN_cpu": r.dN}
+        else:
+            og, r, secs, rw = oracle_full_run(csr, mode_name, tuning if mode_name == "async" else None)
+            out["cpu_baseline"] = {"value": sum(r.edges) / secs, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                   "seconds": round(secs, 3), "iterations": r.iterations,
+                                   "modularity": oracle.modularity(og, r.labels),
+                                   "sample": f"the whole {mode_name} run of the oracle (single-threaded C, "
+                                             f"{'sequential id order' if mode_name == 'async' else 'double-buffered'})"
+                                             f" on the same graph: {sum(r.edges)} CSR entries scanned",
+                                   "host": host}
+            if mode_name == "sync":
+                out["parity"] = {"against": "oracle synchronous run, whole graph",
+                                 "labels_equal": bool(np.array_equal(labels_gpu.numpy(), r.labels)),
+                                 "dN_equal": r.dN == last["changed"], "edges_equal": r.edges == last["edges"],
+                                 "sweeps": r.iterations}
+            else:
+                q_w = oracle.modularity(og, rw.labels)
+                viol = oracle.violations(og, labels_gpu) / og.n
+                out["parity"] = {"against": "oracle asynchronous run under the wave model of the GPU schedule",
+                                 "q_gpu": q, "q_oracle_waves": q_w, "q_oracle_sequential": oracle.modularity(og, r.labels),
+                                 "abs_diff": abs(q - q_w), "within_0_005": abs(q - q_w) <= 0.005,
+                                 "violation_fraction": viol, "violations_within_tolerance": viol <= ALG["tolerance"]}
+    return out
+
+
+def ablations(args, lpa, dev, g, mode):
+    """Section 4.2's probe schemes, Section 4.4's value types and Section 4.1's swap
+    mitigations on the same resident graph (after the timed region)."""
+    res = {}
+    ab = {}
+    names = {0: "quadratic-double", 1: "linear", 2: "quadratic", 3: "double"}
+    for pr in (1, 2, 3, 0):
+        g.set_tuning(probe=pr)
+        best = None
+        for _ in range(2):
+            st = g.run(ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode).to_dict()
+            if best is None or st["total_ms"] < best["total_ms"]:
+                best = st
+        ab[names[pr]] = {"run_ms": round(best["total_ms"], 2), "probe_fallbacks": best["probe_fallbacks"],
+                         "iterations": best["iterations"]}
+    res["probe_ablation"] = ab
+    va = {}
+    for name, fv in (("float64", 2), ("float32", 1), ("uint32", 0)):
+        g.set_tuning(float_values=fv)
+        best = None
+        for _ in range(2):
+            st = g.run(ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], mode).to_dict()
+            if best is None or st["total_ms"] < best["total_ms"]:
+                best = st
+        va[name] = {"run_ms": round(best["total_ms"], 2), "iterations": best["iterations"],
+                    "modularity": g.modularity(), "device_gb": round(g.device_bytes() / 1e9, 2)}
+    res["value_ablation"] = va
+    if mode == lpa.SYNC:
+        sw = {}
+        for name, pl, cc in (("none", 0, 0), ("PL4", 4, 0), ("CC1", 0, 1), ("CC2", 0, 2), ("PL4+CC4", 4, 4),
+                             ("PL2+CC2", 2, 2)):
+            st = g.run(ALG["tolerance"], ALG["max_iters"], pl, mode, cc_period=cc).to_dict()
+            sw[name] = {"run_ms": round(st["total_ms"], 2), "iterations": st["iterations"],
+                        "converged": st["converged"], "modularity": g.modularity()}
+        res["swap_mitigation"] = {"rmat26": sw, "sbm": swap_sbm(lpa, dev)}
+    return res
+
+
+# the other single-graph configurations, reported beside the headline: (workload, mode, steps)
+SIDE_LINES = (("rmat26", "async", 5), ("rmat22", "sync", 10), ("rmat22", "async", 10), ("sbm", "sync", 20),
+              ("sbm", "async", 20))
+
+
+def run_ours(args):
+    from paper_2411_11468_gb300 import build, lpa
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+    lpa.load()
+    line = measure_single(args, lpa, dev, args.workload, args.mode, args.steps, args.warmup, args.e2e_steps,
+                          extras=True)
+    if ws == 1 and not args.no_extras and args.workload == "rmat26" and args.mode == "sync":
+        side = {}
+        for wl, md, k in SIDE_LINES:
+            torch.cuda.empty_cache()
+            side[f"{wl}_{md}"] = measure_single(args, lpa, dev, wl, md, k, max(3, args.warmup), args.e2e_steps)
+        line["lines"] = side
     # the batched and served workloads, summarised in the same line (one GPU only)
     if ws == 1 and not args.no_extras:
-        h_off = h_idx = h_w = h_lab = None
-        csr = g = None
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
+        mode = lpa.SYNC if args.mode == "sync" else lpa.ASYNC
         clocks = Clocks(local)
         clocks.start()
         line["batch"] = bench_batch(args, dev, lpa, mode)

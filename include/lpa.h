@@ -137,9 +137,19 @@ typedef struct lpa_tuning {
                                  2 float64 (Section 4.4's 64-bit hashtable values)       */
     int32_t hub_cluster;      /* 1: hub tables in cluster shared memory where they fit   */
     int32_t probe;            /* table probe scheme (Section 4.2): 0 quadratic-double
-                                 (Algorithm 2), 1 linear, 2 quadratic, 3 double hashing;
+                                 (Algorithm 2: Mersenne moduli p1, p2), 1 linear,
+                                 2 quadratic, 3 double hashing, 4 (the default)
+                                 Algorithm 2's quadratic-double recurrence over the
+                                 whole power-of-two table with multiplicative hashes;
                                  the table contents, hence the labels, do not depend on it */
-    int32_t reserved[3];      /* zero                                                    */
+    int32_t flat_buckets;     /* bit b (b = 0 thread, 1 group, 2 warp): that bucket runs
+                                 the flattened kernel (a warp per batch of vertices whose
+                                 rows it scans as one run) instead of one thread / lane
+                                 group / warp per vertex                                   */
+    int32_t hub_two_pass;     /* 1: hubs with integer sums and HBM tables accumulate in two
+                                 passes (per-chunk shared-memory tables, then per label
+                                 partition) instead of global atomics on the HBM tables  */
+    int32_t reserved[1];      /* zero                                                    */
 } lpa_tuning;
 
 typedef struct lpa_graph lpa_graph;
@@ -335,8 +345,6 @@ double lpa_server_clock(const lpa_server *s);
 int64_t lpa_server_device_bytes(const lpa_server *s);
 void lpa_server_destroy(lpa_server *s);
 
-/* ---- modularity without device allocation ------------------------------------------ */
-
 /* ---- autotuning of the degree buckets ---------------------------------------------- */
 
 /* Picks the handle's degree-bucket configuration by timing: a coordinate descent over fixed
@@ -361,6 +369,8 @@ int lpa_autotune(lpa_graph *g, double tolerance, int max_iters, int pl_period, i
 int lpa_batch_autotune(lpa_batch *b, double tolerance, int max_iters, int pl_period, int mode, int reps,
                        lpa_tuning *best, float *best_ms, int *evaluated);
 
+/* ---- modularity without device allocation ------------------------------------------ */
+
 /* Largest n_vertices accepted by lpa_modularity_noalloc. */
 #define LPA_NOALLOC_MAX_VERTICES (1 << 20)
 
@@ -376,9 +386,10 @@ int lpa_batch_autotune(lpa_batch *b, double tolerance, int max_iters, int pl_per
  * Scratch: one fixed array of LPA_NOALLOC_MAX_VERTICES + 8 doubles (8 MiB) compiled into the
  * library; every GPU that loads the library holds it until the process exits, and every call
  * on that GPU uses it.  Calls that overlap on the GPU (other streams or host threads) race on
- * it; order them.  Each call clears the part it reads first.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) once; make that first call before any
- * stream capture.  The call works on cuda_stream and synchronises it before returning.
+ * it; order them.  Each call clears the part it reads first.  Every call looks up the array's
+ * address on the current device (cudaGetSymbolAddress); cuda_stream must belong to that
+ * device.  The call works on cuda_stream and synchronises it before returning, so it must not
+ * be made on a stream that is being captured into a CUDA graph.
  * Errors: LPA_EINVAL for n_vertices > LPA_NOALLOC_MAX_VERTICES, NULL arrays, or a graph /
  * labels that fail the device-side checks; LPA_ECUDA for a failed CUDA call. */
 int lpa_modularity_noalloc(const int64_t *offsets, const int32_t *indices, const float *weights,

@@ -681,6 +681,8 @@ lpa_tuning default_tuning()
     t.hub_chunk = 16384;
     t.hub_table_shift = 1;
     t.smem_table_shift = 1;
+    t.probe = 4;                                      // quadratic-double over power-of-two tables
+    t.flat_buckets = 2;                               // the lane-group bucket runs the flattened kernel
     return t;
 }
 
@@ -707,7 +709,9 @@ int check_tuning(const lpa_tuning &t)
     if (t.item_vertices < 0 || t.item_vertices > (1 << 20)) return LPA_EINVAL;
     if (t.float_values < 0 || t.float_values > 2) return LPA_EINVAL;
     if (t.hub_cluster != 0 && t.hub_cluster != 1) return LPA_EINVAL;
-    if (t.probe < 0 || t.probe > 3) return LPA_EINVAL;
+    if (t.probe < 0 || t.probe > 4) return LPA_EINVAL;
+    if (t.flat_buckets < 0 || t.flat_buckets > 7) return LPA_EINVAL;
+    if (t.hub_two_pass != 0 && t.hub_two_pass != 1) return LPA_EINVAL;
     for (int r : t.reserved)
         if (r != 0) return LPA_EINVAL;
     const int64_t smem = (int64_t)max_dynamic_smem();
@@ -741,6 +745,8 @@ void free_buckets(lpa_graph *g)
     g->tab_v = nullptr;
     dfree(g, g->used_list);
     g->used_list = nullptr;
+    dfree(g, g->pairs);
+    g->pairs = nullptr;
     dfree(g, g->items_d);
     g->items_d = nullptr;
     g->gdh.hub = HubArgs{};
@@ -845,14 +851,21 @@ int build_buckets(lpa_graph *g)
         const int dsm_bits = (g->tuning.hub_cluster && plan_int_weights(g)) ? dsm_max_class_bits() : 0;
         const bool dsm_ok = dsm_bits > 0;
         std::vector<int64_t> acc_chunks;
+        // two-pass accumulation for integer sums with HBM tables: first-pass chunks and partitions
+        const bool two_pass = plan_int_weights(g) && g->tuning.hub_two_pass;
+        std::vector<uint32_t> hpb((size_t)H, 0u);
+        std::vector<int32_t> hpbase((size_t)H, -1), pch, parth;
+        std::vector<int64_t> pce0, pce1;
         for (int64_t h = 0; h < H; ++h) {
             const int64_t D = o1[h] - o0[h];
+            // capacity_bits stops at 31: p1 <= 2^31 - 1 still holds every distinct label (labels
+            // are below n < 2^31), the probe's secondary modulus 2 p1 + 1 fits in 32 bits and
+            // the remainder multipliers are indexed at b + 1 <= 32, inside their table.
             const int64_t want = std::min<int64_t>(D << g->tuning.hub_table_shift, (int64_t)1 << 31);
             bb[h] = capacity_bits(want);
             p1[h] = (uint32_t)(((int64_t)1 << bb[h]) - 1);
             const bool dsm = dsm_ok && (int)bb[h] <= kDsmSliceBits + dsm_bits;
             for (int64_t e0 = o0[h]; e0 < o1[h]; e0 += chunk) {
-                if (!dsm) acc_chunks.push_back((int64_t)ch.size());
                 ch.push_back((int32_t)h);
                 ce0.push_back(e0);
                 ce1.push_back(std::min(o1[h], e0 + chunk));
@@ -864,20 +877,38 @@ int build_buckets(lpa_graph *g)
                 ubase[h] = -1;
                 continue;
             }
+            if (two_pass) {
+                uint32_t pb = 0;
+                while (pb < (uint32_t)kPartMaxBits && ((D + ((int64_t)1 << pb) - 1) >> pb) > kPartExpect) ++pb;
+                hpb[h] = pb;
+                hpbase[h] = (int32_t)parth.size();
+                for (uint32_t q = 0; q < (1u << pb); ++q) parth.push_back((int32_t)h);
+                for (int64_t e0 = o0[h]; e0 < o1[h]; e0 += kPartChunk) {
+                    pch.push_back((int32_t)h);
+                    pce0.push_back(e0);
+                    pce1.push_back(std::min<int64_t>(o1[h], e0 + kPartChunk));
+                }
+            } else {
+                for (int64_t c = (int64_t)ch.size() - (o1[h] - o0[h] + chunk - 1) / chunk; c < (int64_t)ch.size(); ++c)
+                    acc_chunks.push_back(c);
+            }
             tab[h] = slots;
             ubase[h] = used_total;
-            for (int64_t j = 0; j * kHubSlice < (int64_t)p1[h]; ++j) {   // clear slices cover the table
+            // 2^b = p1 + 1 slots: Algorithm 2 probes p1 of them, the power-of-two probe all
+            for (int64_t j = 0; j * kHubSlice < (int64_t)p1[h] + 1; ++j) {   // clear slices cover the table
                 sh.push_back((int32_t)h);
                 sj.push_back((int32_t)j);
             }
-            slots += p1[h];
+            slots += (int64_t)p1[h] + 1;
             used_total += D;
         }
         const int64_t n_chunks = (int64_t)ch.size(), n_slices = (int64_t)sh.size();
         g->table_slots = slots;
         const bool f64 = g->tuning.float_values == 2;   // float64 values: per-chunk arg-max pairs
-        const size_t n8 = (size_t)(3 * H + 2 * n_chunks + (f64 ? n_chunks : 0));
-        const size_t n4 = (size_t)(4 * H + n_chunks + 2 * n_slices + (f64 ? n_chunks + H + 1 : 0));
+        const int64_t n_pch = (int64_t)pch.size(), n_parts = (int64_t)parth.size();
+        const size_t n8 = (size_t)(3 * H + 2 * n_chunks + (f64 ? n_chunks : 0) + 2 * n_pch);
+        const size_t n4 = (size_t)(4 * H + n_chunks + 2 * n_slices + (f64 ? n_chunks + H + 1 : 0) + n_pch + 2 * H +
+                                   3 * n_parts);
         unsigned char *mem = nullptr;
         LPA_CHECK(dalloc(g, &mem, n8 * 8 + n4 * 4 + 2 * (size_t)H));
         g->hub_mem = mem;
@@ -893,6 +924,8 @@ int build_buckets(lpa_graph *g)
         int64_t *d_ce0 = (int64_t *)take(n_chunks * 8);
         int64_t *d_ce1 = (int64_t *)take(n_chunks * 8);
         double *d_cbv = f64 ? (double *)take(n_chunks * 8) : nullptr;
+        int64_t *d_pce0 = (int64_t *)take(n_pch * 8);
+        int64_t *d_pce1 = (int64_t *)take(n_pch * 8);
         int32_t *d_hv = (int32_t *)take(H * 4);
         uint32_t *d_p1 = (uint32_t *)take(H * 4);
         uint32_t *d_b = (uint32_t *)take(H * 4);
@@ -902,6 +935,12 @@ int build_buckets(lpa_graph *g)
         int32_t *d_sj = (int32_t *)take(n_slices * 4);
         int32_t *d_cbk = f64 ? (int32_t *)take(n_chunks * 4) : nullptr;
         int32_t *d_hc0 = f64 ? (int32_t *)take((H + 1) * 4) : nullptr;
+        int32_t *d_pch = (int32_t *)take(n_pch * 4);
+        uint32_t *d_hpb = (uint32_t *)take(H * 4);
+        int32_t *d_hpbase = (int32_t *)take(H * 4);
+        int32_t *d_parth = (int32_t *)take(n_parts * 4);
+        uint32_t *d_pcnt = (uint32_t *)take(n_parts * 4);
+        int32_t *d_povf = (int32_t *)take(n_parts * 4);
         uint8_t *d_act = (uint8_t *)take(H);
         uint8_t *d_seen = (uint8_t *)take(H);
         LPA_CUDA(cudaMemcpyAsync(d_tab, tab.data(), H * 8, cudaMemcpyHostToDevice, g->stream));
@@ -914,6 +953,18 @@ int build_buckets(lpa_graph *g)
         LPA_CUDA(cudaMemcpyAsync(d_ch, ch.data(), n_chunks * 4, cudaMemcpyHostToDevice, g->stream));
         LPA_CUDA(cudaMemcpyAsync(d_sh, sh.data(), n_slices * 4, cudaMemcpyHostToDevice, g->stream));
         LPA_CUDA(cudaMemcpyAsync(d_sj, sj.data(), n_slices * 4, cudaMemcpyHostToDevice, g->stream));
+        if (n_pch > 0) {
+            LPA_CUDA(cudaMemcpyAsync(d_pce0, pce0.data(), n_pch * 8, cudaMemcpyHostToDevice, g->stream));
+            LPA_CUDA(cudaMemcpyAsync(d_pce1, pce1.data(), n_pch * 8, cudaMemcpyHostToDevice, g->stream));
+            LPA_CUDA(cudaMemcpyAsync(d_pch, pch.data(), n_pch * 4, cudaMemcpyHostToDevice, g->stream));
+        }
+        LPA_CUDA(cudaMemcpyAsync(d_hpb, hpb.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
+        LPA_CUDA(cudaMemcpyAsync(d_hpbase, hpbase.data(), H * 4, cudaMemcpyHostToDevice, g->stream));
+        if (n_parts > 0) {
+            LPA_CUDA(cudaMemcpyAsync(d_parth, parth.data(), n_parts * 4, cudaMemcpyHostToDevice, g->stream));
+            LPA_CUDA(cudaMemsetAsync(d_pcnt, 0, n_parts * 8, g->stream));       // part_cnt and part_ovf
+            LPA_CHECK(dalloc(g, &g->pairs, (size_t)n_parts * kPartCap));
+        }
         LPA_CUDA(cudaMemsetAsync(d_act, 0, 2 * H, g->stream));     // hub_act and hub_seen
         LPA_CUDA(cudaMemsetAsync(d_best, 0, H * 8, g->stream));
         LPA_CUDA(cudaMemsetAsync(d_used, 0, H * 4, g->stream));
@@ -952,6 +1003,15 @@ int build_buckets(lpa_graph *g)
         ha.chunk_bv = d_cbv;
         ha.chunk_bk = d_cbk;
         ha.hub_c0 = d_hc0;
+        ha.pc_h = d_pch;
+        ha.pc_e0 = d_pce0;
+        ha.pc_e1 = d_pce1;
+        ha.hub_pb = d_hpb;
+        ha.hub_pbase = d_hpbase;
+        ha.part_h = d_parth;
+        ha.part_cnt = d_pcnt;
+        ha.part_ovf = d_povf;
+        ha.pairs = g->pairs;
         ha.n_hubs = (int32_t)H;
         ha.n_chunks = (int32_t)n_chunks;
         ha.n_slices = (int32_t)n_slices;
@@ -960,6 +1020,8 @@ int build_buckets(lpa_graph *g)
         for (int64_t c : acc_chunks) g->hub_items_h[HL_ACC].push_back(WorkItem{0, 0, c, 1});
         for (int64_t c = 0; c < n_chunks; ++c) g->hub_items_h[HL_MARK].push_back(WorkItem{0, 0, c, 1});
         for (int64_t j = 0; j < n_slices; ++j) g->hub_items_h[HL_SLICES].push_back(WorkItem{0, 0, j, 1});
+        for (int64_t c = 0; c < n_pch; ++c) g->hub_items_h[HL_PACC].push_back(WorkItem{0, 0, c, 1});
+        for (int64_t q = 0; q < n_parts; ++q) g->hub_items_h[HL_PMERGE].push_back(WorkItem{0, 0, q, 1});
     }
 
     // every item of this graph in one device block: vertex items, hub items, one per-graph item
@@ -1633,6 +1695,7 @@ int lpa_run_cc(lpa_graph *g, double tolerance, int max_iters, int pl_period, int
     p.queues = g->queues;
     p.active_count = g->active;
     p.group_lanes = g->tuning.group_lanes;
+    p.flat_buckets = g->tuning.flat_buckets;
     p.cta_threads = g->tuning.cta_threads;
     p.cta_large_threads = g->tuning.cta_large_threads;
     p.cta_xl_threads = g->tuning.cta_xl_threads;

@@ -39,6 +39,7 @@ struct lpa_graph {
     int32_t *tab_k = nullptr;
     float *tab_v = nullptr;
     int32_t *used_list = nullptr;
+    unsigned long long *pairs = nullptr;             // two-pass hub partitions: [n_parts * kPartCap]
     int64_t table_slots = 0;
     // work items of this graph (graph index 0); batches re-index copies of the host vectors
     std::vector<lpa::WorkItem> items_h[lpa::B_COUNT];

@@ -19,7 +19,20 @@ enum Bucket { B_THREAD = 0, B_GROUP, B_WARP, B_CTA, B_CTA_LARGE, B_CTA_XL, B_HUB
 // Work-item lists of the hub bucket: hubs (begin, move), accumulate chunks of hubs whose table
 // is in HBM, mark chunks of every hub, clear slices of HBM tables, and the hubs whose table
 // lives in the distributed shared memory of a 2-, 4-, 8- or 16-block cluster.
-enum HubList { HL_HUBS = 0, HL_ACC, HL_MARK, HL_SLICES, HL_DSM2, HL_DSM4, HL_DSM8, HL_DSM16, HL_COUNT };
+// Hubs with integer label sums and HBM tables take a two-pass accumulation instead: the
+// chunks of the first pass (kPartChunk entries each) and the label partitions of the second.
+enum HubList { HL_HUBS = 0, HL_ACC, HL_MARK, HL_SLICES, HL_DSM2, HL_DSM4, HL_DSM8, HL_DSM16, HL_PACC, HL_PMERGE,
+               HL_COUNT };
+// Two-pass hub accumulation: the first pass sums each kPartChunk-entry chunk of a hub's row in
+// a shared-memory table and sends the chunk's distinct (label, sum) pairs to the hub's label
+// partitions (2^pb of them, chosen so that a partition expects at most kPartExpect pairs when
+// every label is distinct); the second pass sums each partition's pairs in a shared-memory
+// table.  A partition holds at most kPartCap pairs; one that would overflow sends all its pairs
+// to the hub's HBM table instead.
+constexpr int kPartChunk = 4096;
+constexpr int kPartExpect = 2048;
+constexpr int kPartCap = 4096;
+constexpr int kPartMaxBits = 10;
 constexpr int kDsmSliceBits = 14;  // table slots per cluster block (2^14 x 8 bytes = 128 KB)
 constexpr int kDsmMaxBits = 18;    // largest table in cluster shared memory: 2^18 slots over 16 blocks
 // Work-queue counters: vertex buckets for push and pull launches, then the cluster classes.
@@ -77,6 +90,16 @@ struct HubArgs {
     double *chunk_bv;          // float64 values: [n_chunks] arg-max pair of each accumulate
     int32_t *chunk_bk;         //   block (label < 0: none), reduced per hub by k_hub_move
     const int32_t *hub_c0;     // float64 values: [H + 1] first accumulate chunk of each hub
+    // two-pass accumulation (integer sums, HBM tables)
+    const int32_t *pc_h;       // [n_pchunks] hub of each first-pass chunk
+    const int64_t *pc_e0;      // [n_pchunks] first CSR entry
+    const int64_t *pc_e1;      // [n_pchunks] end CSR entry
+    const uint32_t *hub_pb;    // [H] log2 of the hub's partitions
+    const int32_t *hub_pbase;  // [H] first partition of the hub (-1: not two-pass)
+    const int32_t *part_h;     // [n_parts] hub of each partition
+    uint32_t *part_cnt;        // [n_parts] pairs sent to the partition this sweep
+    int32_t *part_ovf;         // [n_parts] 1: the partition overflowed (pairs go to the HBM table)
+    unsigned long long *pairs; // [n_parts * kPartCap] (label << 32 | sum)
     int32_t n_hubs;
     int32_t n_chunks;
     int32_t n_slices;
@@ -136,6 +159,7 @@ struct SweepPlan {
     unsigned *queues;          // [kQueueCount] work-queue counters, zeroed per sweep
     int32_t *active_count;     // device counter written by k_decide (graphs still running)
     int32_t group_lanes, cta_threads, cta_large_threads, cta_xl_threads, hub_chunk;
+    int32_t flat_buckets;      // bit b: bucket b (thread, group, warp) runs the flattened kernel
     int32_t pull_mode;         // kernels launched for this sweep: 0 push only, 1 pull only, 2 both
     int32_t int_weights;       // 1: every graph of the plan uses uint32 sums (else float32)
     int32_t probe;             // table probe scheme of every graph of the plan (lpa_tuning.probe)

@@ -175,6 +175,7 @@ struct MultiPlan {
         p.queues = queues;
         p.active_count = active;
         p.group_lanes = t.group_lanes;
+        p.flat_buckets = t.flat_buckets;
         p.cta_threads = t.cta_threads;
         p.cta_large_threads = t.cta_large_threads;
         p.cta_xl_threads = t.cta_xl_threads;
@@ -250,6 +251,8 @@ lpa_tuning multi_tuning()
     t.hub_chunk = 16384;
     t.hub_table_shift = 1;
     t.smem_table_shift = 1;
+    t.probe = 4;                                      // quadratic-double over power-of-two tables
+    t.flat_buckets = 2;                               // the lane-group bucket runs the flattened kernel
     return t;
 }
 

@@ -12,7 +12,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
 #include <string>
 
 #include "lpa_internal.h"
@@ -26,25 +25,15 @@ constexpr int kAccWords = 8;      // accumulators after the Sigma part: sigma_in
 // name is only a stand-in for the symbol: its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) double g_noalloc_scratch[kMaxVertices + kAccWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device.  Looked up on every call (a
+// cheap query next to the call's two stream synchronisations), so no address outlives the
+// context it was taken in.
 cudaError_t scratch_address(double **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(TPB) k_hub_clear(HArgs k)
     const bool packed = k.gd[item.g].int_weights != 0;
     const int64_t lo = (int64_t)h.slice_j[item.start] * kHubSlice;
     const int64_t cnt = h.hub_used[hh];
-    const int64_t p1 = h.hub_p1[hh];
+    const int64_t p1 = (int64_t)h.hub_p1[hh] + 1;   // the table's 2^b slots
     int32_t *Hk = h.tab_k + h.hub_tab[hh];
     float *Hv = h.tab_v + h.hub_tab[hh];
     double *Hd = h.tab_vd ? h.tab_vd + h.hub_tab[hh] : nullptr;
@@ -404,9 +404,9 @@ __global__ void k_table_clear(int32_t *k, float *v, double *vd, int64_t n, int p
 template <int CS>
 static int active_clusters()
 {
-    if (cudaFuncSetAttribute(k_hub_dsm<CS, false, kProbeQuadDouble>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDsmSmem) !=
+    if (cudaFuncSetAttribute(k_hub_dsm<CS, false, kProbeQuadDoublePow2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDsmSmem) !=
             cudaSuccess ||
-        (CS > 8 && cudaFuncSetAttribute(k_hub_dsm<CS, false, kProbeQuadDouble>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        (CS > 8 && cudaFuncSetAttribute(k_hub_dsm<CS, false, kProbeQuadDoublePow2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                        cudaSuccess)) {
         cudaGetLastError();
         return 0;
@@ -423,7 +423,7 @@ static int active_clusters()
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_hub_dsm<CS, false, kProbeQuadDouble>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_hub_dsm<CS, false, kProbeQuadDoublePow2>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -455,8 +455,8 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
         return r;
     };
     e = p.f64 ? launch_vertex_phase_f64(p, s, hook, launches)
-              : (p.probe == kProbeQuadDouble ? launch_vertex_phase<kProbeQuadDouble>(p, s, hook, launches)
-                                             : launch_vertex_phase_alt(p, s, hook, launches));
+              : (p.probe == kProbeQuadDoublePow2 ? launch_vertex_phase<kProbeQuadDoublePow2>(p, s, hook, launches)
+                                                 : launch_vertex_phase_alt(p, s, hook, launches));
     if (e != cudaSuccess) return e;
     HArgs h{};
     h.gd = p.gd;
@@ -470,8 +470,8 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
         });
         if (e != cudaSuccess) return e;
         e = p.f64 ? launch_hub_acc_phase_f64(p, h, s, hook, launches)
-                  : (p.probe == kProbeQuadDouble ? launch_hub_acc_phase<kProbeQuadDouble>(p, h, s, hook, launches)
-                                                 : launch_hub_acc_phase_alt(p, h, s, hook, launches));
+                  : (p.probe == kProbeQuadDoublePow2 ? launch_hub_acc_phase<kProbeQuadDoublePow2>(p, h, s, hook, launches)
+                                                     : launch_hub_acc_phase_alt(p, h, s, hook, launches));
         if (e != cudaSuccess) return e;
         if (p.n_hub_items[HL_SLICES] > 0) {
             h.items = p.hub_items[HL_SLICES];

@@ -11,15 +11,15 @@ cudaError_t sweep_init_constants_f64() { return init_magic(); }
 
 cudaError_t launch_vertex_phase_f64(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, int *launches)
 {
-    return p.probe == kProbeQuadDouble ? launch_vertex_phase<kProbeQuadDouble, true>(p, s, hook, launches)
-                                       : launch_vertex_phase<kProbeRuntime, true>(p, s, hook, launches);
+    return p.probe == kProbeQuadDoublePow2 ? launch_vertex_phase<kProbeQuadDoublePow2, true>(p, s, hook, launches)
+                                           : launch_vertex_phase<kProbeRuntime, true>(p, s, hook, launches);
 }
 
 cudaError_t launch_hub_acc_phase_f64(const SweepPlan &p, const HArgs &h, cudaStream_t s, LaunchHook *hook,
                                      int *launches)
 {
-    return p.probe == kProbeQuadDouble ? launch_hub_acc_phase<kProbeQuadDouble, true>(p, h, s, hook, launches)
-                                       : launch_hub_acc_phase<kProbeRuntime, true>(p, h, s, hook, launches);
+    return p.probe == kProbeQuadDoublePow2 ? launch_hub_acc_phase<kProbeQuadDoublePow2, true>(p, h, s, hook, launches)
+                                           : launch_hub_acc_phase<kProbeRuntime, true>(p, h, s, hook, launches);
 }
 
 }  // namespace lpa

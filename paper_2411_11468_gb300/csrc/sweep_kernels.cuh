@@ -135,7 +135,16 @@ __device__ __forceinline__ uint32_t cap_of_bits(uint32_t b) { return b >= 32 ? 0
 // (the default), and for comparison linear probing, quadratic probing and double hashing.
 // PROBE >= 0 fixes the scheme at compile time (the default kernels); PROBE = kProbeRuntime
 // reads it from the table (the comparison kernels, in their own translation unit).
-enum { kProbeRuntime = -1, kProbeQuadDouble = 0, kProbeLinear = 1, kProbeQuadratic = 2, kProbeDouble = 3 };
+// kProbeQuadDoublePow2 keeps Algorithm 2's recurrence (i <- i + delta, delta <- 2 delta + h2(k))
+// but takes it modulo the table's whole power-of-two allocation (2^b slots, mask p1 = 2^b - 1)
+// with multiplicative first and second hashes: the first slot is the top b bits of k times an
+// odd constant (Fibonacci hashing), the second hash is odd, so every step is odd.  It replaces
+// the Mersenne remainders (k mod p1, k mod p2) by two multiplies and masks, and it disperses
+// ids that share their low bits or have few bits set, as the unpermuted ids of R-MAT graphs do.
+enum { kProbeRuntime = -1, kProbeQuadDouble = 0, kProbeLinear = 1, kProbeQuadratic = 2, kProbeDouble = 3,
+       kProbeQuadDoublePow2 = 4 };
+constexpr uint32_t kHashMul1 = 0x9E3779B1u;   // 2^32 / golden ratio, odd
+constexpr uint32_t kHashMul2 = 0x85EBCA77u;   // odd multiplier of the second hash
 
 template <typename V, int PROBE>
 struct SplitTable {
@@ -282,12 +291,40 @@ __device__ __forceinline__ uint32_t second_step(uint32_t uk, uint32_t b, uint32_
 }
 
 template <bool SHARED, bool TRACK, typename T>
+__device__ __forceinline__ void ht_accumulate_pow2(const T &tab, uint32_t mask, uint32_t b, int32_t k, typename T::Val v,
+                                                   typename BestOf<typename T::Val>::type &best, unsigned &fallbacks,
+                                                   uint32_t *ucnt, int32_t *ulist)
+{
+    const uint32_t uk = (uint32_t)k;
+    const uint32_t sh = 32u - b;                       // 1 <= b <= 31
+    uint32_t i = (uk * kHashMul1) >> sh;
+    const uint32_t h2 = ((uk * kHashMul2) >> sh) | 1u;
+    uint32_t delta = 1u;
+#pragma unroll 1
+    for (int t = 0; t < kMaxRetries; ++t) {
+        if (try_slot<SHARED, TRACK>(tab, (size_t)i * tab.stride, k, v, best, ucnt, ulist)) return;
+        i = (i + delta) & mask;
+        delta = (2u * delta + h2) & mask;
+    }
+    ++fallbacks;
+#pragma unroll 1
+    for (uint32_t u = 0; u <= mask; ++u) {
+        const uint32_t q = (i + u) & mask;
+        if (try_slot<SHARED, TRACK>(tab, (size_t)q * tab.stride, k, v, best, ucnt, ulist)) return;
+    }
+}
+
+template <bool SHARED, bool TRACK, typename T>
 __device__ __forceinline__ void ht_accumulate(const T &tab, uint32_t p1, uint32_t b, int32_t k, typename T::Val v,
                                               typename BestOf<typename T::Val>::type &best, unsigned &fallbacks,
                                               uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
 {
     const uint32_t uk = (uint32_t)k;
     const int mode = T::kProbe >= 0 ? T::kProbe : tab.probe;
+    if (mode == kProbeQuadDoublePow2) {               // the whole 2^b allocation, mask p1
+        ht_accumulate_pow2<SHARED, TRACK>(tab, p1, b, k, v, best, fallbacks, ucnt, ulist);
+        return;
+    }
     uint32_t i = mod_mersenne(uk, b, p1);
     uint32_t delta = (p1 > 1u) ? 1u : 0u;
     uint32_t step = 0xFFFFFFFFu;                      // (k mod p2) mod p1, on first need
@@ -426,10 +463,11 @@ __device__ __forceinline__ void clear_table_vec(const PackedTable<PROBE> &T, uin
 }
 
 // Clear of a thread's private interleaved table (slot s at s * stride).
+// Clears slots [0, p1] (the whole 2^b allocation, which the power-of-two probe uses).
 template <typename V, int PROBE>
 __device__ __forceinline__ void clear_table_private(const SplitTable<V, PROBE> &T, uint32_t p1)
 {
-    for (uint32_t s = 0; s < p1; ++s) {
+    for (uint32_t s = 0; s <= p1; ++s) {
         T.k[(size_t)s * T.stride] = kEmpty;
         T.v[(size_t)s * T.stride] = V(0);
     }
@@ -438,7 +476,7 @@ __device__ __forceinline__ void clear_table_private(const SplitTable<V, PROBE> &
 template <int PROBE>
 __device__ __forceinline__ void clear_table_private(const PackedTable<PROBE> &T, uint32_t p1)
 {
-    for (uint32_t s = 0; s < p1; ++s) T.h[(size_t)s * T.stride] = kEmptySlot;
+    for (uint32_t s = 0; s <= p1; ++s) T.h[(size_t)s * T.stride] = kEmptySlot;
 }
 
 // The per-sweep view of one graph: what the sweep kernels read and write for an item of
@@ -851,6 +889,302 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Low-degree buckets (thread, group and warp by default): a warp per batch of vertices, with
+// the batch's rows flattened.  The warp fetches the list entry, processed flag and row bounds
+// of 32 vertices at once, packs as many of them as fit its shared-memory region into a
+// sub-batch (each vertex gets its own table of 2^b slots, 2^b - 1 >= D << tshift), and then
+// scans the sub-batch's rows as one run of entries: in each round lane L takes flat entry
+// f0 + L, finds its vertex (segment) from a bit mask of the segment starts in the round's
+// window (one warp reduction per 32 entries), and inserts the neighbour label into that
+// vertex's table.  Every lane has an entry in every round but the last, whatever the
+// degrees.  A lane's running maximum (sum << 32 | ~label) is folded into its segment's
+// shared maximum when its entries pass into the next segment.  Then one lane per vertex
+// takes the decision of Algorithm 1.  Integer weights keep every sum exact, so the tables
+// and the decisions do not depend on which lane adds first.
+constexpr int kFlatWarps = 8;            // warps per block (256 threads)
+constexpr int kFlatMinSlots = 1024;      // table slots per warp region (8 bytes each) at least
+constexpr int kFlatU = 2;                // 32-entry windows per round (loads in flight per lane)
+
+__device__ __forceinline__ unsigned lanemask_le()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+template <typename V, int PROBE>
+__device__ __forceinline__ void flat_table(SplitTable<V, PROBE> &T, unsigned char *region, int wslots, uint32_t tb)
+{
+    T.k = (int32_t *)region + tb;
+    T.v = (V *)(region + (size_t)wslots * sizeof(int32_t)) + tb;
+    T.stride = 1;
+}
+
+template <int PROBE>
+__device__ __forceinline__ void flat_table(PackedTable<PROBE> &T, unsigned char *region, int, uint32_t tb)
+{
+    T.h = (unsigned long long *)region + tb;
+    T.stride = 1;
+}
+
+// Clears slots [0, total) of a warp region with 16-byte stores (rounded up to whole stores;
+// the region's slot count is a multiple of 4).
+template <typename V, int PROBE>
+__device__ __forceinline__ void flat_clear(const SplitTable<V, PROBE> &, unsigned char *region, int wslots, uint32_t total,
+                                           int lane)
+{
+    int4 *K4 = reinterpret_cast<int4 *>(region);
+    int4 *V4 = reinterpret_cast<int4 *>(region + (size_t)wslots * sizeof(int32_t));
+    constexpr uint32_t per = sizeof(V) / sizeof(int32_t);
+    for (uint32_t q = lane; q < ((total + 3u) >> 2); q += 32) {        // the region holds whole 4-slot groups
+        K4[q] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
+#pragma unroll
+        for (uint32_t r = 0; r < per; ++r) V4[q * per + r] = make_int4(0, 0, 0, 0);
+    }
+}
+
+template <int PROBE>
+__device__ __forceinline__ void flat_clear(const PackedTable<PROBE> &, unsigned char *region, int, uint32_t total, int lane)
+{
+    int4 *H4 = reinterpret_cast<int4 *>(region);
+    for (uint32_t q = lane; q < ((total + 1u) >> 1); q += 32) H4[q] = make_int4(0, kEmpty, 0, kEmpty);
+}
+
+template <typename V, bool PULL, int PROBE>
+__global__ void __launch_bounds__(kFlatWarps * 32, 3) k_flat(KArgs k)
+{
+    if (*k.active == 0) return;                        // every graph has stopped
+    extern __shared__ __align__(16) unsigned char smem[];
+    using Tab = typename TableFor<V, kPackShared, PROBE>::type;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    const int wslots = k.slots;                        // slots per warp region
+    unsigned char *region = smem + (size_t)wid * wslots * 8;
+    __shared__ long long s_eoff[kFlatWarps][32];       // row start minus the segment's first flat index
+    __shared__ int32_t s_vtx[kFlatWarps][32];          // vertex of each segment
+    __shared__ uint32_t s_tab[kFlatWarps][32];         // table base slot << 5 | b
+    __shared__ unsigned long long s_best[kFlatWarps][32];
+    __shared__ int32_t s_seen[kFlatWarps][32];
+    __shared__ int2 s_mov[kFlatWarps][32];
+    int2 *mbuf = s_mov[wid];
+    int nmov = 0;
+    int cur_g = -1;
+    SweepView a{};
+    Tab tab;
+    unsigned fb = 0, c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(k.queue, 1u);
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it >= k.n_items) break;
+        const WorkItem item = k.items[it];
+        if (item.g != cur_g) {
+            if (cur_g >= 0) {
+                movers_flush(a.mover_count, a.mover_v, a.mover_c, mbuf, nmov);
+                warp_flush(a, k.kslot, c_act, c_edges, c_moved, c_marks, fb);
+                fb = c_act = c_edges = c_moved = c_marks = 0;
+            }
+            cur_g = item.g;
+            a = view_of(k.gd, item.g);
+            tab.probe = a.probe;
+        }
+        if (a.done || (a.pull != 0) != PULL) continue;                // the other launch takes it
+        for (int64_t base = 0; base < item.count; base += 32) {       // uniform per warp
+            // lane L: vertex base + L of the item, its flag taken (push sweeps), its row
+            int32_t v = -1, cur = 0;
+            int64_t o0 = 0;
+            uint32_t D = 0;
+            if (base + lane < item.count) {
+                v = __ldg(a.lists + item.start + base + lane);
+                bool cand = PULL;
+                if (!PULL && a.flag_cur[v] != 0) {
+                    a.flag_cur[v] = 0;                 // mark processed
+                    cand = true;
+                }
+                if (cand) {
+                    o0 = a.off[v];
+                    D = (uint32_t)(a.off[v + 1] - o0);
+                    cur = PULL ? (int32_t)((uint32_t)a.C[v] & kLabelMask) : a.C[v];
+                }
+            }
+            // the launcher sizes the region for the bucket's largest degree, so cap <= wslots
+            const uint32_t b = D ? cap_bits(D << a.tshift) : 0u;
+            const uint32_t cap = D ? (1u << b) : 0u;
+            const uint32_t cincl = warp_incl_scan(cap);
+            uint32_t consumed = 0;                     // slots of the earlier sub-batches
+            bool handled = (D == 0);
+#pragma unroll 1
+            while (true) {                             // uniform per warp
+                const bool in = !handled && (cincl - consumed <= (uint32_t)wslots);
+                const unsigned mask = __ballot_sync(0xFFFFFFFFu, in);
+                if (mask == 0) break;                  // every vertex of the batch is done
+                const int ci = __popc(mask & lanemask_lt());           // segment index
+                const uint32_t Dm = in ? D : 0u;
+                const uint32_t dincl = warp_incl_scan(Dm);
+                const uint32_t start = dincl - Dm;                     // first flat entry of the segment
+                const int last = 31 - __clz(mask);
+                const uint32_t E = __shfl_sync(0xFFFFFFFFu, dincl, last);
+                const uint32_t total = __shfl_sync(0xFFFFFFFFu, cincl, last) - consumed;
+                if (in) {
+                    s_eoff[wid][ci] = (long long)o0 - (long long)start;
+                    s_vtx[wid][ci] = v;
+                    s_tab[wid][ci] = ((cincl - cap - consumed) << 5) | b;
+                    s_best[wid][ci] = 0ull;
+                    s_seen[wid][ci] = 0;
+                }
+                flat_clear(tab, region, wslots, total, lane);            // hashtableClear of every table
+                __syncwarp();
+                unsigned long long best = 0ull;
+                int bseg = 0;                          // segment of `best`
+                uint32_t before = 0;                   // segment starts below the round's window
+#pragma unroll 1
+                for (uint32_t f0 = 0; f0 < E; f0 += 32 * kFlatU) {
+                    bool has[kFlatU];
+                    int seg[kFlatU];
+                    int32_t kk[kFlatU];
+                    V wv[kFlatU];
+                    int64_t ee[kFlatU];
+                    int32_t jj[kFlatU];
+#pragma unroll
+                    for (int u = 0; u < kFlatU; ++u) {                   // segment of each entry
+                        const uint32_t w0 = f0 + 32u * u;
+                        const unsigned bit = (in && start >= w0 && start < w0 + 32u) ? (1u << (start - w0)) : 0u;
+                        const unsigned M = __reduce_or_sync(0xFFFFFFFFu, bit);
+                        seg[u] = (int)(before + __popc(M & lanemask_le())) - 1;
+                        before += __popc(M);
+                        has[u] = w0 + lane < E;
+                        ee[u] = has[u] ? s_eoff[wid][seg[u]] + (long long)(w0 + lane) : 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kFlatU; ++u) {                   // indices and weights
+                        jj[u] = has[u] ? a.idx[ee[u]] : 0;
+                        wv[u] = (has[u] && a.w) ? to_value<V>(a.w[ee[u]]) : V(1);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kFlatU; ++u) {                   // labels (self-loops not inserted)
+                        if (PULL) {
+                            const uint32_t cj = has[u] ? (uint32_t)a.C[jj[u]] : 0u;
+                            if (cj & kMovedBit) s_seen[wid][seg[u]] = 1;
+                            kk[u] = (int32_t)(cj & kLabelMask);
+                        } else {
+                            kk[u] = has[u] ? a.C[jj[u]] : 0;
+                        }
+                        has[u] = has[u] && jj[u] != s_vtx[wid][seg[u]];
+                    }
+                    // inserts (sg, key, w) into segment sg's table, folding the lane's maximum of the
+                    // previous segment into that segment's shared maximum first
+                    auto insert = [&](int sg, int32_t key, V w) {
+                        if (sg != bseg) {
+                            if (best) atomicMax(&s_best[wid][bseg], best);
+                            best = 0ull;
+                            bseg = sg;
+                        }
+                        const uint32_t tw = s_tab[wid][sg];
+                        const uint32_t bb = tw & 31u;
+                        Tab t = tab;
+                        flat_table(t, region, wslots, tw >> 5);
+                        ht_accumulate<true, false>(t, cap_of_bits(bb), bb, key, w, best, fb);
+                    };
+#pragma unroll 1
+                    for (int u = 0; u < kFlatU; ++u) {
+                        // lanes holding the same label of the same segment: the lowest inserts their
+                        // summed weight once (up to kPeel labels per step): after the first sweeps most
+                        // neighbours of a vertex share a few labels, and same-slot atomics serialise
+                        unsigned pend = __ballot_sync(0xFFFFFFFFu, has[0]);
+#pragma unroll 1
+                        for (int r = 0; r < kPeel && pend; ++r) {
+                            const int leader = __ffs(pend) - 1;
+                            const int32_t kl = __shfl_sync(0xFFFFFFFFu, kk[0], leader);
+                            const int sl = __shfl_sync(0xFFFFFFFFu, seg[0], leader);
+                            const bool mine = has[0] && kk[0] == kl && seg[0] == sl;
+                            const unsigned same = __ballot_sync(0xFFFFFFFFu, mine);
+                            if (__popc(same) < 2) break;
+                            V sum = mine ? wv[0] : V(0);
+                            if constexpr (std::is_same<V, uint32_t>::value) {
+                                sum = __reduce_add_sync(0xFFFFFFFFu, sum);
+                            } else {
+#pragma unroll
+                                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+                            }
+                            if (lane == leader) insert(sl, kl, sum);
+                            if (mine) has[0] = false;
+                            pend &= ~same;
+                        }
+                        if (has[0]) insert(seg[0], kk[0], wv[0]);
+#pragma unroll
+                        for (int q = 0; q + 1 < kFlatU; ++q) {
+                            has[q] = has[q + 1];
+                            seg[q] = seg[q + 1];
+                            kk[q] = kk[q + 1];
+                            wv[q] = wv[q + 1];
+                        }
+                        has[kFlatU - 1] = false;
+                    }
+                }
+                if (best) atomicMax(&s_best[wid][bseg], best);
+                __syncwarp();
+                // one lane per vertex: the move rule of Algorithm 1
+                int32_t cstar = -1;
+                bool moved = false;
+                if (in) {
+                    const unsigned long long bw = s_best[wid][ci];
+                    const bool act = PULL ? (s_seen[wid][ci] != 0) : true;
+                    moved = act && decide(bw, cur, a.pl, cstar);
+                    if (act) {
+                        c_act += 1;
+                        c_edges += D;
+                    }
+                    if (moved) {
+                        c_moved += 1;
+                        if (a.mark) c_marks += D;
+                        if (a.async_mode) {
+                            a.C[v] = cstar;
+                            __threadfence();
+                        }
+                    }
+                }
+                if (!a.async_mode) movers_push(a, mbuf, nmov, moved, v, cstar);
+                if (a.mark) {                          // mark the movers' neighbours
+                    unsigned mm = __ballot_sync(0xFFFFFFFFu, moved);
+                    while (mm) {
+                        const int src = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        const int64_t r0 = __shfl_sync(0xFFFFFFFFu, o0, src);
+                        const uint32_t rd = __shfl_sync(0xFFFFFFFFu, D, src);
+                        for (uint32_t q = lane; q < rd; q += 32) a.flag_next[a.idx[r0 + q]] = 1;
+                    }
+                }
+                __syncwarp();                          // the region and the segment data are free
+                consumed = __shfl_sync(0xFFFFFFFFu, cincl, last);
+                handled = handled || in;
+            }
+        }
+    }
+    if (cur_g >= 0) {
+        movers_flush(a.mover_count, a.mover_v, a.mover_c, mbuf, nmov);
+        warp_flush(a, k.kslot, c_act, c_edges, c_moved, c_marks, fb);
+    }
+}
+
 // One thread block per vertex; the table (up to k.slots entries) lives in dynamic smem.
 // Persistent: each block takes work items from the queue; the list entries, processed flags
 // and row bounds of up to 32 vertices of the item are fetched at once into shared memory.
@@ -1084,6 +1418,156 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
     }
 }
 
+// Two-pass accumulation of hubs with integer label sums (packed slots) and HBM tables.
+//
+// Pass 1 (k_hub_part, a block per kPartChunk-entry chunk of a hub's row): the chunk's labels
+// are summed in a shared-memory table (Algorithm 2's accumulate), then every distinct (label,
+// sum) pair of the chunk goes to label partition part(label) of the hub: a block-wide count
+// per partition, one global reservation per partition, and the pairs written to the
+// partition's buffer.  Pass 2 (k_hub_merge, a block per partition): the partition's pairs are
+// summed in a shared-memory table, whose running maximum (sum << 32 | ~label) is folded into
+// the hub's maximum.  Every pair of one label goes to the same partition, so a partition's
+// table holds the label's whole sum K_{i->c}, and the hub's maximum over its partitions is the
+// arg-max of Algorithm 1 with the smallest label on ties, as in the single-pass tables.
+// Instead of round-tripping the hub tables through DRAM with global atomics, the sweep streams
+// the pairs once out and once in.  A partition whose reservations pass kPartCap overflows: its
+// pairs beyond the cap go to the hub's HBM table at once, and pass 2 sends the buffered ones
+// there too, so that each label's sum is whole in one place.
+constexpr int kPartThreads = 512;
+constexpr uint32_t kPartTableBits = 13;              // 8192 slots: load <= 1/2 for a full chunk
+constexpr uint32_t kHashMul3 = 0xC2B2AE3Du;          // odd multiplier of the partition hash
+
+__device__ __forceinline__ uint32_t part_of(int32_t k, uint32_t pb)
+{
+    return pb ? (((uint32_t)k * kHashMul3) >> (32u - pb)) : 0u;
+}
+
+template <bool PULL, int PROBE>
+__global__ void __launch_bounds__(kPartThreads, 3) k_hub_part(HArgs k)
+{
+    if (*k.active == 0) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *T = (unsigned long long *)smem;                 // [2^kPartTableBits]
+    uint32_t *s_cnt = (uint32_t *)(smem + ((size_t)8 << kPartTableBits)); // [2^kPartMaxBits] counts, then fill
+    uint32_t *s_base = s_cnt + (1 << kPartMaxBits);                       // [2^kPartMaxBits] reservations
+    __shared__ unsigned long long s_best[kPartThreads / 32];
+    const WorkItem item = k.items[blockIdx.x];
+    const SweepView a = view_of(k.gd, item.g);
+    if (a.done || (a.pull != 0) != PULL) return;      // the other launch takes it
+    const HubArgs &h = k.gd[item.g].hub;
+    const int64_t c = item.start;
+    const int hh = h.pc_h[c];
+    if (!h.hub_act[hh]) return;
+    const int32_t v = h.hub_v[hh];
+    const int64_t e0 = h.pc_e0[c], e1 = h.pc_e1[c];
+    const uint32_t pb = h.hub_pb[hh], np = 1u << pb;
+    const int32_t pbase = h.hub_pbase[hh];
+    constexpr uint32_t b = kPartTableBits;
+    const uint32_t p1 = cap_of_bits(b);
+    const PackedTable<PROBE> tab{T, 1, a.probe};
+    clear_table_vec(tab, p1, threadIdx.x, kPartThreads);
+    for (uint32_t q = threadIdx.x; q < np; q += kPartThreads) s_cnt[q] = 0;
+    __syncthreads();
+    unsigned fb = 0;
+    unsigned long long best = 0ull;                    // (not used: pass 2 takes the maximum)
+    uint32_t seen = 0;
+    scan_row<32, true, false, 2, PULL>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab, p1, b,
+                                       best, fb, seen, nullptr, nullptr, kPartThreads * 2);
+    if (PULL) {
+        if (__syncthreads_or((seen & kMovedBit) != 0) && threadIdx.x == 0) h.hub_seen[hh] = 1;
+    } else {
+        __syncthreads();
+    }
+    // pairs per partition, one reservation per partition, then the pairs themselves
+    for (uint32_t q = threadIdx.x; q <= p1; q += kPartThreads) {
+        const unsigned long long x = T[q];
+        if ((uint32_t)(x >> 32) != 0xFFFFFFFFu) atomicAdd(&s_cnt[part_of((int32_t)(x >> 32), pb)], 1u);
+    }
+    __syncthreads();
+    for (uint32_t q = threadIdx.x; q < np; q += kPartThreads) {
+        const uint32_t n = s_cnt[q];
+        s_base[q] = n ? atomicAdd(h.part_cnt + pbase + q, n) : 0u;
+        s_cnt[q] = 0;
+    }
+    __syncthreads();
+    unsigned long long obest = 0ull;                   // overflow inserts into the HBM table
+    const PackedTable<PROBE, true> htab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
+    for (uint32_t q = threadIdx.x; q <= p1; q += kPartThreads) {
+        const unsigned long long x = T[q];
+        const int32_t key = (int32_t)(x >> 32);
+        if (key == kEmpty) continue;
+        const uint32_t part = part_of(key, pb);
+        const uint32_t pos = s_base[part] + atomicAdd(&s_cnt[part], 1u);
+        if (pos < (uint32_t)kPartCap) {
+            h.pairs[(size_t)(pbase + part) * kPartCap + pos] = x;
+        } else {
+            h.part_ovf[pbase + part] = 1;
+            ht_accumulate<true, true>(htab, h.hub_p1[hh], h.hub_b[hh], key, (uint32_t)x, obest, fb, h.hub_used + hh,
+                                      h.used_list + h.used_base[hh]);
+        }
+    }
+    if (obest) atomicMax(h.hub_best + hh, obest);
+    if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
+}
+
+template <int PROBE>
+__global__ void __launch_bounds__(kPartThreads, 3) k_hub_merge(HArgs k)
+{
+    if (*k.active == 0) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_best[kPartThreads / 32];
+    __shared__ uint32_t s_n;
+    __shared__ int32_t s_ovf;
+    const WorkItem item = k.items[blockIdx.x];
+    const SweepView a = view_of(k.gd, item.g);
+    if (a.done) return;
+    const HubArgs &h = k.gd[item.g].hub;
+    const int32_t q = (int32_t)item.start;
+    const int hh = h.part_h[q];
+    if (threadIdx.x == 0) {
+        const uint32_t c = h.part_cnt[q];
+        s_n = c < (uint32_t)kPartCap ? c : (uint32_t)kPartCap;
+        s_ovf = h.part_ovf[q];
+        h.part_cnt[q] = 0;                             // ready for the next sweep
+        h.part_ovf[q] = 0;
+    }
+    __syncthreads();
+    const uint32_t n = s_n;
+    if (n == 0) return;
+    const unsigned long long *P = h.pairs + (size_t)q * kPartCap;
+    unsigned fb = 0;
+    unsigned long long best = 0ull;
+    if (!s_ovf) {
+        uint32_t b = cap_bits(n << 1);
+        if (b > kPartTableBits) b = kPartTableBits;
+        const uint32_t p1 = cap_of_bits(b);
+        const PackedTable<PROBE> tab{(unsigned long long *)smem, 1, a.probe};
+        clear_table_vec(tab, p1, threadIdx.x, kPartThreads);
+        __syncthreads();
+        for (uint32_t i0 = threadIdx.x & ~31u; i0 < n; i0 += kPartThreads) {     // uniform per warp
+            const uint32_t i = i0 + (threadIdx.x & 31u);
+            const bool has = i < n;
+            const unsigned long long x = has ? P[i] : 0ull;
+            group_insert<32, true, false>(tab, p1, b, has, (int32_t)(x >> 32), (uint32_t)x, best, fb);
+        }
+    } else {                                           // the partition overflowed: all of it to HBM
+        const PackedTable<PROBE, true> htab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
+        for (uint32_t i = threadIdx.x; i < n; i += kPartThreads) {
+            const unsigned long long x = P[i];
+            ht_accumulate<true, true>(htab, h.hub_p1[hh], h.hub_b[hh], (int32_t)(x >> 32), (uint32_t)x, best, fb,
+                                      h.hub_used + hh, h.used_list + h.used_base[hh]);
+        }
+    }
+    best = group_max<32>(best);
+    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kPartThreads / 32; ++w) best = umax64(best, s_best[w]);
+        if (best) atomicMax(h.hub_best + hh, best);
+    }
+    if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
+}
+
 // Hubs whose table fits in the shared memory of a cluster of CS blocks (1024 threads each).
 // Persistent: rank 0 takes a hub from the queue and broadcasts it; every block clears its
 // slice of the hub's table, the cluster synchronises, every block scans 1/CS of the row and
@@ -1201,6 +1685,20 @@ static cudaError_t launch_gv(const KArgs &k, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <typename V, bool PULL, int PROBE>
+static cudaError_t launch_flat(const KArgs &k0, cudaStream_t s)
+{
+    KArgs k = k0;
+    k.slots = k.slots > kFlatMinSlots ? k.slots : kFlatMinSlots;     // a region holds the bucket's largest table
+    const size_t smem = (size_t)kFlatWarps * k.slots * 8;
+    cudaError_t e = set_smem(k_flat<V, PULL, PROBE>, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = persistent_grid(k_flat<V, PULL, PROBE>, kFlatWarps * 32, smem,
+                                           ((int64_t)k.n_items + kFlatWarps - 1) / kFlatWarps);
+    k_flat<V, PULL, PROBE><<<(unsigned)(blocks < 1 ? 1 : blocks), kFlatWarps * 32, smem, s>>>(k);
+    return cudaGetLastError();
+}
+
 // Value type of the tables: double with F64 (lpa_tuning.float_values = 2), else uint32 for
 // integer sums and float for the rest.
 template <int G, int TPB, bool PULL, int PROBE, bool F64>
@@ -1255,6 +1753,8 @@ static cudaError_t launch_vertex(const SweepPlan &p, int b, cudaStream_t s)
     k.active = p.active_count;
     k.kslot = b;                                       // bucket index == kernel slot
     const bool iw = p.int_weights != 0;
+    if (!F64 && b <= B_WARP && ((p.flat_buckets >> b) & 1))   // flattened rows, a warp per batch of vertices
+        return iw ? launch_flat<uint32_t, PULL, PROBE>(k, s) : launch_flat<float, PULL, PROBE>(k, s);
     switch (b) {
     case B_THREAD: return launch_g<1, 128, PULL, PROBE, F64>(k, iw, s);
     case B_GROUP:
@@ -1341,6 +1841,28 @@ static cudaError_t launch_hub_acc_phase(const SweepPlan &p, const HArgs &h, cuda
         if (pull && r == cudaSuccess) {
             r = set_smem(k_hub_acc<1024, true, PROBE, F64>, smem);
             if (r == cudaSuccess) k_hub_acc<1024, true, PROBE, F64><<<p.n_hub_items[HL_ACC], 1024, smem, s>>>(ha);
+            if (launches) ++*launches;
+        }
+    }
+    if (!F64 && p.n_hub_items[HL_PACC] > 0 && r == cudaSuccess) {     // two-pass hubs
+        HArgs ha = h;
+        ha.items = p.hub_items[HL_PACC];
+        const size_t smem_a = ((size_t)8 << kPartTableBits) + 2 * sizeof(uint32_t) * ((size_t)1 << kPartMaxBits);
+        if (push && r == cudaSuccess) {
+            r = set_smem(k_hub_part<false, PROBE>, smem_a);
+            if (r == cudaSuccess) k_hub_part<false, PROBE><<<p.n_hub_items[HL_PACC], kPartThreads, smem_a, s>>>(ha);
+            if (launches) ++*launches;
+        }
+        if (pull && r == cudaSuccess) {
+            r = set_smem(k_hub_part<true, PROBE>, smem_a);
+            if (r == cudaSuccess) k_hub_part<true, PROBE><<<p.n_hub_items[HL_PACC], kPartThreads, smem_a, s>>>(ha);
+            if (launches) ++*launches;
+        }
+        if (r == cudaSuccess && p.n_hub_items[HL_PMERGE] > 0) {
+            ha.items = p.hub_items[HL_PMERGE];
+            const size_t smem_b = (size_t)8 << kPartTableBits;
+            r = set_smem(k_hub_merge<PROBE>, smem_b);
+            if (r == cudaSuccess) k_hub_merge<PROBE><<<p.n_hub_items[HL_PMERGE], kPartThreads, smem_b, s>>>(ha);
             if (launches) ++*launches;
         }
     }

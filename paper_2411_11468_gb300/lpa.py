@@ -91,7 +91,8 @@ class Tuning(ct.Structure):
     _fields_ = [(name, ct.c_int32) for name in (
         "thread_max", "group_max", "group_lanes", "warp_max", "cta_max", "cta_threads", "cta_large_max",
         "cta_large_threads", "hub_chunk", "hub_table_shift", "smem_table_shift", "cta_xl_max",
-        "cta_xl_threads", "item_vertices", "float_values", "hub_cluster", "probe")] + [("reserved", ct.c_int32 * 3)]
+        "cta_xl_threads", "item_vertices", "float_values", "hub_cluster", "probe", "flat_buckets", "hub_two_pass")] + \
+        [("reserved", ct.c_int32 * 1)]
 
     def to_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

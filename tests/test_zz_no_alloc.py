@@ -1,4 +1,5 @@
-"""lpa_modularity_noalloc, called through the C ABI, against lpa_modularity on the same labels.
+"""lpa_modularity_noalloc, called through the C ABI, against the oracle's Eq. 1 and against
+lpa_modularity on the same labels.
 
 The no-allocation entry point serves callers that cannot allocate device memory; it keeps its
 scratch in a fixed array compiled into the library, shared by every call.  Two calls in a row
@@ -10,6 +11,7 @@ import ctypes as ct
 import pytest
 import torch
 
+import oracle
 from paper_2411_11468_gb300 import graphgen as gg
 
 pytestmark = pytest.mark.gpu
@@ -55,9 +57,11 @@ def test_noalloc_matches_handle_modularity_twice(libs, which):
     g.run(0.05, 20, 4, lpa.SYNC)
     labels = g.labels()
     q_ref = g.modularity()
+    q_orc = oracle.modularity(oracle.Graph.of(csr), labels.cpu())
     for _ in range(2):
         rc, q = noalloc_q(L, dev, labels, stream)
         assert rc == lpa.OK
+        assert abs(q - q_orc) < 1e-12, (q, q_orc)
         assert abs(q - q_ref) < 1e-12, (q, q_ref)
     # a different labelling right after: the shared scratch must not leak the previous sums
     ident = torch.arange(dev.n, dtype=torch.int32, device="cuda")
@@ -65,6 +69,7 @@ def test_noalloc_matches_handle_modularity_twice(libs, which):
     q_ref2 = g.modularity()
     rc, q2 = noalloc_q(L, dev, ident, stream)
     assert rc == lpa.OK and abs(q2 - q_ref2) < 1e-12
+    assert abs(q2 - oracle.modularity(oracle.Graph.of(csr), ident.cpu())) < 1e-12
 
 
 def test_noalloc_rejects_oversized_and_bad_labels(libs):
