@@ -69,7 +69,7 @@ def lib():
         L.orc_cross_check.restype = i64
         L.orc_lpa_async.argtypes = L.orc_lpa_sync.argtypes
         L.orc_lpa_async.restype = ct.c_int
-        L.orc_lpa_async_waves.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, P, i32, P, P, P, P, P, P]
+        L.orc_lpa_async_waves.argtypes = [i64, P, P, P, dbl, ct.c_int, ct.c_int, ct.c_int, P, P, i32, P, P, P, P, P, P]
         L.orc_lpa_async_waves.restype = ct.c_int
         L.orc_sweep_range.argtypes = [i64, P, P, P, ct.c_int, i64, i64, P, P]
         L.orc_sweep_range.restype = i64
@@ -176,25 +176,29 @@ def lpa_async(g: Graph, tol=0.05, max_iters=20, pl_period=4, labels=None, active
 
 
 def lpa_async_waves(g: Graph, wave_of, tol=0.05, max_iters=20, pl_period=4, labels=None, active=None,
-                    start_iter=0):
-    """Asynchronous LPA under a wave schedule: each sweep runs the waves 0, 1, ... in turn
-    (vertex i in wave wave_of[i]); a wave reads the labels and flags as they stand at its
-    start and its moves and marks land at its end.  One vertex per wave in id order is
-    lpa_async; a single wave is lpa_sync."""
+                    start_iter=0, take_of=None):
+    """Asynchronous LPA under a wave schedule: each sweep runs the waves 0, 1, ... in turn;
+    vertex i takes its processed flag when wave take_of[i] starts (default: wave_of[i]) and
+    decides in wave wave_of[i], on the labels as they stand when that wave starts; a wave's
+    moves and marks land at its end.  One vertex per wave in id order is lpa_async; a single
+    wave is lpa_sync."""
     W = _np(wave_of, np.int32)
     if W.size != g.n:
         raise ValueError("wave_of needs one entry per vertex")
+    T = None if take_of is None else _np(take_of, np.int32)
+    if T is not None and T.size != g.n:
+        raise ValueError("take_of needs one entry per vertex")
     n_waves = int(W.max()) + 1 if W.size else 1
     L = lib()
     out = _run(lambda n, o, i, w, t, m, p, s, *rest: _waves_rc(L.orc_lpa_async_waves(n, o, i, w, t, m, p, s, _p(W),
-                                                                                       n_waves, *rest)),
+                                                                                       _p(T), n_waves, *rest)),
                g, tol, max_iters, pl_period, labels, active, start_iter)
     return out
 
 
 def _waves_rc(rc):
     if rc == -2:
-        raise ValueError("wave index outside [0, n_waves)")
+        raise ValueError("wave index outside [0, n_waves), or a flag taken after its vertex decides")
     return rc
 
 

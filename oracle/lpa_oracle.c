@@ -261,62 +261,80 @@ int orc_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, const float
 }
 
 /* Asynchronous LPA under a wave schedule: a reading of Section 4 item 1 for a sweep that
- * many threads run at once.  Each sweep visits the waves 0, 1, ..., n_waves - 1 in turn;
- * vertex i belongs to wave wave_of[i].  Within a wave every flagged vertex is marked
- * processed and computes c* from the labels as they stand when the wave starts (no
- * vertex of the wave sees another's move); the moves of the wave and the neighbour marks
- * of its movers take effect when the wave ends, before the next wave starts.  So a
- * schedule of one vertex per wave in id order is orc_lpa_async, and one wave holding every
- * vertex is orc_lpa_sync; a parallel sweep sits between the two.  Pick-Less and the stop
- * rule are those of Algorithm 1.  Returns 0, -1 on allocation failure, -2 for a wave
- * index outside [0, n_waves). */
+ * many threads run at once.  Each sweep visits the waves 0, 1, ..., n_waves - 1 in turn.
+ * Vertex i takes its processed flag (reads it and marks itself processed) when wave
+ * take_of[i] starts, and decides in wave wave_of[i] >= take_of[i]: if its flag was set when
+ * taken, it computes c* from the labels as they stand when its deciding wave starts (no
+ * vertex of a wave sees another's move of the same wave).  The moves of a wave and the
+ * neighbour marks of its movers take effect when the wave ends.  take_of = NULL takes every
+ * flag in the vertex's deciding wave.  So a schedule of one vertex per wave in id order is
+ * orc_lpa_async, and one wave holding every vertex is orc_lpa_sync; a parallel sweep sits
+ * between the two.  Pick-Less and the stop rule are those of Algorithm 1.  Returns 0, -1 on
+ * allocation failure, -2 for a wave index outside [0, n_waves) or a take after the decision. */
+static int orc_bucket_by(int64_t n, const int32_t *key, int32_t n_keys, int64_t **first_out, int64_t **member_out)
+{
+    int64_t *first = (int64_t *)calloc((size_t)n_keys + 1, sizeof(int64_t));
+    int64_t *member = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *fill = (int64_t *)malloc((size_t)n_keys * sizeof(int64_t));
+    if (!first || !member || !fill) {
+        free(first);
+        free(member);
+        free(fill);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i) ++first[key[i] + 1];
+    for (int32_t q = 0; q < n_keys; ++q) first[q + 1] += first[q];
+    memcpy(fill, first, (size_t)n_keys * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) member[fill[key[i]]++] = i;     /* ascending ids per key */
+    free(fill);
+    *first_out = first;
+    *member_out = member;
+    return 0;
+}
+
 int orc_lpa_async_waves(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                         double tol, int max_iters, int pl_period, int start_iter,
-                        const int32_t *wave_of, int32_t n_waves,
+                        const int32_t *wave_of, const int32_t *take_of, int32_t n_waves,
                         int32_t *C, uint8_t *active, int64_t *dN, int32_t *iters, int32_t *converged,
                         int64_t *edges)
 {
     *converged = 0;
     *iters = start_iter;
     if (n <= 0) return 0;
+    const int32_t *take = take_of ? take_of : wave_of;
     for (int64_t i = 0; i < n; ++i)
-        if (wave_of[i] < 0 || wave_of[i] >= n_waves) return -2;
-    /* members of each wave, ascending ids (counting sort by wave) */
-    int64_t *first = (int64_t *)calloc((size_t)n_waves + 1, sizeof(int64_t));
-    int64_t *member = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+        if (wave_of[i] < 0 || wave_of[i] >= n_waves || take[i] < 0 || take[i] > wave_of[i]) return -2;
+    int64_t *first = NULL, *member = NULL, *tfirst = NULL, *tmember = NULL;
     int32_t *newc = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    uint8_t *taken = (uint8_t *)malloc((size_t)n);
     orc_work wk;
-    if (!first || !member || !newc || orc_work_alloc(&wk, orc_max_degree(n, off)) != 0) {
+    int bad = !newc || !taken || orc_bucket_by(n, wave_of, n_waves, &first, &member) != 0 ||
+              orc_bucket_by(n, take, n_waves, &tfirst, &tmember) != 0;
+    if (!bad && orc_work_alloc(&wk, orc_max_degree(n, off)) != 0) bad = 1;
+    if (bad) {
         free(first);
         free(member);
+        free(tfirst);
+        free(tmember);
         free(newc);
+        free(taken);
         return -1;
-    }
-    for (int64_t i = 0; i < n; ++i) ++first[wave_of[i] + 1];
-    for (int32_t q = 0; q < n_waves; ++q) first[q + 1] += first[q];
-    {
-        int64_t *fill = (int64_t *)malloc((size_t)n_waves * sizeof(int64_t));
-        if (!fill) {
-            free(first);
-            free(member);
-            free(newc);
-            orc_work_free(&wk);
-            return -1;
-        }
-        memcpy(fill, first, (size_t)n_waves * sizeof(int64_t));
-        for (int64_t i = 0; i < n; ++i) member[fill[wave_of[i]]++] = i;
-        free(fill);
     }
     for (int l = start_iter; l < max_iters; ++l) {
         int pl = (pl_period > 0) && (l % pl_period == 0);
         int64_t changed = 0, scanned = 0;
         for (int32_t q = 0; q < n_waves; ++q) {
-            /* the wave reads: flags taken and c* computed on the labels at its start */
+            /* the wave starts: flags taken (each vertex marks itself processed) */
+            for (int64_t r = tfirst[q]; r < tfirst[q + 1]; ++r) {
+                const int64_t i = tmember[r];
+                taken[i] = active[i];
+                active[i] = 0;
+            }
+            /* the wave reads: c* of every deciding vertex whose flag was set, on the labels at its start */
             for (int64_t r = first[q]; r < first[q + 1]; ++r) {
                 const int64_t i = member[r];
                 newc[i] = -1;
-                if (!active[i]) continue;
-                active[i] = 0;                              /* mark processed */
+                if (!taken[i]) continue;
                 scanned += off[i + 1] - off[i];
                 newc[i] = orc_best_label(i, off, idx, w, C, wk.lab, wk.sum, wk.scratch);
             }
@@ -343,7 +361,10 @@ int orc_lpa_async_waves(int64_t n, const int64_t *off, const int32_t *idx, const
     }
     free(first);
     free(member);
+    free(tfirst);
+    free(tmember);
     free(newc);
+    free(taken);
     orc_work_free(&wk);
     return 0;
 }

@@ -586,22 +586,26 @@ def test_tolerance_test_is_strict_and_skips_pick_less_sweeps():
 # the asynchronous mode under a wave schedule (a reading of Section 4 item 1 for a parallel
 # sweep: each wave reads the state at its start, its moves and marks land at its end)
 
-def _dense_waves(W, wave_of, tol, max_iters, pl_period):
-    """Dense restatement: per sweep, per wave in increasing index, take the flagged members,
-    clear their flags, decide each on the labels frozen at the wave's start, then apply."""
+def _dense_waves(W, wave_of, tol, max_iters, pl_period, take_of=None):
+    """Dense restatement: per sweep, per wave in increasing index, the vertices whose take wave
+    it is read and clear their flags; then the flagged vertices deciding in the wave decide on
+    the labels frozen at its start, then the wave's moves and marks apply."""
     n = W.shape[0]
+    take_of = wave_of if take_of is None else take_of
     C = list(range(n))
     act = [True] * n
     dns = []
-    waves = sorted(set(wave_of))
     for l in range(max_iters):
         pl = pl_period > 0 and l % pl_period == 0
         ch = 0
-        for q in waves:
+        taken = [False] * n
+        for q in range(max(wave_of) + 1):
+            for i in range(n):
+                if take_of[i] == q:
+                    taken[i] = act[i]
+                    act[i] = False
             frozen = list(C)
-            members = [i for i in range(n) if wave_of[i] == q and act[i]]
-            for i in members:
-                act[i] = False
+            members = [i for i in range(n) if wave_of[i] == q and taken[i]]
             moves = []
             for i in members:
                 c = _best_dense(W, frozen, i)
@@ -710,3 +714,44 @@ def test_async_edges_by_hand():
     assert a.dN == [25, 0] and a.edges == [150, 125]
     assert oracle.lpa_sync(g, 0.05, 20, 4).edges == [150, 150]
     assert oracle.lpa_async_waves(g, np.arange(g.n), 0.05, 20, 4).edges == [150, 125]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_async_waves_with_early_flag_takes_match_dense_restatement(seed):
+    """Flags taken at an earlier wave than the decision (as when a warp fetches the flags of a
+    batch before deciding its vertices one step at a time): labels, dN and flags equal an
+    independent dense restatement; taking each flag in its own deciding wave is the default."""
+    rnd = random.Random(1700 + seed)
+    n = rnd.randint(5, 48)
+    g = G(gg.random_small(n, rnd.choice([0.08, 0.2, 0.35]), 1900 + seed, wmax=rnd.choice([1, 6]),
+                          self_loops=(seed % 4 == 1)))
+    W = _dense(g)
+    n_waves = rnd.choice([2, 3, 6, n])
+    wave_of = [rnd.randrange(n_waves) for _ in range(n)]
+    wave_of[0] = n_waves - 1
+    take_of = [rnd.randint(0, w) for w in wave_of]
+    tol, mi, pl = rnd.choice([0.0, 0.05]), rnd.choice([6, 20]), rnd.choice([0, 2, 4])
+    dns, C, act = _dense_waves(W, wave_of, tol, mi, pl, take_of)
+    r = oracle.lpa_async_waves(g, wave_of, tol, mi, pl, take_of=take_of)
+    assert r.dN == dns
+    assert r.labels.tolist() == C
+    assert r.active.astype(bool).tolist() == act
+    same = oracle.lpa_async_waves(g, wave_of, tol, mi, pl, take_of=wave_of)
+    plain = oracle.lpa_async_waves(g, wave_of, tol, mi, pl)
+    assert (same.dN, same.labels.tolist(), same.edges) == (plain.dN, plain.labels.tolist(), plain.edges)
+
+
+def test_async_waves_early_take_by_hand():
+    """One edge {0, 1}, no Pick-Less; vertex 0 decides in wave 0, vertex 1 in wave 1.
+    Flags taken in the deciding wave: sweep 0 moves 0 to label 1, which marks 1; vertex 1 then
+    takes its flag (set, cleared), sees label 1 (its own) and stays: dN = [1], no flag left, so
+    sweep 1 processes nothing (edges [2, 0]).  Both flags taken at wave 0: vertex 1 takes its
+    flag before vertex 0's mark lands, so the mark survives, and sweep 1 processes vertex 1
+    again (edges [2, 1]); labels and dN are the same."""
+    g = G(gg.from_edges(2, [(0, 1)]))
+    a = oracle.lpa_async_waves(g, [0, 1], 0.05, 20, 0)
+    b = oracle.lpa_async_waves(g, [0, 1], 0.05, 20, 0, take_of=[0, 0])
+    assert a.dN == [1, 0] and a.edges == [2, 0] and a.labels.tolist() == [1, 1]
+    assert b.dN == [1, 0] and b.edges == [2, 1] and b.labels.tolist() == [1, 1]
+    with pytest.raises(ValueError):
+        oracle.lpa_async_waves(g, [0, 1], take_of=[1, 1])        # a take after the decision
