@@ -422,10 +422,10 @@ def oracle_full_run(csr_dev, mode, waves_tuning=None):
     secs = time.perf_counter() - t0
     rw = None
     if waves_tuning is not None:
-        from oracle.schedule import gpu_waves
+        from oracle.schedule import gpu_schedule
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        rw = oracle.lpa_async_waves(og, gpu_waves(og.off, waves_tuning, sms), ALG["tolerance"], ALG["max_iters"],
-                                    ALG["pl_period"])
+        waves, takes = gpu_schedule(og.off, waves_tuning, sms)
+        rw = oracle.lpa_async_waves(og, waves, ALG["tolerance"], ALG["max_iters"], ALG["pl_period"], take_of=takes)
     return og, r, secs, rw
 
 
@@ -463,10 +463,11 @@ def measure_single(args, lpa, dev, workload, mode_name, steps, warmup, e2e_steps
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    plain = []
+    plain, qs = [], []
     for _ in range(steps):
         st, q = step()
         plain.append(st.to_dict())
+        qs.append(q)
     e1.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
@@ -578,10 +579,15 @@ def measure_single(args, lpa, dev, workload, mode_name, steps, warmup, e2e_steps
             else:
                 q_w = oracle.modularity(og, rw.labels)
                 viol = oracle.violations(og, labels_gpu) / og.n
-                out["parity"] = {"against": "oracle asynchronous run under the wave model of the GPU schedule",
-                                 "q_gpu": q, "q_oracle_waves": q_w, "q_oracle_sequential": oracle.modularity(og, r.labels),
-                                 "abs_diff": abs(q - q_w), "within_0_005": abs(q - q_w) <= 0.005,
-                                 "violation_fraction": viol, "violations_within_tolerance": viol <= ALG["tolerance"]}
+                q_med = statistics.median(qs)
+                out["parity"] = {"against": "oracle asynchronous run under the wave model of the GPU schedule; the "
+                                            "GPU's racy result read as the median over the timed runs",
+                                 "q_gpu_median": q_med, "q_gpu_min": min(qs), "q_gpu_max": max(qs), "runs": len(qs),
+                                 "q_oracle_waves": q_w, "q_oracle_sequential": oracle.modularity(og, r.labels),
+                                 "abs_diff_median": abs(q_med - q_w), "within_0_005": abs(q_med - q_w) <= 0.005,
+                                 "max_abs_diff": max(abs(x - q_w) for x in qs),
+                                 "violation_fraction_last_run": viol,
+                                 "violations_within_tolerance": viol <= ALG["tolerance"]}
     return out
 
 

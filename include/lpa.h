@@ -244,6 +244,14 @@ const char *lpa_last_error(void);
  * were full; a negative value turns it off.  Every entry point must then fail cleanly
  * (no partial handle, nothing leaked).  The paper has no counterpart. */
 void lpa_debug_fail_allocations(long long after);
+
+/* Returns the device memory that destroyed single-graph handles left in the library's memory
+ * pools to the driver.  Handles take their device memory from one stream-ordered pool per
+ * device that keeps freed blocks, so that creating a handle after destroying another does not
+ * allocate and free gigabytes again; call this when the memory is wanted elsewhere (another
+ * library, a larger allocation).  Synchronises every device that has a pool.  The paper has no
+ * counterpart.  LPA_ECUDA if a CUDA call fails. */
+int lpa_trim_memory(void);
 const char *lpa_kernel_name(int slot);
 
 /* ---- batches: many independent graphs solved together -------------------------------- */

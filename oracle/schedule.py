@@ -21,6 +21,8 @@ queue.
 The model lets every resident warp (block) advance one step per time unit, taking the next
 item from the queue when its item is done; the vertices decided at the same time form one
 wave, which reads the labels as they stand at its start and publishes its moves at its end.
+Every kernel takes the processed flags of a 32-vertex batch when it fetches the batch, before
+its first step on it: that is each vertex's take wave (`take_of`).
 The racy GPU sweep drifts from this lockstep; the model is the schedule the asynchronous
 acceptance test compares against.
 """
@@ -55,8 +57,14 @@ def _schedule(durations, resident):
 
 
 def gpu_waves(offsets, tuning: dict, sms: int = 152) -> np.ndarray:
-    """wave_of[i] for every vertex of a CSR graph (int64 offsets), for the degree buckets and
-    launch shapes in `tuning` (the lpa_tuning fields by name)."""
+    """wave_of[i] (the deciding wave) for every vertex of a CSR graph (int64 offsets)."""
+    return gpu_schedule(offsets, tuning, sms)[0]
+
+
+def gpu_schedule(offsets, tuning: dict, sms: int = 152):
+    """(wave_of, take_of) for every vertex of a CSR graph (int64 offsets), for the degree
+    buckets and launch shapes in `tuning` (the lpa_tuning fields by name): the wave in which
+    each vertex decides and the wave in which its batch's flags are taken."""
     off = np.asarray(offsets, dtype=np.int64)
     n = off.size - 1
     deg = np.diff(off)
@@ -71,6 +79,7 @@ def gpu_waves(offsets, tuning: dict, sms: int = 152) -> np.ndarray:
         lo = hi + 1
     bucket[deg > limits[-1]] = 6                      # hubs
     wave = np.zeros(n, dtype=np.int64)
+    take = np.zeros(n, dtype=np.int64)
     base = 0
     for b in range(6):
         members = np.nonzero(bucket == b)[0]          # ascending ids = bucket-list order
@@ -113,10 +122,14 @@ def gpu_waves(offsets, tuning: dict, sms: int = 152) -> np.ndarray:
             dur[-1] = members.size - (n_items - 1) * item
             resident = sms * max(1, 2048 // threads[b])
         starts = _schedule(dur, resident)
-        k_of = np.arange(members.size, dtype=np.int64) // item
+        p = np.arange(members.size, dtype=np.int64)
+        k_of = p // item
         wave[members] = base + starts[k_of] + step
+        first = k_of * item + ((p % item) // 32) * 32          # first position of the vertex's batch
+        take[members] = base + starts[k_of] + step[first]
         base = int(wave[members].max()) + 1
     hubs = np.nonzero(bucket == 6)[0]
     if hubs.size:
         wave[hubs] = base
-    return wave.astype(np.int32)
+        take[hubs] = base
+    return wave.astype(np.int32), take.astype(np.int32)

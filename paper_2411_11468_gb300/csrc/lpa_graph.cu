@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 
 #include <algorithm>
 #include <climits>
@@ -624,6 +625,35 @@ bool injected_alloc_failure()
     return false;
 }
 
+// Device memory of single-graph handles comes from a stream-ordered pool per device that keeps
+// freed blocks (release threshold: never), so creating a handle after destroying another does
+// not pay for cudaMalloc / cudaFree of gigabytes again; lpa_trim_memory returns the cached
+// blocks to the driver.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaMemPool_t handle_pool(int dev)
+{
+    if (dev < 0 || dev >= kMaxPoolDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
 template <typename T>
 int dalloc(lpa_graph *g, T **p, size_t count)
 {
@@ -636,9 +666,13 @@ int dalloc(lpa_graph *g, T **p, size_t count)
     }
     if (g->arena) {
         q = g->arena->alloc(bytes);
-    } else if (cudaMalloc(&q, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        q = nullptr;
+    } else {
+        cudaMemPool_t pool = handle_pool(g->device);
+        const cudaError_t e = pool ? cudaMallocFromPoolAsync(&q, bytes, pool, g->stream) : cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            q = nullptr;
+        }
     }
     if (!q) {
         set_error("device allocation of " + std::to_string(bytes) + " bytes failed" +
@@ -661,7 +695,7 @@ void dfree(lpa_graph *g, void *p)
         break;
     }
     if (g->arena) g->arena->free(p);
-    else cudaFree(p);
+    else cudaFreeAsync(p, g->stream);
 }
 
 lpa_tuning default_tuning()
@@ -682,7 +716,7 @@ lpa_tuning default_tuning()
     t.hub_table_shift = 1;
     t.smem_table_shift = 1;
     t.probe = 4;                                      // quadratic-double over power-of-two tables
-    t.flat_buckets = 2;                               // the lane-group bucket runs the flattened kernel
+    t.flat_buckets = 0;                               // one thread / lane group / warp per vertex
     return t;
 }
 
@@ -1186,9 +1220,10 @@ void destroy_graph(lpa_graph *g)
     if (g->stream) cudaStreamSynchronize(g->stream);
     for (auto &a : g->allocs) {
         if (g->arena) g->arena->free(a.first);
-        else cudaFree(a.first);
+        else cudaFreeAsync(a.first, g->stream);
     }
     g->allocs.clear();
+    if (g->stream && !g->arena) cudaStreamSynchronize(g->stream);
     if (g->h_ctr) cudaFreeHost(g->h_ctr);
     if (g->hm) cudaFreeHost(g->hm);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
@@ -1442,6 +1477,26 @@ const char *lpa_strerror(int status)
 }
 
 const char *lpa_last_error(void) { return t_error.c_str(); }
+
+int lpa_trim_memory(void)
+{
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    for (int d = 0; d < kMaxPoolDevices; ++d) {
+        if (!g_pools[d]) continue;
+        cudaSetDevice(d);
+        cudaDeviceSynchronize();
+        const cudaError_t e = cudaMemPoolTrimTo(g_pools[d], 0);
+        if (e != cudaSuccess) {
+            if (prev >= 0) cudaSetDevice(prev);
+            set_error(std::string("lpa_trim_memory: ") + cudaGetErrorString(e));
+            return LPA_ECUDA;
+        }
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return LPA_OK;
+}
 
 void lpa_debug_fail_allocations(long long after) { g_alloc_budget.store(after < 0 ? -1 : after); }
 

@@ -252,7 +252,7 @@ lpa_tuning multi_tuning()
     t.hub_table_shift = 1;
     t.smem_table_shift = 1;
     t.probe = 4;                                      // quadratic-double over power-of-two tables
-    t.flat_buckets = 2;                               // the lane-group bucket runs the flattened kernel
+    t.flat_buckets = 0;                               // one thread / lane group / warp per vertex
     return t;
 }
 

@@ -412,10 +412,19 @@ constexpr int kPeel = 3;
 template <int G, bool SHARED, bool TRACK, typename T>
 __device__ __forceinline__ void group_insert(const T &tab, uint32_t p1, uint32_t b, bool has, int32_t k,
                                              typename T::Val w, typename BestOf<typename T::Val>::type &best,
-                                             unsigned &fb, uint32_t *ucnt = nullptr, int32_t *ulist = nullptr)
+                                             unsigned &fb, uint32_t *ucnt = nullptr, int32_t *ulist = nullptr,
+                                             bool peel = true, bool unit = false)
 {
     using V = typename T::Val;
-    if (G >= 2) {
+    if (G >= 2 && peel && unit) {                      // uniform over the group
+        // unit weights: every group of lanes holding one label is found at once, and its lowest
+        // lane inserts the group's size (its weight sum) for all of them, every group in parallel
+        const unsigned same = __match_any_sync(group_mask<G>(), has ? (unsigned)k : 0xFFFFFFFFu);
+        if (has && (__ffs(same) - 1) == (int)(threadIdx.x & 31))
+            ht_accumulate<SHARED, TRACK>(tab, p1, b, k, V(__popc(same)), best, fb, ucnt, ulist);
+        return;
+    }
+    if (G >= 2 && peel) {                              // uniform over the group
         const unsigned gm = group_mask<G>();
         const int lane = threadIdx.x & 31;
         unsigned pend = __ballot_sync(gm, has);
@@ -496,6 +505,7 @@ struct SweepView {
     int32_t pl, async_mode, tshift, done;
     int32_t mark, pull;        // marks written this sweep; activity from moved bits (sync)
     int32_t probe;             // probe scheme of the tables
+    int32_t peel;              // sum the weights of lanes holding the same label before inserting
 };
 
 __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
@@ -524,6 +534,9 @@ __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
     v.mark = rs->mark;
     v.pull = rs->pull;
     v.probe = G.probe;
+    // The first sweep of a run from fresh labels (label = vertex id) finds every neighbour label
+    // distinct in a duplicate-free row, so the duplicate-label rounds would find nothing there.
+    v.peel = l > 0;
     const int slot = (l - rs->first) % (G.ctr_iters > 0 ? G.ctr_iters : 1);
     v.ctr = G.ctr + (size_t)(slot < 0 ? 0 : slot) * kPerSweep;
     v.fallbacks = G.fallbacks;
@@ -612,7 +625,8 @@ __device__ __forceinline__ void scan_row(const SweepView &a, int32_t v, int64_t 
         for (int u = 0; u < U; ++u) load_entry<SEEN>(a, v, eb + (int64_t)u * step + lane, end, has[u], k[u], wv[u], seen);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            group_insert<G, SHARED, TRACK>(tab, p1, b, has[u], k[u], wv[u], best, fb, ucnt, ulist);
+            group_insert<G, SHARED, TRACK>(tab, p1, b, has[u], k[u], wv[u], best, fb, ucnt, ulist, a.peel != 0,
+                                           a.w == nullptr);
     }
 }
 
@@ -839,7 +853,8 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
 #pragma unroll 1
                         for (int u = 0; u < U; ++u) {
                             if (!__any_sync(group_mask<G>(), has[0])) break;     // lanes of this group only
-                            group_insert<G, (G > 1), false>(tab, p1, b, has[0], kk[0], wv[0], best, fb);
+                            group_insert<G, (G > 1), false>(tab, p1, b, has[0], kk[0], wv[0], best, fb, nullptr,
+                                                            nullptr, a.peel != 0, a.w == nullptr);
 #pragma unroll
                             for (int q = 0; q + 1 < U; ++q) {
                                 has[q] = has[q + 1];
@@ -1109,9 +1124,16 @@ __global__ void __launch_bounds__(kFlatWarps * 32, 3) k_flat(KArgs k)
                         // lanes holding the same label of the same segment: the lowest inserts their
                         // summed weight once (up to kPeel labels per step): after the first sweeps most
                         // neighbours of a vertex share a few labels, and same-slot atomics serialise
+                        if (a.peel && a.w == nullptr) {          // unit weights: all label groups at once
+                            // lanes with the same label and the same segment: two 32-bit matches
+                            const unsigned same = __match_any_sync(0xFFFFFFFFu, has[0] ? (uint32_t)kk[0] : 0xFFFFFFFFu) &
+                                                  __match_any_sync(0xFFFFFFFFu, (uint32_t)seg[0]);
+                            if (has[0] && (__ffs(same) - 1) == lane) insert(seg[0], kk[0], V(__popc(same)));
+                            has[0] = false;
+                        }
                         unsigned pend = __ballot_sync(0xFFFFFFFFu, has[0]);
 #pragma unroll 1
-                        for (int r = 0; r < kPeel && pend; ++r) {
+                        for (int r = 0; r < kPeel && pend && a.peel; ++r) {
                             const int leader = __ffs(pend) - 1;
                             const int32_t kl = __shfl_sync(0xFFFFFFFFu, kk[0], leader);
                             const int sl = __shfl_sync(0xFFFFFFFFu, seg[0], leader);
@@ -1271,7 +1293,7 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
                 Best best;
                 best_init(best);
                 uint32_t seen = 0;
-                constexpr int U = TPB >= 1024 ? 2 : 1;     // loads in flight per thread
+                constexpr int U = 2;                           // loads in flight per thread
                 scan_row<32, true, false, U, PULL>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, tab,
                                                    p1, b, best, fb, seen, nullptr, nullptr, TPB * U);
                 best = group_max<32>(best);

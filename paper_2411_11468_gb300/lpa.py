@@ -37,7 +37,7 @@ SYMBOLS = ["lpa_create", "lpa_run", "lpa_labels", "lpa_modularity", "lpa_set_lab
            "lpa_batch_modularity", "lpa_batch_graph", "lpa_batch_size", "lpa_batch_device_bytes", "lpa_batch_destroy",
            "lpa_server_create", "lpa_server_submit", "lpa_server_step", "lpa_server_poll", "lpa_server_result",
            "lpa_server_clock", "lpa_server_device_bytes", "lpa_server_destroy", "lpa_batch_get_tuning",
-           "lpa_batch_set_tuning", "lpa_autotune", "lpa_batch_autotune", "lpa_modularity_noalloc", "lpa_run_cc", "lpa_server_cancel",
+           "lpa_batch_set_tuning", "lpa_autotune", "lpa_batch_autotune", "lpa_modularity_noalloc", "lpa_run_cc", "lpa_server_cancel", "lpa_trim_memory",
            "lpa_debug_fail_allocations"]
 
 
@@ -329,6 +329,14 @@ def debug_fail_allocations(after: int):
     L.lpa_debug_fail_allocations.argtypes = [ct.c_longlong]
     L.lpa_debug_fail_allocations.restype = None
     L.lpa_debug_fail_allocations(int(after))
+
+
+def trim_memory():
+    """lpa_trim_memory: returns the device memory cached by destroyed handles to the driver."""
+    L = load()
+    L.lpa_trim_memory.argtypes = []
+    L.lpa_trim_memory.restype = ct.c_int
+    _check(L.lpa_trim_memory(), "lpa_trim_memory")
 
 
 def _load_multi():
