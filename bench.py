@@ -46,6 +46,9 @@ WORKLOADS = {
     "rmat22": dict(kind="rmat", scale=22, weights="int8",
                    desc="R-MAT scale 22, edge factor 16, (a,b,c,d)=(.57,.19,.19,.05), symmetrised, integer "
                         "weights 1..8 as float32"),
+    "rmat22u": dict(kind="rmat", scale=22, weights="unit",
+                    desc="R-MAT scale 22 with unit float32 weights: the smaller case on which the counters behind "
+                         "the R-MAT 26 roofline's traffic are captured"),
     "sbm": dict(kind="sbm", n=10_000, block=100, d_in=16.0, d_out=2.0, weights="unit",
                 desc="planted partition 10,000 vertices / 100 blocks, intra-degree 16, inter-degree 2, unit weights"),
 }

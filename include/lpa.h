@@ -146,9 +146,11 @@ typedef struct lpa_tuning {
                                  the flattened kernel (a warp per batch of vertices whose
                                  rows it scans as one run) instead of one thread / lane
                                  group / warp per vertex                                   */
-    int32_t hub_two_pass;     /* 1: hubs with integer sums and HBM tables accumulate in two
-                                 passes (per-chunk shared-memory tables, then per label
-                                 partition) instead of global atomics on the HBM tables  */
+    int32_t hub_two_pass;     /* hubs with integer sums and HBM tables accumulate in two
+                                 passes through shared memory (entries or per-chunk sums sent
+                                 to label partitions, then each partition summed) instead of
+                                 global atomics on the HBM tables: 0 never, 1 in the first
+                                 sweep of a run from fresh labels, 2 in every sweep        */
     int32_t reserved[1];      /* zero                                                    */
 } lpa_tuning;
 

@@ -717,6 +717,7 @@ lpa_tuning default_tuning()
     t.smem_table_shift = 1;
     t.probe = 4;                                      // quadratic-double over power-of-two tables
     t.flat_buckets = 0;                               // one thread / lane group / warp per vertex
+    t.hub_two_pass = 1;                               // hubs in two passes in a run's first sweep
     return t;
 }
 
@@ -745,7 +746,7 @@ int check_tuning(const lpa_tuning &t)
     if (t.hub_cluster != 0 && t.hub_cluster != 1) return LPA_EINVAL;
     if (t.probe < 0 || t.probe > 4) return LPA_EINVAL;
     if (t.flat_buckets < 0 || t.flat_buckets > 7) return LPA_EINVAL;
-    if (t.hub_two_pass != 0 && t.hub_two_pass != 1) return LPA_EINVAL;
+    if (t.hub_two_pass < 0 || t.hub_two_pass > 2) return LPA_EINVAL;
     for (int r : t.reserved)
         if (r != 0) return LPA_EINVAL;
     const int64_t smem = (int64_t)max_dynamic_smem();
@@ -922,7 +923,8 @@ int build_buckets(lpa_graph *g)
                     pce0.push_back(e0);
                     pce1.push_back(std::min<int64_t>(o1[h], e0 + kPartChunk));
                 }
-            } else {
+            }
+            if (!two_pass || g->tuning.hub_two_pass == 1) {     // single-pass accumulate chunks
                 for (int64_t c = (int64_t)ch.size() - (o1[h] - o0[h] + chunk - 1) / chunk; c < (int64_t)ch.size(); ++c)
                     acc_chunks.push_back(c);
             }
@@ -1209,6 +1211,7 @@ int upload_descriptor(lpa_graph *g)
     d.tshift = g->tuning.smem_table_shift;
     d.probe = g->tuning.probe;
     d.int_weights = plan_int_weights(g) ? 1 : 0;
+    d.hub_tp = plan_int_weights(g) ? g->tuning.hub_two_pass : 0;     // the lists exist for integer sums
     LPA_CUDA(cudaMemcpyAsync(g->gdd, &g->gdh, sizeof(GraphDev), cudaMemcpyHostToDevice, g->stream));
     return LPA_OK;
 }

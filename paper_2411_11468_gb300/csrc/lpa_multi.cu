@@ -253,6 +253,7 @@ lpa_tuning multi_tuning()
     t.smem_table_shift = 1;
     t.probe = 4;                                      // quadratic-double over power-of-two tables
     t.flat_buckets = 0;                               // one thread / lane group / warp per vertex
+    t.hub_two_pass = 1;                               // hubs in two passes in a run's first sweep
     return t;
 }
 

@@ -1361,6 +1361,15 @@ __global__ void __launch_bounds__(TPB) k_cta(KArgs k)
 // hub_best), clear (a block per slice of the used-slot list or of the table), move (the
 // decision), mark (a block per CSR chunk of the hubs that moved).  Items: begin and move take
 // a graph's hubs [start, start + count); accumulate, clear and mark take one chunk / slice.
+// Whether graph g's hubs take the two passes in this sweep: every sweep (hub_tp = 2), or only
+// in the first sweep of a run from fresh labels (hub_tp = 1), where every neighbour label of a
+// duplicate-free row is distinct and the HBM tables' atomics miss the most; later sweeps,
+// with few labels left, are cheaper in the single pass.
+__device__ __forceinline__ bool hub_two_pass_now(const GraphDev &G, const SweepView &a)
+{
+    return G.hub_tp == 2 || (G.hub_tp == 1 && !a.peel);
+}
+
 struct HArgs {
     const GraphDev *gd;
     const WorkItem *items;
@@ -1422,6 +1431,7 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
     const WorkItem item = k.items[blockIdx.x];
     const SweepView a = view_of(k.gd, item.g);
     if (a.done || (a.pull != 0) != PULL) return;      // the other launch takes it
+    if (hub_two_pass_now(k.gd[item.g], a)) return;    // the two-pass kernels take this sweep
     const HubArgs &h = k.gd[item.g].hub;
     const int64_t c = item.start;
     const int hh = h.chunk_h[c];
@@ -1464,130 +1474,200 @@ __device__ __forceinline__ uint32_t part_of(int32_t k, uint32_t pb)
     return pb ? (((uint32_t)k * kHashMul3) >> (32u - pb)) : 0u;
 }
 
+
+// Sends (label, sum) to its partition: a reserved position below kPartCap, else the hub's HBM
+// table (and the partition is marked overflowed).
+template <int PROBE>
+__device__ __forceinline__ void part_put(const HubArgs &h, const SweepView &a, int hh, int32_t pbase,
+                                         const uint32_t *s_base, uint32_t *s_fill, uint32_t part, int32_t key,
+                                         uint32_t sum, unsigned long long &obest, unsigned &fb)
+{
+    const uint32_t pos = s_base[part] + atomicAdd(&s_fill[part], 1u);
+    if (pos < (uint32_t)kPartCap) {
+        h.pairs[(size_t)(pbase + part) * kPartCap + pos] = ((unsigned long long)(uint32_t)key << 32) | sum;
+    } else {
+        h.part_ovf[pbase + part] = 1;
+        const PackedTable<PROBE, true> htab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
+        ht_accumulate<true, true>(htab, h.hub_p1[hh], h.hub_b[hh], key, sum, obest, fb, h.hub_used + hh,
+                                  h.used_list + h.used_base[hh]);
+    }
+}
+
+// Pass 1.  Blocks loop over the first-pass chunks.  In a sweep on fresh labels (no duplicate
+// grouping) the chunk's entries go to the partitions as they are; otherwise the chunk's
+// labels are first summed in a shared-memory table and its distinct pairs go.
 template <bool PULL, int PROBE>
-__global__ void __launch_bounds__(kPartThreads, 3) k_hub_part(HArgs k)
+__global__ void __launch_bounds__(kPartThreads, 2) k_hub_part(HArgs k, int32_t n_items)
 {
     if (*k.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *T = (unsigned long long *)smem;                 // [2^kPartTableBits]
     uint32_t *s_cnt = (uint32_t *)(smem + ((size_t)8 << kPartTableBits)); // [2^kPartMaxBits] counts, then fill
     uint32_t *s_base = s_cnt + (1 << kPartMaxBits);                       // [2^kPartMaxBits] reservations
-    __shared__ unsigned long long s_best[kPartThreads / 32];
-    const WorkItem item = k.items[blockIdx.x];
-    const SweepView a = view_of(k.gd, item.g);
-    if (a.done || (a.pull != 0) != PULL) return;      // the other launch takes it
-    const HubArgs &h = k.gd[item.g].hub;
-    const int64_t c = item.start;
-    const int hh = h.pc_h[c];
-    if (!h.hub_act[hh]) return;
-    const int32_t v = h.hub_v[hh];
-    const int64_t e0 = h.pc_e0[c], e1 = h.pc_e1[c];
-    const uint32_t pb = h.hub_pb[hh], np = 1u << pb;
-    const int32_t pbase = h.hub_pbase[hh];
-    constexpr uint32_t b = kPartTableBits;
-    const uint32_t p1 = cap_of_bits(b);
-    const PackedTable<PROBE> tab{T, 1, a.probe};
-    clear_table_vec(tab, p1, threadIdx.x, kPartThreads);
-    for (uint32_t q = threadIdx.x; q < np; q += kPartThreads) s_cnt[q] = 0;
-    __syncthreads();
-    unsigned fb = 0;
-    unsigned long long best = 0ull;                    // (not used: pass 2 takes the maximum)
-    uint32_t seen = 0;
-    scan_row<32, true, false, 2, PULL>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab, p1, b,
-                                       best, fb, seen, nullptr, nullptr, kPartThreads * 2);
-    if (PULL) {
-        if (__syncthreads_or((seen & kMovedBit) != 0) && threadIdx.x == 0) h.hub_seen[hh] = 1;
-    } else {
-        __syncthreads();
-    }
-    // pairs per partition, one reservation per partition, then the pairs themselves
-    for (uint32_t q = threadIdx.x; q <= p1; q += kPartThreads) {
-        const unsigned long long x = T[q];
-        if ((uint32_t)(x >> 32) != 0xFFFFFFFFu) atomicAdd(&s_cnt[part_of((int32_t)(x >> 32), pb)], 1u);
-    }
-    __syncthreads();
-    for (uint32_t q = threadIdx.x; q < np; q += kPartThreads) {
-        const uint32_t n = s_cnt[q];
-        s_base[q] = n ? atomicAdd(h.part_cnt + pbase + q, n) : 0u;
-        s_cnt[q] = 0;
-    }
-    __syncthreads();
-    unsigned long long obest = 0ull;                   // overflow inserts into the HBM table
-    const PackedTable<PROBE, true> htab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
-    for (uint32_t q = threadIdx.x; q <= p1; q += kPartThreads) {
-        const unsigned long long x = T[q];
-        const int32_t key = (int32_t)(x >> 32);
-        if (key == kEmpty) continue;
-        const uint32_t part = part_of(key, pb);
-        const uint32_t pos = s_base[part] + atomicAdd(&s_cnt[part], 1u);
-        if (pos < (uint32_t)kPartCap) {
-            h.pairs[(size_t)(pbase + part) * kPartCap + pos] = x;
-        } else {
-            h.part_ovf[pbase + part] = 1;
-            ht_accumulate<true, true>(htab, h.hub_p1[hh], h.hub_b[hh], key, (uint32_t)x, obest, fb, h.hub_used + hh,
-                                      h.used_list + h.used_base[hh]);
+    constexpr int PER = kPartChunk / kPartThreads;                        // entries per thread (8)
+    int skip_g = -1;                                   // a graph whose hubs take the single pass now
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {            // uniform per block
+        const WorkItem item = k.items[it];
+        if (item.g == skip_g) continue;
+        const GraphDev &G = k.gd[item.g];
+        const SweepView a = view_of(k.gd, item.g);
+        if (a.done || (a.pull != 0) != PULL || !hub_two_pass_now(G, a)) {
+            skip_g = item.g;
+            continue;
         }
+        const HubArgs &h = G.hub;
+        const int64_t c = item.start;
+        const int hh = h.pc_h[c];
+        if (!h.hub_act[hh]) continue;
+        const int32_t v = h.hub_v[hh];
+        const int64_t e0 = h.pc_e0[c], e1 = h.pc_e1[c];
+        const uint32_t pb = h.hub_pb[hh], np = 1u << pb;
+        const int32_t pbase = h.hub_pbase[hh];
+        __syncthreads();                               // the previous item's shared data is consumed
+        for (uint32_t q = threadIdx.x; q < np; q += kPartThreads) s_cnt[q] = 0;
+        unsigned fb = 0;
+        unsigned long long obest = 0ull;               // overflow inserts into the HBM table
+        uint32_t seen = 0;
+        if (!a.peel) {
+            // the entries themselves: count per partition, reserve, write
+            int32_t key[PER];
+            uint32_t wsum[PER];
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int64_t e = e0 + threadIdx.x + (int64_t)u * kPartThreads;
+                key[u] = -1;
+                wsum[u] = 0;
+                if (e < e1) {
+                    const int32_t j = a.idx[e];
+                    if (j != v) wsum[u] = a.w ? (uint32_t)a.w[e] : 1u;
+                    key[u] = j;                        // neighbour id first; its label below
+                    if (j == v) key[u] = -1;
+                }
+            }
+            __syncthreads();                           // s_cnt cleared
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                if (key[u] < 0) continue;
+                const uint32_t cj = (uint32_t)a.C[key[u]];
+                if (PULL) seen |= cj;
+                key[u] = (int32_t)(cj & kLabelMask);
+                atomicAdd(&s_cnt[part_of(key[u], pb)], 1u);
+            }
+            __syncthreads();
+            for (uint32_t q = threadIdx.x; q < np; q += kPartThreads) {
+                const uint32_t n = s_cnt[q];
+                s_base[q] = n ? atomicAdd(h.part_cnt + pbase + q, n) : 0u;
+                s_cnt[q] = 0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < PER; ++u)
+                if (key[u] >= 0)
+                    part_put<PROBE>(h, a, hh, pbase, s_base, s_cnt, part_of(key[u], pb), key[u], wsum[u], obest, fb);
+        } else {
+            // the chunk's labels summed first, then its distinct pairs
+            constexpr uint32_t b = kPartTableBits;
+            const uint32_t p1 = cap_of_bits(b);
+            const PackedTable<PROBE> tab{T, 1, a.probe};
+            clear_table_vec(tab, p1, threadIdx.x, kPartThreads);
+            __syncthreads();
+            unsigned long long best = 0ull;            // (not used: pass 2 takes the maximum)
+            scan_row<32, true, false, 2, PULL>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab,
+                                               p1, b, best, fb, seen, nullptr, nullptr, kPartThreads * 2);
+            __syncthreads();
+            for (uint32_t q = threadIdx.x; q <= p1; q += kPartThreads) {
+                const unsigned long long x = T[q];
+                if ((uint32_t)(x >> 32) != 0xFFFFFFFFu) atomicAdd(&s_cnt[part_of((int32_t)(x >> 32), pb)], 1u);
+            }
+            __syncthreads();
+            for (uint32_t q = threadIdx.x; q < np; q += kPartThreads) {
+                const uint32_t n = s_cnt[q];
+                s_base[q] = n ? atomicAdd(h.part_cnt + pbase + q, n) : 0u;
+                s_cnt[q] = 0;
+            }
+            __syncthreads();
+            for (uint32_t q = threadIdx.x; q <= p1; q += kPartThreads) {
+                const unsigned long long x = T[q];
+                const int32_t key = (int32_t)(x >> 32);
+                if (key != kEmpty)
+                    part_put<PROBE>(h, a, hh, pbase, s_base, s_cnt, part_of(key, pb), key, (uint32_t)x, obest, fb);
+            }
+        }
+        if (PULL && __syncthreads_or((seen & kMovedBit) != 0) && threadIdx.x == 0) h.hub_seen[hh] = 1;
+        if (obest) atomicMax(h.hub_best + hh, obest);
+        if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
     }
-    if (obest) atomicMax(h.hub_best + hh, obest);
-    if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
 }
 
+// Pass 2.  Blocks loop over the partitions: each partition's pairs summed in a shared-memory
+// table (or, after an overflow, all of them in the hub's HBM table), the running maximum
+// folded into the hub's; the partition's counters are reset for the next sweep.
 template <int PROBE>
-__global__ void __launch_bounds__(kPartThreads, 3) k_hub_merge(HArgs k)
+__global__ void __launch_bounds__(kPartThreads, 3) k_hub_merge(HArgs k, int32_t n_items)
 {
     if (*k.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_best[kPartThreads / 32];
     __shared__ uint32_t s_n;
     __shared__ int32_t s_ovf;
-    const WorkItem item = k.items[blockIdx.x];
-    const SweepView a = view_of(k.gd, item.g);
-    if (a.done) return;
-    const HubArgs &h = k.gd[item.g].hub;
-    const int32_t q = (int32_t)item.start;
-    const int hh = h.part_h[q];
-    if (threadIdx.x == 0) {
-        const uint32_t c = h.part_cnt[q];
-        s_n = c < (uint32_t)kPartCap ? c : (uint32_t)kPartCap;
-        s_ovf = h.part_ovf[q];
-        h.part_cnt[q] = 0;                             // ready for the next sweep
-        h.part_ovf[q] = 0;
-    }
-    __syncthreads();
-    const uint32_t n = s_n;
-    if (n == 0) return;
-    const unsigned long long *P = h.pairs + (size_t)q * kPartCap;
-    unsigned fb = 0;
-    unsigned long long best = 0ull;
-    if (!s_ovf) {
-        uint32_t b = cap_bits(n << 1);
-        if (b > kPartTableBits) b = kPartTableBits;
-        const uint32_t p1 = cap_of_bits(b);
-        const PackedTable<PROBE> tab{(unsigned long long *)smem, 1, a.probe};
-        clear_table_vec(tab, p1, threadIdx.x, kPartThreads);
+    int skip_g = -1;                                   // a graph whose hubs take the single pass now
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {            // uniform per block
+        const WorkItem item = k.items[it];
+        if (item.g == skip_g) continue;
+        const GraphDev &G = k.gd[item.g];
+        const SweepView a = view_of(k.gd, item.g);
+        if (a.done || !hub_two_pass_now(G, a)) {
+            skip_g = item.g;
+            continue;
+        }
+        const HubArgs &h = G.hub;
+        const int32_t q = (int32_t)item.start;
+        const int hh = h.part_h[q];
+        __syncthreads();                               // the previous item's shared data is consumed
+        if (threadIdx.x == 0) {
+            const uint32_t c = h.part_cnt[q];
+            s_n = c < (uint32_t)kPartCap ? c : (uint32_t)kPartCap;
+            s_ovf = h.part_ovf[q];
+            h.part_cnt[q] = 0;                         // ready for the next sweep
+            h.part_ovf[q] = 0;
+        }
         __syncthreads();
-        for (uint32_t i0 = threadIdx.x & ~31u; i0 < n; i0 += kPartThreads) {     // uniform per warp
-            const uint32_t i = i0 + (threadIdx.x & 31u);
-            const bool has = i < n;
-            const unsigned long long x = has ? P[i] : 0ull;
-            group_insert<32, true, false>(tab, p1, b, has, (int32_t)(x >> 32), (uint32_t)x, best, fb);
+        const uint32_t n = s_n;
+        if (n == 0) continue;
+        const unsigned long long *P = h.pairs + (size_t)q * kPartCap;
+        unsigned fb = 0;
+        unsigned long long best = 0ull;
+        if (!s_ovf) {
+            uint32_t b = cap_bits(n << 1);
+            if (b > kPartTableBits) b = kPartTableBits;
+            const uint32_t p1 = cap_of_bits(b);
+            const PackedTable<PROBE> tab{(unsigned long long *)smem, 1, a.probe};
+            clear_table_vec(tab, p1, threadIdx.x, kPartThreads);
+            __syncthreads();
+            for (uint32_t i0 = threadIdx.x & ~31u; i0 < n; i0 += kPartThreads) {     // uniform per warp
+                const uint32_t i = i0 + (threadIdx.x & 31u);
+                const bool has = i < n;
+                const unsigned long long x = has ? P[i] : 0ull;
+                group_insert<32, true, false>(tab, p1, b, has, (int32_t)(x >> 32), (uint32_t)x, best, fb, nullptr,
+                                              nullptr, a.peel != 0);
+            }
+        } else {                                       // the partition overflowed: all of it to HBM
+            const PackedTable<PROBE, true> htab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
+            for (uint32_t i = threadIdx.x; i < n; i += kPartThreads) {
+                const unsigned long long x = P[i];
+                ht_accumulate<true, true>(htab, h.hub_p1[hh], h.hub_b[hh], (int32_t)(x >> 32), (uint32_t)x, best, fb,
+                                          h.hub_used + hh, h.used_list + h.used_base[hh]);
+            }
         }
-    } else {                                           // the partition overflowed: all of it to HBM
-        const PackedTable<PROBE, true> htab{(unsigned long long *)h.tab_k + h.hub_tab[hh], 1, a.probe};
-        for (uint32_t i = threadIdx.x; i < n; i += kPartThreads) {
-            const unsigned long long x = P[i];
-            ht_accumulate<true, true>(htab, h.hub_p1[hh], h.hub_b[hh], (int32_t)(x >> 32), (uint32_t)x, best, fb,
-                                      h.hub_used + hh, h.used_list + h.used_base[hh]);
+        best = group_max<32>(best);
+        if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < kPartThreads / 32; ++w) best = umax64(best, s_best[w]);
+            if (best) atomicMax(h.hub_best + hh, best);
         }
+        if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
     }
-    best = group_max<32>(best);
-    if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < kPartThreads / 32; ++w) best = umax64(best, s_best[w]);
-        if (best) atomicMax(h.hub_best + hh, best);
-    }
-    if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
 }
 
 // Hubs whose table fits in the shared memory of a cluster of CS blocks (1024 threads each).
@@ -1844,6 +1924,14 @@ static cudaError_t launch_vertex_phase(const SweepPlan &p, cudaStream_t s, Launc
     return cudaSuccess;
 }
 
+// Persistent grid of the two-pass hub kernels: `per_sm` 512-thread blocks per SM.
+static unsigned part_grid(int32_t n_items, int per_sm)
+{
+    query_device();
+    const int64_t cap = (int64_t)g_num_sms * per_sm;
+    return (unsigned)(n_items < cap ? (n_items < 1 ? 1 : n_items) : cap);
+}
+
 template <int PROBE, bool F64 = false>
 static cudaError_t launch_hub_acc_phase(const SweepPlan &p, const HArgs &h, cudaStream_t s, LaunchHook *hook,
                                         int *launches)
@@ -1872,19 +1960,25 @@ static cudaError_t launch_hub_acc_phase(const SweepPlan &p, const HArgs &h, cuda
         const size_t smem_a = ((size_t)8 << kPartTableBits) + 2 * sizeof(uint32_t) * ((size_t)1 << kPartMaxBits);
         if (push && r == cudaSuccess) {
             r = set_smem(k_hub_part<false, PROBE>, smem_a);
-            if (r == cudaSuccess) k_hub_part<false, PROBE><<<p.n_hub_items[HL_PACC], kPartThreads, smem_a, s>>>(ha);
+            if (r == cudaSuccess)
+                k_hub_part<false, PROBE><<<part_grid(p.n_hub_items[HL_PACC], 2), kPartThreads, smem_a, s>>>(
+                    ha, p.n_hub_items[HL_PACC]);
             if (launches) ++*launches;
         }
         if (pull && r == cudaSuccess) {
             r = set_smem(k_hub_part<true, PROBE>, smem_a);
-            if (r == cudaSuccess) k_hub_part<true, PROBE><<<p.n_hub_items[HL_PACC], kPartThreads, smem_a, s>>>(ha);
+            if (r == cudaSuccess)
+                k_hub_part<true, PROBE><<<part_grid(p.n_hub_items[HL_PACC], 2), kPartThreads, smem_a, s>>>(
+                    ha, p.n_hub_items[HL_PACC]);
             if (launches) ++*launches;
         }
         if (r == cudaSuccess && p.n_hub_items[HL_PMERGE] > 0) {
             ha.items = p.hub_items[HL_PMERGE];
             const size_t smem_b = (size_t)8 << kPartTableBits;
             r = set_smem(k_hub_merge<PROBE>, smem_b);
-            if (r == cudaSuccess) k_hub_merge<PROBE><<<p.n_hub_items[HL_PMERGE], kPartThreads, smem_b, s>>>(ha);
+            if (r == cudaSuccess)
+                k_hub_merge<PROBE><<<part_grid(p.n_hub_items[HL_PMERGE], 3), kPartThreads, smem_b, s>>>(
+                    ha, p.n_hub_items[HL_PMERGE]);
             if (launches) ++*launches;
         }
     }

@@ -92,7 +92,7 @@ def test_sync_random_graphs_all_buckets(lpa, seed):
     csr = gg.random_small(n, rnd.choice([0.01, 0.05, 0.15, 0.4]), 1000 + seed, wmax=rnd.choice([1, 4, 8]),
                           self_loops=(seed % 3 == 0))
     tuning = dict(PAPER_TABLES if seed % 2 else SMALL_BUCKETS, flat_buckets=rnd.choice([0, 2, 5, 7]),
-                  hub_two_pass=seed % 3 == 1)
+                  hub_two_pass=seed % 3)
     check_sync_every_iteration(lpa, csr, rnd.choice([0.0, 0.05]), 20, rnd.choice([0, 2, 4]), tuning)
 
 
@@ -104,7 +104,8 @@ def test_sync_rmat_default_buckets(lpa, scale, weights):
 
 @pytest.mark.parametrize("scale,weights,tuning", [(20, "unit", None), (21, "int8", None),
                                                   (20, "int8", dict(hub_two_pass=1, flat_buckets=7)),
-                                                  (20, "unit", dict(flat_buckets=0))])
+                                                  (20, "unit", dict(hub_two_pass=1)),
+                                                  (20, "unit", dict(hub_two_pass=2, flat_buckets=2))])
 def test_sync_rmat_large_every_sweep(lpa, scale, weights, tuning):
     """The benchmark's path at a size where hubs span several 16K-entry accumulate chunks
     (R-MAT 20: 211 hubs above 8,191 entries, the largest 64,843) and tables of 2^17 slots:
@@ -141,7 +142,7 @@ def test_sync_rmat_small_buckets_with_hubs(lpa, scale, tables):
     csr = gg.rmat(scale, weights="int8")
     tuning = {"half": SMALL_BUCKETS, "paper": PAPER_TABLES, "cluster": CLUSTER_HUBS,
               "cluster-paper": dict(PAPER_TABLES, hub_cluster=1), "two-pass": dict(SMALL_BUCKETS, hub_two_pass=1),
-              "two-pass-paper": dict(PAPER_TABLES, hub_two_pass=1, probe=0)}[tables]
+              "two-pass-paper": dict(PAPER_TABLES, hub_two_pass=2, probe=0)}[tables]
     check_sync_every_iteration(lpa, csr, 0.05, 20, 4, tuning)
 
 
