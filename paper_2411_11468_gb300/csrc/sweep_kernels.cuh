@@ -1497,7 +1497,7 @@ __device__ __forceinline__ void part_put(const HubArgs &h, const SweepView &a, i
 // grouping) the chunk's entries go to the partitions as they are; otherwise the chunk's
 // labels are first summed in a shared-memory table and its distinct pairs go.
 template <bool PULL, int PROBE>
-__global__ void __launch_bounds__(kPartThreads, 2) k_hub_part(HArgs k, int32_t n_items)
+__global__ void __launch_bounds__(kPartThreads, 2) k_hub_part(HArgs k, int32_t n_items, int32_t one_graph)
 {
     if (*k.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1512,6 +1512,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_hub_part(HArgs k, int32_t n
         const GraphDev &G = k.gd[item.g];
         const SweepView a = view_of(k.gd, item.g);
         if (a.done || (a.pull != 0) != PULL || !hub_two_pass_now(G, a)) {
+            if (one_graph) return;                     // every item belongs to this graph
             skip_g = item.g;
             continue;
         }
@@ -1544,13 +1545,15 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_hub_part(HArgs k, int32_t n
                     if (j == v) key[u] = -1;
                 }
             }
+            uint32_t cj[PER];
+#pragma unroll
+            for (int u = 0; u < PER; ++u) cj[u] = key[u] >= 0 ? (uint32_t)a.C[key[u]] : 0u;   // all gathers in flight
             __syncthreads();                           // s_cnt cleared
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
                 if (key[u] < 0) continue;
-                const uint32_t cj = (uint32_t)a.C[key[u]];
-                if (PULL) seen |= cj;
-                key[u] = (int32_t)(cj & kLabelMask);
+                if (PULL) seen |= cj[u];
+                key[u] = (int32_t)(cj[u] & kLabelMask);
                 atomicAdd(&s_cnt[part_of(key[u], pb)], 1u);
             }
             __syncthreads();
@@ -1603,7 +1606,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) k_hub_part(HArgs k, int32_t n
 // table (or, after an overflow, all of them in the hub's HBM table), the running maximum
 // folded into the hub's; the partition's counters are reset for the next sweep.
 template <int PROBE>
-__global__ void __launch_bounds__(kPartThreads, 3) k_hub_merge(HArgs k, int32_t n_items)
+__global__ void __launch_bounds__(kPartThreads, 3) k_hub_merge(HArgs k, int32_t n_items, int32_t one_graph)
 {
     if (*k.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1617,6 +1620,7 @@ __global__ void __launch_bounds__(kPartThreads, 3) k_hub_merge(HArgs k, int32_t 
         const GraphDev &G = k.gd[item.g];
         const SweepView a = view_of(k.gd, item.g);
         if (a.done || !hub_two_pass_now(G, a)) {
+            if (one_graph) return;                     // every item belongs to this graph
             skip_g = item.g;
             continue;
         }
@@ -1962,14 +1966,14 @@ static cudaError_t launch_hub_acc_phase(const SweepPlan &p, const HArgs &h, cuda
             r = set_smem(k_hub_part<false, PROBE>, smem_a);
             if (r == cudaSuccess)
                 k_hub_part<false, PROBE><<<part_grid(p.n_hub_items[HL_PACC], 2), kPartThreads, smem_a, s>>>(
-                    ha, p.n_hub_items[HL_PACC]);
+                    ha, p.n_hub_items[HL_PACC], p.n_graphs == 1);
             if (launches) ++*launches;
         }
         if (pull && r == cudaSuccess) {
             r = set_smem(k_hub_part<true, PROBE>, smem_a);
             if (r == cudaSuccess)
                 k_hub_part<true, PROBE><<<part_grid(p.n_hub_items[HL_PACC], 2), kPartThreads, smem_a, s>>>(
-                    ha, p.n_hub_items[HL_PACC]);
+                    ha, p.n_hub_items[HL_PACC], p.n_graphs == 1);
             if (launches) ++*launches;
         }
         if (r == cudaSuccess && p.n_hub_items[HL_PMERGE] > 0) {
@@ -1978,7 +1982,7 @@ static cudaError_t launch_hub_acc_phase(const SweepPlan &p, const HArgs &h, cuda
             r = set_smem(k_hub_merge<PROBE>, smem_b);
             if (r == cudaSuccess)
                 k_hub_merge<PROBE><<<part_grid(p.n_hub_items[HL_PMERGE], 3), kPartThreads, smem_b, s>>>(
-                    ha, p.n_hub_items[HL_PMERGE]);
+                    ha, p.n_hub_items[HL_PMERGE], p.n_graphs == 1);
             if (launches) ++*launches;
         }
     }
