@@ -524,23 +524,21 @@ bool Arena::add_region(size_t bytes)
     Region r;
     r.base = static_cast<unsigned char *>(p);
     r.cap = bytes;
-    r.free_.push_back({0, bytes});
+    r.free_.emplace(0, bytes);
     regions_.push_back(std::move(r));
     return true;
 }
 
+// First fit in offset order; ordered maps keep allocation and release logarithmic, so that a
+// batch of thousands of graphs (tens of thousands of blocks) is created and released quickly.
 void *Arena::region_alloc(Region &r, size_t bytes)
 {
-    for (size_t i = 0; i < r.free_.size(); ++i) {
-        if (r.free_[i].size < bytes) continue;
-        const size_t off = r.free_[i].off;
-        r.free_[i].off += bytes;
-        r.free_[i].size -= bytes;
-        if (r.free_[i].size == 0) r.free_.erase(r.free_.begin() + (long)i);
-        const Block b{off, bytes};
-        auto it = std::lower_bound(r.taken_.begin(), r.taken_.end(), b,
-                                   [](const Block &x, const Block &y) { return x.off < y.off; });
-        r.taken_.insert(it, b);
+    for (auto it = r.free_.begin(); it != r.free_.end(); ++it) {
+        if (it->second < bytes) continue;
+        const size_t off = it->first, size = it->second;
+        r.free_.erase(it);
+        if (size > bytes) r.free_.emplace(off + bytes, size - bytes);
+        r.taken_.emplace(off, bytes);
         r.used += bytes;
         return r.base + off;
     }
@@ -549,6 +547,7 @@ void *Arena::region_alloc(Region &r, size_t bytes)
 
 void *Arena::alloc(size_t bytes)
 {
+    std::lock_guard<std::mutex> lock(mu_);
     bytes = (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
     for (Region &r : regions_)
         if (void *p = region_alloc(r, bytes)) return p;
@@ -559,27 +558,30 @@ void *Arena::alloc(size_t bytes)
 void Arena::free(void *p)
 {
     if (!p) return;
+    std::lock_guard<std::mutex> lock(mu_);
     unsigned char *q = static_cast<unsigned char *>(p);
     for (Region &r : regions_) {
         if (q < r.base || q >= r.base + r.cap) continue;
         const size_t off = (size_t)(q - r.base);
-        auto it = std::lower_bound(r.taken_.begin(), r.taken_.end(), Block{off, 0},
-                                   [](const Block &x, const Block &y) { return x.off < y.off; });
-        if (it == r.taken_.end() || it->off != off) return;
-        Block b = *it;
-        r.taken_.erase(it);
-        r.used -= b.size;
-        auto f = std::lower_bound(r.free_.begin(), r.free_.end(), b,
-                                  [](const Block &x, const Block &y) { return x.off < y.off; });
-        f = r.free_.insert(f, b);
-        if (f + 1 != r.free_.end() && f->off + f->size == (f + 1)->off) {   // merge with the next block
-            f->size += (f + 1)->size;
-            r.free_.erase(f + 1);
+        auto t = r.taken_.find(off);
+        if (t == r.taken_.end()) return;
+        size_t start = off, size = t->second;
+        r.taken_.erase(t);
+        r.used -= size;
+        auto next = r.free_.lower_bound(start);
+        if (next != r.free_.end() && start + size == next->first) {   // merge with the next block
+            size += next->second;
+            next = r.free_.erase(next);
         }
-        if (f != r.free_.begin() && (f - 1)->off + (f - 1)->size == f->off) {   // and with the previous one
-            (f - 1)->size += f->size;
-            r.free_.erase(f);
+        if (next != r.free_.begin()) {                                  // and with the previous one
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == start) {
+                start = prev->first;
+                size += prev->second;
+                r.free_.erase(prev);
+            }
         }
+        r.free_.emplace(start, size);
         return;
     }
 }
@@ -602,7 +604,7 @@ size_t Arena::largest_free() const
 {
     size_t m = 0;
     for (const Region &r : regions_)
-        for (const Block &b : r.free_) m = std::max(m, b.size);
+        for (const auto &b : r.free_) m = std::max(m, b.second);
     return m;
 }
 
@@ -1216,11 +1218,15 @@ int upload_descriptor(lpa_graph *g)
     return LPA_OK;
 }
 
-void destroy_graph(lpa_graph *g)
+void destroy_graph(lpa_graph *g, bool arena_released)
 {
     if (!g) return;
     DeviceGuard dg(g->device);
-    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (arena_released && g->arena) {                 // the owner releases the whole arena after this
+        g->allocs.clear();
+    } else if (g->stream) {
+        cudaStreamSynchronize(g->stream);
+    }
     for (auto &a : g->allocs) {
         if (g->arena) g->arena->free(a.first);
         else cudaFreeAsync(a.first, g->stream);
@@ -1411,9 +1417,10 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
     return LPA_OK;
 }
 
-int graph_modularity(lpa_graph *g, double *q)
+// Eq. 1 in two halves: the kernels that fill the graph's four accumulator words (no wait), and
+// Q from those words once they are on the host (exact integers, or float64).
+int graph_modularity_enqueue(lpa_graph *g)
 {
-    *q = 0.0;
     if (g->n == 0) return LPA_OK;
     if (!g->Sig) {
         LPA_CHECK(dalloc(g, &g->Sig, (size_t)g->n));
@@ -1441,22 +1448,38 @@ int graph_modularity(lpa_graph *g, double *q)
         unsigned long long *acc = reinterpret_cast<unsigned long long *>(g->macc);
         run_lists(SigU, acc);
         k_mod_sq_int<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(SigU, g->n, acc);
-        unsigned long long h[4];
-        LPA_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
-        LPA_CUDA(cudaStreamSynchronize(g->stream));
+    } else {
+        run_lists(g->Sig, g->macc);
+        k_mod_sq<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->Sig, g->n, g->macc);
+    }
+    LPA_CUDA(cudaGetLastError());
+    return LPA_OK;
+}
+
+double graph_modularity_finish(const lpa_graph *g, const void *acc_words)
+{
+    if (g->n == 0) return 0.0;
+    if (g->int_weights) {
+        const unsigned long long *h = static_cast<const unsigned long long *>(acc_words);
         const __int128 two_m = (__int128)h[1], in = (__int128)h[0];
         const __int128 sq = ((__int128)h[3] << 64) | (__int128)h[2];
         const __int128 num = two_m * in - sq, den = two_m * two_m;
-        *q = (den == 0) ? 0.0 : (double)num / (double)den;
-        return LPA_OK;
+        return (den == 0) ? 0.0 : (double)num / (double)den;
     }
-    run_lists(g->Sig, g->macc);
-    k_mod_sq<<<grid_for(g->n, 256, 16), 256, 0, g->stream>>>(g->Sig, g->n, g->macc);
-    double h[3];
+    const double *h = static_cast<const double *>(acc_words);
+    const double in = h[0], two_m = h[1], sq = h[2];
+    return (two_m == 0.0) ? 0.0 : in / two_m - sq / (two_m * two_m);
+}
+
+int graph_modularity(lpa_graph *g, double *q)
+{
+    *q = 0.0;
+    if (g->n == 0) return LPA_OK;
+    LPA_CHECK(graph_modularity_enqueue(g));
+    unsigned long long h[4];
     LPA_CUDA(cudaMemcpyAsync(h, g->macc, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
     LPA_CUDA(cudaStreamSynchronize(g->stream));
-    const double in = h[0], two_m = h[1], sq = h[2];
-    *q = (two_m == 0.0) ? 0.0 : in / two_m - sq / (two_m * two_m);
+    *q = graph_modularity_finish(g, h);
     return LPA_OK;
 }
 

@@ -71,7 +71,9 @@ namespace lpa {
 int create_graph(const void *offsets, const int32_t *indices, const float *weights, int64_t n_vertices,
                  int64_t n_entries, int flags, cudaStream_t stream, Arena *arena, const lpa_tuning *tuning,
                  lpa_graph **out);
-void destroy_graph(lpa_graph *g);
+// Frees a graph handle.  arena_released: the caller has synchronised the graph's stream and
+// releases the whole arena the graph's blocks came from, so they are not returned one by one.
+void destroy_graph(lpa_graph *g, bool arena_released = false);
 // Counter rows for `iters` sweeps (device; the pinned mirror only when `mirror`).
 int ensure_counters(lpa_graph *g, int iters, bool mirror);
 // Smem slots per table of each vertex kernel for a tuning.
@@ -81,5 +83,9 @@ int upload_descriptor(lpa_graph *g);
 bool plan_int_weights(const lpa_graph *g);
 // Modularity of one graph (float64, or exact for integer weights).
 int graph_modularity(lpa_graph *g, double *q);
+// The same in two halves: enqueue the kernels that fill g->macc (four 8-byte words, on
+// g->stream), then Q from a host copy of those words.
+int graph_modularity_enqueue(lpa_graph *g);
+double graph_modularity_finish(const lpa_graph *g, const void *acc_words);
 
 }  // namespace lpa

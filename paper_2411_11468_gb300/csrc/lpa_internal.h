@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -209,17 +211,15 @@ class Arena {
     size_t largest_free() const;
 
   private:
-    struct Block {
-        size_t off, size;
-    };
     struct Region {
         unsigned char *base = nullptr;
         size_t cap = 0, used = 0;
-        std::vector<Block> free_;        // sorted by offset, coalesced
-        std::vector<Block> taken_;       // sorted by offset
+        std::map<size_t, size_t> free_;  // offset -> size, coalesced
+        std::map<size_t, size_t> taken_; // offset -> size
     };
     bool add_region(size_t bytes);
     static void *region_alloc(Region &r, size_t bytes);
+    std::mutex mu_;                      // allocations from several host threads (batch creation)
     std::vector<Region> regions_;
     bool grow_ = false;
     size_t grow_chunk_ = 0;

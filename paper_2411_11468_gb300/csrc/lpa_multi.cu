@@ -6,12 +6,14 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <deque>
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lpa_graph_internal.h"
@@ -274,6 +276,7 @@ struct lpa_batch {
     int exec_span = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool built = false;
+    unsigned long long *h_macc = nullptr;  // pinned: four modularity words per graph
 };
 
 static void batch_free(lpa_batch *b)
@@ -281,15 +284,75 @@ static void batch_free(lpa_batch *b)
     if (!b) return;
     DeviceGuard dg(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
-    for (lpa_graph *g : b->graphs) destroy_graph(g);
+    for (lpa_graph *g : b->graphs) destroy_graph(g, true);      // the arena goes below
     b->graphs.clear();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     delete b->arena;
     b->arena = nullptr;
+    if (b->h_macc) cudaFreeHost(b->h_macc);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;                                          // frees the plan arrays
+}
+
+// Runs fn(k, stream) for k = 0..count-1 on up to kHostThreads host threads, each with its own
+// non-blocking stream (ordered after the batch stream's work so far) and the batch's device;
+// every stream is synchronised before returning.  Returns the first failure's status, with
+// its message in *msg (graph index k + index_base).
+constexpr int kHostThreads = 8;
+
+template <class Fn>
+static int for_graphs_in_parallel(lpa_batch *b, int count, Fn fn, std::string *msg, int index_base)
+{
+    if (count <= 0) return LPA_OK;
+    unsigned hc = std::thread::hardware_concurrency();
+    const int threads = std::max(1, std::min<int>({kHostThreads, count, hc ? (int)hc : 1}));
+    cudaEvent_t after = nullptr;
+    if (cudaEventCreateWithFlags(&after, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        *msg = "event creation failed";
+        return LPA_ECUDA;
+    }
+    cudaEventRecord(after, b->stream);
+    std::atomic<int> next{0};
+    std::atomic<int> status{LPA_OK};
+    std::mutex mu;
+    auto worker = [&]() {
+        cudaSetDevice(b->device);
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            std::lock_guard<std::mutex> lock(mu);
+            if (status.load() == LPA_OK) {
+                status = LPA_ECUDA;
+                *msg = "stream creation failed";
+            }
+            return;
+        }
+        cudaStreamWaitEvent(s, after, 0);
+        for (;;) {
+            const int k = next.fetch_add(1);
+            if (k >= count || status.load() != LPA_OK) break;
+            const int st = fn(k, s);
+            if (st != LPA_OK) {
+                std::lock_guard<std::mutex> lock(mu);
+                if (status.load() == LPA_OK) {
+                    status = st;
+                    *msg = std::string(lpa_last_error()) + " (graph " + std::to_string(k + index_base) + ")";
+                }
+                break;
+            }
+        }
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(worker);     // and this thread
+    worker();
+    for (std::thread &t : pool) t.join();
+    cudaEventDestroy(after);
+    return status.load();
 }
 
 extern "C" {
@@ -335,18 +398,29 @@ int lpa_batch_create(int n_graphs, const lpa_graph_desc *descs, int flags, void 
         return LPA_ENOMEM;
     }
     b->mp.stream = b->stream;
-    for (int i = 0; i < n_graphs; ++i) {
+    b->graphs.assign((size_t)n_graphs, nullptr);
+    auto create_one = [&](int i, cudaStream_t s) {
         const lpa_graph_desc &d = descs[i];
-        lpa_graph *g = nullptr;
-        const int st = create_graph(d.offsets, d.indices, d.weights, d.n_vertices, d.n_entries, flags, b->stream,
-                                    b->arena, &b->tuning, &g);
-        if (st != LPA_OK) {
-            const std::string msg = std::string(lpa_last_error()) + " (graph " + std::to_string(i) + ")";
-            batch_free(b);
-            set_error(msg);
-            return st;
-        }
-        b->graphs.push_back(g);
+        return create_graph(d.offsets, d.indices, d.weights, d.n_vertices, d.n_entries, flags, s, b->arena,
+                            &b->tuning, &b->graphs[(size_t)i]);
+    };
+    // The first graph on this thread (it also settles the device properties computed on first
+    // use); the others on several host threads, each with its own stream: creating a graph
+    // waits on the device a few times (validation, weight properties, bucket sizes), and the
+    // waits of different graphs then overlap.
+    int st = create_one(0, b->stream);
+    std::string msg = st == LPA_OK ? std::string() : std::string(lpa_last_error()) + " (graph 0)";
+    if (st == LPA_OK && n_graphs > 1) {
+        dsm_max_class_bits();
+        st = for_graphs_in_parallel(b, n_graphs - 1, [&](int k, cudaStream_t s) { return create_one(k + 1, s); }, &msg,
+                                    1);
+    }
+    for (lpa_graph *g : b->graphs)
+        if (g) g->stream = b->stream;
+    if (st != LPA_OK) {
+        batch_free(b);
+        set_error(msg);
+        return st;
     }
     *out = b;
     return LPA_OK;
@@ -445,7 +519,24 @@ int lpa_batch_modularity(lpa_batch *b, double *q)
 {
     if (!b || !q) return LPA_EINVAL;
     DeviceGuard dg(b->device);
-    for (size_t i = 0; i < b->graphs.size(); ++i) LPA_CHECK(graph_modularity(b->graphs[i], q + i));
+    const size_t n = b->graphs.size();
+    if (!b->h_macc && cudaMallocHost((void **)&b->h_macc, n * 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        b->h_macc = nullptr;
+        set_error("lpa_batch_modularity: cudaMallocHost failed");
+        return LPA_ENOMEM;
+    }
+    // every graph's kernels and the copy of its four words on the batch stream, one wait at the
+    // end (launches from several host threads measured slower: they contend for the context)
+    for (size_t i = 0; i < n; ++i) {
+        lpa_graph *g = b->graphs[i];
+        LPA_CHECK(graph_modularity_enqueue(g));
+        if (g->n > 0)
+            LPA_CUDA(cudaMemcpyAsync(b->h_macc + 4 * i, g->macc, 4 * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, b->stream));
+    }
+    LPA_CUDA(cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < n; ++i) q[i] = graph_modularity_finish(b->graphs[i], b->h_macc + 4 * i);
     return LPA_OK;
 }
 

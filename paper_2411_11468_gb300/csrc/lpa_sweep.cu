@@ -18,15 +18,26 @@
 // lane that made its last add and no observed sum exceeds a final sum (weights are >= 0),
 // so the reduction equals the maximum over the table: the largest weight and, among equal
 // weights, the smallest label (Section 4 item 5).
+#include <mutex>
+
 #include "sweep_kernels.cuh"
 
 namespace lpa {
 
+// The remainder multipliers are copied to each device once (every handle creation asks).
 cudaError_t sweep_init_constants()
 {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
     cudaError_t e = init_magic();
     if (e == cudaSuccess) e = sweep_init_constants_alt();
-    return e != cudaSuccess ? e : sweep_init_constants_f64();
+    if (e == cudaSuccess) e = sweep_init_constants_f64();
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
 }
 
 size_t max_dynamic_smem()

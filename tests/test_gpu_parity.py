@@ -190,6 +190,35 @@ def test_sync_non_integer_weights(lpa, seed):
     assert abs(q - oracle.modularity(oracle_graph(csr), ref.labels)) < 1e-12
 
 
+def with_zero_weights(csr, seed, table):
+    """Same graph, each edge's weight drawn from `table` by a hash of the unordered pair (both
+    directions equal), zeros included: a zero-weight neighbour is still a candidate label with
+    sum 0, and a vertex whose neighbours all weigh 0 ties at 0 (smallest label)."""
+    n = csr.n
+    u = torch.repeat_interleave(torch.arange(n), csr.degrees())
+    v = csr.indices.long()
+    key = torch.minimum(u, v) * n + torch.maximum(u, v)
+    h = gg.draws53(seed, 11, key) % len(table)
+    w = torch.tensor(table, dtype=torch.float32)[h]
+    return gg.CSRGraph(csr.offsets, csr.indices, w, "zero-weights")
+
+
+@pytest.mark.parametrize("case", ["int-rmat", "int-small", "dyadic", "int-random"])
+def test_sync_zero_weight_edges(lpa, case):
+    """Weights w = 0 are allowed (finite, >= 0): integer sums (packed tables, exact modularity),
+    float sums (non-integer weights) and every bucket, against the oracle at every sweep."""
+    if case == "int-rmat":
+        csr, tuning = with_zero_weights(gg.rmat(13, weights="unit"), 1, [0.0, 1.0, 2.0, 3.0]), None
+    elif case == "int-small":
+        csr, tuning = with_zero_weights(gg.rmat(12, weights="unit"), 2, [0.0, 0.0, 5.0]), SMALL_BUCKETS
+    elif case == "dyadic":
+        csr, tuning = with_zero_weights(gg.rmat(12, weights="unit"), 3, [0.0, 0.5, 1.25]), SMALL_BUCKETS
+    else:
+        csr, tuning = with_zero_weights(gg.random_small(500, 0.05, 77, self_loops=True), 4, [0.0, 1.0]), PAPER_TABLES
+    g, ref = check_sync_every_iteration(lpa, csr, 0.05, 20, 4, tuning)
+    assert abs(g.modularity() - oracle.modularity(oracle_graph(csr), ref.labels)) < 1e-12
+
+
 @pytest.mark.parametrize("seed", range(2))
 def test_sync_non_integer_weights_float64_values(lpa, seed):
     csr = dyadic(gg.rmat(12 + seed, weights="unit"), seed)
