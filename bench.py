@@ -58,23 +58,29 @@ BYTES_PER_EDGE_U = 8       # unit weights (NULL, or all exactly 1: not read): in
 BYTES_PER_VERTEX = 17      # offsets 2x4 (amortised) + own label 4 + label write 4 + flag 1
 
 
-# DRAM bytes per launch of the dominant kernel, from one ncu capture of this bench's own command
-# on the default workload (profiles/hub_acc_rmat26_dram.md: mean of the four hub-accumulate
-# launches of one run).  Reported while the sweep sources hash as they did at capture time.
+# DRAM bytes per scanned CSR entry of each kernel slot (all launches of the slot over one run,
+# read + write, divided by the entries the slot scanned in that run), from one ncu capture of
+# the counters on R-MAT 22 with unit weights, a case small enough to capture with counters.  The
+# traffic reported for a launch of a larger graph is that rate times the entries the launch
+# scans: a scaled figure, not a measurement of the larger graph (its label gathers miss L2 more
+# often than R-MAT 22's).  Reported while the sweep sources hash as they did at capture time.
 TRAFFIC = {
-    "kernel": "hub_acc", "workload": "rmat26", "bytes_per_launch": 11.889e9,
+    "captured_on": "rmat22u",
+    "bytes_per_entry": {"cta": 4.68, "cta_large": 5.11, "group": 12.83, "hub_acc": 13.45, "thread": 31.15, "warp": 7.1},
     "sources": {
-        "sweep_kernels.cuh": "00243f705dafa377d69aacb39e4ecffbc1c40fc0bc3d19ac08111c802fd8be6b",
-        "lpa_sweep.cu": "c56f7b1dab01bfda7178475a2ef3e657b6b22c1064b6c79bd059a0cbdd94f710",
-        "lpa_internal.h": "9d205a69fd4a3e0c95545856e8d398b9e0d6e078554f05c87780059ad362406e",
-        "lpa_graph.cu": "fe05abc931c4e147f686a4faf0d2927afeb1b1c4b79b8b2db1d4b563ef06391e",
+        "sweep_kernels.cuh": "6bf66bd676d34194607304c782c38417876e159abbc48628ff862a4b719313de",
+        "lpa_sweep.cu": "4d3047241292df963a932efc55c2f81a366a8488ebad16538a6950acaed8c969",
+        "lpa_internal.h": "e7fe7dafe22c7897129871bb7f30ac95215fa3355e6ae82e13173f44f0d52d19",
+        "lpa_graph.cu": "eb9774b9ecd36dc53418623cc87ff74c60561eedae75797c20c78740456a384e",
     },
 }
 
 
-def traffic_for(kernel: str, workload: str):
+def traffic_for(kernel: str, entries_per_launch: float):
+    """Scaled DRAM bytes per launch of a kernel slot, or None (no rate, or sources changed)."""
     import hashlib
-    if kernel != TRAFFIC["kernel"] or workload != TRAFFIC["workload"]:
+    rate = TRAFFIC["bytes_per_entry"].get(kernel)
+    if rate is None or not TRAFFIC["sources"]:
         return None
     csrc = os.path.join(ROOT, "paper_2411_11468_gb300", "csrc")
     for name, digest in TRAFFIC["sources"].items():
@@ -84,7 +90,7 @@ def traffic_for(kernel: str, workload: str):
                     return None
         except OSError:
             return None
-    return TRAFFIC["bytes_per_launch"]
+    return rate * entries_per_launch
 
 
 def log(*a):
@@ -381,6 +387,7 @@ def roofline_of(stats, weighted, peak, peak_src, workload, steps):
     kms = [0.0] * lpa.NUM_KERNELS
     kbytes = [0.0] * lpa.NUM_KERNELS
     klaunch = [0] * lpa.NUM_KERNELS
+    kentries = [0] * lpa.NUM_KERNELS
     for s in stats:
         kb = kernel_bytes(s, weighted)
         for it in range(len(s["kernel_ms"])):
@@ -388,6 +395,7 @@ def roofline_of(stats, weighted, peak, peak_src, workload, steps):
                 if s["kernel_ms"][it][k] > 0:
                     kms[k] += s["kernel_ms"][it][k]
                     klaunch[k] += 1
+                    kentries[k] += s["kernel_edges"][it][k]
         for k in range(lpa.NUM_KERNELS):
             kbytes[k] += kb[k]
     dom = max(range(lpa.NUM_KERNELS), key=lambda k: kms[k])
@@ -407,7 +415,9 @@ def roofline_of(stats, weighted, peak, peak_src, workload, steps):
                  "frac": round(sweep0_bytes / (sweep0_ms / 1000.0) / 1e9 / peak, 4)}
     return {"bound": "hbm", "kernel": lpa.KERNEL_NAMES[dom], "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": traffic_for(lpa.KERNEL_NAMES[dom], workload), "peak_source": peak_src,
+            "traffic": traffic_for(lpa.KERNEL_NAMES[dom], kentries[dom] / max(1, klaunch[dom])),
+            "traffic_note": f"DRAM bytes per scanned entry captured on {TRAFFIC['captured_on']}, scaled by the "
+                            "entries one launch scans", "peak_source": peak_src,
             "bytes_model": f"{per_edge} B per scanned entry + {BYTES_PER_VERTEX} B per processed vertex",
             "first_sweep": first, "kernels": kernel_table}
 

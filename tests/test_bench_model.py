@@ -30,16 +30,16 @@ def test_kernel_bytes_counts_entries_and_vertices_per_slot():
     assert sum(1 for x in w if x) == 2
 
 
-def test_traffic_is_reported_only_for_its_kernel_workload_and_sources(monkeypatch):
+def test_traffic_is_a_scaled_rate_reported_only_while_sources_match(monkeypatch):
     csrc = os.path.join(ROOT, "paper_2411_11468_gb300", "csrc")
     name = "lpa_internal.h"
     digest = hashlib.sha256(open(os.path.join(csrc, name), "rb").read()).hexdigest()
-    rec = {"kernel": "hub_acc", "workload": "rmat26", "bytes_per_launch": 1.5e9, "sources": {name: digest}}
+    rec = {"captured_on": "rmat22u", "bytes_per_entry": {"hub_acc": 13.5, "warp": 7.0}, "sources": {name: digest}}
     monkeypatch.setattr(bench, "TRAFFIC", rec)
-    assert bench.traffic_for("hub_acc", "rmat26") == 1.5e9
-    assert bench.traffic_for("warp", "rmat26") is None
-    assert bench.traffic_for("hub_acc", "rmat22") is None
+    assert bench.traffic_for("hub_acc", 1e6) == 13.5e6
+    assert bench.traffic_for("warp", 2e6) == 14e6
+    assert bench.traffic_for("cta", 1e6) is None                     # no rate captured for the slot
     monkeypatch.setattr(bench, "TRAFFIC", dict(rec, sources={name: "0" * 64}))
-    assert bench.traffic_for("hub_acc", "rmat26") is None          # source changed since the capture
+    assert bench.traffic_for("hub_acc", 1e6) is None                 # source changed since the capture
     monkeypatch.setattr(bench, "TRAFFIC", dict(rec, sources={"no_such_file.cu": digest}))
-    assert bench.traffic_for("hub_acc", "rmat26") is None
+    assert bench.traffic_for("hub_acc", 1e6) is None
