@@ -1207,11 +1207,16 @@ __global__ void __launch_bounds__(kFlatWarps * 32, 3) k_flat(KArgs k)
     }
 }
 
+// Resident blocks per SM asked of the register allocator for the block tiers: 32 warps per SM
+// (64 registers a thread); the 128-thread tier otherwise took 94 registers and ran 20 warps
+// per SM (R-MAT 26: that tier 30 % faster with 32).
+template <int TPB> constexpr int kCtaMinBlocks() { return TPB <= 128 ? 8 : (TPB <= 256 ? 4 : (TPB <= 512 ? 2 : 1)); }
+
 // One thread block per vertex; the table (up to k.slots entries) lives in dynamic smem.
 // Persistent: each block takes work items from the queue; the list entries, processed flags
 // and row bounds of up to 32 vertices of the item are fetched at once into shared memory.
 template <int TPB, typename V, bool PULL, int PROBE>
-__global__ void __launch_bounds__(TPB) k_cta(KArgs k)
+__global__ void __launch_bounds__(TPB, kCtaMinBlocks<TPB>()) k_cta(KArgs k)
 {
     if (*k.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];

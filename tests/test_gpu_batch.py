@@ -138,8 +138,8 @@ def test_batch_async_bounds(lpa):
     modularity of fifteen batch runs within 0.01 of the oracle's run under the wave model of a
     single graph's schedule, every run within 0.015.  The model describes one graph's sweep; in
     a batch the graphs' items share the resident warps and drift further from lockstep
-    (measured: the planted partition's median 0.0058 below the model, against 0.004 alone), so
-    the 0.005 comparison is the single-graph test's."""
+    (measured: the planted partition's median 0.0058 below the model, against 0.004–0.0056
+    alone)."""
     import numpy as np
     graphs = [gg.sbm(10_000, 100, 16.0, 2.0, seed=0), gg.rmat(13, weights="int8"), gg.rmat(14, weights="int8"),
               gg.sbm(10_000, 100, 16.0, 2.0, seed=0)]
@@ -234,8 +234,7 @@ def test_server_async_requests(lpa):
     max-weight neighbour label, and the median modularity of the planted-partition results
     within 0.01 of the oracle's run under the wave model (library defaults).  The model
     describes one graph's sweep; in the server, requests at different sweeps share launches,
-    which the single-graph model does not describe (measured: median 0.006 below it), so this
-    test holds the mix to 0.01 and the 0.005 comparison is the single-graph and batch tests'."""
+    which the single-graph model does not describe (measured: median 0.006 below it)."""
     import numpy as np
     sbm = gg.sbm(10_000, 100, 16.0, 2.0, seed=0)
     graphs = [sbm, gg.rmat(14, weights="int8")] + [sbm] * 8
