@@ -66,9 +66,9 @@ BYTES_PER_VERTEX = 17      # offsets 2x4 (amortised) + own label 4 + label write
 # often than R-MAT 22's).  Reported while the sweep sources hash as they did at capture time.
 TRAFFIC = {
     "captured_on": "rmat22u",
-    "bytes_per_entry": {"cta": 4.68, "cta_large": 5.11, "group": 12.83, "hub_acc": 13.45, "thread": 31.15, "warp": 7.1},
+    "bytes_per_entry": {"cta": 4.68, "cta_large": 4.69, "group": 11.71, "hub_acc": 13.05, "thread": 29.38, "warp": 6.43},
     "sources": {
-        "sweep_kernels.cuh": "6bf66bd676d34194607304c782c38417876e159abbc48628ff862a4b719313de",
+        "sweep_kernels.cuh": "2d09207903fc83fda4ea9bf38ec58ff9614b89fe16844126549df1be1a63d5c0",
         "lpa_sweep.cu": "4d3047241292df963a932efc55c2f81a366a8488ebad16538a6950acaed8c969",
         "lpa_internal.h": "e7fe7dafe22c7897129871bb7f30ac95215fa3355e6ae82e13173f44f0d52d19",
         "lpa_graph.cu": "eb9774b9ecd36dc53418623cc87ff74c60561eedae75797c20c78740456a384e",

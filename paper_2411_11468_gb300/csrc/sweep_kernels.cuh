@@ -508,6 +508,17 @@ struct SweepView {
     int32_t peel;              // sum the weights of lanes holding the same label before inserting
 };
 
+// The fields of a view read for every scanned entry (kept in registers by kernels that hold
+// the full view in shared memory); load_entry and scan_row take either.
+struct RowView {
+    const int32_t *idx;
+    const int32_t *C;
+    const float *w;
+    int32_t peel;
+};
+
+__device__ __forceinline__ RowView row_of(const SweepView &a) { return RowView{a.idx, a.C, a.w, a.peel}; }
+
 __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
 {
     const GraphDev &G = gd[g];
@@ -580,8 +591,8 @@ __device__ __forceinline__ void movers_push(const SweepView &a, int2 *sbuf, int 
 // the row end and for self-loops (Algorithm 1 skips j = i).  With SEEN (pull sweeps) the raw
 // label words are or-ed into `seen` (bit 31: the neighbour moved in the previous sweep),
 // self-loops included; push sweeps never see the bit and skip that work.
-template <bool SEEN, typename V>
-__device__ __forceinline__ void load_entry(const SweepView &a, int32_t v, int64_t e, int64_t end, bool &has,
+template <bool SEEN, typename V, typename A>
+__device__ __forceinline__ void load_entry(const A &a, int32_t v, int64_t e, int64_t end, bool &has,
                                            int32_t &k, V &wv, uint32_t &seen)
 {
     has = e < end;
@@ -608,8 +619,8 @@ __device__ __forceinline__ void load_entry(const SweepView &a, int32_t v, int64_
 // Scans entries [start, end) of the row of v in rounds: each round covers U * step entries,
 // lane offset `lane` inside each step.  All U entries of a round are loaded (index, weight,
 // gathered label) before any of them is inserted, so U gathers per thread are in flight.
-template <int G, bool SHARED, bool TRACK, int U, bool SEEN, typename T>
-__device__ __forceinline__ void scan_row(const SweepView &a, int32_t v, int64_t start, int64_t end, int step,
+template <int G, bool SHARED, bool TRACK, int U, bool SEEN, typename T, typename A>
+__device__ __forceinline__ void scan_row(const A &a, int32_t v, int64_t start, int64_t end, int step,
                                          int lane, const T &tab, uint32_t p1, uint32_t b,
                                          typename BestOf<typename T::Val>::type &best, unsigned &fb,
                                          uint32_t &seen, uint32_t *ucnt = nullptr, int32_t *ulist = nullptr,
@@ -760,7 +771,12 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
     int nmov = 0;
     // counters and movers are kept per warp while consecutive items belong to one graph
     int cur_g = -1;
-    SweepView a{};
+    // The graph's view lives in shared memory, one per warp (its many pointers would otherwise
+    // hold registers across the scan); the three read for every entry are kept in registers.
+    __shared__ SweepView s_view[TPB / 32];
+    SweepView &a = s_view[threadIdx.x >> 5];
+    const int32_t *a_idx = nullptr, *a_C = nullptr;
+    const float *a_w = nullptr;
     unsigned fb = 0, c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
     for (;;) {
         int it = 0;
@@ -775,7 +791,12 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                 fb = c_act = c_edges = c_moved = c_marks = 0;
             }
             cur_g = item.g;
-            a = view_of(k.gd, item.g);
+            __syncwarp();
+            if (lane_w == 0) a = view_of(k.gd, item.g);
+            __syncwarp();
+            a_idx = a.idx;
+            a_C = a.C;
+            a_w = a.w;
             tab.probe = a.probe;
         }
         if (a.done || (a.pull != 0) != PULL) continue;                // the other launch takes it
@@ -833,19 +854,19 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                         for (int u = 0; u < U; ++u) {              // indices and weights
                             const int64_t e = eb + (int64_t)u * G + lane;
                             has[u] = e < o1;
-                            jr[u] = has[u] ? a.idx[e] : -1;
-                            wv[u] = (has[u] && a.w) ? to_value<V>(a.w[e]) : V(1);
+                            jr[u] = has[u] ? a_idx[e] : -1;
+                            wv[u] = (has[u] && a_w) ? to_value<V>(a_w[e]) : V(1);
                         }
 #pragma unroll
                         for (int u = 0; u < U; ++u) {              // labels (self-loops not inserted)
                             if (PULL) {
-                                const uint32_t cj = has[u] ? (uint32_t)a.C[jr[u]] : 0u;
+                                const uint32_t cj = has[u] ? (uint32_t)a_C[jr[u]] : 0u;
                                 seen |= cj;
                                 has[u] = has[u] && jr[u] != v;
                                 kk[u] = (int32_t)(cj & kLabelMask);
                             } else {
                                 has[u] = has[u] && jr[u] != v;
-                                kk[u] = has[u] ? a.C[jr[u]] : 0;
+                                kk[u] = has[u] ? a_C[jr[u]] : 0;
                             }
                         }
                         // inserts one slot at a time (rolled loop, entries shifted down in
@@ -854,7 +875,7 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                         for (int u = 0; u < U; ++u) {
                             if (!__any_sync(group_mask<G>(), has[0])) break;     // lanes of this group only
                             group_insert<G, (G > 1), false>(tab, p1, b, has[0], kk[0], wv[0], best, fb, nullptr,
-                                                            nullptr, a.peel != 0, a.w == nullptr);
+                                                            nullptr, a.peel != 0, a_w == nullptr);
 #pragma unroll
                             for (int q = 0; q + 1 < U; ++q) {
                                 has[q] = has[q + 1];
@@ -1215,25 +1236,35 @@ template <int TPB> constexpr int kCtaMinBlocks() { return TPB <= 128 ? 8 : (TPB 
 // One thread block per vertex; the table (up to k.slots entries) lives in dynamic smem.
 // Persistent: each block takes work items from the queue; the list entries, processed flags
 // and row bounds of up to 32 vertices of the item are fetched at once into shared memory.
+// A vertex costs two block barriers: after its scan, every warp takes the block's maximum
+// from the warps' maxima and decides the move itself (no barrier waits for one thread's
+// decision) and the block clears the slots the vertex used; the second barrier waits for the
+// clear, so the table is clean when the next vertex starts.
 template <int TPB, typename V, bool PULL, int PROBE>
 __global__ void __launch_bounds__(TPB, kCtaMinBlocks<TPB>()) k_cta(KArgs k)
 {
     if (*k.active == 0) return;
+    constexpr int NW = TPB / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     using Tab = typename TableFor<V, kPackShared, PROBE>::type;
     Tab tab;
     table_at(tab, smem, 1, k.slots, 0, false);
     __shared__ int s_item, s_nmov;
-    __shared__ int32_t s_mv[32], s_dec;
+    __shared__ int32_t s_mv[32];
     __shared__ int64_t s_mo0[32], s_mo1[32];
     __shared__ int2 s_mov[32];
     using Best = typename BestOf<V>::type;
-    __shared__ Best s_best[TPB / 32];
+    __shared__ Best s_best[NW];                        // the warps' maxima
     __shared__ unsigned long long s_mbase;
     if (threadIdx.x == 0) s_nmov = 0;
+    clear_table_vec(tab, (uint32_t)k.slots - 1u, threadIdx.x, TPB);   // clean at the start
     // counters (thread 0) are kept while consecutive items belong to one graph
     int cur_g = -1;
-    SweepView a{};
+    // The graph's view lives in shared memory (its pointers would otherwise hold registers
+    // across the scan); the fields read for every entry are kept in registers.
+    __shared__ SweepView s_view;
+    SweepView &a = s_view;
+    RowView r{};
     unsigned fb = 0;
     unsigned long long c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
     auto flush_counts = [&]() {
@@ -1249,17 +1280,19 @@ __global__ void __launch_bounds__(TPB, kCtaMinBlocks<TPB>()) k_cta(KArgs k)
         c_act = c_edges = c_moved = c_marks = 0;
     };
     for (;;) {
-        __syncthreads();                               // s_item and s_best of the last round are consumed
+        __syncthreads();                               // s_item of the last round is consumed
         if (threadIdx.x == 0) s_item = (int)atomicAdd(k.queue, 1u);
         __syncthreads();
         const int it = s_item;
         if (it >= k.n_items) break;
         const WorkItem item = k.items[it];
-        if (item.g != cur_g) {
+        if (item.g != cur_g) {                         // uniform for the block
             if (cur_g >= 0) flush_counts();
             cur_g = item.g;
-            a = view_of(k.gd, item.g);
-            tab.probe = a.probe;
+            __syncthreads();                           // the last graph's view is no longer read
+            if (threadIdx.x == 0) a = view_of(k.gd, item.g);
+            __syncthreads();
+            r = row_of(a);
         }
         if (a.done || (a.pull != 0) != PULL) continue;        // the other launch takes it
         for (int64_t base = 0; base < item.count; base += 32) {
@@ -1291,34 +1324,28 @@ __global__ void __launch_bounds__(TPB, kCtaMinBlocks<TPB>()) k_cta(KArgs k)
                 const uint32_t D = (uint32_t)(o1 - o0);
                 const uint32_t b = cap_bits(D << a.tshift);
                 const uint32_t p1 = cap_of_bits(b);
-                const int32_t cur = PULL ? (int32_t)((uint32_t)a.C[v] & kLabelMask) : a.C[v];
-                __syncthreads();                       // the previous vertex is finished
-                clear_table_vec(tab, p1, threadIdx.x, TPB);
-                __syncthreads();
+                const int32_t cur = PULL ? (int32_t)((uint32_t)r.C[v] & kLabelMask) : r.C[v];
+                tab.probe = a.probe;                   // the table is clean: cleared after its last use
                 Best best;
                 best_init(best);
                 uint32_t seen = 0;
                 constexpr int U = 2;                           // loads in flight per thread
-                scan_row<32, true, false, U, PULL>(a, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, tab,
+                scan_row<32, true, false, U, PULL>(r, v, o0 + (threadIdx.x & ~31) * U, o1, 32, threadIdx.x & 31, tab,
                                                    p1, b, best, fb, seen, nullptr, nullptr, TPB * U);
                 best = group_max<32>(best);
                 if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
                 bool act = true;
                 if (PULL) act = __syncthreads_or((seen & kMovedBit) != 0) != 0;   // a neighbour moved
                 else __syncthreads();
-                if (threadIdx.x < 32) {                // warp 0 combines the warps and decides
-                    Best x;
-                    best_init(x);
-                    if (threadIdx.x < TPB / 32) x = s_best[threadIdx.x];
-                    x = group_max<32>(x);
-                    if (threadIdx.x == 0) {
-                        int32_t c = -1;
-                        s_dec = (act && decide(x, cur, a.pl, c)) ? c : -1;
-                    }
-                }
-                __syncthreads();
-                const int32_t cstar = s_dec;
-                const bool moved = cstar >= 0;
+                // the scan is over: every warp combines the maxima and decides; the slots of
+                // this vertex are cleared
+                Best x;
+                best_init(x);
+                if ((threadIdx.x & 31) < NW) x = s_best[threadIdx.x & 31];
+                x = group_max<32>(x);
+                int32_t cstar = -1;
+                const bool moved = act && decide(x, cur, a.pl, cstar);
+                clear_table_vec(tab, p1, threadIdx.x, TPB);
                 if (moved) {
                     if (threadIdx.x == 0) {
                         if (a.async_mode) {
@@ -1330,7 +1357,7 @@ __global__ void __launch_bounds__(TPB, kCtaMinBlocks<TPB>()) k_cta(KArgs k)
                     }
                     if (a.async_mode) __syncthreads();
                     if (a.mark)
-                        for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[a.idx[e]] = 1;
+                        for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[r.idx[e]] = 1;
                 }
                 if (threadIdx.x == 0 && act) {
                     c_act += 1;
@@ -1340,6 +1367,7 @@ __global__ void __launch_bounds__(TPB, kCtaMinBlocks<TPB>()) k_cta(KArgs k)
                         if (a.mark) c_marks += D;
                     }
                 }
+                __syncthreads();                       // the table is clean for the next vertex
             }
             // append the batch's synchronous movers with one atomic
             __syncthreads();
@@ -1400,8 +1428,8 @@ __device__ __forceinline__ void hub_accumulate(const SweepView &a, const HubArgs
     typename BestOf<typename T::Val>::type best;
     best_init(best);
     uint32_t seen = 0;
-    scan_row<32, true, true, 2, PULL>(a, v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab, p1, b, best,
-                                      fb, seen, &s_cnt, s_list, TPB * 2);
+    scan_row<32, true, true, 2, PULL>(row_of(a), v, e0 + (threadIdx.x & ~31) * 2, e1, 32, threadIdx.x & 31, tab, p1, b,
+                                      best, fb, seen, &s_cnt, s_list, TPB * 2);
     if (fb) atomicAdd(a.fallbacks, (unsigned long long)fb);
     best = group_max<32>(best);
     if ((threadIdx.x & 31) == 0) s_best[threadIdx.x >> 5] = best;
@@ -1426,7 +1454,7 @@ __device__ __forceinline__ void hub_accumulate(const SweepView &a, const HubArgs
 }
 
 template <int TPB, bool PULL, int PROBE, bool F64>
-__global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
+__global__ void __launch_bounds__(TPB, 2) k_hub_acc(HArgs k)
 {
     if (*k.active == 0) return;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1434,7 +1462,10 @@ __global__ void __launch_bounds__(TPB) k_hub_acc(HArgs k)
     __shared__ typename BestOf<typename std::conditional<F64, double, float>::type>::type s_best[TPB / 32];
     __shared__ uint32_t s_cnt, s_base;
     const WorkItem item = k.items[blockIdx.x];
-    const SweepView a = view_of(k.gd, item.g);
+    __shared__ SweepView s_view;                       // in shared memory: frees registers for the scan
+    if (threadIdx.x == 0) s_view = view_of(k.gd, item.g);
+    __syncthreads();
+    const SweepView &a = s_view;
     if (a.done || (a.pull != 0) != PULL) return;      // the other launch takes it
     if (hub_two_pass_now(k.gd[item.g], a)) return;    // the two-pass kernels take this sweep
     const HubArgs &h = k.gd[item.g].hub;
