@@ -97,7 +97,7 @@ typedef struct lpa_stats {
     int64_t changed[LPA_STATS_MAX_ITERS];   /* dN: vertices that changed label        */
     int64_t active[LPA_STATS_MAX_ITERS];    /* vertices processed (unprocessed at start) */
     int64_t edges[LPA_STATS_MAX_ITERS];     /* CSR entries scanned                    */
-    int64_t marks[LPA_STATS_MAX_ITERS];     /* CSR entries of moved vertices (marks)  */
+    int64_t marks[LPA_STATS_MAX_ITERS];     /* CSR entries of the vertices that moved */
     float   iter_ms[LPA_STATS_MAX_ITERS];   /* device time of each sweep              */
     float   total_ms;                       /* device time of the whole call          */
     int32_t launches;                       /* kernels launched by this call          */

@@ -1214,6 +1214,7 @@ int upload_descriptor(lpa_graph *g)
     d.probe = g->tuning.probe;
     d.int_weights = plan_int_weights(g) ? 1 : 0;
     d.hub_tp = plan_int_weights(g) ? g->tuning.hub_two_pass : 0;     // the lists exist for integer sums
+    d.hub_deg = g->tuning.cta_xl_max;
     LPA_CUDA(cudaMemcpyAsync(g->gdd, &g->gdh, sizeof(GraphDev), cudaMemcpyHostToDevice, g->stream));
     return LPA_OK;
 }

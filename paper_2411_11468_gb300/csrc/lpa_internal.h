@@ -128,7 +128,7 @@ struct GraphDev {
     int32_t int_weights;       // integer weights with weighted degrees < 2^24 (uint32 sums)
     int32_t probe;             // table probe scheme (lpa_tuning.probe)
     int32_t hub_tp;            // two-pass hubs: 0 never, 1 in a run's first sweep, 2 every sweep
-    int32_t pad_tp;
+    int32_t hub_deg;           // rows longer than this are hubs (the hub bucket)
     // Cross-Check (allocated when a run asks for it): labels before the sweep of each mover,
     // vertex -> position in the mover list (-1 otherwise), per position the parent position
     // (or -1 / -2 for a move found good / bad directly) and the resolution word

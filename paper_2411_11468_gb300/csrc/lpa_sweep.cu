@@ -149,9 +149,9 @@ __global__ void k_hub_move(HArgs k)
                 a.mover_v[pos] = v;
                 a.mover_c[pos] = cstar;
             }
-            if (a.mark) h.hub_act[hh] = 2;          // k_hub_mark marks its neighbours
+            h.hub_act[hh] = a.mark ? 2 : 3;          // 2: k_hub_mark marks its neighbours now; 3: maybe after k_decide
             n_moved += 1;
-            if (a.mark) n_marks += D;
+            n_marks += D;
         }
     }
     unsigned long long *c = a.ctr + LPA_K_HUB_ACC * kCtrFields;
@@ -161,18 +161,30 @@ __global__ void k_hub_move(HArgs k)
     if (n_marks) atomicAdd(c + CTR_MARKS, n_marks);
 }
 
+// Marks the neighbours of the moved hubs, a block per chunk of their rows: in the sweep
+// (deferred = 0: hubs that moved in a marking sweep, into the next sweep's flags), or after
+// k_decide (deferred = 1: hubs that moved in a sweep without marks when k_decide chose marks
+// for the next sweep (rs->fin), into the flags of sweep rs->l, also after the run's last sweep).
 template <int TPB>
-__global__ void __launch_bounds__(TPB) k_hub_mark(HArgs k)
+__global__ void __launch_bounds__(TPB) k_hub_mark(HArgs k, int deferred)
 {
-    if (*k.active == 0) return;
     const WorkItem item = k.items[blockIdx.x];
-    const SweepView a = view_of(k.gd, item.g);
-    if (a.done) return;
-    const HubArgs &h = k.gd[item.g].hub;
+    const GraphDev &G = k.gd[item.g];
+    const HubArgs &h = G.hub;
     const int64_t c = item.start;
-    if (h.hub_act[h.chunk_h[c]] != 2) return;
+    uint8_t *flags;
+    if (deferred) {
+        const RunState *rs = G.rs;
+        if (!rs->fin || h.hub_act[h.chunk_h[c]] != 3) return;
+        flags = (rs->l & 1) ? G.flags1 : G.flags0;
+    } else {
+        if (*k.active == 0) return;
+        const SweepView a = view_of(k.gd, item.g);
+        if (a.done || h.hub_act[h.chunk_h[c]] != 2) return;
+        flags = a.flag_next;
+    }
     const int64_t e0 = h.chunk_e0[c], e1 = h.chunk_e1[c];
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += TPB) a.flag_next[a.idx[e]] = 1;
+    mark_range(flags, G.idx, e0, e1, threadIdx.x, TPB);
 }
 
 // Synchronous mode, after a pull sweep: clear the moved bits of the previous sweep's movers
@@ -334,10 +346,15 @@ __global__ void k_cc_revert(HArgs k, const unsigned *ctr)
 
 // After each sweep, per graph: the stop test of Algorithm 1 (after a sweep without Pick-Less,
 // stop when dN / n < tolerance; stop at max_iters), then advance to the next sweep.
-// Synchronous mode: the next sweep pulls its active vertices from moved bits when this sweep
-// wrote no marks.  Only the first sweep of a fresh run skips its marks (it moves most vertices
-// and its marks are the costliest); every later sweep marks, which measured cheaper than
-// processing every vertex in the sweep after it.
+// Synchronous mode: the next sweep finds its active vertices (those with a neighbour that
+// moved) from marks or from moved bits.  Marks cost a scattered byte store per entry of every
+// mover; moved bits cost the next sweep a scan of every row.  So a sweep whose movers hold
+// fewer than 1 / kFewMovedEntries of the CSR entries has its movers' neighbours marked: by the
+// sweep itself when it was told to mark (rs->mark), else after it (rs->fin: k_finalize, and
+// k_hub_mark for hubs); otherwise the next sweep pulls.  A sweep marks as it goes when the
+// sweep before it moved few entries (a fresh run's first sweep moves most vertices and never
+// does).  Cross-Check runs always mark.
+constexpr long long kFewMovedEntries = 4;
 
 __global__ void k_decide(const GraphDev *gd, int n_graphs, int32_t *active)
 {
@@ -360,11 +377,16 @@ __global__ void k_decide(const GraphDev *gd, int n_graphs, int32_t *active)
         done = 1;
     }
     if (!rs->async_mode) {
+        long long me = 0;                             // CSR entries of this sweep's movers
+        for (int q = 0; q < LPA_NUM_KERNELS; ++q) me += (long long)a.ctr[q * kCtrFields + CTR_MARKS];
+        const long long m = (long long)gd[g].off[rs->n];
+        const bool few = rs->cc_period > 0 || me * kFewMovedEntries < m;
         if (done) {
             rs->fin = rs->mark ? 0 : 1;               // this sweep's moved bits still stand
         } else {
-            rs->pull = rs->mark ? 0 : 1;
-            rs->mark = 1;
+            rs->fin = (!rs->mark && few) ? 1 : 0;     // mark after the sweep
+            rs->pull = (rs->mark || few) ? 0 : 1;
+            rs->mark = few ? 1 : 0;
         }
     }
     rs->l = l + 1;
@@ -375,10 +397,15 @@ __global__ void k_decide(const GraphDev *gd, int n_graphs, int32_t *active)
     if (!done) atomicAdd(active, 1);
 }
 
-// After the last sweep of a synchronous run that set moved bits: turn them into the marks of
-// the next sweep's processed flags (so the state is that of the marking sweep) and clear them.
-// blockIdx.y: graph; a warp per mover of the last sweep.
-__global__ void k_finalize(const GraphDev *gd)
+// After a synchronous sweep that set moved bits, when k_decide chose marks for the next sweep
+// (rs->fin: few moved entries, or the run's last sweep, so that the saved state is that of a
+// marking sweep): turn the bits into marks on the processed flags of sweep rs->l and clear
+// them.  blockIdx.y: graph.  A warp takes 32 movers at a time: a lane marks the row of its
+// own mover when it is short, and the warp marks the longer rows one after the other, all
+// lanes on one row; hubs' rows are left to the chunked k_hub_mark.
+constexpr int kFinalizeThreads = 256;
+constexpr int64_t kFinalizeShort = kMarkUnroll;        // rows a lane marks alone
+__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const GraphDev *gd)
 {
     const GraphDev &G = gd[blockIdx.y];
     const RunState *rs = G.rs;
@@ -387,13 +414,32 @@ __global__ void k_finalize(const GraphDev *gd)
     const int32_t *mv = (last & 1) ? G.mover_v1 : G.mover_v;
     const unsigned long long n = G.mover_count[last & 1];
     uint8_t *flags = (rs->l & 1) ? G.flags1 : G.flags0;      // processed flags of sweep rs->l
+    // in registers: the byte stores to the flags could otherwise alias the descriptor
+    const int64_t *off = G.off;
+    const int32_t *idx = G.idx;
+    int32_t *C = G.C;
+    const int64_t hub_deg = G.hub_deg;
     const int lane = threadIdx.x & 31;
-    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
-    for (unsigned long long i = blockIdx.x * (unsigned long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
-         i += warps) {
-        const int32_t v = mv[i];
-        if (lane == 0) G.C[v] = (int32_t)((uint32_t)G.C[v] & kLabelMask);
-        for (int64_t e = G.off[v] + lane; e < G.off[v + 1]; e += 32) flags[G.idx[e]] = 1;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (kFinalizeThreads / 32);
+    for (unsigned long long base = (blockIdx.x * (unsigned long long)(kFinalizeThreads / 32) + (threadIdx.x >> 5)) * 32;
+         base < n; base += warps * 32) {
+        int64_t e0 = 0, D = 0;
+        if (base + lane < n) {
+            const int32_t v = mv[base + lane];
+            C[v] = (int32_t)((uint32_t)C[v] & kLabelMask);
+            e0 = off[v];
+            D = off[v + 1] - e0;
+            if (D > hub_deg) D = 0;                   // a hub
+        }
+        if (D <= kFinalizeShort) mark_range(flags, idx, e0, e0 + D, 0, 1);
+        unsigned longm = __ballot_sync(0xFFFFFFFFu, D > kFinalizeShort);
+        while (longm) {
+            const int src = __ffs(longm) - 1;
+            longm &= longm - 1;
+            const int64_t r0 = __shfl_sync(0xFFFFFFFFu, e0, src);
+            const int64_t r1 = r0 + __shfl_sync(0xFFFFFFFFu, D, src);
+            mark_range(flags, idx, r0, r1, lane, 32);
+        }
     }
 }
 
@@ -500,7 +546,7 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
         if (e != cudaSuccess) return e;
         h.items = p.hub_items[HL_MARK];
         e = timed(LPA_K_HUB_MARK, [&] {
-            k_hub_mark<512><<<p.n_hub_items[HL_MARK], 512, 0, s>>>(h);
+            k_hub_mark<512><<<p.n_hub_items[HL_MARK], 512, 0, s>>>(h, 0);
             return cudaGetLastError();
         });
         if (e != cudaSuccess) return e;
@@ -528,8 +574,13 @@ cudaError_t enqueue_sweep(const SweepPlan &p, cudaStream_t s, LaunchHook *hook, 
     e = cudaMemsetAsync(p.active_count, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     k_decide<<<(p.n_graphs + 127) / 128, 128, 0, s>>>(p.gd, p.n_graphs, p.active_count);
-    k_finalize<<<dim3(bx, (unsigned)p.n_graphs), 256, 0, s>>>(p.gd);
+    k_finalize<<<dim3(bx, (unsigned)p.n_graphs), kFinalizeThreads, 0, s>>>(p.gd);
     if (launches) *launches += 2;
+    if (p.n_hub_items[HL_MARK] > 0) {                 // the hubs' share of k_finalize's marks
+        h.items = p.hub_items[HL_MARK];
+        k_hub_mark<512><<<p.n_hub_items[HL_MARK], 512, 0, s>>>(h, 1);
+        if (launches) ++*launches;
+    }
     return cudaGetLastError();
 }
 

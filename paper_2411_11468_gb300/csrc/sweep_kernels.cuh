@@ -519,6 +519,27 @@ struct RowView {
 
 __device__ __forceinline__ RowView row_of(const SweepView &a) { return RowView{a.idx, a.C, a.w, a.peel}; }
 
+// Marks the neighbours in entries [e0, e1) (first entry `first`, stride `step`) unprocessed for
+// the next sweep.  Each thread loads kMarkUnroll indices before it stores their flags: a byte
+// store may alias the index array as far as the compiler knows, so a plain loop would wait a
+// full load latency per entry.
+constexpr int kMarkUnroll = 8;
+__device__ __forceinline__ void mark_range(uint8_t *flags, const int32_t *idx, int64_t e0, int64_t e1, int64_t first,
+                                           int64_t step)
+{
+    for (int64_t eb = e0 + first; eb < e1; eb += kMarkUnroll * step) {
+        int32_t j[kMarkUnroll];
+#pragma unroll
+        for (int u = 0; u < kMarkUnroll; ++u) {
+            const int64_t e = eb + u * step;
+            j[u] = e < e1 ? idx[e] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kMarkUnroll; ++u)
+            if (j[u] >= 0) flags[j[u]] = 1;
+    }
+}
+
 __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
 {
     const GraphDev &G = gd[g];
@@ -903,7 +924,7 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                             for (int u = 0; u < U; ++u)
                                 if (jr[u] >= 0) a.flag_next[jr[u]] = 1;
                         } else {
-                            for (int64_t e = o0 + lane; e < o1; e += G) a.flag_next[a.idx[e]] = 1;
+                            mark_range(a.flag_next, a_idx, o0, o1, lane, G);
                         }
                     }
                     if (lane == 0 && act) {
@@ -911,7 +932,7 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                         c_edges += D;
                         if (moved) {
                             c_moved += 1;
-                            if (a.mark) c_marks += D;
+                            c_marks += D;                  // entries of the movers
                         }
                     }
                 }
@@ -1198,7 +1219,7 @@ __global__ void __launch_bounds__(kFlatWarps * 32, 3) k_flat(KArgs k)
                     }
                     if (moved) {
                         c_moved += 1;
-                        if (a.mark) c_marks += D;
+                        c_marks += D;                  // entries of the movers
                         if (a.async_mode) {
                             a.C[v] = cstar;
                             __threadfence();
@@ -1213,7 +1234,7 @@ __global__ void __launch_bounds__(kFlatWarps * 32, 3) k_flat(KArgs k)
                         mm &= mm - 1;
                         const int64_t r0 = __shfl_sync(0xFFFFFFFFu, o0, src);
                         const uint32_t rd = __shfl_sync(0xFFFFFFFFu, D, src);
-                        for (uint32_t q = lane; q < rd; q += 32) a.flag_next[a.idx[r0 + q]] = 1;
+                        mark_range(a.flag_next, a.idx, r0, r0 + rd, lane, 32);
                     }
                 }
                 __syncwarp();                          // the region and the segment data are free
@@ -1357,14 +1378,14 @@ __global__ void __launch_bounds__(TPB, kCtaMinBlocks<TPB>()) k_cta(KArgs k)
                     }
                     if (a.async_mode) __syncthreads();
                     if (a.mark)
-                        for (int64_t e = o0 + threadIdx.x; e < o1; e += TPB) a.flag_next[r.idx[e]] = 1;
+                        mark_range(a.flag_next, r.idx, o0, o1, threadIdx.x, TPB);
                 }
                 if (threadIdx.x == 0 && act) {
                     c_act += 1;
                     c_edges += D;
                     if (moved) {
                         c_moved += 1;
-                        if (a.mark) c_marks += D;
+                        c_marks += D;                  // entries of the movers
                     }
                 }
                 __syncthreads();                       // the table is clean for the next vertex
