@@ -229,12 +229,15 @@ template <> __device__ __forceinline__ double acc_weight<double>(const float *w,
     return w ? (double)w[e] : 1.0;
 }
 
-// Sums over entries e = start, start + STEP, ... < end of one row: k += w_e, and in += w_e
-// where the neighbour's label equals ci.  Four entries per round so that four label gathers
-// are in flight per thread.
+// Sums over entries e = start, start + STEP, ... < end of the row of vertex i (label ci):
+// k += w_e, and in += w_e where the neighbour's label equals ci.  The graph is undirected with
+// symmetric weights, so an edge {i, j} is counted from the entry with j > i at twice its weight
+// (the entry j -> i holds the same weight) and a self-loop entry as it stands: half the label
+// gathers, the same sums.  Four entries per round so that four label gathers are in flight
+// per thread.
 template <int STEP, typename ACC>
 __device__ __forceinline__ void mod_row(const int32_t *idx, const float *w, const int32_t *C, int64_t start,
-                                        int64_t end, int32_t ci, ACC &k, ACC &in)
+                                        int64_t end, int32_t i, int32_t ci, ACC &k, ACC &in)
 {
     for (int64_t e = start; e < end; e += 4 * (int64_t)STEP) {
         int32_t j[4];
@@ -248,7 +251,11 @@ __device__ __forceinline__ void mod_row(const int32_t *idx, const float *w, cons
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             k += we[u];
-            if (j[u] >= 0 && C[j[u]] == ci) in += we[u];
+            if (j[u] > i) {
+                if (C[j[u]] == ci) in += we[u] + we[u];
+            } else if (j[u] == i) {
+                in += we[u];
+            }
         }
     }
 }
@@ -276,7 +283,7 @@ __global__ void __launch_bounds__(256) k_mod_list(const int64_t *off, const int3
         const int64_t o0 = off[i], o1 = off[i + 1];
         const int32_t ci = C[i];
         ACC k = ACC(0), in = ACC(0);
-        mod_row<G, ACC>(idx, w, C, o0 + lane, o1, ci, k, in);
+        mod_row<G, ACC>(idx, w, C, o0 + lane, o1, i, ci, k, in);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
             k += __shfl_xor_sync(gm, k, o);
@@ -322,7 +329,7 @@ __global__ void __launch_bounds__(256) k_mod_hub_chunks(const int32_t *idx, cons
     const int32_t v = hub_v[chunk_h[blockIdx.x]];
     const int32_t ci = C[v];
     ACC k = ACC(0), in = ACC(0);
-    mod_row<256, ACC>(idx, w, C, chunk_e0[blockIdx.x] + threadIdx.x, chunk_e1[blockIdx.x], ci, k, in);
+    mod_row<256, ACC>(idx, w, C, chunk_e0[blockIdx.x] + threadIdx.x, chunk_e1[blockIdx.x], v, ci, k, in);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         k += __shfl_xor_sync(0xFFFFFFFFu, k, o);
