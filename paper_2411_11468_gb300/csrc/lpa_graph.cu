@@ -52,28 +52,37 @@ __global__ void k_off32to64(const int32_t *in, int64_t *out, int64_t n1)
 }
 
 // error bits: 1 offsets decrease, 2 offsets[0] != 0, 4 offsets[n] != m, 8 index out of
-// range, 16 weight negative / NaN / Inf
+// range, 16 weight negative / NaN / Inf.  Also counts the adjacent index pairs that do not
+// increase, over the whole index array (desc[0]) and where the second entry starts a
+// non-empty row (desc[1]): every row's indices strictly increase iff the two are equal.
 __global__ void k_validate(const int64_t *off, const int32_t *idx, const float *w, int64_t n, int64_t m,
-                           unsigned *err)
+                           unsigned *err, unsigned long long *desc)
 {
     unsigned bad = 0;
+    unsigned long long d_all = 0, d_row = 0;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (tid == 0) {
         if (off[0] != 0) bad |= 2u;
         if (off[n] != m) bad |= 4u;
     }
-    for (int64_t i = tid; i < n; i += stride)
-        if (off[i] > off[i + 1]) bad |= 1u;
+    for (int64_t i = tid; i < n; i += stride) {
+        const int64_t b = off[i], b1 = off[i + 1];
+        if (b > b1) bad |= 1u;
+        if (i > 0 && b > 0 && b < m && b1 > b && idx[b - 1] >= idx[b]) ++d_row;
+    }
     for (int64_t e = tid; e < m; e += stride) {
         const int32_t j = idx[e];
         if (j < 0 || (int64_t)j >= n) bad |= 8u;
+        if (e + 1 < m && j >= idx[e + 1]) ++d_all;
         if (w) {
             const float x = w[e];
             if (!(isfinite(x) && x >= 0.0f)) bad |= 16u;
         }
     }
     if (bad) atomicOr(err, bad);
+    if (d_all) atomicAdd(desc + 0, d_all);
+    if (d_row) atomicAdd(desc + 1, d_row);
 }
 
 __device__ __forceinline__ unsigned long long mix_sym(unsigned long long z)
@@ -1222,6 +1231,7 @@ int upload_descriptor(lpa_graph *g)
     d.int_weights = plan_int_weights(g) ? 1 : 0;
     d.hub_tp = plan_int_weights(g) ? g->tuning.hub_two_pass : 0;     // the lists exist for integer sums
     d.hub_deg = g->tuning.cta_xl_max;
+    d.rows_strict = g->rows_strict ? 1 : 0;
     LPA_CUDA(cudaMemcpyAsync(g->gdd, &g->gdh, sizeof(GraphDev), cudaMemcpyHostToDevice, g->stream));
     return LPA_OK;
 }
@@ -1333,12 +1343,20 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
         }
     }
     // validation on the device
+    unsigned long long *desc = nullptr;
+    if ((st = dalloc(g, &desc, 2)) != LPA_OK) return fail(st);
     cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s);
-    k_validate<<<grid_for(std::max<int64_t>(n, m), 256, 16), 256, 0, s>>>(g->off, g->idx, g->w, n, m, g->d_err);
+    cudaMemsetAsync(desc, 0, 2 * sizeof(unsigned long long), s);
+    k_validate<<<grid_for(std::max<int64_t>(n, m), 256, 16), 256, 0, s>>>(g->off, g->idx, g->w, n, m, g->d_err,
+                                                                          desc);
     unsigned err = 0;
+    unsigned long long hdesc[2] = {0ull, 1ull};
     cudaMemcpyAsync(&err, g->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(hdesc, desc, sizeof(hdesc), cudaMemcpyDeviceToHost, s);
     e = cudaStreamSynchronize(s);
+    dfree(g, desc);
     if (e != cudaSuccess) return cuda_fail(e, "validate");
+    g->rows_strict = hdesc[0] == hdesc[1];
     if (err) {
         std::string msg = "lpa_create: invalid graph:";
         if (err & 1) msg += " offsets decrease;";
@@ -1763,6 +1781,7 @@ int lpa_run_cc(lpa_graph *g, double tolerance, int max_iters, int pl_period, int
     rs.cc_period = cc_period;
     rs.tol = tolerance;
     rs.n = g->n;
+    rs.fresh = (mode & LPA_RESUME) ? 0 : 1;
     g->hm->active = 1;
     LPA_CUDA(cudaMemcpyAsync(g->rs_d, &g->hm->rs, sizeof(RunState), cudaMemcpyHostToDevice, s));
     LPA_CUDA(cudaMemcpyAsync(g->active, &g->hm->active, sizeof(int32_t), cudaMemcpyHostToDevice, s));

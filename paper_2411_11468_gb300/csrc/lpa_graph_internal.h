@@ -61,6 +61,7 @@ struct lpa_graph {
     } *hm = nullptr;                                 // pinned
     int next_iter = 0;
     bool int_weights = false;                        // integer weights, weighted degrees < 2^24
+    bool rows_strict = false;                        // every row's indices strictly increase
     int64_t bytes = 0;
     std::vector<cudaEvent_t> events;
 };

@@ -60,6 +60,8 @@ struct RunState {
     int32_t fin;          // stopped after a sweep that set moved bits: k_finalize turns them into marks
     int32_t cc_period;    // Cross-Check after sweeps l with l mod cc_period = 0 (0: never; sync only)
     int32_t cc_unresolved;  // set when the Cross-Check resolution did not finish (not expected)
+    int32_t fresh;        // the run started from labels = vertex ids (not resumed)
+    int32_t pad_fresh;
 };
 
 // Synchronous mode, sweeps that move many vertices: instead of marking the neighbours of each
@@ -129,6 +131,8 @@ struct GraphDev {
     int32_t probe;             // table probe scheme (lpa_tuning.probe)
     int32_t hub_tp;            // two-pass hubs: 0 never, 1 in a run's first sweep, 2 every sweep
     int32_t hub_deg;           // rows longer than this are hubs (the hub bucket)
+    int32_t rows_strict;       // every row's indices strictly increase (no repeated neighbour)
+    int32_t pad_rs;
     // Cross-Check (allocated when a run asks for it): labels before the sweep of each mover,
     // vertex -> position in the mover list (-1 otherwise), per position the parent position
     // (or -1 / -2 for a move found good / bad directly) and the resolution word

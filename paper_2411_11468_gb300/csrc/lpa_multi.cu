@@ -218,6 +218,7 @@ RunState fresh_state(int64_t n, double tol, int max_iters, int pl_period, bool a
     r.mark = async_mode ? 1 : 0;                    // see lpa_run: a fresh synchronous run starts without marks
     r.tol = tol;
     r.n = n;
+    r.fresh = 1;
     r.done = (n == 0 || max_iters <= 0) ? 1 : 0;
     return r;
 }

@@ -413,9 +413,13 @@ template <int G, bool SHARED, bool TRACK, typename T>
 __device__ __forceinline__ void group_insert(const T &tab, uint32_t p1, uint32_t b, bool has, int32_t k,
                                              typename T::Val w, typename BestOf<typename T::Val>::type &best,
                                              unsigned &fb, uint32_t *ucnt = nullptr, int32_t *ulist = nullptr,
-                                             bool peel = true, bool unit = false)
+                                             bool peel = true, bool unit = false, bool notab = false)
 {
     using V = typename T::Val;
+    if (notab) {                                       // distinct labels: the entry is its label's sum
+        if (has) best_add(best, w, k);
+        return;
+    }
     if (G >= 2 && peel && unit) {                      // uniform over the group
         // unit weights: every group of lanes holding one label is found at once, and its lowest
         // lane inserts the group's size (its weight sum) for all of them, every group in parallel
@@ -506,6 +510,8 @@ struct SweepView {
     int32_t mark, pull;        // marks written this sweep; activity from moved bits (sync)
     int32_t probe;             // probe scheme of the tables
     int32_t peel;              // sum the weights of lanes holding the same label before inserting
+    int32_t notab;             // every label of a row is distinct: the maximum needs no table
+    int32_t pad_notab;
 };
 
 // The fields of a view read for every scanned entry (kept in registers by kernels that hold
@@ -515,9 +521,10 @@ struct RowView {
     const int32_t *C;
     const float *w;
     int32_t peel;
+    int32_t notab;
 };
 
-__device__ __forceinline__ RowView row_of(const SweepView &a) { return RowView{a.idx, a.C, a.w, a.peel}; }
+__device__ __forceinline__ RowView row_of(const SweepView &a) { return RowView{a.idx, a.C, a.w, a.peel, a.notab}; }
 
 // Marks the neighbours in entries [e0, e1) (first entry `first`, stride `step`) unprocessed for
 // the next sweep.  Each thread loads kMarkUnroll indices before it stores their flags: a byte
@@ -569,6 +576,12 @@ __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
     // The first sweep of a run from fresh labels (label = vertex id) finds every neighbour label
     // distinct in a duplicate-free row, so the duplicate-label rounds would find nothing there.
     v.peel = l > 0;
+    // Synchronous sweep 0 of a fresh run on rows whose indices strictly increase: every
+    // neighbour label of a row is a distinct vertex id, so K_{i->c} is the weight of the one
+    // entry holding c, and the arg-max of Algorithm 1 is the maximum over the entries of
+    // (weight, smallest label): the kernels skip the tables.
+    v.notab = (rs->fresh && l == 0 && !rs->async_mode && G.rows_strict) ? 1 : 0;
+    v.pad_notab = 0;
     const int slot = (l - rs->first) % (G.ctr_iters > 0 ? G.ctr_iters : 1);
     v.ctr = G.ctr + (size_t)(slot < 0 ? 0 : slot) * kPerSweep;
     v.fallbacks = G.fallbacks;
@@ -658,7 +671,7 @@ __device__ __forceinline__ void scan_row(const A &a, int32_t v, int64_t start, i
 #pragma unroll
         for (int u = 0; u < U; ++u)
             group_insert<G, SHARED, TRACK>(tab, p1, b, has[u], k[u], wv[u], best, fb, ucnt, ulist, a.peel != 0,
-                                           a.w == nullptr);
+                                           a.w == nullptr, a.notab != 0);
     }
 }
 
@@ -798,6 +811,7 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
     SweepView &a = s_view[threadIdx.x >> 5];
     const int32_t *a_idx = nullptr, *a_C = nullptr;
     const float *a_w = nullptr;
+    bool notab = false;
     unsigned fb = 0, c_act = 0, c_edges = 0, c_moved = 0, c_marks = 0;
     for (;;) {
         int it = 0;
@@ -818,6 +832,7 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
             a_idx = a.idx;
             a_C = a.C;
             a_w = a.w;
+            notab = a.notab != 0;
             tab.probe = a.probe;
         }
         if (a.done || (a.pull != 0) != PULL) continue;                // the other launch takes it
@@ -855,7 +870,8 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                     const uint32_t p1 = cap_of_bits(b);
                     const int32_t cur = PULL ? (int32_t)((uint32_t)a.C[v] & kLabelMask) : a.C[v];
                     uint32_t seen = 0;
-                    if (G == 1) {
+                    if (notab) {
+                    } else if (G == 1) {
                         clear_table_private(tab, p1);              // hashtableClear
                     } else {
                         group_sync<G>();                           // previous vertex's inserts are done
@@ -896,7 +912,7 @@ __global__ void __launch_bounds__(TPB, GroupUnroll<G>::kMinBlocks) k_group(KArgs
                         for (int u = 0; u < U; ++u) {
                             if (!__any_sync(group_mask<G>(), has[0])) break;     // lanes of this group only
                             group_insert<G, (G > 1), false>(tab, p1, b, has[0], kk[0], wv[0], best, fb, nullptr,
-                                                            nullptr, a.peel != 0, a_w == nullptr);
+                                                            nullptr, a.peel != 0, a_w == nullptr, notab);
 #pragma unroll
                             for (int q = 0; q + 1 < U; ++q) {
                                 has[q] = has[q + 1];
@@ -1366,7 +1382,7 @@ __global__ void __launch_bounds__(TPB, kCtaMinBlocks<TPB>()) k_cta(KArgs k)
                 x = group_max<32>(x);
                 int32_t cstar = -1;
                 const bool moved = act && decide(x, cur, a.pl, cstar);
-                clear_table_vec(tab, p1, threadIdx.x, TPB);
+                if (!r.notab) clear_table_vec(tab, p1, threadIdx.x, TPB);
                 if (moved) {
                     if (threadIdx.x == 0) {
                         if (a.async_mode) {
@@ -1418,10 +1434,12 @@ __global__ void __launch_bounds__(TPB, kCtaMinBlocks<TPB>()) k_cta(KArgs k)
 // Whether graph g's hubs take the two passes in this sweep: every sweep (hub_tp = 2), or only
 // in the first sweep of a run from fresh labels (hub_tp = 1), where every neighbour label of a
 // duplicate-free row is distinct and the HBM tables' atomics miss the most; later sweeps,
-// with few labels left, are cheaper in the single pass.
+// with few labels left, are cheaper in the single pass.  With hub_tp = 1 a sweep that needs no
+// tables (notab) takes the single pass, which then only takes the maximum (with hub_tp = 2
+// the single-pass chunks do not exist).
 __device__ __forceinline__ bool hub_two_pass_now(const GraphDev &G, const SweepView &a)
 {
-    return G.hub_tp == 2 || (G.hub_tp == 1 && !a.peel);
+    return G.hub_tp == 2 || (G.hub_tp == 1 && !a.peel && !a.notab);
 }
 
 struct HArgs {

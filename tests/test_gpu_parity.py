@@ -219,6 +219,67 @@ def test_sync_zero_weight_edges(lpa, case):
     assert abs(g.modularity() - oracle.modularity(oracle_graph(csr), ref.labels)) < 1e-12
 
 
+def shuffled_rows(csr, seed):
+    """The same graph with every row's entries in a seeded random order: the rows no longer
+    increase, so a run's first sweep cannot take its labels as distinct from the layout."""
+    off = csr.offsets.numpy()
+    rng = np.random.default_rng(seed)
+    perm = np.arange(csr.indices.numel())
+    for i in range(csr.n):
+        perm[off[i]:off[i + 1]] = off[i] + rng.permutation(off[i + 1] - off[i])
+    p = torch.from_numpy(perm)
+    w = None if csr.weights is None else csr.weights[p]
+    return gg.CSRGraph(csr.offsets, csr.indices[p], w, "shuffled-rows")
+
+
+def repeated_entries(csr, seed, frac=0.2):
+    """A multigraph: a seeded fraction of the edges {i, j} (i < j) stored twice in both
+    directions, rows kept sorted: repeated neighbours whose weights Algorithm 1 sums."""
+    n = csr.n
+    u = torch.repeat_interleave(torch.arange(n), csr.degrees())
+    v = csr.indices.long()
+    w = torch.ones(v.numel()) if csr.weights is None else csr.weights
+    key = torch.minimum(u, v) * n + torch.maximum(u, v)
+    pick = (gg.draws53(seed, 12, key) % 1000) < int(frac * 1000)
+    pick &= u != v
+    uu, vv, ww = torch.cat([u, u[pick]]), torch.cat([v, v[pick]]), torch.cat([w, w[pick]])
+    order = torch.argsort(uu * n + vv, stable=True)
+    uu, vv, ww = uu[order], vv[order], ww[order]
+    off = torch.zeros(n + 1, dtype=torch.int64)
+    off[1:] = torch.cumsum(torch.bincount(uu, minlength=n), 0)
+    return gg.CSRGraph(off, vv.to(torch.int32), None if csr.weights is None else ww, "repeated-entries")
+
+
+@pytest.mark.parametrize("case", ["shuffled-rmat", "shuffled-small", "repeated-rmat", "repeated-small",
+                                  "repeated-random"])
+def test_sync_rows_not_increasing(lpa, case):
+    """A fresh run's first sweep skips the tables only when every row strictly increases (its
+    neighbour labels, the vertex ids, are then distinct; checked at creation).  Rows in any
+    order and repeated neighbours take the tables: equal to the oracle at every sweep, and the
+    shuffled graph's labels equal those of the same graph with sorted rows."""
+    if case == "shuffled-rmat":
+        base, tuning = gg.rmat(13, weights="int8"), None
+        csr = shuffled_rows(base, 5)
+    elif case == "shuffled-small":
+        base, tuning = gg.rmat(12, weights="unit"), SMALL_BUCKETS
+        csr = shuffled_rows(base, 6)
+    elif case == "repeated-rmat":
+        base, tuning = gg.rmat(13, weights="unit"), None
+        csr = repeated_entries(base, 7)
+    elif case == "repeated-small":
+        base, tuning = gg.rmat(12, weights="int8"), SMALL_BUCKETS
+        csr = repeated_entries(base, 8)
+    else:
+        base, tuning = gg.random_small(500, 0.05, 78, wmax=3, self_loops=True), PAPER_TABLES
+        csr = repeated_entries(base, 9, 0.5)
+    g, ref = check_sync_every_iteration(lpa, csr, 0.05, 20, 4, tuning)
+    assert abs(g.modularity() - oracle.modularity(oracle_graph(csr), ref.labels)) < 1e-12
+    if case.startswith("shuffled"):
+        g2 = make(lpa, base, True, tuning)
+        g2.run(0.05, 20, 4, lpa.SYNC)
+        assert g2.labels().cpu().numpy().tolist() == ref.labels.tolist()
+
+
 @pytest.mark.parametrize("seed", range(2))
 def test_sync_non_integer_weights_float64_values(lpa, seed):
     csr = dyadic(gg.rmat(12 + seed, weights="unit"), seed)
