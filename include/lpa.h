@@ -208,7 +208,9 @@ int lpa_labels(const lpa_graph *g, int32_t *out, int64_t n, int out_on_device);
 /* Modularity of the current labels, Eq. 1 in its community form
  * Q = sum_c [sigma_c / 2m - (Sigma_c / 2m)^2].  With integer weights (and weighted degrees
  * below 2^24) every sum is an exact integer on the device and Q = (2m sigma - sum Sigma_c^2)
- * / (2m)^2 is rounded once; otherwise the sums are accumulated in float64.
+ * / (2m)^2 is rounded once; otherwise the sums are accumulated in float64.  The graph is
+ * undirected with symmetric weights (lpa_create's precondition): sigma_c counts each edge
+ * {i, j} from its entry with j > i at twice its weight.
  * A graph with no edge weight (2m = 0) has Q = 0. */
 int lpa_modularity(const lpa_graph *g, double *q);
 
