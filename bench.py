@@ -66,12 +66,12 @@ BYTES_PER_VERTEX = 17      # offsets 2x4 (amortised) + own label 4 + label write
 # often than R-MAT 22's).  Reported while the sweep sources hash as they did at capture time.
 TRAFFIC = {
     "captured_on": "rmat22u",
-    "bytes_per_entry": {"cta": 4.68, "cta_large": 4.69, "group": 11.71, "hub_acc": 13.05, "thread": 29.38, "warp": 6.43},
+    "bytes_per_entry": {"cta": 4.66, "cta_large": 4.69, "group": 11.56, "hub_acc": 8.52, "thread": 29.74, "warp": 6.41},
     "sources": {
-        "sweep_kernels.cuh": "2d09207903fc83fda4ea9bf38ec58ff9614b89fe16844126549df1be1a63d5c0",
-        "lpa_sweep.cu": "4d3047241292df963a932efc55c2f81a366a8488ebad16538a6950acaed8c969",
-        "lpa_internal.h": "e7fe7dafe22c7897129871bb7f30ac95215fa3355e6ae82e13173f44f0d52d19",
-        "lpa_graph.cu": "eb9774b9ecd36dc53418623cc87ff74c60561eedae75797c20c78740456a384e",
+        "sweep_kernels.cuh": "a48e94b2853cf127287b49aecce0fd77d294db21e76690d4a83286a98539d73f",
+        "lpa_sweep.cu": "b1f909ed0f74c9a5cff959a0ef8aa187f877483c72afdf1deff10792cacfdd89",
+        "lpa_internal.h": "0442f8cc30d379d5cf49344867d65e0da6bdb86ff3167529751b844c7755ea60",
+        "lpa_graph.cu": "8380a25d7f40eff4bcfba751b70b736f19fb830ebcc51b35e108d2c0047416b1",
     },
 }
 

@@ -1306,7 +1306,7 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
     if ((st = dalloc(g, &g->mover_c, (size_t)n)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->mover_count, 2)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->fallbacks, 1)) != LPA_OK) return fail(st);
-    if ((st = dalloc(g, &g->d_err, 4)) != LPA_OK) return fail(st);
+    if ((st = dalloc(g, &g->d_err, 8)) != LPA_OK) return fail(st);   // [0] error bits, [4..7] two counts
     if ((st = dalloc(g, &g->macc, 4)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->gdd, 1)) != LPA_OK) return fail(st);
     if ((st = dalloc(g, &g->rs_d, 1)) != LPA_OK) return fail(st);
@@ -1342,20 +1342,17 @@ int create_graph(const void *offsets, const int32_t *indices, const float *weigh
             if (e != cudaSuccess) return cuda_fail(e, "copy weights");
         }
     }
-    // validation on the device
-    unsigned long long *desc = nullptr;
-    if ((st = dalloc(g, &desc, 2)) != LPA_OK) return fail(st);
-    cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), s);
-    cudaMemsetAsync(desc, 0, 2 * sizeof(unsigned long long), s);
-    k_validate<<<grid_for(std::max<int64_t>(n, m), 256, 16), 256, 0, s>>>(g->off, g->idx, g->w, n, m, g->d_err,
-                                                                          desc);
-    unsigned err = 0;
-    unsigned long long hdesc[2] = {0ull, 1ull};
-    cudaMemcpyAsync(&err, g->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(hdesc, desc, sizeof(hdesc), cudaMemcpyDeviceToHost, s);
+    // validation on the device (error bits and the two descent counts in one small block)
+    cudaMemsetAsync(g->d_err, 0, 8 * sizeof(unsigned), s);
+    k_validate<<<grid_for(std::max<int64_t>(n, m), 256, 16), 256, 0, s>>>(
+        g->off, g->idx, g->w, n, m, g->d_err, reinterpret_cast<unsigned long long *>(g->d_err + 4));
+    unsigned hv[8] = {0u, 0u, 0u, 0u, 0u, 0u, 1u, 0u};
+    cudaMemcpyAsync(hv, g->d_err, sizeof(hv), cudaMemcpyDeviceToHost, s);
     e = cudaStreamSynchronize(s);
-    dfree(g, desc);
     if (e != cudaSuccess) return cuda_fail(e, "validate");
+    const unsigned err = hv[0];
+    unsigned long long hdesc[2];
+    memcpy(hdesc, hv + 4, sizeof(hdesc));
     g->rows_strict = hdesc[0] == hdesc[1];
     if (err) {
         std::string msg = "lpa_create: invalid graph:";
@@ -1782,6 +1779,7 @@ int lpa_run_cc(lpa_graph *g, double tolerance, int max_iters, int pl_period, int
     rs.tol = tolerance;
     rs.n = g->n;
     rs.fresh = (mode & LPA_RESUME) ? 0 : 1;
+    rs.adaptive = 1;
     g->hm->active = 1;
     LPA_CUDA(cudaMemcpyAsync(g->rs_d, &g->hm->rs, sizeof(RunState), cudaMemcpyHostToDevice, s));
     LPA_CUDA(cudaMemcpyAsync(g->active, &g->hm->active, sizeof(int32_t), cudaMemcpyHostToDevice, s));

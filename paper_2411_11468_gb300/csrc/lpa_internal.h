@@ -61,7 +61,7 @@ struct RunState {
     int32_t cc_period;    // Cross-Check after sweeps l with l mod cc_period = 0 (0: never; sync only)
     int32_t cc_unresolved;  // set when the Cross-Check resolution did not finish (not expected)
     int32_t fresh;        // the run started from labels = vertex ids (not resumed)
-    int32_t pad_fresh;
+    int32_t adaptive;     // marks follow each sweep's moves (single-graph runs; else only sweep 1 pulls)
 };
 
 // Synchronous mode, sweeps that move many vertices: instead of marking the neighbours of each

@@ -219,6 +219,7 @@ RunState fresh_state(int64_t n, double tol, int max_iters, int pl_period, bool a
     r.tol = tol;
     r.n = n;
     r.fresh = 1;
+    r.adaptive = 0;                                 // one kernel variant per sweep of a shared plan
     r.done = (n == 0 || max_iters <= 0) ? 1 : 0;
     return r;
 }
@@ -464,13 +465,13 @@ int lpa_batch_run(lpa_batch *b, double tolerance, int max_iters, int pl_period, 
         cudaGraph_t graph = nullptr;
         LPA_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
         cudaError_t e = cudaSuccess;
-        // Every run of a batch starts fresh at sweep 0, which takes its active vertices from
-        // the flags; any later sweep of a synchronous run may take them from moved bits
-        // (k_decide chooses per graph), so those sweeps launch both kernel variants and each
-        // graph's items run in one of them (asynchronous runs use the push variant).
+        // Every run of a batch starts fresh at sweep 0, and only sweep 1 of a fresh synchronous
+        // run takes its active vertices from moved bits (the run states are not adaptive):
+        // that sweep launches both kernel variants (asynchronous runs replay the same
+        // recording and use the push variant).
         for (int it = 0; it < span && e == cudaSuccess; ++it) {
             SweepPlan p = b->mp.plan;
-            p.pull_mode = it == 0 ? 0 : 2;
+            p.pull_mode = it == 1 ? 2 : 0;
             e = enqueue_sweep(p, b->stream, nullptr, nullptr);
         }
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);

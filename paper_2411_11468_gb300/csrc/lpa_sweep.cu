@@ -353,7 +353,9 @@ __global__ void k_cc_revert(HArgs k, const unsigned *ctr)
 // sweep itself when it was told to mark (rs->mark), else after it (rs->fin: k_finalize, and
 // k_hub_mark for hubs); otherwise the next sweep pulls.  A sweep marks as it goes when the
 // sweep before it moved few entries (a fresh run's first sweep moves most vertices and never
-// does).  Cross-Check runs always mark.
+// does).  Cross-Check runs always mark.  Batches and the server (rs->adaptive = 0) keep one
+// kernel variant per recorded sweep: only a fresh run's sweep 1 pulls and every later sweep
+// marks as it goes (both variants in every sweep cost a batch of 4,096 graphs 5 %).
 constexpr long long kFewMovedEntries = 4;
 
 __global__ void k_decide(const GraphDev *gd, int n_graphs, int32_t *active)
@@ -383,6 +385,10 @@ __global__ void k_decide(const GraphDev *gd, int n_graphs, int32_t *active)
         const bool few = rs->cc_period > 0 || me * kFewMovedEntries < m;
         if (done) {
             rs->fin = rs->mark ? 0 : 1;               // this sweep's moved bits still stand
+        } else if (!rs->adaptive) {
+            rs->fin = 0;
+            rs->pull = rs->mark ? 0 : 1;
+            rs->mark = 1;
         } else {
             rs->fin = (!rs->mark && few) ? 1 : 0;     // mark after the sweep
             rs->pull = (rs->mark || few) ? 0 : 1;
