@@ -66,9 +66,9 @@ BYTES_PER_VERTEX = 17      # offsets 2x4 (amortised) + own label 4 + label write
 # often than R-MAT 22's).  Reported while the sweep sources hash as they did at capture time.
 TRAFFIC = {
     "captured_on": "rmat22u",
-    "bytes_per_entry": {"cta": 4.66, "cta_large": 4.69, "group": 11.56, "hub_acc": 8.52, "thread": 29.74, "warp": 6.41},
+    "bytes_per_entry": {"cta": 4.66, "cta_large": 4.7, "group": 11.56, "hub_acc": 8.53, "thread": 29.78, "warp": 6.41},
     "sources": {
-        "sweep_kernels.cuh": "a48e94b2853cf127287b49aecce0fd77d294db21e76690d4a83286a98539d73f",
+        "sweep_kernels.cuh": "01c8c54c550a37545072c04afdea60ee675cdc1a5d0ea5dace66c75d9e61f914",
         "lpa_sweep.cu": "b1f909ed0f74c9a5cff959a0ef8aa187f877483c72afdf1deff10792cacfdd89",
         "lpa_internal.h": "0442f8cc30d379d5cf49344867d65e0da6bdb86ff3167529751b844c7755ea60",
         "lpa_graph.cu": "8380a25d7f40eff4bcfba751b70b736f19fb830ebcc51b35e108d2c0047416b1",

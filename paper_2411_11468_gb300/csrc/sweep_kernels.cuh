@@ -574,8 +574,10 @@ __device__ __forceinline__ SweepView view_of(const GraphDev *gd, int g)
     v.pull = rs->pull;
     v.probe = G.probe;
     // The first sweep of a run from fresh labels (label = vertex id) finds every neighbour label
-    // distinct in a duplicate-free row, so the duplicate-label rounds would find nothing there.
-    v.peel = l > 0;
+    // distinct in a duplicate-free row, so the duplicate-label rounds would find nothing there;
+    // not so in an asynchronous sweep, whose labels change as it goes (by the time the hubs run,
+    // most of their neighbours have moved to a few shared labels).
+    v.peel = l > 0 || rs->async_mode;
     // Synchronous sweep 0 of a fresh run on rows whose indices strictly increase: every
     // neighbour label of a row is a distinct vertex id, so K_{i->c} is the weight of the one
     // entry holding c, and the arg-max of Algorithm 1 is the maximum over the entries of
